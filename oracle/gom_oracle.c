@@ -1,0 +1,645 @@
+/*
+ * gom_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU statement of parallel Gene-pool Optimal
+ * Mixing (GOM) for weighted Max-Cut, written from Bouter & Bosman, "GPU-Accelerated
+ * Parallel Gene-pool Optimal Mixing in a Gray-Box Optimization Setting"
+ * (arXiv 2203.08680).  It is the checker of the CUDA library, not part of it:
+ * only the test suite, the smoke check and the benchmark's CPU-baseline arm may
+ * load it.  It shares no code, header, table or helper with the CUDA path.
+ *
+ * Everything is integer (int32 weights, int64 fitness), so every result is
+ * exact and must be matched bit for bit.
+ *
+ * Population storage is the plainest possible: uint8 x[i*n + v] in {0,1}.
+ *
+ * Readings of the paper taken here (the paper is silent or ambiguous):
+ *  R1 objective: f(x) = sum over undirected edges {u,v} of w_uv [x_u != x_v];
+ *     this is the Max-Cut formula of Sec. 6.2 with x in {-1,1} mapped from {0,1}.
+ *  R2 FOS: neighbourhood F_j = {j} u adj(j) (sorted), or singleton F_j = {j}.
+ *  R3 LMIG (Sec. 5.2): F_i ~ F_j iff they intersect or a VIG edge joins them.
+ *  R4 Welsh-Powell (Sec. 5.2): visit elements by LMIG degree descending, ties
+ *     by ascending index; give each the smallest colour unused by its
+ *     already-coloured neighbours.  Groups list their elements ascending.
+ *  R5 group order (Alg. 3, "random order"): colours sorted ascending by a
+ *     64-bit Philox key per (colour, generation), ties by colour index.
+ *  R6 donor (Sec. 4, SelectDonorFromPopulation): a uniform random start in the
+ *     other p-1 individuals of the generation-start population P, then a
+ *     cyclic scan to the first whose bits on F_j differ from the parent's
+ *     current bits; no such individual means the trial is skipped.
+ *  R7 partial evaluation (Sec. 2.2, Alg. 4): delta = sum over the set union of
+ *     edges incident to F_j (each edge once) of new minus old contribution.
+ *  R8 acceptance (Alg. 2, Sec. 5.3): accept iff delta > 0, or delta == 0 and
+ *     the individual's generation-start genotype P[i] differs from the elitist.
+ *  R9 elitist: after each generation, if max f > f_e the elitist becomes the
+ *     lowest-index individual attaining max f.
+ *  R10 random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ *     (seed low, seed high), counters as in the functions below.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAG_INIT 0x494E4954u  /* 'INIT' */
+#define ORC_TAG_DONOR 0x444F4E52u /* 'DONR' */
+#define ORC_TAG_ORDER 0x4F524452u /* 'ORDR' */
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from its published definition (SC'11, Sec. 4 and Table 2). */
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t c, uint32_t tag, int word)
+{
+    uint32_t ctr[4] = {a, b, c, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* floor(r * n / 2^32): maps a uniform 32-bit word onto [0, n). */
+static uint32_t bounded(uint32_t r, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)r * (uint64_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The graph (the Max-Cut instance, which is also the VIG, Sec. 2.3). */
+
+/* 0 if the CSR is a simple undirected graph: rows sorted strictly ascending,
+ * no self-loops, every (u,v,w) mirrored by (v,u,w).  -1 otherwise. */
+int orc_check_graph(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w)
+{
+    if (n < 0 || rp[0] != 0) return -1;
+    for (int32_t u = 0; u < n; ++u) {
+        if (rp[u + 1] < rp[u]) return -1;
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            int32_t v = col[e];
+            if (v < 0 || v >= n || v == u) return -1;
+            if (e > rp[u] && col[e - 1] >= v) return -1;
+            /* find the mirror entry by a plain linear search */
+            int found = 0;
+            for (int64_t q = rp[v]; q < rp[v + 1]; ++q)
+                if (col[q] == u) { found = (w[q] == w[e]); break; }
+            if (!found) return -1;
+        }
+    }
+    return 0;
+}
+
+/* R1: the cut weight of one assignment x[0..n). */
+int64_t orc_cut_value(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                      const uint8_t *x)
+{
+    int64_t f = 0;
+    for (int32_t u = 0; u < n; ++u)
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            int32_t v = col[e];
+            if (u < v && x[u] != x[v]) f += w[e];
+        }
+    return f;
+}
+
+/* Exhaustive maximum cut for n <= 26, fixing x_0 = 0 (a cut and its
+ * complement have equal weight); each assignment evaluated from scratch. */
+int64_t orc_brute_force_maxcut(int32_t n, const int64_t *rp, const int32_t *col,
+                               const int32_t *w, uint8_t *best_x)
+{
+    if (n <= 0) return 0;
+    if (n > 26) return -1;
+    uint8_t *x = (uint8_t *)calloc((size_t)n, 1);
+    int64_t best = INT64_MIN;
+    uint64_t total = 1ull << (n - 1);
+    for (uint64_t code = 0; code < total; ++code) {
+        for (int32_t v = 1; v < n; ++v) x[v] = (uint8_t)((code >> (v - 1)) & 1u);
+        x[0] = 0;
+        int64_t f = orc_cut_value(n, rp, col, w, x);
+        if (f > best) {
+            best = f;
+            if (best_x) memcpy(best_x, x, (size_t)n);
+        }
+    }
+    free(x);
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FOS (Sec. 4.1), R2.  kind 0 = neighbourhood, 1 = singleton. */
+
+int64_t orc_fos_total(int32_t n, const int64_t *rp, int32_t kind)
+{
+    if (kind == 1) return n;
+    return rp[n] + n;
+}
+
+void orc_build_fos(int32_t n, const int64_t *rp, const int32_t *col, int32_t kind,
+                   int64_t *eptr, int32_t *evars)
+{
+    int64_t pos = 0;
+    for (int32_t j = 0; j < n; ++j) {
+        eptr[j] = pos;
+        if (kind == 1) {
+            evars[pos++] = j;
+            continue;
+        }
+        /* merge j into its (sorted) neighbour list */
+        int placed = 0;
+        for (int64_t e = rp[j]; e < rp[j + 1]; ++e) {
+            if (!placed && j < col[e]) { evars[pos++] = j; placed = 1; }
+            evars[pos++] = col[e];
+        }
+        if (!placed) evars[pos++] = j;
+    }
+    eptr[n] = pos;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LMIG (Sec. 5.2), R3, and its Welsh-Powell colouring, R4. */
+
+typedef struct {
+    int64_t m;
+    int64_t *nptr;   /* [m+1] */
+    int32_t *nbr;    /* LMIG neighbours of each element, ascending */
+} lmig_t;
+
+/* The elements containing each variable (an inverted index of the FOS). */
+static void invert_fos(int32_t n, int64_t m, const int64_t *eptr, const int32_t *evars,
+                       int64_t **vptr_out, int32_t **velems_out)
+{
+    int64_t *vptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t q = 0; q < eptr[m]; ++q) vptr[evars[q] + 1]++;
+    for (int32_t v = 0; v < n; ++v) vptr[v + 1] += vptr[v];
+    int32_t *velems = (int32_t *)malloc(sizeof(int32_t) * (size_t)(eptr[m] > 0 ? eptr[m] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    memcpy(fill, vptr, sizeof(int64_t) * ((size_t)n + 1));
+    for (int64_t j = 0; j < m; ++j)
+        for (int64_t q = eptr[j]; q < eptr[j + 1]; ++q) velems[fill[evars[q]]++] = (int32_t)j;
+    free(fill);
+    *vptr_out = vptr;
+    *velems_out = velems;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* F_j' is an LMIG neighbour of F_j iff F_j' shares a variable with
+ * F_j u adj(F_j): that covers both the intersection and the edge case of R3. */
+static lmig_t build_lmig(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
+                         const int64_t *eptr, const int32_t *evars)
+{
+    int64_t *vptr;
+    int32_t *velems;
+    invert_fos(n, m, eptr, evars, &vptr, &velems);
+    int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) seen[j] = -1;
+    int64_t cap = 1024, cnt = 0;
+    int32_t *nbr = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    int64_t *nptr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+    for (int64_t j = 0; j < m; ++j) {
+        nptr[j] = cnt;
+        for (int64_t q = eptr[j]; q < eptr[j + 1]; ++q) {
+            int32_t u = evars[q];
+            /* u itself, then every VIG neighbour of u */
+            for (int64_t e = rp[u] - 1; e < rp[u + 1]; ++e) {
+                int32_t v = (e < rp[u]) ? u : col[e];
+                for (int64_t r = vptr[v]; r < vptr[v + 1]; ++r) {
+                    int32_t jj = velems[r];
+                    if (jj == j || seen[jj] == j) continue;
+                    seen[jj] = j;
+                    if (cnt == cap) {
+                        cap *= 2;
+                        nbr = (int32_t *)realloc(nbr, sizeof(int32_t) * (size_t)cap);
+                    }
+                    nbr[cnt++] = jj;
+                }
+            }
+        }
+        qsort(nbr + nptr[j], (size_t)(cnt - nptr[j]), sizeof(int32_t), cmp_i32);
+    }
+    nptr[m] = cnt;
+    free(seen);
+    free(vptr);
+    free(velems);
+    lmig_t L = {m, nptr, nbr};
+    return L;
+}
+
+static void free_lmig(lmig_t *L)
+{
+    free(L->nptr);
+    free(L->nbr);
+}
+
+/* Number of LMIG edges; writes up to cap (a<b) pairs into out_pairs. */
+int64_t orc_lmig_edges(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
+                       const int64_t *eptr, const int32_t *evars, int32_t *out_pairs, int64_t cap)
+{
+    lmig_t L = build_lmig(n, rp, col, m, eptr, evars);
+    int64_t cnt = 0;
+    for (int64_t a = 0; a < m; ++a)
+        for (int64_t q = L.nptr[a]; q < L.nptr[a + 1]; ++q) {
+            int32_t b = L.nbr[q];
+            if (a < b) {
+                if (cnt < cap) {
+                    out_pairs[2 * cnt] = (int32_t)a;
+                    out_pairs[2 * cnt + 1] = b;
+                }
+                ++cnt;
+            }
+        }
+    free_lmig(&L);
+    return cnt;
+}
+
+static const int64_t *g_sort_deg;
+static int cmp_wp(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    if (g_sort_deg[x] != g_sort_deg[y]) return g_sort_deg[x] > g_sort_deg[y] ? -1 : 1;
+    return (x > y) - (x < y);
+}
+
+/* R4.  Returns the number of colours k; color_of_elem[j] in [0,k). */
+int32_t orc_color(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
+                  const int64_t *eptr, const int32_t *evars, int32_t *color_of_elem)
+{
+    lmig_t L = build_lmig(n, rp, col, m, eptr, evars);
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) {
+        deg[j] = L.nptr[j + 1] - L.nptr[j];
+        order[j] = (int32_t)j;
+        color_of_elem[j] = -1;
+    }
+    g_sort_deg = deg;
+    qsort(order, (size_t)m, sizeof(int32_t), cmp_wp);
+    int32_t k = 0;
+    int64_t *used = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    for (int64_t c = 0; c <= m; ++c) used[c] = -1;
+    for (int64_t t = 0; t < m; ++t) {
+        int32_t j = order[t];
+        for (int64_t q = L.nptr[j]; q < L.nptr[j + 1]; ++q) {
+            int32_t c = color_of_elem[L.nbr[q]];
+            if (c >= 0) used[c] = j;
+        }
+        int32_t c = 0;
+        while (used[c] == j) ++c;
+        color_of_elem[j] = c;
+        if (c + 1 > k) k = c + 1;
+    }
+    free(used);
+    free(order);
+    free(deg);
+    free_lmig(&L);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Partial evaluation (Sec. 2.2 and Alg. 4), R7. */
+
+/* in_f[v] == stamp marks the variables of F.  x is the parent; y_on_f[q] is
+ * the new value of F[q].  Returns new minus old over the union of the edges
+ * incident to F, each edge counted once. */
+static int64_t partial_delta(const int64_t *rp, const int32_t *col, const int32_t *w,
+                             const uint8_t *x, const int32_t *F, int32_t sz, const uint8_t *y_on_f,
+                             const int32_t *pos_in_f, const int64_t *in_f, int64_t stamp)
+{
+    int64_t d = 0;
+    for (int32_t q = 0; q < sz; ++q) {
+        int32_t u = F[q];
+        uint8_t xu = x[u], yu = y_on_f[q];
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            int32_t v = col[e];
+            uint8_t xv = x[v], yv = x[v];
+            if (in_f[v] == stamp) {
+                if (v < u) continue; /* counted from v's side */
+                yv = y_on_f[pos_in_f[v]];
+            }
+            int64_t cut_new = (yu != yv), cut_old = (xu != xv);
+            d += (int64_t)w[e] * (cut_new - cut_old);
+        }
+    }
+    return d;
+}
+
+/* Exposed for the pins: delta of setting x on F[0..sz) to y_on_f. */
+int64_t orc_partial_delta(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                          const uint8_t *x, const int32_t *F, int32_t sz, const uint8_t *y_on_f)
+{
+    int64_t *in_f = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t v = 0; v < n; ++v) in_f[v] = -1;
+    for (int32_t q = 0; q < sz; ++q) { in_f[F[q]] = 1; pos[F[q]] = q; }
+    int64_t d = partial_delta(rp, col, w, x, F, sz, y_on_f, pos, in_f, 1);
+    free(in_f);
+    free(pos);
+    return d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parallel GOMEA state (Alg. 3). */
+
+typedef struct {
+    int64_t generation;   /* index of the generation these counters describe */
+    int64_t best;         /* max_i f[i] after the generation */
+    int64_t elite;        /* f_e after the generation */
+    int64_t trials;       /* (individual, element) pairs, donor-less included */
+    int64_t donorless;
+    int64_t accepted;
+    int64_t improving;
+    int64_t reached;      /* 1 if best >= target */
+} orc_stats;
+
+typedef struct {
+    int32_t n;
+    int64_t *rp;
+    int32_t *col, *w;
+    int64_t m;
+    int64_t *eptr;
+    int32_t *evars;
+    int32_t k;
+    int64_t *cptr;   /* colour -> elements, ascending */
+    int32_t *celems;
+    int32_t p;
+    uint64_t seed;
+    uint8_t *O, *P;  /* [p][n] */
+    int64_t *f;
+    uint8_t *xe;
+    int64_t fe;
+    uint32_t g;
+    /* scratch */
+    int64_t *in_f;
+    int32_t *pos_in_f;
+    int64_t stamp;
+    uint8_t *eq;
+    uint8_t *ybuf; /* [max element size] */
+} orc_state;
+
+static void *dup_mem(const void *src, size_t bytes)
+{
+    void *d = malloc(bytes ? bytes : 1);
+    if (bytes) memcpy(d, src, bytes);
+    return d;
+}
+
+static void elitist_from_scratch(orc_state *s)
+{
+    int64_t best = INT64_MIN;
+    int32_t arg = 0;
+    for (int32_t i = 0; i < s->p; ++i)
+        if (s->f[i] > best) { best = s->f[i]; arg = i; }
+    memcpy(s->xe, s->O + (size_t)arg * s->n, (size_t)s->n);
+    s->fe = best;
+}
+
+/* InitializePopulation (Alg. 3): bit v of individual i is bit (v mod 32) of
+ * word (v/32 mod 4) of Philox(ctr = (v/128, i, 0, TAG_INIT)). */
+orc_state *orc_new(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                   int64_t m, const int64_t *eptr, const int32_t *evars,
+                   const int32_t *color_of_elem, int32_t k, int32_t p, uint64_t seed)
+{
+    orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
+    s->n = n;
+    s->rp = (int64_t *)dup_mem(rp, sizeof(int64_t) * ((size_t)n + 1));
+    s->col = (int32_t *)dup_mem(col, sizeof(int32_t) * (size_t)rp[n]);
+    s->w = (int32_t *)dup_mem(w, sizeof(int32_t) * (size_t)rp[n]);
+    s->m = m;
+    s->eptr = (int64_t *)dup_mem(eptr, sizeof(int64_t) * ((size_t)m + 1));
+    s->evars = (int32_t *)dup_mem(evars, sizeof(int32_t) * (size_t)eptr[m]);
+    s->k = k;
+    s->cptr = (int64_t *)calloc((size_t)k + 1, sizeof(int64_t));
+    s->celems = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) s->cptr[color_of_elem[j] + 1]++;
+    for (int32_t c = 0; c < k; ++c) s->cptr[c + 1] += s->cptr[c];
+    {
+        int64_t *fill = (int64_t *)dup_mem(s->cptr, sizeof(int64_t) * ((size_t)k + 1));
+        for (int64_t j = 0; j < m; ++j) s->celems[fill[color_of_elem[j]]++] = (int32_t)j;
+        free(fill);
+    }
+    s->p = p;
+    s->seed = seed;
+    s->O = (uint8_t *)malloc((size_t)p * (size_t)n + 1);
+    s->P = (uint8_t *)malloc((size_t)p * (size_t)n + 1);
+    s->f = (int64_t *)malloc(sizeof(int64_t) * (size_t)p);
+    s->xe = (uint8_t *)malloc((size_t)n + 1);
+    s->in_f = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    s->pos_in_f = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t v = 0; v < n; ++v) s->in_f[v] = -1;
+    s->stamp = 0;
+    s->eq = (uint8_t *)malloc((size_t)p);
+    {
+        int64_t mx = 1;
+        for (int64_t j = 0; j < m; ++j)
+            if (eptr[j + 1] - eptr[j] > mx) mx = eptr[j + 1] - eptr[j];
+        s->ybuf = (uint8_t *)malloc((size_t)mx);
+    }
+    for (int32_t i = 0; i < p; ++i)
+        for (int32_t v = 0; v < n; ++v) {
+            uint32_t r = draw(seed, (uint32_t)v >> 7, (uint32_t)i, 0u, ORC_TAG_INIT, (v >> 5) & 3);
+            s->O[(size_t)i * n + v] = (uint8_t)((r >> (v & 31)) & 1u);
+        }
+    for (int32_t i = 0; i < p; ++i) s->f[i] = orc_cut_value(n, rp, col, w, s->O + (size_t)i * n);
+    elitist_from_scratch(s);
+    s->g = 0;
+    return s;
+}
+
+void orc_free(orc_state *s)
+{
+    if (!s) return;
+    free(s->rp); free(s->col); free(s->w); free(s->eptr); free(s->evars);
+    free(s->cptr); free(s->celems); free(s->O); free(s->P); free(s->f); free(s->xe);
+    free(s->in_f); free(s->pos_in_f); free(s->eq); free(s->ybuf);
+    free(s);
+}
+
+/* Overwrite the state (used to resume from, or replay, a given point). */
+void orc_load(orc_state *s, const uint8_t *pop, const int64_t *f, const uint8_t *xe, int64_t fe,
+              uint32_t g)
+{
+    memcpy(s->O, pop, (size_t)s->p * s->n);
+    memcpy(s->f, f, sizeof(int64_t) * (size_t)s->p);
+    memcpy(s->xe, xe, (size_t)s->n);
+    s->fe = fe;
+    s->g = g;
+}
+
+void orc_get(const orc_state *s, uint8_t *pop, int64_t *f, uint8_t *xe, int64_t *fe, uint32_t *g)
+{
+    if (pop) memcpy(pop, s->O, (size_t)s->p * s->n);
+    if (f) memcpy(f, s->f, sizeof(int64_t) * (size_t)s->p);
+    if (xe) memcpy(xe, s->xe, (size_t)s->n);
+    if (fe) *fe = s->fe;
+    if (g) *g = s->g;
+}
+
+/* R5: the order of the colour groups in generation g. */
+static uint64_t order_key(uint64_t seed, int32_t c, uint32_t g)
+{
+    uint32_t ctr[4] = {(uint32_t)c, 0u, g, ORC_TAG_ORDER};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return ((uint64_t)out[0] << 32) | out[1];
+}
+
+void orc_group_order(uint64_t seed, int32_t k, uint32_t g, int32_t *order)
+{
+    /* selection of the smallest remaining (key, colour) pair, k times */
+    uint8_t *taken = (uint8_t *)calloc((size_t)k + 1, 1);
+    for (int32_t t = 0; t < k; ++t) {
+        int32_t best = -1;
+        uint64_t bk = 0;
+        for (int32_t c = 0; c < k; ++c) {
+            if (taken[c]) continue;
+            uint64_t key = order_key(seed, c, g);
+            if (best < 0 || key < bk) { best = c; bk = key; }
+        }
+        taken[best] = 1;
+        order[t] = best;
+    }
+    free(taken);
+}
+
+/* One GOM trial (Alg. 2) of individual i with element j. */
+static void gom_trial(orc_state *s, int32_t i, int32_t j, orc_stats *st)
+{
+    const int32_t n = s->n, p = s->p;
+    const int32_t *F = s->evars + s->eptr[j];
+    const int32_t sz = (int32_t)(s->eptr[j + 1] - s->eptr[j]);
+    uint8_t *o = s->O + (size_t)i * n;
+
+    /* SelectDonorFromPopulation, R6 */
+    uint32_t r = draw(s->seed, (uint32_t)j, (uint32_t)i >> 2, s->g, ORC_TAG_DONOR, i & 3);
+    uint32_t u = bounded(r, (uint32_t)(p - 1));
+    int32_t donor = -1;
+    for (int32_t t = 0; t <= p - 2 && donor < 0; ++t) {
+        int32_t d = (int32_t)((i + 1 + (int64_t)((u + (uint32_t)t) % (uint32_t)(p - 1))) % p);
+        const uint8_t *pd = s->P + (size_t)d * n;
+        for (int32_t q = 0; q < sz; ++q)
+            if (pd[F[q]] != o[F[q]]) { donor = d; break; }
+    }
+    st->trials++;
+    if (donor < 0) { st->donorless++; return; }
+
+    /* PartialEvaluation, R7 */
+    const uint8_t *pd = s->P + (size_t)donor * n;
+    uint8_t *y = s->ybuf;
+    s->stamp++;
+    for (int32_t q = 0; q < sz; ++q) {
+        y[q] = pd[F[q]];
+        s->in_f[F[q]] = s->stamp;
+        s->pos_in_f[F[q]] = q;
+    }
+    int64_t d = partial_delta(s->rp, s->col, s->w, o, F, sz, y, s->pos_in_f, s->in_f, s->stamp);
+
+    /* acceptance, R8 */
+    if (d > 0 || (d == 0 && !s->eq[i])) {
+        for (int32_t q = 0; q < sz; ++q) o[F[q]] = y[q];
+        s->f[i] += d;
+        st->accepted++;
+        if (d > 0) st->improving++;
+    }
+}
+
+/* Small deterministic generator used only to permute the trials of one group
+ * in the order-invariance test (it is not one of the method's random draws). */
+static uint64_t splitmix_next(uint64_t *x)
+{
+    uint64_t z = (*x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* One generation of Par-GOMEA (Alg. 3).  `shuffle` != 0 visits the trials of
+ * each group in a permuted order; `only`/`n_only` restricts the trials to a
+ * subset of individuals (the elitist update is then skipped, since it needs the
+ * whole population).  A run stops once a generation ends with max f >= target;
+ * that stop is the caller's loop, st->reached reports it. */
+int32_t orc_generation_ex(orc_state *s, int64_t target, uint64_t shuffle, const int32_t *only,
+                          int32_t n_only, orc_stats *st)
+{
+    memset(st, 0, sizeof(*st));
+    const int32_t n = s->n, p = s->p;
+    /* Clone: P <- O */
+    memcpy(s->P, s->O, (size_t)p * n);
+    /* R8: the elitist flag of each individual is fixed at generation start */
+    for (int32_t i = 0; i < p; ++i) s->eq[i] = memcmp(s->P + (size_t)i * n, s->xe, (size_t)n) == 0;
+
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->k > 0 ? s->k : 1));
+    orc_group_order(s->seed, s->k, s->g, order);
+
+    int32_t n_ind = only ? n_only : p;
+    for (int32_t t = 0; t < s->k; ++t) {
+        int32_t c = order[t];
+        int64_t gsz = s->cptr[c + 1] - s->cptr[c];
+        int64_t ntr = gsz * n_ind;
+        int64_t *perm = NULL;
+        uint64_t sm = shuffle;
+        if (shuffle) {
+            perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ntr > 0 ? ntr : 1));
+            for (int64_t q = 0; q < ntr; ++q) perm[q] = q;
+            for (int64_t q = ntr - 1; q > 0; --q) {
+                int64_t r = (int64_t)(splitmix_next(&sm) % (uint64_t)(q + 1));
+                int64_t tmp = perm[q]; perm[q] = perm[r]; perm[r] = tmp;
+            }
+        }
+        for (int64_t q = 0; q < ntr; ++q) {
+            int64_t id = perm ? perm[q] : q;
+            int32_t j = s->celems[s->cptr[c] + id / n_ind];
+            int32_t ii = (int32_t)(id % n_ind);
+            int32_t i = only ? only[ii] : ii;
+            gom_trial(s, i, j, st);
+        }
+        free(perm);
+    }
+    free(order);
+
+    st->generation = s->g;
+    if (!only) {
+        /* R9: elitist update at the end of the generation */
+        int64_t best = INT64_MIN;
+        int32_t arg = 0;
+        for (int32_t i = 0; i < p; ++i)
+            if (s->f[i] > best) { best = s->f[i]; arg = i; }
+        if (best > s->fe) {
+            s->fe = best;
+            memcpy(s->xe, s->O + (size_t)arg * n, (size_t)n);
+        }
+        st->best = best;
+        st->elite = s->fe;
+        st->reached = best >= target;
+    }
+    s->g++;
+    return 0;
+}
+
+int32_t orc_generation(orc_state *s, int64_t target, orc_stats *st)
+{
+    return orc_generation_ex(s, target, 0, NULL, 0, st);
+}

@@ -1,0 +1,438 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each checks a published value
+(Philox known answers, the paper's worked LMIG example), a closed form (maximum
+cuts of bipartite tori and complete graphs), brute force on tiny inputs, or an
+invariant that a dropped term, a wrong sign or a wrong index would break.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from paper_2203_08680_gb300 import instances as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------------------
+# Philox4x32-10 (the method's random numbers; Salmon et al., SC'11)
+
+def test_philox_known_answers(oracle):
+    for row in _read_golden("philox4x32_10_kat.txt"):
+        vals = [int(v, 16) for v in row]
+        out = oracle.philox(vals[0:4], vals[4:6])
+        assert [int(x) for x in out] == vals[6:10]
+
+
+def test_philox_bit_balance(oracle):
+    ones = 0
+    n = 4000
+    for c in range(n):
+        out = oracle.philox((c, 7, 0, 0x494E4954), (1, 0))
+        ones += sum(bin(int(x)).count("1") for x in out)
+    bits = n * 128
+    # binomial(bits, 1/2): 6 standard deviations
+    assert abs(ones - bits / 2) < 6 * np.sqrt(bits / 4)
+
+
+# ----------------------------------------------------------------------------
+# The Max-Cut objective (Sec. 6.2)
+
+def _paper_formula(g, x01):
+    """1/2 sum_{i<j} w_ij (1 - x_i x_j) with x in {-1, 1}, over a dense matrix."""
+    W = np.zeros((g.n, g.n), dtype=np.int64)
+    u = np.repeat(np.arange(g.n), g.degrees())
+    W[u, g.col] = g.weight
+    x = 2 * np.asarray(x01, dtype=np.int64) - 1
+    iu = np.triu_indices(g.n, 1)
+    return int((W[iu] * (1 - np.outer(x, x)[iu])).sum()) // 2
+
+
+@pytest.mark.parametrize("gname", ["torus4", "rreg", "torus3d3"])
+def test_objective_matches_paper_formula(oracle, gname):
+    g = {"torus4": I.torus2d(4, seed=3), "rreg": I.random_regular(30, 5, seed=2),
+         "torus3d3": I.torus3d(3, seed=4)}[gname]
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        x = rng.integers(0, 2, g.n).astype(np.uint8)
+        assert oracle.cut_value(g, x) == _paper_formula(g, x)
+
+
+def test_negative_weights_objective(oracle):
+    g = I.random_regular(20, 4, seed=5, wmin=-50, wmax=50)
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        x = rng.integers(0, 2, g.n).astype(np.uint8)
+        assert oracle.cut_value(g, x) == _paper_formula(g, x)
+
+
+def test_even_torus_optimum_is_total_weight(oracle):
+    # An even torus is bipartite: the checkerboard cuts every edge.
+    for L, unit in [(4, False), (4, True)]:
+        g = I.torus2d(L, seed=9, unit=unit)
+        best, x = oracle.brute_force_maxcut(g)
+        assert best == g.total_weight()
+        if unit:
+            assert best == 2 * L * L
+        cb = np.array([(v % L + v // L) % 2 for v in range(g.n)], dtype=np.uint8)
+        assert oracle.cut_value(g, cb) == g.total_weight()
+    g3 = I.torus3d(4, seed=2, unit=True)
+    cb = np.array([((v % 4) + (v // 4) % 4 + v // 16) % 2 for v in range(g3.n)], dtype=np.uint8)
+    assert oracle.cut_value(g3, cb) == 3 * 4 ** 3 == g3.total_weight()
+
+
+def test_odd_torus_and_complete_graph_closed_forms(oracle):
+    # 3x3 unit torus: 6 odd 3-cycles, each cut at most twice -> 12, attained.
+    g = I.torus2d(3, unit=True)
+    assert oracle.brute_force_maxcut(g)[0] == 12
+    # K_n with unit weights: floor(n/2) * ceil(n/2).
+    for n in (5, 7, 8):
+        u, v = zip(*itertools.combinations(range(n), 2))
+        Kn = I.from_edges(n, u, v, np.ones(len(u), dtype=np.int32))
+        assert oracle.brute_force_maxcut(Kn)[0] == (n // 2) * ((n + 1) // 2)
+
+
+def test_brute_force_dominates_random_assignments(oracle):
+    g = I.random_regular(16, 3, seed=11)
+    best, bx = oracle.brute_force_maxcut(g)
+    assert oracle.cut_value(g, bx) == best
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        assert oracle.cut_value(g, rng.integers(0, 2, g.n).astype(np.uint8)) <= best
+
+
+# ----------------------------------------------------------------------------
+# Partial evaluation (Sec. 2.2, Alg. 4)
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_partial_delta_equals_full_difference(oracle, kind):
+    g = I.random_regular(40, 6, seed=3, wmin=-20, wmax=100)
+    eptr, evars = oracle.build_fos(g, kind)
+    rng = np.random.default_rng(kind)
+    for _ in range(300):
+        j = int(rng.integers(0, g.n))
+        F = evars[eptr[j]:eptr[j + 1]]
+        x = rng.integers(0, 2, g.n).astype(np.uint8)
+        y = rng.integers(0, 2, len(F)).astype(np.uint8)
+        x2 = x.copy()
+        x2[F] = y
+        assert oracle.partial_delta(g, x, F, y) == oracle.cut_value(g, x2) - oracle.cut_value(g, x)
+
+
+def test_partial_delta_random_subsets(oracle):
+    g = I.torus2d(6, seed=8)
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        sz = int(rng.integers(1, 12))
+        F = np.sort(rng.choice(g.n, sz, replace=False)).astype(np.int32)
+        x = rng.integers(0, 2, g.n).astype(np.uint8)
+        y = rng.integers(0, 2, sz).astype(np.uint8)
+        x2 = x.copy()
+        x2[F] = y
+        assert oracle.partial_delta(g, x, F, y) == oracle.cut_value(g, x2) - oracle.cut_value(g, x)
+
+
+def test_singleton_delta_is_one_flip_gain(oracle):
+    g = I.random_regular(30, 4, seed=6)
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 2, g.n).astype(np.uint8)
+    for u in range(g.n):
+        nb = g.col[g.row_ptr[u]:g.row_ptr[u + 1]]
+        wt = g.weight[g.row_ptr[u]:g.row_ptr[u + 1]].astype(np.int64)
+        # flipping u: uncut edges become cut (+w), cut edges become uncut (-w)
+        gain = int((wt * np.where(x[nb] == x[u], 1, -1)).sum())
+        assert oracle.partial_delta(g, x, [u], [1 - x[u]]) == gain
+
+
+# ----------------------------------------------------------------------------
+# FOS, LMIG and colouring (Sec. 4.1, Sec. 5.2)
+
+def _golden_fig3():
+    rows = _read_golden("fig3_lmig.txt")
+    vig = [(int(a) - 1, int(b) - 1) for t, a, b in (r for r in rows if r[0] == "vig")]
+    fos = [[int(v) - 1 for v in r[2:]] for r in rows if r[0] == "fos"]
+    lmig = {tuple(sorted((int(a) - 1, int(b) - 1))) for t, a, b in (r for r in rows if r[0] == "lmig")}
+    ncol = [int(r[1]) for r in rows if r[0] == "colors"][0]
+    return vig, fos, lmig, ncol
+
+
+def test_paper_figure3_lmig(oracle):
+    vig, fos, lmig, _ = _golden_fig3()
+    u, v = zip(*vig)
+    g = I.from_edges(5, u, v, np.ones(len(u), dtype=np.int32))
+    eptr = np.cumsum([0] + [len(F) for F in fos]).astype(np.int64)
+    evars = np.concatenate([np.array(F, dtype=np.int32) for F in fos])
+    got = {tuple(p) for p in oracle.lmig_edges(g, eptr, evars).tolist()}
+    assert len(lmig) == 22
+    assert got == lmig
+
+
+def test_paper_figure3_coloring(oracle):
+    vig, fos, lmig, ncol = _golden_fig3()
+    u, v = zip(*vig)
+    g = I.from_edges(5, u, v, np.ones(len(u), dtype=np.int32))
+    eptr = np.cumsum([0] + [len(F) for F in fos]).astype(np.int64)
+    evars = np.concatenate([np.array(F, dtype=np.int32) for F in fos])
+    k, colors = oracle.color(g, eptr, evars)
+    # {F3,F4,F5,F6,F7,F8} is a 6-clique of the figure, so 6 colours is optimal
+    clique = [2, 3, 4, 5, 6, 7]
+    assert all(tuple(sorted(p)) in lmig for p in itertools.combinations(clique, 2))
+    assert k == ncol == 6
+    for a, b in lmig:
+        assert colors[a] != colors[b]
+    groups = sorted(sorted(np.nonzero(colors == c)[0].tolist()) for c in range(k))
+    # Welsh-Powell order by (degree desc, index asc): F3 F6 F8 F4 F5 F7 F1 F2
+    assert groups == sorted([[2], [5], [7], [0, 3], [1, 4], [6]])
+
+
+def _brute_lmig(g, eptr, evars):
+    sets = [set(evars[eptr[j]:eptr[j + 1]].tolist()) for j in range(len(eptr) - 1)]
+    adj = [set(g.col[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    out = set()
+    for a, b in itertools.combinations(range(len(sets)), 2):
+        if sets[a] & sets[b] or any(adj[x] & sets[b] for x in sets[a]):
+            out.add((a, b))
+    return out
+
+
+@pytest.mark.parametrize("gname,kind", [("torus5", 0), ("torus5", 1), ("rreg", 0), ("t3d", 0)])
+def test_lmig_brute_force_and_coloring_properties(oracle, gname, kind):
+    g = {"torus5": I.torus2d(5, seed=1), "rreg": I.random_regular(24, 3, seed=4),
+         "t3d": I.torus3d(3, seed=1)}[gname]
+    eptr, evars = oracle.build_fos(g, kind)
+    # FOS is complete and each element is {j} u adj(j) (or {j})
+    assert set(evars.tolist()) == set(range(g.n))
+    for j in range(g.n):
+        F = evars[eptr[j]:eptr[j + 1]].tolist()
+        want = [j] if kind == 1 else sorted([j] + g.col[g.row_ptr[j]:g.row_ptr[j + 1]].tolist())
+        assert F == want
+    edges = _brute_lmig(g, eptr, evars)
+    got = {tuple(p) for p in oracle.lmig_edges(g, eptr, evars).tolist()}
+    assert got == edges
+    k, colors = oracle.color(g, eptr, evars)
+    assert colors.min() == 0 and colors.max() == k - 1
+    for a, b in edges:
+        assert colors[a] != colors[b]
+    # first-fit in (degree desc, index asc) order
+    m = len(eptr) - 1
+    nbrs = [set() for _ in range(m)]
+    for a, b in edges:
+        nbrs[a].add(b)
+        nbrs[b].add(a)
+    order = sorted(range(m), key=lambda j: (-len(nbrs[j]), j))
+    rank = {j: t for t, j in enumerate(order)}
+    for j in range(m):
+        earlier = {colors[q] for q in nbrs[j] if rank[q] < rank[j]}
+        assert colors[j] == min(set(range(k + 1)) - earlier)
+
+
+def test_torus_neighbourhood_lmig_needs_eight_colours(oracle):
+    # On Z^2 the neighbourhood elements of a 3x2 block of vertices plus the
+    # vertex above and below its middle column are pairwise within graph
+    # distance 3, so the LMIG holds an 8-clique.
+    g = I.torus2d(8, seed=1)
+    eptr, evars = oracle.build_fos(g, 0)
+    k, colors = oracle.color(g, eptr, evars)
+    pts = [(x, y) for y in (1, 2) for x in (0, 1, 2)] + [(1, 0), (1, 3)]
+    block = [y * 8 + x for x, y in pts]
+    edges = {tuple(p) for p in oracle.lmig_edges(g, eptr, evars).tolist()}
+    assert all(tuple(sorted(q)) in edges for q in itertools.combinations(block, 2))
+    assert k >= 8
+    assert len(set(colors[block].tolist())) == 8
+
+
+def test_group_order_is_uniform_permutation(oracle):
+    k = 3
+    counts = {}
+    for g in range(3000):
+        o = tuple(oracle.group_order(1, k, g).tolist())
+        assert sorted(o) == list(range(k))
+        counts[o] = counts.get(o, 0) + 1
+    assert len(counts) == 6
+    exp = 3000 / 6
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert chi2 < 25  # 5 dof, far above the 0.999 quantile (20.5)
+
+
+# ----------------------------------------------------------------------------
+# Parallel GOMEA (Alg. 2, Alg. 3)
+
+def _setup(oracle, g, kind=0):
+    eptr, evars = oracle.build_fos(g, kind)
+    k, colors = oracle.color(g, eptr, evars)
+    return eptr, evars, k, colors
+
+
+@pytest.mark.parametrize("gname,p", [("torus10", 16), ("rreg", 40), ("t3d", 33), ("neg", 20)])
+def test_gom_incremental_fitness_and_monotonicity(oracle, gname, p):
+    g = {"torus10": I.torus2d(10), "rreg": I.random_regular(60, 5, seed=2),
+         "t3d": I.torus3d(4, seed=3), "neg": I.random_regular(50, 4, seed=1, wmin=-30, wmax=60)}[gname]
+    eptr, evars, k, colors = _setup(oracle, g)
+    run = oracle.Run(g, eptr, evars, colors, k, p, seed=7)
+    s0 = run.get()
+    assert all(s0["f"][i] == oracle.cut_value(g, s0["pop"][i]) for i in range(p))
+    assert s0["fe"] == s0["f"].max()
+    assert np.array_equal(s0["xe"], s0["pop"][int(np.argmax(s0["f"]))])
+    prev_f, prev_fe = s0["f"].copy(), s0["fe"]
+    for gen in range(12):
+        st = run.generation()
+        s = run.get()
+        assert st["trials"] == p * (len(eptr) - 1)
+        assert st["improving"] <= st["accepted"] <= st["trials"] - st["donorless"]
+        for i in range(p):
+            assert s["f"][i] == oracle.cut_value(g, s["pop"][i])
+        assert np.all(s["f"] >= prev_f)
+        assert s["fe"] >= prev_fe and s["fe"] == max(prev_fe, s["f"].max())
+        assert s["fe"] == oracle.cut_value(g, s["xe"])
+        assert st["best"] == s["f"].max() and st["elite"] == s["fe"]
+        assert s["g"] == gen + 1
+        prev_f, prev_fe = s["f"].copy(), s["fe"]
+
+
+@pytest.mark.parametrize("gname,p", [("torus10", 16), ("rreg", 24)])
+def test_gom_group_order_invariance(oracle, gname, p):
+    """Trials of one colour group give the same result in any order: the
+    sequential run equals the parallel semantics of Alg. 3."""
+    g = {"torus10": I.torus2d(10), "rreg": I.random_regular(60, 4, seed=5)}[gname]
+    eptr, evars, k, colors = _setup(oracle, g)
+    a = oracle.Run(g, eptr, evars, colors, k, p, seed=3)
+    b = oracle.Run(g, eptr, evars, colors, k, p, seed=3)
+    for gen in range(8):
+        sa = a.generation()
+        sb = b.generation(shuffle=1000 + gen)
+        assert sa == sb
+    ga, gb = a.get(), b.get()
+    assert np.array_equal(ga["pop"], gb["pop"]) and np.array_equal(ga["f"], gb["f"])
+
+
+def test_gom_wrong_coloring_breaks_invariance(oracle):
+    """Putting all elements into one group violates the LMIG: the order of the
+    trials then changes the result, which the invariance test would catch."""
+    g = I.torus2d(6, seed=2)
+    eptr, evars = oracle.build_fos(g, 0)
+    one = np.zeros(g.n, dtype=np.int32)
+    a = oracle.Run(g, eptr, evars, one, 1, 8, seed=3)
+    b = oracle.Run(g, eptr, evars, one, 1, 8, seed=3)
+    differ = False
+    for gen in range(5):
+        a.generation()
+        b.generation(shuffle=77 + gen)
+        if not np.array_equal(a.get()["pop"], b.get()["pop"]):
+            differ = True
+    assert differ
+
+
+def test_gom_identical_population_is_all_donorless(oracle):
+    g = I.torus2d(5, seed=1)
+    eptr, evars, k, colors = _setup(oracle, g)
+    p = 6
+    run = oracle.Run(g, eptr, evars, colors, k, p, seed=1)
+    x = run.get()["pop"][0]
+    pop = np.tile(x, (p, 1))
+    f = np.full(p, oracle.cut_value(g, x), dtype=np.int64)
+    run.load(pop, f, x, int(f[0]), 0)
+    st = run.generation()
+    assert st["donorless"] == st["trials"] == p * g.n
+    assert st["accepted"] == 0
+    assert np.array_equal(run.get()["pop"], pop)
+
+
+def test_gom_tie_rule_uses_generation_start_genotype(oracle):
+    """Empty graph, singleton FOS: every move is neutral (delta = 0), so a
+    move is accepted exactly when P[i] differs from the elitist (Alg. 2 with
+    the flag of Sec. 5.3).  Individuals 0..2 equal the elitist, 3 does not."""
+    g = I.empty_graph(9)
+    eptr, evars, k, colors = _setup(oracle, g, kind=1)
+    assert k == 1
+    p = 4
+    run = oracle.Run(g, eptr, evars, colors, k, p, seed=5)
+    pop = np.zeros((p, g.n), dtype=np.uint8)
+    pop[3] = 1
+    run.load(pop, np.zeros(p, dtype=np.int64), pop[0], 0, 0)
+    st = run.generation()
+    assert st == {"generation": 0, "best": 0, "elite": 0, "trials": p * g.n, "donorless": 0,
+                  "accepted": g.n, "improving": 0, "reached": 0}
+    assert np.array_equal(run.get()["pop"], np.zeros((p, g.n), dtype=np.uint8))
+    st = run.generation()
+    assert st["donorless"] == st["trials"] and st["accepted"] == 0
+
+
+def test_gom_two_individuals_neutral_copy(oracle):
+    """p = 2 on an empty graph: the donor of each individual is the other.
+    Individual 0 is the elitist (all f = 0, lowest index) and rejects its
+    neutral moves; individual 1 takes every differing bit of individual 0."""
+    g = I.empty_graph(40)
+    eptr, evars, k, colors = _setup(oracle, g, kind=1)
+    run = oracle.Run(g, eptr, evars, colors, k, 2, seed=9)
+    s0 = run.get()
+    ndiff = int((s0["pop"][0] != s0["pop"][1]).sum())
+    assert ndiff > 0
+    st = run.generation()
+    assert st["accepted"] == ndiff and st["donorless"] == 2 * (g.n - ndiff)
+    s1 = run.get()
+    assert np.array_equal(s1["pop"][1], s0["pop"][0]) and np.array_equal(s1["pop"][0], s0["pop"][0])
+
+
+def test_gom_split_runs_and_resume(oracle):
+    g = I.torus2d(8, seed=4)
+    eptr, evars, k, colors = _setup(oracle, g)
+    a = oracle.Run(g, eptr, evars, colors, k, 12, seed=2)
+    for _ in range(10):
+        a.generation()
+    b = oracle.Run(g, eptr, evars, colors, k, 12, seed=2)
+    for _ in range(4):
+        b.generation()
+    snap = b.get()
+    c = oracle.Run(g, eptr, evars, colors, k, 12, seed=2)
+    c.load(snap["pop"], snap["f"], snap["xe"], snap["fe"], snap["g"])
+    for _ in range(6):
+        c.generation()
+    ga, gc = a.get(), c.get()
+    for key in ("pop", "f", "xe"):
+        assert np.array_equal(ga[key], gc[key])
+    assert ga["fe"] == gc["fe"] and ga["g"] == gc["g"] == 10
+
+
+def test_gom_target_stop_and_optimum_bound(oracle):
+    g = I.torus2d(4, seed=6)
+    best, _ = oracle.brute_force_maxcut(g)
+    eptr, evars, k, colors = _setup(oracle, g)
+    run = oracle.Run(g, eptr, evars, colors, k, 16, seed=1)
+    stats = run.run(50, target=best)
+    assert all(s["best"] <= best for s in stats)
+    if stats[-1]["reached"]:
+        assert stats[-1]["best"] == best and len(stats) <= 50
+        assert not any(s["reached"] for s in stats[:-1])
+
+
+def test_gom_subset_replay_matches_full_generation(oracle):
+    """Individuals are independent within a generation (donors come from the
+    frozen P), so replaying a generation for a subset reproduces those rows."""
+    g = I.random_regular(80, 5, seed=3)
+    eptr, evars, k, colors = _setup(oracle, g)
+    a = oracle.Run(g, eptr, evars, colors, k, 20, seed=4)
+    for _ in range(3):
+        a.generation()
+    snap = a.get()
+    a.generation()
+    full = a.get()
+    b = oracle.Run(g, eptr, evars, colors, k, 20, seed=4)
+    b.load(snap["pop"], snap["f"], snap["xe"], snap["fe"], snap["g"])
+    only = [0, 7, 19]
+    b.generation(only=only)
+    part = b.get()
+    for i in only:
+        assert np.array_equal(part["pop"][i], full["pop"][i])
+        assert part["f"][i] == full["f"][i]
