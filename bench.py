@@ -1,0 +1,386 @@
+"""Benchmark of parallel GOM (weighted Max-Cut) on GB300.
+
+A step is one generation of parallel GOMEA (Alg. 3): generation start, group
+order, one mixing launch per colour group, generation end.  The metric is GOM
+trials per second (a trial is one (individual, FOS element) pair, donor-less
+trials included); time-to-target and the mixing kernel's HBM roofline
+fraction are reported beside it.
+
+Default workload: 2D torus 100x100 (n = 10,000, 20,000 edges), int32 weights
+uniform in [1,100] from seed 1, neighbourhood FOS, Welsh-Powell colouring,
+population 64, Philox seed 1.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gom|reference]
+                [--workload NAME] [--pop P]
+Under torchrun (N > 1) each rank runs an independent replica (seed + rank):
+replicas only, weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2203_08680_gb300 import instances as I  # noqa: E402
+
+WORKLOADS = {
+    # name: (graph builder, population, description)
+    "torus100": (lambda: I.torus2d(100), 64,
+                 "2D torus 100x100 (n=10,000, 20,000 edges), int32 weights U[1,100] seed 1, pop 64"),
+    "torus10": (lambda: I.torus2d(10), 16,
+                "2D torus 10x10 (n=100, 200 edges), int32 weights U[1,100] seed 1, pop 16"),
+    "torus3d50": (lambda: I.torus3d(50), 512,
+                  "3D torus 50^3 (n=125,000, 375,000 edges), int32 weights U[1,100], pop 512"),
+    "rreg1m_d3": (lambda: I.random_regular(1_000_000, 3), 512,
+                  "random 3-regular n=1,000,000, int32 weights U[1,100], pop 512"),
+    "rreg1m_d6": (lambda: I.random_regular(1_000_000, 6), 512,
+                  "random 6-regular n=1,000,000, int32 weights U[1,100], pop 512"),
+    "rreg1m_d12": (lambda: I.random_regular(1_000_000, 12), 512,
+                   "random 12-regular n=1,000,000, int32 weights U[1,100], pop 512"),
+    "torus1000": (lambda: I.torus2d(1000), 256,
+                  "2D torus 1000x1000 (n=1,000,000), int32 weights U[1,100], pop 256"),
+}
+SEED = 1
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "GOM trials/sec (plain parallel GOM, weighted Max-Cut)"
+
+
+def mixing_bytes_per_generation(g, eptr, evars, p: int) -> int:
+    """Algorithmic bytes of all mixing launches of one generation: per element
+    j, p (|C_j| + 2|F_j|) / 8 bytes of bit-sliced population (parent closure
+    C_j = F_j u adj(F_j), donor bits and the write on F_j) plus the element's
+    adjacency, 8 bytes per CSR entry of its variables and 4 bytes per
+    variable, read once for all p individuals."""
+    import scipy.sparse as sp
+    n = g.n
+    m = len(eptr) - 1
+    sizes = np.diff(eptr)
+    A = sp.csr_matrix((np.ones(len(g.col), dtype=np.int8), g.col, g.row_ptr), shape=(n, n))
+    AI = (A + sp.identity(n, dtype=np.int8, format="csr")).tocsr()
+    closure = np.zeros(m, dtype=np.int64)
+    chunk = 65536
+    for a in range(0, m, chunk):
+        b = min(m, a + chunk)
+        rows = np.repeat(np.arange(b - a), sizes[a:b])
+        M = sp.csr_matrix((np.ones(len(rows), dtype=np.int8), (rows, evars[eptr[a]:eptr[b]])),
+                          shape=(b - a, n))
+        closure[a:b] = np.diff((M @ AI).tocsr().indptr)
+    deg = np.diff(g.row_ptr)
+    csr_bytes = 8 * np.add.reduceat(deg[evars], eptr[:-1]) + 4 * sizes
+    pop_bytes = p * (closure + 2 * sizes) / 8.0
+    return int(round(float(pop_bytes.sum() + csr_bytes.sum())))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("gom_kernels.cu", "gom_internal.h"):
+        with open(os.path.join(ROOT, "paper_2203_08680_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per mixing launch from the committed ncu summary, if it was
+    taken on this workload with the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_mix_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda") if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_trials_per_sec(g, p: int, seed: int, budget_s: float, warmup: int = 0, steps: int = None):
+    """The CPU oracle as it stands, single-threaded, timed on a bounded sample
+    (generations until budget_s, or `steps` generations after `warmup`)."""
+    from oracle import oracle as O
+    ep, ev = O.build_fos(g)
+    k, co = O.color(g, ep, ev)
+    run = O.Run(g, ep, ev, co, k, p, seed)
+    m = len(ep) - 1
+    for _ in range(warmup):
+        run.generation()
+    gens, t0 = 0, time.perf_counter()
+    while True:
+        run.generation()
+        gens += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and gens >= steps) or (steps is None and el >= budget_s):
+            break
+    return p * m * gens / el, gens, el
+
+
+def run_reference(args, wl, rank, world):
+    """Reference arm: the CPU oracle on this workload, rank 0 only."""
+    if rank != 0:
+        return
+    build, p, desc = WORKLOADS[wl]
+    g = build()
+    val, gens, el = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "trials/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / gens,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": wl, "description": desc},
+            "cpu_baseline": {"value": val, "unit": "trials/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{gens} generations of the workload after {args.warmup} warm-up"},
+            "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, wl, rank, world, local):
+    import torch
+
+    from paper_2203_08680_gb300 import gom
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build, p, desc = WORKLOADS[wl]
+    if args.pop:
+        p = args.pop
+    g = build()
+    seed = SEED + rank
+    stream = torch.cuda.current_stream()
+    P = gom.Population(g, p, seed, stream=stream)
+    m, k = P.m, P.k
+    trials_per_step = p * m
+    launches_per_step = gom.gom_launches_per_generation(P.ctx)
+    ex = gom.gom_fos_export(P.fos)
+    mix_bytes = mixing_bytes_per_generation(g, ex["elem_ptr"], ex["elem_vars"], p)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    # warm-up generations (untimed)
+    P.generation(args.warmup, want_stats=False)
+    torch.cuda.synchronize()
+    gom.gom_set_timing(P.ctx, True)
+    gom.gom_read_timing(P.ctx)  # reset
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)  # L2 flush between timed generations (outside the events)
+            ev0[s].record(stream)
+            gom.gom_generation(P.ctx, 1, gom.INT64_MAX, want_stats=False)
+            ev1[s].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    mix_ms, mix_launches = gom.gom_read_timing(P.ctx)
+    gom.gom_set_timing(P.ctx, False)
+    dist_barrier(world)
+    total_ms = dist_max(sum(step_ms), world)
+    value = world * trials_per_step * args.steps / (total_ms / 1e3)
+
+    # time to target: fresh population, within 0.1% of the closed-form optimum
+    # (every edge cut on an even torus) or a generation cap
+    tw = g.total_weight()
+    target = int(math.ceil(0.999 * tw))
+    P2 = gom.Population(g, p, seed, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats, nrun = P2.generation(args.ttt_gens, target)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ttt = {"target": target, "closed_form_optimum": tw if wl.startswith("torus") else None,
+           "reached": bool(stats and stats[-1]["reached_target"]), "generations": nrun,
+           "best": stats[-1]["best_fitness"] if stats else None, "ms": e0.elapsed_time(e1),
+           "max_generations": args.ttt_gens}
+    del P2
+
+    # end to end through the C ABI from host buffers: FOS, colouring, upload,
+    # generations with host statistics, population and fitness back to host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = gom.Graph(g)
+    fos = gom.gom_build_fos(G)
+    gom.gom_color_fos(G, fos)
+    nbytes = gom.gom_workspace_bytes(G, fos, p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    ctx = gom.gom_init_population(G, fos, p, seed, ws, nbytes, stream)
+    est, _ = gom.gom_generation(ctx, args.steps, gom.INT64_MAX, True)
+    dpop = torch.empty((p, g.n), dtype=torch.uint8, device=dev)
+    dfit = torch.empty(p, dtype=torch.int64, device=dev)
+    gom.gom_get_population(ctx, dpop, dfit, True)
+    hpop = torch.empty((p, g.n), dtype=torch.uint8, pin_memory=True)
+    hfit = torch.empty(p, dtype=torch.int64, pin_memory=True)
+    hpop.copy_(dpop, non_blocking=True)
+    hfit.copy_(dfit, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = dist_max(e2e_s, world)
+    h2d = (G.row_ptr.nbytes + G.col.nbytes + G.weight.nbytes + ex["elem_ptr"].nbytes // 2 +
+           ex["elem_vars"].nbytes + 8 * (m + 1) + 8 * int(np.diff(G.row_ptr).sum()) + 2 * (len(ex["elem_vars"]) + m))
+    d2h = 64 * args.steps + p * g.n + 8 * p
+    del ctx, ws
+
+    # CPU baseline: the oracle, bounded sample, rank 0
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds)
+        cpu = {"value": cval, "unit": "trials/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, single thread)"}
+
+    peak, peak_kind = peaks()
+    mix_avg_ms = mix_ms / max(mix_launches, 1)
+    bytes_per_launch = mix_bytes / k
+    achieved = bytes_per_launch / (mix_avg_ms / 1e3) / 1e9 if mix_launches else None
+    traffic = profiled_traffic(wl)
+    line = {
+        "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl, "description": desc, "population": p, "elements": m, "colours": k,
+                   "l2": "flushed between timed generations (2x L2 buffer write)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": "k_mix", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": mix_avg_ms, "launches_timed": mix_launches},
+        "time_to_target": ttt,
+        "e2e": {"value": trials_per_step * args.steps * world / e2e_s, "unit": "trials/s",
+                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)},
+        "gpu_launches": launches_per_step * args.steps + args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gom", choices=["gom", "reference"])
+    ap.add_argument("--workload", default="torus100", choices=sorted(WORKLOADS))
+    ap.add_argument("--pop", type=int, default=0)
+    ap.add_argument("--ttt-gens", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, args.workload, rank, world)
+    else:
+        run_gpu(args, args.workload, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * gom.h -- C ABI of the GB300 parallel Gene-pool Optimal Mixing (GOM) library
+ * for weighted Max-Cut.
+ *
+ * The method is parallel GOMEA of Bouter & Bosman, "GPU-Accelerated Parallel
+ * Gene-pool Optimal Mixing in a Gray-Box Optimization Setting" (arXiv
+ * 2203.08680): a population of binary solutions is improved generation by
+ * generation; in each generation the elements of the linkage model (FOS,
+ * Sec. 4.1) are split into colour groups of mutually independent elements
+ * (Sec. 5.2), the groups are visited in random order (Alg. 3), and every
+ * (individual, element) pair of a group is one GOM trial (Alg. 2): copy a
+ * donor's bits on the element, take the cut-weight change by partial
+ * evaluation (Sec. 2.2, Alg. 4) and keep the change unless it makes the
+ * solution worse.
+ *
+ * Conventions for every call:
+ *  - Return value: GOM_OK (0) or a negative GOM_E_* code; gom_strerror() names it.
+ *  - Host pointers are read during the call only and stay owned by the caller.
+ *  - Device memory is never allocated by the library: the caller passes one
+ *    device workspace (sized by gom_workspace_bytes) to gom_init_population
+ *    and device output buffers to the export calls.
+ *  - Device work is enqueued on the caller's CUDA stream given at
+ *    gom_init_population; a call returns before that work finishes unless it
+ *    says otherwise.  Handles are not thread-safe.
+ *  - Integer arithmetic throughout: int32 edge weights, int64 fitness.  Results
+ *    are bit-exact and reproducible from (graph, FOS, population size, seed).
+ *
+ * Random numbers are Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) with
+ * key (seed low 32 bits, seed high 32 bits) and these counters:
+ *  - initial bit v of individual i: bit (v mod 32) of word (v/32 mod 4) of
+ *    ctr (v/128, i, 0, 0x494E4954);
+ *  - group order of generation g: colours sorted ascending by the 64-bit key
+ *    (word0 << 32 | word1) of ctr (colour, 0, g, 0x4F524452), ties by colour;
+ *  - donor of trial (individual i, element j) in generation g: r = word (i mod 4)
+ *    of ctr (j, i/4, g, 0x444F4E52); start = (i + 1 + floor(r (p-1) / 2^32)) mod p;
+ *    the donor is the first individual, scanning cyclically upwards from start
+ *    and skipping i, whose generation-start bits on the element differ from
+ *    the parent's current bits (no such individual: the trial is skipped).
+ */
+#ifndef GOM_H_
+#define GOM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define GOM_OK 0
+#define GOM_E_ARG (-1)          /* null pointer, population < 2, unknown kind, ... */
+#define GOM_E_GRAPH (-2)        /* CSR not a simple symmetric graph with sorted rows */
+#define GOM_E_NOT_COLORED (-3)  /* gom_color_fos has not run on this FOS */
+#define GOM_E_WORKSPACE (-4)    /* workspace null, misaligned or too small */
+#define GOM_E_CUDA (-5)         /* a CUDA call failed; gom_last_cuda_error has it */
+#define GOM_E_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define GOM_E_STATE (-7)        /* call not valid in the handle's state */
+#define GOM_E_LIMIT (-8)        /* size beyond what this build supports */
+#define GOM_E_FOS (-9)          /* FOS incomplete, out of range or for another graph */
+
+/* FOS kinds for gom_build_fos. */
+#define GOM_FOS_NEIGHBOURHOOD 0 /* F_j = {j} u adj(j), one element per vertex */
+#define GOM_FOS_SINGLETON 1     /* F_j = {j} */
+
+/* Supported maxima of this build. */
+#define GOM_MAX_POPULATION 1024 /* individuals */
+#define GOM_MAX_ELEMENT 64      /* variables in one FOS element */
+#define GOM_MAX_COLORS 28000    /* colour groups */
+
+/*
+ * Weighted undirected graph in symmetric CSR form (Sec. 6.2: the Max-Cut
+ * instance, which is also the variable interaction graph of Sec. 2.3).
+ * row_ptr[num_vertices+1] (int64, row_ptr[0] = 0, row_ptr[n] = num_adj),
+ * col[num_adj] and weight[num_adj]; each undirected edge {u,v} appears as
+ * (u,v,w) and (v,u,w); rows sorted strictly ascending; no self-loops.  Host
+ * memory, caller-owned, read during the call.  Any int32 weight is allowed.
+ */
+typedef struct gom_graph {
+    int32_t num_vertices;
+    int64_t num_adj;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const int32_t *weight;
+} gom_graph_t;
+
+typedef struct gom_fos gom_fos_t; /* linkage model + colouring (host, library-owned) */
+typedef struct gom_ctx gom_ctx_t; /* one population on one GPU (library-owned) */
+
+/* Counters of one generation. */
+typedef struct gom_gen_stats {
+    int64_t generation;     /* index g of the generation (0 = first after init) */
+    int64_t best_fitness;   /* max_i f[i] at its end */
+    int64_t elite_fitness;  /* fitness of the elitist at its end */
+    int64_t trials;         /* (individual, element) pairs = p * m, donor-less included */
+    int64_t donorless;      /* trials with no donor differing on the element */
+    int64_t accepted;       /* trials whose change was kept */
+    int64_t improving;      /* accepted trials with a positive delta */
+    int64_t reached_target; /* 1 if best_fitness >= the call's target */
+} gom_gen_stats_t;
+
+/*
+ * Builds the linkage model (FOS, Sec. 4.1) of a graph.  kind is
+ * GOM_FOS_NEIGHBOURHOOD (element j = {j} u adj(j), variables ascending) or
+ * GOM_FOS_SINGLETON; param is reserved (pass 0).  Validates the graph
+ * (GOM_E_GRAPH).  *out receives a handle to free with gom_fos_destroy.
+ */
+int gom_build_fos(const gom_graph_t *g, int32_t kind, int32_t param, gom_fos_t **out);
+
+/*
+ * Wraps a caller-given FOS over num_vars variables: m elements, element j =
+ * elem_vars[elem_ptr[j] .. elem_ptr[j+1]), each ascending without repeats.  The
+ * FOS must be complete (Sec. 4.1: every variable in some element), else
+ * GOM_E_FOS.  Arrays are copied.  Elements above GOM_MAX_ELEMENT variables are
+ * accepted here and rejected by gom_init_population with GOM_E_LIMIT.
+ */
+int gom_fos_create(int32_t num_vars, int64_t m, const int64_t *elem_ptr,
+                   const int32_t *elem_vars, gom_fos_t **out);
+
+/*
+ * Colours the linkage-model interaction graph (LMIG, Sec. 5.2: elements i and j
+ * are joined iff they share a variable or a graph edge joins them) with the
+ * greedy Welsh-Powell algorithm: elements by LMIG degree descending, ties by
+ * ascending index, each given the smallest colour unused by its coloured
+ * neighbours.  The LMIG is never materialised.  Stores the colouring in fos
+ * and writes the number of colours k to *num_colors.  Host-only work.
+ */
+int gom_color_fos(const gom_graph_t *g, gom_fos_t *fos, int32_t *num_colors);
+
+/* Sizes of a FOS: elements m, total variables over all elements, colours k
+ * (-1 if not coloured).  Any output pointer may be NULL. */
+int gom_fos_sizes(const gom_fos_t *fos, int64_t *m, int64_t *total_vars, int32_t *k);
+
+/*
+ * Copies a FOS and its colouring into caller-sized host arrays (any may be
+ * NULL): elem_ptr[m+1], elem_vars[total_vars], color_of_elem[m],
+ * color_ptr[k+1], color_elems[m] (the elements of colour c, ascending, are
+ * color_elems[color_ptr[c] .. color_ptr[c+1])).  Colour arrays need a coloured
+ * FOS (GOM_E_NOT_COLORED).
+ */
+int gom_fos_export(const gom_fos_t *fos, int64_t *elem_ptr, int32_t *elem_vars,
+                   int32_t *color_of_elem, int64_t *color_ptr, int32_t *color_elems);
+
+void gom_fos_destroy(gom_fos_t *fos);
+
+/*
+ * Bytes of device workspace gom_init_population needs for this graph, FOS
+ * and population size (0 on invalid arguments).  The workspace must be
+ * 256-byte aligned.
+ */
+size_t gom_workspace_bytes(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop);
+
+/*
+ * InitializePopulation (Alg. 3): validates and uploads the graph, the coloured
+ * FOS and its per-element dependency lists (the edges incident to each
+ * element, Alg. 4) into d_workspace, draws the population uniformly at random
+ * with Philox (counters above), evaluates it fully (Sec. 6.2) and takes the
+ * elitist (lowest index of maximal fitness).  pop in [2, GOM_MAX_POPULATION].
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).  d_workspace
+ * (caller-owned device memory of ws_bytes >= gom_workspace_bytes) must outlive
+ * the handle.  Synchronises the stream before returning.
+ */
+int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop, uint64_t seed,
+                        void *d_workspace, size_t ws_bytes, void *cuda_stream, gom_ctx_t **out);
+
+/*
+ * Runs up to num_generations generations of parallel GOMEA (Alg. 3): P <- O;
+ * the elitist flag of each individual (P[i] equals the elitist); the colour
+ * groups in random order, each group one mixing launch over all its
+ * (individual, element) trials (donor, partial evaluation, accept, write);
+ * then the fitness fold, the elitist update (if max f beats it) and the
+ * counters.  Stops after the first generation whose best fitness is >=
+ * target_fitness (INT64_MAX: never).  With host_stats (an array of
+ * num_generations entries) or generations_run non-NULL the call waits for the
+ * stream and fills them (entries past the stop are zeroed); otherwise it only
+ * enqueues.  The generation counter lives in the handle, so split calls
+ * reproduce one long call exactly.
+ */
+int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitness,
+                   gom_gen_stats_t *host_stats, int32_t *generations_run);
+
+/* Full re-evaluation (Sec. 6.2) of the current population into the caller's
+ * device buffer d_fitness_out[pop] (int64).  Enqueued only. */
+int gom_fitness(gom_ctx_t *ctx, int64_t *d_fitness_out);
+
+/*
+ * Exports the current population as uint8 {0,1} rows d_pop[pop][num_vertices]
+ * and its fitness d_fit[pop] (device buffers, either may be NULL), and writes
+ * the elitist's fitness to *elite_f (host, may be NULL; waits for the stream).
+ */
+int gom_get_population(gom_ctx_t *ctx, uint8_t *d_pop, int64_t *d_fit, int64_t *elite_f);
+
+/* Exports the elitist solution as uint8 d_elite[num_vertices] (device) and its
+ * fitness (host, may be NULL; waits for the stream). */
+int gom_get_elite(gom_ctx_t *ctx, uint8_t *d_elite, int64_t *elite_f);
+
+/*
+ * Replaces the state (checkpoint resume): population d_pop[pop][num_vertices]
+ * (uint8 {0,1}, device), elitist d_elite[num_vertices] (device) with fitness
+ * elite_f, and the generation counter.  Fitness is re-evaluated on the device.
+ */
+int gom_set_population(gom_ctx_t *ctx, const uint8_t *d_pop, const uint8_t *d_elite,
+                       int64_t elite_f, int64_t generation);
+
+/* Current generation counter (generations run since init or the last set). */
+int gom_get_generation(gom_ctx_t *ctx, int64_t *generation);
+
+/*
+ * Kernel timing.  gom_set_timing(ctx, 1) makes each following generation
+ * record a CUDA event pair around every mixing launch; gom_read_timing waits
+ * for the stream and adds the measured milliseconds and the launch count since
+ * the last read.  Timing adds event records to the generation; off by default.
+ */
+int gom_set_timing(gom_ctx_t *ctx, int32_t enable);
+int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches);
+
+/* Kernel launches one generation makes (for launch accounting). */
+int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches);
+
+/* Last CUDA error code seen by the handle (0 if none). */
+int gom_last_cuda_error(gom_ctx_t *ctx);
+
+void gom_destroy(gom_ctx_t *ctx);
+
+const char *gom_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOM_H_ */

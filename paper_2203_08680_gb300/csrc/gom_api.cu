@@ -1,0 +1,595 @@
+// gom_api.cu -- the C ABI declared in include/gom.h: handles, workspace
+// layout, uploads, the per-generation CUDA graph and the exports.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gom_internal.h"
+#include "gom_kernels.cuh"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxMixBlocks = 4096; // per-block partial slots reserved in the workspace
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int words_for(int32_t p)
+{
+    int wv = (p + 31) / 32, w = 1;
+    while (w < wv) w <<= 1;
+    return w;
+}
+
+// Byte offsets of every device array inside the workspace.
+struct Layout {
+    size_t O, P, f, eqw, xe, st, stats, order, part_f, part_cnt;
+    size_t row_ptr, col, wgt, eptr, evars, dep_ptr, dep, seg, cptr, celems;
+    size_t total;
+};
+
+Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_vars, int64_t ndeps,
+                   int32_t k)
+{
+    const int64_t W = words_for(p);
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + std::max<size_t>(bytes, 1));
+        return at;
+    };
+    L.O = take(sizeof(uint32_t) * n * W);
+    L.P = take(sizeof(uint32_t) * n * W);
+    L.f = take(sizeof(int64_t) * 32 * W);
+    L.eqw = take(sizeof(uint32_t) * W);
+    L.xe = take(n);
+    L.st = take(sizeof(GomDevState));
+    L.stats = take(sizeof(GomDevStats) * kStatsCap);
+    L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
+    L.part_f = take(sizeof(int64_t) * 32 * W * kMaxMixBlocks);
+    L.part_cnt = take(sizeof(int64_t) * 4 * kMaxMixBlocks);
+    L.row_ptr = take(sizeof(int64_t) * (n + 1));
+    L.col = take(sizeof(int32_t) * nadj);
+    L.wgt = take(sizeof(int32_t) * nadj);
+    L.eptr = take(sizeof(int32_t) * (m + 1));
+    L.evars = take(sizeof(int32_t) * total_vars);
+    L.dep_ptr = take(sizeof(int64_t) * (m + 1));
+    L.dep = take(sizeof(int32_t) * 2 * ndeps);
+    L.seg = take(sizeof(uint16_t) * (total_vars + m));
+    L.cptr = take(sizeof(int32_t) * (std::max<int32_t>(k, 0) + 1));
+    L.celems = take(sizeof(int32_t) * m);
+    L.total = off;
+    return L;
+}
+
+} // namespace
+
+struct gom_ctx {
+    GomParams prm{};
+    cudaStream_t stream = nullptr;
+    int32_t n = 0, p = 0, W = 0, k = 0;
+    int64_t m = 0;
+    int sms = 0;
+    int grid_mix = 0, grid_fit = 0, grid_start = 0, grid_order = 0, grid_io = 0;
+    size_t order_smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t tgraph = nullptr; // variant with event records around each mixing launch
+    cudaGraphExec_t texec = nullptr;
+    std::vector<cudaEvent_t> events;
+    bool timing = false;
+    double mix_ms = 0.0;
+    int64_t mix_launches = 0;
+    int last_cuda = 0;
+};
+
+namespace {
+
+int cuda_fail(gom_ctx *ctx, cudaError_t e)
+{
+    if (ctx) ctx->last_cuda = static_cast<int>(e);
+    return GOM_E_CUDA;
+}
+
+#define GOM_CUDA(ctx, call)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
+    } while (0)
+
+template <class T>
+cudaError_t upload(void *base, size_t off, const std::vector<T> &v, cudaStream_t s)
+{
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(static_cast<char *>(base) + off, v.data(), sizeof(T) * v.size(),
+                           cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t upload_raw(void *base, size_t off, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (!bytes) return cudaSuccess;
+    return cudaMemcpyAsync(static_cast<char *>(base) + off, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
+// Adds a kernel node after `dep` (may be null) and returns it.
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const void *fn,
+                       int grid, int block, size_t smem, void **args)
+{
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.sharedMemBytes = static_cast<unsigned>(smem);
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+// One generation as a chain of nodes: gen_start, order, k mixing launches,
+// gen_end.  With `timed`, event records bracket every mixing launch.
+int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_t *out_exec)
+{
+    cudaGraph_t g;
+    GOM_CUDA(ctx, cudaGraphCreate(&g, 0));
+    GomParams prm = ctx->prm;
+    void *args1[] = {&prm};
+    cudaGraphNode_t last = nullptr, node;
+    cudaError_t e = add_kernel(g, &node, last, (const void *)k_gen_start, ctx->grid_start, 256, 0, args1);
+    if (e == cudaSuccess) {
+        last = node;
+        e = add_kernel(g, &node, last, (const void *)k_order, ctx->grid_order, 256, ctx->order_smem, args1);
+    }
+    std::vector<int> ts(ctx->k);
+    for (int t = 0; t < ctx->k && e == cudaSuccess; ++t) {
+        last = node;
+        if (timed) {
+            e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t]);
+            if (e != cudaSuccess) break;
+            last = node;
+        }
+        ts[t] = t;
+        void *args2[] = {&prm, &ts[t]};
+        e = add_kernel(g, &node, last, (const void *)k_mix, ctx->grid_mix, kMixThreads, 0, args2);
+        if (e == cudaSuccess && timed) {
+            last = node;
+            e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
+        }
+    }
+    if (e == cudaSuccess) {
+        last = node;
+        e = add_kernel(g, &node, last, (const void *)k_gen_end, 1, 1024, 0, args1);
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ctx, e);
+    }
+    *out_graph = g;
+    *out_exec = ex;
+    return GOM_OK;
+}
+
+int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *run_out)
+{
+    GomDevState st;
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int32_t run = static_cast<int32_t>(st.g - st.call_g0);
+    if (run_out) *run_out = run;
+    if (host_stats) {
+        std::memset(host_stats, 0, sizeof(gom_gen_stats_t) * num);
+        std::vector<GomDevStats> ring(kStatsCap);
+        GOM_CUDA(ctx, cudaMemcpyAsync(ring.data(), ctx->prm.stats, sizeof(GomDevStats) * kStatsCap,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int32_t q = 0; q < run && q < num; ++q) {
+            const GomDevStats &S = ring[(st.call_g0 + q) % kStatsCap];
+            gom_gen_stats_t &H = host_stats[q];
+            H.generation = S.generation;
+            H.best_fitness = S.best;
+            H.elite_fitness = S.elite;
+            H.trials = S.trials;
+            H.donorless = S.donorless;
+            H.accepted = S.accepted;
+            H.improving = S.improving;
+            H.reached_target = S.reached;
+        }
+    }
+    return GOM_OK;
+}
+
+int accumulate_timing(gom_ctx *ctx)
+{
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int t = 0; t < ctx->k; ++t) {
+        float ms = 0.f;
+        GOM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * t], ctx->events[2 * t + 1]));
+        ctx->mix_ms += ms;
+    }
+    return GOM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char *gom_strerror(int code)
+{
+    switch (code) {
+    case GOM_OK: return "ok";
+    case GOM_E_ARG: return "invalid argument";
+    case GOM_E_GRAPH: return "graph is not a simple symmetric CSR with sorted rows";
+    case GOM_E_NOT_COLORED: return "FOS has not been coloured";
+    case GOM_E_WORKSPACE: return "workspace missing, misaligned or too small";
+    case GOM_E_CUDA: return "CUDA call failed";
+    case GOM_E_TIMEOUT: return "bounded device wait gave up";
+    case GOM_E_STATE: return "call not valid in this state";
+    case GOM_E_LIMIT: return "size beyond this build's limits";
+    case GOM_E_FOS: return "FOS incomplete, out of range or for another graph";
+    default: return "unknown error";
+    }
+}
+
+int gom_build_fos(const gom_graph_t *g, int32_t kind, int32_t param, gom_fos_t **out)
+{
+    if (!g || !out || param != 0) return GOM_E_ARG;
+    if (kind != GOM_FOS_NEIGHBOURHOOD && kind != GOM_FOS_SINGLETON) return GOM_E_ARG;
+    int rc = gomh::validate_graph(g);
+    if (rc) return rc;
+    std::unique_ptr<gom_fos> fos(new (std::nothrow) gom_fos());
+    if (!fos) return GOM_E_ARG;
+    rc = gomh::build_fos(g, kind, fos.get());
+    if (rc) return rc;
+    *out = fos.release();
+    return GOM_OK;
+}
+
+int gom_fos_create(int32_t num_vars, int64_t m, const int64_t *elem_ptr, const int32_t *elem_vars,
+                   gom_fos_t **out)
+{
+    if (!out || num_vars < 0 || m < 0 || !elem_ptr || (m > 0 && !elem_vars)) return GOM_E_ARG;
+    std::unique_ptr<gom_fos> fos(new (std::nothrow) gom_fos());
+    if (!fos) return GOM_E_ARG;
+    fos->n = num_vars;
+    fos->m = m;
+    fos->eptr.assign(elem_ptr, elem_ptr + m + 1);
+    if (fos->eptr[0] != 0 || fos->eptr[m] < 0) return GOM_E_FOS;
+    for (int64_t j = 0; j < m; ++j)
+        if (fos->eptr[j + 1] < fos->eptr[j]) return GOM_E_FOS;
+    fos->evars.assign(elem_vars, elem_vars + fos->eptr[m]);
+    int rc = gomh::check_fos(num_vars, *fos);
+    if (rc) return rc;
+    *out = fos.release();
+    return GOM_OK;
+}
+
+int gom_color_fos(const gom_graph_t *g, gom_fos_t *fos, int32_t *num_colors)
+{
+    if (!g || !fos) return GOM_E_ARG;
+    int rc = gomh::validate_graph(g);
+    if (rc) return rc;
+    if (fos->n != g->num_vertices) return GOM_E_FOS;
+    rc = gomh::color_fos(g, fos);
+    if (rc) return rc;
+    if (num_colors) *num_colors = fos->k;
+    return GOM_OK;
+}
+
+int gom_fos_sizes(const gom_fos_t *fos, int64_t *m, int64_t *total_vars, int32_t *k)
+{
+    if (!fos) return GOM_E_ARG;
+    if (m) *m = fos->m;
+    if (total_vars) *total_vars = static_cast<int64_t>(fos->evars.size());
+    if (k) *k = fos->k;
+    return GOM_OK;
+}
+
+int gom_fos_export(const gom_fos_t *fos, int64_t *elem_ptr, int32_t *elem_vars, int32_t *color_of_elem,
+                   int64_t *color_ptr, int32_t *color_elems)
+{
+    if (!fos) return GOM_E_ARG;
+    if ((color_of_elem || color_ptr || color_elems) && fos->k < 0) return GOM_E_NOT_COLORED;
+    if (elem_ptr) std::copy(fos->eptr.begin(), fos->eptr.end(), elem_ptr);
+    if (elem_vars) std::copy(fos->evars.begin(), fos->evars.end(), elem_vars);
+    if (color_of_elem) std::copy(fos->color_of.begin(), fos->color_of.end(), color_of_elem);
+    if (color_ptr) std::copy(fos->cptr.begin(), fos->cptr.end(), color_ptr);
+    if (color_elems) std::copy(fos->celems.begin(), fos->celems.end(), color_elems);
+    return GOM_OK;
+}
+
+void gom_fos_destroy(gom_fos_t *fos) { delete fos; }
+
+size_t gom_workspace_bytes(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop)
+{
+    if (!g || !fos || pop < 2 || pop > GOM_MAX_POPULATION || g->num_vertices < 0) return 0;
+    if (fos->n != g->num_vertices || !g->row_ptr) return 0;
+    const int64_t ndeps = gomh::count_deps(g, *fos);
+    return make_layout(g->num_vertices, pop, g->num_adj, fos->m, static_cast<int64_t>(fos->evars.size()),
+                       ndeps, std::max<int32_t>(fos->k, 1))
+        .total;
+}
+
+int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop, uint64_t seed,
+                        void *d_workspace, size_t ws_bytes, void *cuda_stream, gom_ctx_t **out)
+{
+    if (!g || !fos || !out) return GOM_E_ARG;
+    if (pop < 2) return GOM_E_ARG;
+    if (pop > GOM_MAX_POPULATION) return GOM_E_LIMIT;
+    int rc = gomh::validate_graph(g);
+    if (rc) return rc;
+    if (fos->n != g->num_vertices) return GOM_E_FOS;
+    if (fos->k < 0) return GOM_E_NOT_COLORED;
+    if (fos->k > GOM_MAX_COLORS) return GOM_E_LIMIT;
+    if (static_cast<int64_t>(fos->evars.size()) + fos->m >= INT_MAX || fos->m >= INT_MAX) return GOM_E_LIMIT;
+    for (int64_t j = 0; j < fos->m; ++j)
+        if (fos->eptr[j + 1] - fos->eptr[j] > GOM_MAX_ELEMENT) return GOM_E_LIMIT;
+    const int64_t ndeps_bound = gomh::count_deps(g, *fos);
+    const Layout L = make_layout(g->num_vertices, pop, g->num_adj, fos->m,
+                                 static_cast<int64_t>(fos->evars.size()), ndeps_bound, fos->k);
+    if (!d_workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
+        return GOM_E_WORKSPACE;
+
+    gomh::DepTables deps;
+    rc = gomh::build_deps(g, *fos, &deps);
+    if (rc) return rc;
+
+    std::unique_ptr<gom_ctx> ctx(new (std::nothrow) gom_ctx());
+    if (!ctx) return GOM_E_ARG;
+    gom_ctx *c = ctx.get();
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->n = g->num_vertices;
+    c->p = pop;
+    c->W = words_for(pop);
+    c->m = fos->m;
+    c->k = fos->k;
+
+    int dev = 0;
+    GOM_CUDA(c, cudaGetDevice(&dev));
+    GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    int occ = 0;
+    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mix, kMixThreads, 0));
+    occ = std::max(occ, 1);
+    // mixing grid: enough warps for the largest group, a multiple of W warps
+    int64_t max_group = 1;
+    for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
+    const int warps_per_block = kMixThreads / 32;
+    const int64_t need_blocks = (max_group * c->W + warps_per_block - 1) / warps_per_block;
+    int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
+    grid = std::min<int64_t>(grid, kMaxMixBlocks);
+    const int blk_mult = std::max(1, c->W / warps_per_block);
+    grid = std::max<int64_t>(blk_mult, grid / blk_mult * blk_mult);
+    c->grid_mix = static_cast<int>(grid);
+    c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
+    c->grid_start = c->sms * 4;
+    c->grid_io = c->sms * 4;
+    c->grid_order = (c->k + 255) / 256;
+    c->order_smem = sizeof(unsigned long long) * std::max(c->k, 1);
+    if (c->order_smem > 48 * 1024)
+        GOM_CUDA(c, cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(c->order_smem)));
+
+    char *base = static_cast<char *>(d_workspace);
+    GomParams &P = c->prm;
+    P.n = c->n;
+    P.p = pop;
+    P.W = c->W;
+    P.Wv = (pop + 31) / 32;
+    P.m = static_cast<int32_t>(fos->m);
+    P.k = fos->k;
+    P.nblk_mix = c->grid_mix;
+    P.seed = seed;
+    P.O = reinterpret_cast<uint32_t *>(base + L.O);
+    P.P = reinterpret_cast<uint32_t *>(base + L.P);
+    P.f = reinterpret_cast<int64_t *>(base + L.f);
+    P.eqw = reinterpret_cast<uint32_t *>(base + L.eqw);
+    P.xe = reinterpret_cast<uint8_t *>(base + L.xe);
+    P.st = reinterpret_cast<GomDevState *>(base + L.st);
+    P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
+    P.order = reinterpret_cast<int32_t *>(base + L.order);
+    P.part_f = reinterpret_cast<int64_t *>(base + L.part_f);
+    P.part_cnt = reinterpret_cast<int64_t *>(base + L.part_cnt);
+    P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
+    P.col = reinterpret_cast<const int32_t *>(base + L.col);
+    P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);
+    P.eptr = reinterpret_cast<const int32_t *>(base + L.eptr);
+    P.evars = reinterpret_cast<const int32_t *>(base + L.evars);
+    P.dep_ptr = reinterpret_cast<const int64_t *>(base + L.dep_ptr);
+    P.dep = reinterpret_cast<const int2 *>(base + L.dep);
+    P.seg = reinterpret_cast<const uint16_t *>(base + L.seg);
+    P.cptr = reinterpret_cast<const int32_t *>(base + L.cptr);
+    P.celems = reinterpret_cast<const int32_t *>(base + L.celems);
+
+    // uploads (host vectors outlive the copies: the stream is synchronised below)
+    std::vector<int32_t> eptr32(fos->eptr.begin(), fos->eptr.end());
+    std::vector<int32_t> cptr32(fos->cptr.begin(), fos->cptr.end());
+    cudaStream_t s = c->stream;
+    GOM_CUDA(c, cudaMemsetAsync(base, 0, L.row_ptr, s)); // all state arrays
+    GOM_CUDA(c, upload_raw(base, L.row_ptr, g->row_ptr, sizeof(int64_t) * (c->n + 1), s));
+    GOM_CUDA(c, upload_raw(base, L.col, g->col, sizeof(int32_t) * g->num_adj, s));
+    GOM_CUDA(c, upload_raw(base, L.wgt, g->weight, sizeof(int32_t) * g->num_adj, s));
+    GOM_CUDA(c, upload(base, L.eptr, eptr32, s));
+    GOM_CUDA(c, upload(base, L.evars, fos->evars, s));
+    GOM_CUDA(c, upload(base, L.dep_ptr, deps.dep_ptr, s));
+    GOM_CUDA(c, upload(base, L.dep, deps.dep, s));
+    GOM_CUDA(c, upload(base, L.seg, deps.seg, s));
+    GOM_CUDA(c, upload(base, L.cptr, cptr32, s));
+    GOM_CUDA(c, upload(base, L.celems, fos->celems, s));
+
+    k_init_pop<<<c->grid_io, 256, 0, s>>>(P);
+    GOM_CUDA(c, cudaGetLastError());
+    k_fitness<<<c->grid_fit, 256, 0, s>>>(P, P.f);
+    GOM_CUDA(c, cudaGetLastError());
+    k_elite_init<<<1, 1024, 0, s>>>(P);
+    GOM_CUDA(c, cudaGetLastError());
+
+    c->events.resize(2 * static_cast<size_t>(std::max(c->k, 1)), nullptr);
+    for (auto &ev : c->events) GOM_CUDA(c, cudaEventCreate(&ev));
+    rc = build_graph(c, false, &c->graph, &c->exec);
+    if (rc) {
+        gom_destroy(ctx.release());
+        return rc;
+    }
+    GOM_CUDA(c, cudaStreamSynchronize(s));
+    *out = ctx.release();
+    return GOM_OK;
+}
+
+int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitness,
+                   gom_gen_stats_t *host_stats, int32_t *generations_run)
+{
+    if (!ctx || num_generations < 0) return GOM_E_ARG;
+    int32_t done_total = 0;
+    int32_t remaining = num_generations;
+    gom_gen_stats_t *stats_out = host_stats;
+    const bool want = host_stats || generations_run;
+    do {
+        // with host statistics the device ring bounds one chunk
+        const int32_t chunk = want ? std::min<int32_t>(remaining, kStatsCap) : remaining;
+        k_begin_call<<<1, 1, 0, ctx->stream>>>(ctx->prm, target_fitness);
+        GOM_CUDA(ctx, cudaGetLastError());
+        for (int32_t q = 0; q < chunk; ++q) {
+            if (ctx->timing) {
+                GOM_CUDA(ctx, cudaGraphLaunch(ctx->texec, ctx->stream));
+                int rc = accumulate_timing(ctx);
+                if (rc) return rc;
+            } else {
+                GOM_CUDA(ctx, cudaGraphLaunch(ctx->exec, ctx->stream));
+            }
+        }
+        remaining -= chunk;
+        if (want) {
+            int32_t run = 0;
+            int rc = read_stats(ctx, chunk, stats_out, &run);
+            if (rc) return rc;
+            done_total += run;
+            if (ctx->timing) ctx->mix_launches += static_cast<int64_t>(run) * ctx->k;
+            if (stats_out) stats_out += chunk;
+            if (run < chunk) { // target reached: zero the rest
+                if (stats_out) std::memset(stats_out, 0, sizeof(gom_gen_stats_t) * remaining);
+                break;
+            }
+        } else if (ctx->timing) {
+            int32_t run = 0;
+            int rc = read_stats(ctx, 0, nullptr, &run);
+            if (rc) return rc;
+            ctx->mix_launches += static_cast<int64_t>(run) * ctx->k;
+        }
+    } while (remaining > 0);
+    if (generations_run) *generations_run = done_total;
+    return GOM_OK;
+}
+
+int gom_fitness(gom_ctx_t *ctx, int64_t *d_fitness_out)
+{
+    if (!ctx || !d_fitness_out) return GOM_E_ARG;
+    GOM_CUDA(ctx, cudaMemsetAsync(d_fitness_out, 0, sizeof(int64_t) * ctx->p, ctx->stream));
+    k_fitness<<<ctx->grid_fit, 256, 0, ctx->stream>>>(ctx->prm, d_fitness_out);
+    GOM_CUDA(ctx, cudaGetLastError());
+    return GOM_OK;
+}
+
+int gom_get_population(gom_ctx_t *ctx, uint8_t *d_pop, int64_t *d_fit, int64_t *elite_f)
+{
+    if (!ctx) return GOM_E_ARG;
+    if (d_pop) {
+        k_export_pop<<<ctx->grid_io, 256, 0, ctx->stream>>>(ctx->prm, d_pop);
+        GOM_CUDA(ctx, cudaGetLastError());
+    }
+    if (d_fit)
+        GOM_CUDA(ctx, cudaMemcpyAsync(d_fit, ctx->prm.f, sizeof(int64_t) * ctx->p, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    if (elite_f) {
+        GomDevState st;
+        GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+        GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        *elite_f = st.fe;
+    }
+    return GOM_OK;
+}
+
+int gom_get_elite(gom_ctx_t *ctx, uint8_t *d_elite, int64_t *elite_f)
+{
+    if (!ctx) return GOM_E_ARG;
+    if (d_elite) {
+        k_export_elite<<<ctx->grid_io, 256, 0, ctx->stream>>>(ctx->prm, d_elite);
+        GOM_CUDA(ctx, cudaGetLastError());
+    }
+    return gom_get_population(ctx, nullptr, nullptr, elite_f);
+}
+
+int gom_set_population(gom_ctx_t *ctx, const uint8_t *d_pop, const uint8_t *d_elite, int64_t elite_f,
+                       int64_t generation)
+{
+    if (!ctx || !d_pop || !d_elite || generation < 0 || generation > UINT32_MAX) return GOM_E_ARG;
+    k_import_pop<<<ctx->grid_io, 256, 0, ctx->stream>>>(ctx->prm, d_pop, d_elite);
+    GOM_CUDA(ctx, cudaGetLastError());
+    GOM_CUDA(ctx, cudaMemsetAsync(ctx->prm.f, 0, sizeof(int64_t) * 32 * ctx->W, ctx->stream));
+    k_fitness<<<ctx->grid_fit, 256, 0, ctx->stream>>>(ctx->prm, ctx->prm.f);
+    GOM_CUDA(ctx, cudaGetLastError());
+    k_set_state<<<1, 256, 0, ctx->stream>>>(ctx->prm, elite_f, generation);
+    GOM_CUDA(ctx, cudaGetLastError());
+    return GOM_OK;
+}
+
+int gom_get_generation(gom_ctx_t *ctx, int64_t *generation)
+{
+    if (!ctx || !generation) return GOM_E_ARG;
+    GomDevState st;
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *generation = st.g;
+    return GOM_OK;
+}
+
+int gom_set_timing(gom_ctx_t *ctx, int32_t enable)
+{
+    if (!ctx) return GOM_E_ARG;
+    if (enable && !ctx->texec) {
+        int rc = build_graph(ctx, true, &ctx->tgraph, &ctx->texec);
+        if (rc) return rc;
+    }
+    ctx->timing = enable != 0;
+    return GOM_OK;
+}
+
+int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches)
+{
+    if (!ctx) return GOM_E_ARG;
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (mix_ms) *mix_ms = ctx->mix_ms;
+    if (mix_launches) *mix_launches = ctx->mix_launches;
+    ctx->mix_ms = 0.0;
+    ctx->mix_launches = 0;
+    return GOM_OK;
+}
+
+int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches)
+{
+    if (!ctx || !launches) return GOM_E_ARG;
+    *launches = 3 + static_cast<int64_t>(ctx->k);
+    return GOM_OK;
+}
+
+int gom_last_cuda_error(gom_ctx_t *ctx) { return ctx ? ctx->last_cuda : 0; }
+
+void gom_destroy(gom_ctx_t *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
+    if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
+    for (auto ev : ctx->events)
+        if (ev) cudaEventDestroy(ev);
+    delete ctx;
+}
+
+} // extern "C"

@@ -1,0 +1,295 @@
+// gom_host.cpp -- one-time host set-up of parallel GOM: graph validation, the
+// linkage model (FOS, Sec. 4.1), the Welsh-Powell colouring of the linkage
+// model interaction graph (LMIG, Sec. 5.2) and the per-element dependency
+// lists (the edges incident to each element, Alg. 4).
+//
+// Large instances (10^6 elements) are handled without materialising the LMIG:
+// the neighbours of an element are enumerated on the fly through a
+// variable -> elements index, and the degree pass runs on all host threads.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector_types.h>
+
+#include "gom_internal.h"
+
+namespace gomh {
+
+namespace {
+
+int num_threads()
+{
+    unsigned t = std::thread::hardware_concurrency();
+    return t == 0 ? 1 : static_cast<int>(std::min(t, 64u));
+}
+
+// Runs body(begin, end) over [0, count) split into contiguous ranges.
+template <class F>
+void parallel_ranges(int64_t count, F body)
+{
+    int nt = num_threads();
+    if (count < 4096 || nt == 1) {
+        body(int64_t(0), count);
+        return;
+    }
+    std::vector<std::thread> pool;
+    int64_t chunk = (count + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        int64_t b = t * chunk, e = std::min(count, b + chunk);
+        if (b >= e) break;
+        pool.emplace_back([=] { body(b, e); });
+    }
+    for (auto &th : pool) th.join();
+}
+
+} // namespace
+
+int validate_graph(const gom_graph_t *g)
+{
+    if (!g || g->num_vertices < 0 || g->num_adj < 0) return GOM_E_ARG;
+    const int32_t n = g->num_vertices;
+    if (!g->row_ptr) return GOM_E_ARG;
+    if (g->num_adj > 0 && (!g->col || !g->weight)) return GOM_E_ARG;
+    if (g->row_ptr[0] != 0 || g->row_ptr[n] != g->num_adj) return GOM_E_GRAPH;
+    for (int32_t u = 0; u < n; ++u)
+        if (g->row_ptr[u + 1] < g->row_ptr[u]) return GOM_E_GRAPH;
+    std::atomic<int> bad{0};
+    parallel_ranges(n, [&](int64_t b, int64_t e) {
+        for (int64_t u = b; u < e && !bad.load(std::memory_order_relaxed); ++u) {
+            const int64_t r0 = g->row_ptr[u], r1 = g->row_ptr[u + 1];
+            for (int64_t q = r0; q < r1; ++q) {
+                const int32_t v = g->col[q];
+                if (v < 0 || v >= n || v == u || (q > r0 && g->col[q - 1] >= v)) {
+                    bad = 1;
+                    break;
+                }
+                // the mirror entry (v, u) with the same weight, by binary search
+                const int32_t *lo = g->col + g->row_ptr[v], *hi = g->col + g->row_ptr[v + 1];
+                const int32_t *it = std::lower_bound(lo, hi, static_cast<int32_t>(u));
+                if (it == hi || *it != u || g->weight[it - g->col] != g->weight[q]) {
+                    bad = 1;
+                    break;
+                }
+            }
+        }
+    });
+    return bad ? GOM_E_GRAPH : GOM_OK;
+}
+
+int build_fos(const gom_graph_t *g, int32_t kind, gom_fos *out)
+{
+    const int32_t n = g->num_vertices;
+    out->n = n;
+    out->m = n;
+    out->k = -1;
+    out->eptr.assign(static_cast<size_t>(n) + 1, 0);
+    if (kind == GOM_FOS_SINGLETON) {
+        out->evars.resize(n);
+        for (int32_t j = 0; j < n; ++j) {
+            out->eptr[j + 1] = j + 1;
+            out->evars[j] = j;
+        }
+        return GOM_OK;
+    }
+    if (kind != GOM_FOS_NEIGHBOURHOOD) return GOM_E_ARG;
+    for (int32_t j = 0; j < n; ++j)
+        out->eptr[j + 1] = out->eptr[j] + (g->row_ptr[j + 1] - g->row_ptr[j]) + 1;
+    out->evars.resize(out->eptr[n]);
+    parallel_ranges(n, [&](int64_t b, int64_t e) {
+        for (int64_t j = b; j < e; ++j) {
+            int32_t *dst = out->evars.data() + out->eptr[j];
+            const int32_t *nb = g->col + g->row_ptr[j];
+            const int64_t d = g->row_ptr[j + 1] - g->row_ptr[j];
+            // the row is sorted: j goes before the first larger neighbour
+            int64_t split = std::lower_bound(nb, nb + d, static_cast<int32_t>(j)) - nb;
+            std::memcpy(dst, nb, sizeof(int32_t) * split);
+            dst[split] = static_cast<int32_t>(j);
+            std::memcpy(dst + split + 1, nb + split, sizeof(int32_t) * (d - split));
+        }
+    });
+    return GOM_OK;
+}
+
+int check_fos(int32_t n, const gom_fos &fos)
+{
+    if (fos.eptr.size() != static_cast<size_t>(fos.m) + 1 || fos.eptr[0] != 0) return GOM_E_FOS;
+    std::vector<uint8_t> covered(n, 0);
+    for (int64_t j = 0; j < fos.m; ++j) {
+        if (fos.eptr[j + 1] <= fos.eptr[j]) return GOM_E_FOS; // empty element
+        for (int64_t q = fos.eptr[j]; q < fos.eptr[j + 1]; ++q) {
+            const int32_t v = fos.evars[q];
+            if (v < 0 || v >= n) return GOM_E_FOS;
+            if (q > fos.eptr[j] && fos.evars[q - 1] >= v) return GOM_E_FOS;
+            covered[v] = 1;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (!covered[v]) return GOM_E_FOS; // FOS must be complete (Sec. 4.1)
+    return GOM_OK;
+}
+
+namespace {
+
+// variable -> elements containing it
+struct Inverted {
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> elems;
+};
+
+Inverted invert(int32_t n, const gom_fos &fos)
+{
+    Inverted inv;
+    inv.ptr.assign(static_cast<size_t>(n) + 1, 0);
+    for (int32_t v : fos.evars) inv.ptr[v + 1]++;
+    for (int32_t v = 0; v < n; ++v) inv.ptr[v + 1] += inv.ptr[v];
+    inv.elems.resize(fos.evars.size());
+    std::vector<int64_t> fill(inv.ptr.begin(), inv.ptr.end() - 1);
+    for (int64_t j = 0; j < fos.m; ++j)
+        for (int64_t q = fos.eptr[j]; q < fos.eptr[j + 1]; ++q)
+            inv.elems[fill[fos.evars[q]]++] = static_cast<int32_t>(j);
+    return inv;
+}
+
+// Calls visit(j2) once for every LMIG neighbour j2 of element j: the elements
+// holding a variable of F_j or of adj(F_j).  mark/stamp deduplicate.
+template <class V>
+void for_each_lmig_neighbour(const gom_graph_t *g, const gom_fos &fos, const Inverted &inv,
+                             int64_t j, std::vector<int64_t> &mark, V visit)
+{
+    auto touch_var = [&](int32_t v) {
+        for (int64_t r = inv.ptr[v]; r < inv.ptr[v + 1]; ++r) {
+            const int32_t j2 = inv.elems[r];
+            if (j2 != j && mark[j2] != j) {
+                mark[j2] = j;
+                visit(j2);
+            }
+        }
+    };
+    for (int64_t q = fos.eptr[j]; q < fos.eptr[j + 1]; ++q) {
+        const int32_t u = fos.evars[q];
+        touch_var(u);
+        for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; ++e) touch_var(g->col[e]);
+    }
+}
+
+} // namespace
+
+int color_fos(const gom_graph_t *g, gom_fos *fos)
+{
+    const int64_t m = fos->m;
+    const Inverted inv = invert(fos->n, *fos);
+
+    // LMIG degree of every element
+    std::vector<int64_t> deg(m, 0);
+    parallel_ranges(m, [&](int64_t b, int64_t e) {
+        std::vector<int64_t> mark(m, -1);
+        for (int64_t j = b; j < e; ++j) {
+            int64_t d = 0;
+            for_each_lmig_neighbour(g, *fos, inv, j, mark, [&](int32_t) { ++d; });
+            deg[j] = d;
+        }
+    });
+
+    // Welsh-Powell order: degree descending, index ascending
+    std::vector<int32_t> order(m);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+
+    // first fit in that order
+    std::vector<int32_t> color(m, -1);
+    std::vector<int64_t> mark(m, -1);
+    std::vector<int64_t> used; // used[c] == j: colour c taken by a neighbour of j
+    int32_t k = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        const int32_t j = order[t];
+        for_each_lmig_neighbour(g, *fos, inv, j, mark, [&](int32_t j2) {
+            const int32_t c = color[j2];
+            if (c >= 0) used[c] = j;
+        });
+        int32_t c = 0;
+        while (c < k && used[c] == j) ++c;
+        if (c == k) {
+            ++k;
+            used.push_back(-1);
+        }
+        color[j] = c;
+    }
+
+    fos->k = k;
+    fos->color_of = std::move(color);
+    fos->cptr.assign(static_cast<size_t>(k) + 1, 0);
+    for (int64_t j = 0; j < m; ++j) fos->cptr[fos->color_of[j] + 1]++;
+    for (int32_t c = 0; c < k; ++c) fos->cptr[c + 1] += fos->cptr[c];
+    fos->celems.resize(m);
+    std::vector<int64_t> fill(fos->cptr.begin(), fos->cptr.end() - 1);
+    for (int64_t j = 0; j < m; ++j) fos->celems[fill[fos->color_of[j]]++] = static_cast<int32_t>(j);
+    return GOM_OK;
+}
+
+int64_t count_deps(const gom_graph_t *g, const gom_fos &fos)
+{
+    int64_t total = 0;
+    for (int32_t v : fos.evars) total += g->row_ptr[v + 1] - g->row_ptr[v];
+    return total;
+}
+
+int build_deps(const gom_graph_t *g, const gom_fos &fos, DepTables *out)
+{
+    const int64_t m = fos.m;
+    out->dep_ptr.assign(static_cast<size_t>(m) + 1, 0);
+    out->seg.assign(fos.evars.size() + static_cast<size_t>(m), 0);
+    std::atomic<int> too_big{0};
+
+    // pass 1: entries per element (internal edges once) and the segment offsets
+    parallel_ranges(m, [&](int64_t b, int64_t e) {
+        std::vector<int32_t> pos(fos.n, -1);
+        for (int64_t j = b; j < e; ++j) {
+            const int64_t f0 = fos.eptr[j], s = fos.eptr[j + 1] - f0;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = static_cast<int32_t>(a);
+            uint16_t *seg = out->seg.data() + f0 + j;
+            int64_t cnt = 0;
+            for (int64_t a = 0; a < s; ++a) {
+                seg[a] = static_cast<uint16_t>(cnt);
+                const int32_t u = fos.evars[f0 + a];
+                for (int64_t q = g->row_ptr[u]; q < g->row_ptr[u + 1]; ++q) {
+                    const int32_t bb = pos[g->col[q]];
+                    if (bb < 0 || bb > a) ++cnt;
+                }
+                if (cnt > 65535) too_big = 1;
+            }
+            seg[s] = static_cast<uint16_t>(cnt);
+            out->dep_ptr[j + 1] = cnt;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = -1;
+        }
+    });
+    if (too_big) return GOM_E_LIMIT;
+    for (int64_t j = 0; j < m; ++j) out->dep_ptr[j + 1] += out->dep_ptr[j];
+    out->dep.resize(2 * static_cast<size_t>(out->dep_ptr[m]));
+
+    // pass 2: fill
+    parallel_ranges(m, [&](int64_t b, int64_t e) {
+        std::vector<int32_t> pos(fos.n, -1);
+        for (int64_t j = b; j < e; ++j) {
+            const int64_t f0 = fos.eptr[j], s = fos.eptr[j + 1] - f0;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = static_cast<int32_t>(a);
+            int32_t *dst = out->dep.data() + 2 * out->dep_ptr[j];
+            for (int64_t a = 0; a < s; ++a) {
+                const int32_t u = fos.evars[f0 + a];
+                for (int64_t q = g->row_ptr[u]; q < g->row_ptr[u + 1]; ++q) {
+                    const int32_t v = g->col[q];
+                    const int32_t bb = pos[v];
+                    if (bb >= 0 && bb < a) continue; // listed from the other endpoint
+                    *dst++ = bb >= 0 ? -1 - bb : v;
+                    *dst++ = g->weight[q];
+                }
+            }
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = -1;
+        }
+    });
+    return GOM_OK;
+}
+
+} // namespace gomh

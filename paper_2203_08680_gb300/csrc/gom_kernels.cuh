@@ -1,0 +1,20 @@
+// gom_kernels.cuh -- declarations of the kernels in gom_kernels.cu for the
+// host code that launches them and builds the per-generation CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gom_internal.h"
+
+__global__ void k_init_pop(GomParams P);
+__global__ void k_fitness(GomParams P, int64_t *out);
+__global__ void k_elite_init(GomParams P);
+__global__ void k_set_state(GomParams P, int64_t fe, int64_t g);
+__global__ void k_begin_call(GomParams P, int64_t target);
+__global__ void k_gen_start(GomParams P);
+__global__ void k_order(GomParams P);
+__global__ void k_mix(GomParams P, int t);
+__global__ void k_gen_end(GomParams P);
+__global__ void k_export_pop(GomParams P, uint8_t *out);
+__global__ void k_export_elite(GomParams P, uint8_t *out);
+__global__ void k_import_pop(GomParams P, const uint8_t *in, const uint8_t *elite);

@@ -1,0 +1,368 @@
+"""Thin Python binding of libgom.so (include/gom.h): same names, argument
+marshalling only.  Every step of the method runs in the library's CUDA
+kernels; there is no Python or CPU fallback, and a missing library is an
+error.
+
+Device buffers are passed as torch CUDA tensors (or raw integer device
+addresses); PyTorch only provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GOM_OK = 0
+GOM_FOS_NEIGHBOURHOOD = 0
+GOM_FOS_SINGLETON = 1
+GOM_MAX_POPULATION = 1024
+GOM_MAX_ELEMENT = 64
+INT64_MAX = 2 ** 63 - 1
+
+ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
+          -5: "GOM_E_CUDA", -6: "GOM_E_TIMEOUT", -7: "GOM_E_STATE", -8: "GOM_E_LIMIT",
+          -9: "GOM_E_FOS"}
+
+
+class GomError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({gom_strerror(code)})")
+
+
+class GraphT(C.Structure):
+    _fields_ = [("num_vertices", C.c_int32), ("num_adj", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("weight", C.c_void_p)]
+
+
+class GenStats(C.Structure):
+    _fields_ = [(name, C.c_int64) for name in
+                ("generation", "best_fitness", "elite_fitness", "trials", "donorless", "accepted",
+                 "improving", "reached_target")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/gom.h
+_P, _I32, _I64, _U64, _SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
+SIGNATURES = [
+    ("gom_build_fos", C.c_int, [_P, _I32, _I32, _P]),
+    ("gom_fos_create", C.c_int, [_I32, _I64, _P, _P, _P]),
+    ("gom_color_fos", C.c_int, [_P, _P, _P]),
+    ("gom_fos_sizes", C.c_int, [_P, _P, _P, _P]),
+    ("gom_fos_export", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("gom_fos_destroy", None, [_P]),
+    ("gom_workspace_bytes", _SZ, [_P, _P, _I32]),
+    ("gom_init_population", C.c_int, [_P, _P, _I32, _U64, _P, _SZ, _P, _P]),
+    ("gom_generation", C.c_int, [_P, _I32, _I64, _P, _P]),
+    ("gom_fitness", C.c_int, [_P, _P]),
+    ("gom_get_population", C.c_int, [_P, _P, _P, _P]),
+    ("gom_get_elite", C.c_int, [_P, _P, _P]),
+    ("gom_set_population", C.c_int, [_P, _P, _P, _I64, _I64]),
+    ("gom_get_generation", C.c_int, [_P, _P]),
+    ("gom_set_timing", C.c_int, [_P, _I32]),
+    ("gom_read_timing", C.c_int, [_P, _P, _P]),
+    ("gom_launches_per_generation", C.c_int, [_P, _P]),
+    ("gom_last_cuda_error", C.c_int, [_P]),
+    ("gom_destroy", None, [_P]),
+    ("gom_strerror", C.c_char_p, [C.c_int]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libgom.so, building it first if its sources are newer."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libgom.so not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != GOM_OK:
+        raise GomError(rc, what)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+class Graph:
+    """Keeps the CSR arrays alive for a gom_graph_t."""
+
+    def __init__(self, g):
+        self.n = int(g.n)
+        self.row_ptr = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(g.col, dtype=np.int32)
+        self.weight = np.ascontiguousarray(g.weight, dtype=np.int32)
+        self.c = GraphT(self.n, int(self.row_ptr[-1]), self.row_ptr.ctypes.data,
+                        self.col.ctypes.data if len(self.col) else None,
+                        self.weight.ctypes.data if len(self.weight) else None)
+
+    def ref(self):
+        return C.byref(self.c)
+
+
+def _graph(g):
+    return g if isinstance(g, Graph) else Graph(g)
+
+
+class Fos:
+    """Owning wrapper of a gom_fos_t handle."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gom_fos_destroy(self.h)
+            self.h = None
+
+
+class Ctx:
+    """Owning wrapper of a gom_ctx_t handle; keeps its workspace alive."""
+
+    def __init__(self, handle, workspace, n: int, p: int):
+        self.h = handle
+        self.workspace = workspace
+        self.n, self.p = n, p
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gom_destroy(self.h)
+            self.h = None
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+
+def gom_strerror(code: int) -> str:
+    return load().gom_strerror(code).decode()
+
+
+def gom_build_fos(g, kind: int = GOM_FOS_NEIGHBOURHOOD, param: int = 0) -> Fos:
+    G = _graph(g)
+    h = C.c_void_p()
+    _check(load().gom_build_fos(G.ref(), kind, param, C.byref(h)), "gom_build_fos")
+    return Fos(h)
+
+
+def gom_fos_create(num_vars: int, elem_ptr, elem_vars) -> Fos:
+    ep = np.ascontiguousarray(elem_ptr, dtype=np.int64)
+    ev = np.ascontiguousarray(elem_vars, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load().gom_fos_create(num_vars, len(ep) - 1, ep.ctypes.data,
+                                 ev.ctypes.data if len(ev) else None, C.byref(h)), "gom_fos_create")
+    return Fos(h)
+
+
+def gom_color_fos(g, fos: Fos) -> int:
+    G = _graph(g)
+    k = C.c_int32()
+    _check(load().gom_color_fos(G.ref(), fos.h, C.byref(k)), "gom_color_fos")
+    return int(k.value)
+
+
+def gom_fos_sizes(fos: Fos):
+    m, t, k = C.c_int64(), C.c_int64(), C.c_int32()
+    _check(load().gom_fos_sizes(fos.h, C.byref(m), C.byref(t), C.byref(k)), "gom_fos_sizes")
+    return int(m.value), int(t.value), int(k.value)
+
+
+def gom_fos_export(fos: Fos) -> dict:
+    m, total, k = gom_fos_sizes(fos)
+    ep = np.zeros(m + 1, dtype=np.int64)
+    ev = np.zeros(max(total, 1), dtype=np.int32)
+    out = {"elem_ptr": ep, "elem_vars": ev[:total], "k": k}
+    if k >= 0:
+        co = np.zeros(max(m, 1), dtype=np.int32)
+        cp = np.zeros(k + 1, dtype=np.int64)
+        ce = np.zeros(max(m, 1), dtype=np.int32)
+        _check(load().gom_fos_export(fos.h, ep.ctypes.data, ev.ctypes.data, co.ctypes.data, cp.ctypes.data,
+                                     ce.ctypes.data), "gom_fos_export")
+        out.update(color_of_elem=co[:m], color_ptr=cp, color_elems=ce[:m])
+    else:
+        _check(load().gom_fos_export(fos.h, ep.ctypes.data, ev.ctypes.data, None, None, None),
+               "gom_fos_export")
+    return out
+
+
+def gom_fos_destroy(fos: Fos):
+    if fos.h:
+        load().gom_fos_destroy(fos.h)
+        fos.h = None
+
+
+def gom_workspace_bytes(g, fos: Fos, pop: int) -> int:
+    G = _graph(g)
+    return int(load().gom_workspace_bytes(G.ref(), fos.h, pop))
+
+
+def gom_init_population(g, fos: Fos, pop: int, seed: int, workspace, ws_bytes: int = None,
+                        stream=None) -> Ctx:
+    """workspace: a CUDA tensor (kept alive by the handle) or a device address."""
+    G = _graph(g)
+    if ws_bytes is None:
+        ws_bytes = workspace.numel() * workspace.element_size()
+    h = C.c_void_p()
+    _check(load().gom_init_population(G.ref(), fos.h, pop, seed & 0xFFFFFFFFFFFFFFFF, _ptr(workspace),
+                                      ws_bytes, _stream(stream), C.byref(h)), "gom_init_population")
+    return Ctx(h, workspace, G.n, pop)
+
+
+def gom_generation(ctx: Ctx, num_generations: int, target_fitness: int = INT64_MAX,
+                   want_stats: bool = True):
+    """Returns (list of per-generation stats dicts, generations run); with
+    want_stats=False only enqueues and returns (None, None)."""
+    if not want_stats:
+        _check(load().gom_generation(ctx.h, num_generations, target_fitness, None, None), "gom_generation")
+        return None, None
+    arr = (GenStats * max(num_generations, 1))()
+    run = C.c_int32()
+    _check(load().gom_generation(ctx.h, num_generations, target_fitness, arr, C.byref(run)), "gom_generation")
+    return [arr[q].as_dict() for q in range(run.value)], int(run.value)
+
+
+def gom_fitness(ctx: Ctx, d_fitness_out):
+    _check(load().gom_fitness(ctx.h, _ptr(d_fitness_out)), "gom_fitness")
+
+
+def gom_get_population(ctx: Ctx, d_pop=None, d_fit=None, want_elite: bool = True):
+    fe = C.c_int64()
+    _check(load().gom_get_population(ctx.h, _ptr(d_pop), _ptr(d_fit), C.byref(fe) if want_elite else None),
+           "gom_get_population")
+    return int(fe.value) if want_elite else None
+
+
+def gom_get_elite(ctx: Ctx, d_elite=None, want_elite: bool = True):
+    fe = C.c_int64()
+    _check(load().gom_get_elite(ctx.h, _ptr(d_elite), C.byref(fe) if want_elite else None), "gom_get_elite")
+    return int(fe.value) if want_elite else None
+
+
+def gom_set_population(ctx: Ctx, d_pop, d_elite, elite_f: int, generation: int):
+    _check(load().gom_set_population(ctx.h, _ptr(d_pop), _ptr(d_elite), elite_f, generation),
+           "gom_set_population")
+
+
+def gom_get_generation(ctx: Ctx) -> int:
+    g = C.c_int64()
+    _check(load().gom_get_generation(ctx.h, C.byref(g)), "gom_get_generation")
+    return int(g.value)
+
+
+def gom_set_timing(ctx: Ctx, enable: bool):
+    _check(load().gom_set_timing(ctx.h, 1 if enable else 0), "gom_set_timing")
+
+
+def gom_read_timing(ctx: Ctx):
+    ms, n = C.c_double(), C.c_int64()
+    _check(load().gom_read_timing(ctx.h, C.byref(ms), C.byref(n)), "gom_read_timing")
+    return float(ms.value), int(n.value)
+
+
+def gom_launches_per_generation(ctx: Ctx) -> int:
+    n = C.c_int64()
+    _check(load().gom_launches_per_generation(ctx.h, C.byref(n)), "gom_launches_per_generation")
+    return int(n.value)
+
+
+def gom_last_cuda_error(ctx: Ctx) -> int:
+    return int(load().gom_last_cuda_error(ctx.h))
+
+
+def gom_destroy(ctx: Ctx):
+    if ctx.h:
+        load().gom_destroy(ctx.h)
+        ctx.h = None
+
+
+# ---------------------------------------------------------------------------
+# convenience: a population with a torch-allocated workspace
+
+class Population:
+    """One GOM population on the current CUDA device.  Allocates the device
+    workspace with torch and drives the C ABI above."""
+
+    def __init__(self, graph, pop: int, seed: int, kind: int = GOM_FOS_NEIGHBOURHOOD, fos: Fos = None,
+                 stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.graph = _graph(graph)
+        if fos is None:
+            fos = gom_build_fos(self.graph, kind)
+            self.k = gom_color_fos(self.graph, fos)
+        else:
+            self.k = gom_fos_sizes(fos)[2]
+            if self.k < 0:
+                self.k = gom_color_fos(self.graph, fos)
+        self.fos = fos
+        self.n, self.p = self.graph.n, pop
+        self.m = gom_fos_sizes(fos)[0]
+        self.device = torch.device(device or "cuda")
+        nbytes = gom_workspace_bytes(self.graph, fos, pop)
+        if nbytes == 0:
+            raise GomError(-1, "gom_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self.stream = stream
+        self.ctx = gom_init_population(self.graph, fos, pop, seed, self.workspace.data_ptr() + off, nbytes,
+                                       stream)
+        self.ctx.workspace = self.workspace
+
+    def generation(self, num: int = 1, target: int = INT64_MAX, want_stats: bool = True):
+        return gom_generation(self.ctx, num, target, want_stats)
+
+    def population(self):
+        t = self.torch
+        pop = t.empty((self.p, self.n), dtype=t.uint8, device=self.device)
+        fit = t.empty(self.p, dtype=t.int64, device=self.device)
+        fe = gom_get_population(self.ctx, pop, fit, True)
+        return pop, fit, fe
+
+    def elite(self):
+        t = self.torch
+        xe = t.empty(self.n, dtype=t.uint8, device=self.device)
+        fe = gom_get_elite(self.ctx, xe, True)
+        return xe, fe
+
+    def fitness(self):
+        t = self.torch
+        out = t.empty(self.p, dtype=t.int64, device=self.device)
+        gom_fitness(self.ctx, out)
+        return out
+
+    def set_population(self, pop, elite, elite_f: int, generation: int):
+        gom_set_population(self.ctx, pop, elite, elite_f, generation)
+
+    def generation_counter(self) -> int:
+        return gom_get_generation(self.ctx)

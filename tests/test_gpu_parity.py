@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit for
+bit (population, int64 fitness, elitist and counters), on seeded synthetic
+instances small enough for the oracle, spanning several tiles and ragged
+population words, plus the method's degenerate cases."""
+import numpy as np
+import pytest
+
+from paper_2203_08680_gb300 import gom
+from paper_2203_08680_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+STAT_KEYS = [("generation", "generation"), ("best_fitness", "best"), ("elite_fitness", "elite"),
+             ("trials", "trials"), ("donorless", "donorless"), ("accepted", "accepted"),
+             ("improving", "improving"), ("reached_target", "reached")]
+
+
+def _oracle_run(oracle, g, p, seed, kind=0):
+    ep, ev = oracle.build_fos(g, kind)
+    k, co = oracle.color(g, ep, ev)
+    return oracle.Run(g, ep, ev, co, k, p, seed), k
+
+
+def _gpu_state(P):
+    pop, fit, fe = P.population()
+    xe, fe2 = P.elite()
+    assert fe == fe2
+    return {"pop": pop.cpu().numpy(), "f": fit.cpu().numpy(), "xe": xe.cpu().numpy(), "fe": fe}
+
+
+def _assert_same_state(gs, os_, where=""):
+    assert np.array_equal(gs["f"], os_["f"]), where
+    assert gs["fe"] == os_["fe"], where
+    assert np.array_equal(gs["pop"], os_["pop"]), where
+    assert np.array_equal(gs["xe"], os_["xe"]), where
+
+
+def _assert_same_stats(gst, ost):
+    for gk, ok in STAT_KEYS:
+        assert gst[gk] == ost[ok], (gk, gst, ost)
+
+
+def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MAX):
+    P = gom.Population(g, p, seed, kind)
+    run, k = _oracle_run(oracle, g, p, seed, kind)
+    assert P.k == k
+    _assert_same_state(_gpu_state(P), run.get(), "init")
+    for gen in range(gens):
+        gst, nrun = P.generation(1, target)
+        ost = run.generation(target)
+        assert nrun == 1
+        _assert_same_stats(gst[0], ost)
+        if (gen + 1) % check_every == 0 or gen == gens - 1:
+            _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")
+            # incremental fitness equals full re-evaluation on the device
+            assert np.array_equal(P.fitness().cpu().numpy(), run.get()["f"])
+    return P, run
+
+
+def test_config_torus10_p16_every_generation(oracle):
+    """2D torus 10x10, int32 weights U[1,100], p = 16, 20 generations, seed 1."""
+    _parity(oracle, I.torus2d(10), 16, 1, 20)
+
+
+def test_config_torus100_p64(oracle):
+    """2D torus 100x100, weights U[1,100], p = 64 (oracle-sized run length)."""
+    _parity(oracle, I.torus2d(100), 64, 1, 30, check_every=5)
+
+
+@pytest.mark.parametrize("p", [2, 3, 31, 33, 100, 257])
+def test_ragged_population_sizes(oracle, p):
+    _parity(oracle, I.torus2d(9, seed=p), p, 11 + p, 6)
+
+
+def test_torus3d_ragged(oracle):
+    _parity(oracle, I.torus3d(8, seed=2), 100, 5, 8, check_every=2)
+
+
+@pytest.mark.parametrize("d,p", [(3, 128), (6, 40), (12, 96)])
+def test_random_regular(oracle, d, p):
+    _parity(oracle, I.random_regular(2000, d, seed=d), p, 3, 5)
+
+
+def test_singleton_fos(oracle):
+    _parity(oracle, I.random_regular(500, 4, seed=1), 64, 2, 8, kind=gom.GOM_FOS_SINGLETON)
+
+
+def test_negative_weights(oracle):
+    _parity(oracle, I.random_regular(400, 5, seed=3, wmin=-100, wmax=100), 48, 9, 8)
+
+
+def test_max_population(oracle):
+    _parity(oracle, I.torus2d(6, seed=4), 1024, 21, 3)
+
+
+def test_empty_graph_all_neutral(oracle):
+    _parity(oracle, I.empty_graph(70), 40, 5, 3, kind=gom.GOM_FOS_SINGLETON)
+
+
+def test_unit_weight_torus_reaches_closed_form(oracle):
+    """Even torus, unit weights: the optimum is every edge cut (2 L^2); the
+    target stop must match the oracle generation by generation."""
+    g = I.torus2d(8, unit=True)
+    target = 2 * 8 * 8
+    P = gom.Population(g, 32, 3)
+    run, _ = _oracle_run(oracle, g, 32, 3)
+    gst, nrun = P.generation(200, target)
+    ost = run.run(200, target)
+    assert nrun == len(ost)
+    for a, b in zip(gst, ost):
+        _assert_same_stats(a, b)
+    _assert_same_state(_gpu_state(P), run.get())
+    if ost[-1]["reached"]:
+        assert gst[-1]["best_fitness"] == target
+
+
+def test_target_stop_midway(oracle):
+    g = I.torus2d(20, seed=3)
+    run, _ = _oracle_run(oracle, g, 24, 4)
+    probe = run.run(6)
+    target = probe[3]["best"]  # reached at or before generation 3
+    P = gom.Population(g, 24, 4)
+    run2, _ = _oracle_run(oracle, g, 24, 4)
+    gst, nrun = P.generation(10, target)
+    ost = run2.run(10, target)
+    assert nrun == len(ost) <= 4
+    for a, b in zip(gst, ost):
+        _assert_same_stats(a, b)
+    _assert_same_state(_gpu_state(P), run2.get())
+    # the next call starts from where this one stopped
+    gst2, nrun2 = P.generation(2)
+    ost2 = run2.run(2)
+    assert nrun2 == 2
+    for a, b in zip(gst2, ost2):
+        _assert_same_stats(a, b)
+
+
+def test_split_calls_equal_one_call():
+    g = I.random_regular(1000, 4, seed=8)
+    A = gom.Population(g, 64, 5)
+    A.generation(12)
+    B = gom.Population(g, 64, 5)
+    for n in (3, 4, 5):
+        B.generation(n)
+    sa, sb = _gpu_state(A), _gpu_state(B)
+    for key in ("pop", "f", "xe"):
+        assert np.array_equal(sa[key], sb[key])
+    assert sa["fe"] == sb["fe"] and A.generation_counter() == B.generation_counter() == 12
+
+
+def test_async_calls_equal_sync_calls():
+    g = I.torus2d(30, seed=2)
+    A = gom.Population(g, 48, 6)
+    A.generation(7)
+    B = gom.Population(g, 48, 6)
+    B.generation(7, want_stats=False)
+    torch.cuda.synchronize()
+    sa, sb = _gpu_state(A), _gpu_state(B)
+    assert np.array_equal(sa["pop"], sb["pop"]) and np.array_equal(sa["f"], sb["f"])
+
+
+def test_resume_from_oracle_state(oracle):
+    """Checkpoint/resume: a state written into the GPU continues exactly as the
+    oracle continues from the same state."""
+    g = I.random_regular(600, 5, seed=4)
+    run, _ = _oracle_run(oracle, g, 40, 7)
+    for _ in range(3):
+        run.generation()
+    s = run.get()
+    P = gom.Population(g, 40, 7)
+    dev = torch.device("cuda")
+    P.set_population(torch.from_numpy(s["pop"]).to(dev), torch.from_numpy(s["xe"]).to(dev), s["fe"], s["g"])
+    assert np.array_equal(P.fitness().cpu().numpy(), s["f"])
+    for _ in range(4):
+        gst, _ = P.generation(1)
+        _assert_same_stats(gst[0], run.generation())
+    _assert_same_state(_gpu_state(P), run.get())
+
+
+def test_identical_population_is_all_donorless(oracle):
+    g = I.torus2d(12, seed=6)
+    run, _ = _oracle_run(oracle, g, 36, 2)
+    x = run.get()["pop"][5]
+    pop = np.tile(x, (36, 1))
+    fx = oracle.cut_value(g, x)
+    P = gom.Population(g, 36, 2)
+    dev = torch.device("cuda")
+    P.set_population(torch.from_numpy(pop).to(dev), torch.from_numpy(x).to(dev), fx, 0)
+    gst, _ = P.generation(1)
+    assert gst[0]["donorless"] == gst[0]["trials"] == 36 * g.n
+    assert gst[0]["accepted"] == 0
+    assert np.array_equal(_gpu_state(P)["pop"], pop)
+
+
+def test_timing_mode_keeps_results_and_counts_launches(oracle):
+    g = I.torus2d(16, seed=7)
+    A = gom.Population(g, 64, 8)
+    gom.gom_set_timing(A.ctx, True)
+    A.generation(5)
+    ms, launches = gom.gom_read_timing(A.ctx)
+    assert launches == 5 * A.k and ms > 0
+    B = gom.Population(g, 64, 8)
+    B.generation(5)
+    sa, sb = _gpu_state(A), _gpu_state(B)
+    assert np.array_equal(sa["pop"], sb["pop"]) and np.array_equal(sa["f"], sb["f"])
+    assert gom.gom_launches_per_generation(A.ctx) == A.k + 3
+
+
+def test_user_stream(oracle):
+    g = I.torus2d(10)
+    s = torch.cuda.Stream()
+    P = gom.Population(g, 16, 1, stream=s)
+    run, _ = _oracle_run(oracle, g, 16, 1)
+    for _ in range(5):
+        gst, _ = P.generation(1)
+        _assert_same_stats(gst[0], run.generation())
+    with torch.cuda.stream(s):
+        st = _gpu_state(P)
+    torch.cuda.synchronize()
+    _assert_same_state(st, run.get())
