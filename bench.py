@@ -283,6 +283,28 @@ def run_gpu(args, wl, rank, world, local):
 
     # time to target: fresh population, within 0.1% of the closed-form optimum
     # (every edge cut on an even torus) or a generation cap
+    ttt = None
+    if not args.no_ttt:
+        ttt = time_to_target(args, g, p, seed, stream, wl)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step)
+
+    # CPU baseline: the oracle, bounded sample, rank 0
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds)
+        cpu = {"value": cval, "unit": "trials/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, single thread)"}
+    return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, mix_ms, mix_launches, mix_bytes,
+                  ttt, e2e, launches_per_step, clk, cpu)
+
+
+def time_to_target(args, g, p, seed, stream, wl):
+    import torch
+
+    from paper_2203_08680_gb300 import gom
     tw = g.total_weight()
     target = int(math.ceil(0.999 * tw))
     P2 = gom.Population(g, p, seed, stream=stream)
@@ -297,9 +319,15 @@ def run_gpu(args, wl, rank, world, local):
            "best": stats[-1]["best_fitness"] if stats else None, "ms": e0.elapsed_time(e1),
            "max_generations": args.ttt_gens}
     del P2
+    return ttt
 
-    # end to end through the C ABI from host buffers: FOS, colouring, upload,
-    # generations with host statistics, population and fitness back to host
+
+def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step):
+    """End to end through the C ABI from host buffers: FOS, colouring, upload,
+    generations with host statistics, population and fitness back to host."""
+    import torch
+
+    from paper_2203_08680_gb300 import gom
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     G = gom.Graph(g)
@@ -323,14 +351,12 @@ def run_gpu(args, wl, rank, world, local):
            ex["elem_vars"].nbytes + 8 * (m + 1) + 8 * int(np.diff(G.row_ptr).sum()) + 2 * (len(ex["elem_vars"]) + m))
     d2h = 64 * args.steps + p * g.n + 8 * p
     del ctx, ws
+    return {"value": trials_per_step * args.steps * world / e2e_s, "unit": "trials/s",
+            "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
 
-    # CPU baseline: the oracle, bounded sample, rank 0
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds)
-        cpu = {"value": cval, "unit": "trials/s", "cores": 1, "kind": "oracle",
-               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, single thread)"}
 
+def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, mix_ms, mix_launches, mix_bytes, ttt, e2e,
+           launches_per_step, clk, cpu):
     peak, peak_kind = peaks()
     mix_avg_ms = mix_ms / max(mix_launches, 1)
     bytes_per_launch = mix_bytes / k
@@ -348,8 +374,7 @@ def run_gpu(args, wl, rank, world, local):
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": mix_avg_ms, "launches_timed": mix_launches},
         "time_to_target": ttt,
-        "e2e": {"value": trials_per_step * args.steps * world / e2e_s, "unit": "trials/s",
-                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)},
+        "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps + args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -369,6 +394,8 @@ def main():
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

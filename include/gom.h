@@ -207,9 +207,12 @@ int gom_get_generation(gom_ctx_t *ctx, int64_t *generation);
 
 /*
  * Kernel timing.  gom_set_timing(ctx, 1) makes each following generation
- * record a CUDA event pair around every mixing launch; gom_read_timing waits
- * for the stream and adds the measured milliseconds and the launch count since
- * the last read.  Timing adds event records to the generation; off by default.
+ * record a CUDA event pair around every mixing launch (event-record nodes in
+ * the generation's graph; off by default).  A timed generation's events are
+ * read when the next timed generation is enqueued or by gom_read_timing,
+ * which waits for the stream and returns the summed mixing-kernel
+ * milliseconds and the number of mixing launches run since timing was enabled
+ * or last read.
  */
 int gom_set_timing(gom_ctx_t *ctx, int32_t enable);
 int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches);

@@ -15,7 +15,7 @@
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxMixBlocks = 4096; // per-block partial slots reserved in the workspace
+constexpr int kMaxMixBlocks = 8192;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, stats, order, part_f, part_cnt;
+    size_t O, P, f, eqw, xe, st, stats, order;
     size_t row_ptr, col, wgt, eptr, evars, dep_ptr, dep, seg, cptr, celems;
     size_t total;
 };
@@ -52,8 +52,6 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.st = take(sizeof(GomDevState));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
-    L.part_f = take(sizeof(int64_t) * 32 * W * kMaxMixBlocks);
-    L.part_cnt = take(sizeof(int64_t) * 4 * kMaxMixBlocks);
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
@@ -84,8 +82,9 @@ struct gom_ctx {
     cudaGraphExec_t texec = nullptr;
     std::vector<cudaEvent_t> events;
     bool timing = false;
+    bool timing_pending = false; // the events hold a generation not yet added to mix_ms
     double mix_ms = 0.0;
-    int64_t mix_launches = 0;
+    int64_t timing_g0 = 0;       // generation counter when timing was (re)started
     int last_cuda = 0;
 };
 
@@ -206,6 +205,8 @@ int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *
 
 int accumulate_timing(gom_ctx *ctx)
 {
+    if (!ctx->timing_pending) return GOM_OK;
+    ctx->timing_pending = false;
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (int t = 0; t < ctx->k; ++t) {
         float ms = 0.f;
@@ -382,7 +383,6 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.Wv = (pop + 31) / 32;
     P.m = static_cast<int32_t>(fos->m);
     P.k = fos->k;
-    P.nblk_mix = c->grid_mix;
     P.seed = seed;
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);
@@ -392,8 +392,6 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.st = reinterpret_cast<GomDevState *>(base + L.st);
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
-    P.part_f = reinterpret_cast<int64_t *>(base + L.part_f);
-    P.part_cnt = reinterpret_cast<int64_t *>(base + L.part_cnt);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);
@@ -455,9 +453,11 @@ int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitne
         GOM_CUDA(ctx, cudaGetLastError());
         for (int32_t q = 0; q < chunk; ++q) {
             if (ctx->timing) {
-                GOM_CUDA(ctx, cudaGraphLaunch(ctx->texec, ctx->stream));
+                // the events of the previous timed generation are read first
                 int rc = accumulate_timing(ctx);
                 if (rc) return rc;
+                GOM_CUDA(ctx, cudaGraphLaunch(ctx->texec, ctx->stream));
+                ctx->timing_pending = true;
             } else {
                 GOM_CUDA(ctx, cudaGraphLaunch(ctx->exec, ctx->stream));
             }
@@ -468,17 +468,11 @@ int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitne
             int rc = read_stats(ctx, chunk, stats_out, &run);
             if (rc) return rc;
             done_total += run;
-            if (ctx->timing) ctx->mix_launches += static_cast<int64_t>(run) * ctx->k;
             if (stats_out) stats_out += chunk;
             if (run < chunk) { // target reached: zero the rest
                 if (stats_out) std::memset(stats_out, 0, sizeof(gom_gen_stats_t) * remaining);
                 break;
             }
-        } else if (ctx->timing) {
-            int32_t run = 0;
-            int rc = read_stats(ctx, 0, nullptr, &run);
-            if (rc) return rc;
-            ctx->mix_launches += static_cast<int64_t>(run) * ctx->k;
         }
     } while (remaining > 0);
     if (generations_run) *generations_run = done_total;
@@ -554,6 +548,13 @@ int gom_set_timing(gom_ctx_t *ctx, int32_t enable)
         int rc = build_graph(ctx, true, &ctx->tgraph, &ctx->texec);
         if (rc) return rc;
     }
+    int rc = accumulate_timing(ctx);
+    if (rc) return rc;
+    if (enable && !ctx->timing) {
+        ctx->mix_ms = 0.0;
+        rc = gom_get_generation(ctx, &ctx->timing_g0);
+        if (rc) return rc;
+    }
     ctx->timing = enable != 0;
     return GOM_OK;
 }
@@ -561,11 +562,15 @@ int gom_set_timing(gom_ctx_t *ctx, int32_t enable)
 int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches)
 {
     if (!ctx) return GOM_E_ARG;
-    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int rc = accumulate_timing(ctx);
+    if (rc) return rc;
+    int64_t g = 0;
+    rc = gom_get_generation(ctx, &g);
+    if (rc) return rc;
     if (mix_ms) *mix_ms = ctx->mix_ms;
-    if (mix_launches) *mix_launches = ctx->mix_launches;
+    if (mix_launches) *mix_launches = (g - ctx->timing_g0) * ctx->k;
     ctx->mix_ms = 0.0;
-    ctx->mix_launches = 0;
+    ctx->timing_g0 = g;
     return GOM_OK;
 }
 

@@ -152,19 +152,23 @@ Inverted invert(int32_t n, const gom_fos &fos)
     return inv;
 }
 
-// Calls visit(j2) once for every LMIG neighbour j2 of element j: the elements
-// holding a variable of F_j or of adj(F_j).  mark/stamp deduplicate.
+// Calls visit(j2) for every LMIG neighbour j2 of element j: the elements
+// holding a variable of F_j or of adj(F_j).  With a mark array each neighbour
+// is visited once; without one (mark == nullptr) a neighbour may be visited
+// several times, which is enough for first-fit colouring.
 template <class V>
 void for_each_lmig_neighbour(const gom_graph_t *g, const gom_fos &fos, const Inverted &inv,
-                             int64_t j, std::vector<int64_t> &mark, V visit)
+                             int64_t j, int32_t *mark, V visit)
 {
     auto touch_var = [&](int32_t v) {
         for (int64_t r = inv.ptr[v]; r < inv.ptr[v + 1]; ++r) {
             const int32_t j2 = inv.elems[r];
-            if (j2 != j && mark[j2] != j) {
-                mark[j2] = j;
-                visit(j2);
+            if (j2 == j) continue;
+            if (mark) {
+                if (mark[j2] == j) continue;
+                mark[j2] = static_cast<int32_t>(j);
             }
+            visit(j2);
         }
     };
     for (int64_t q = fos.eptr[j]; q < fos.eptr[j + 1]; ++q) {
@@ -184,10 +188,10 @@ int color_fos(const gom_graph_t *g, gom_fos *fos)
     // LMIG degree of every element
     std::vector<int64_t> deg(m, 0);
     parallel_ranges(m, [&](int64_t b, int64_t e) {
-        std::vector<int64_t> mark(m, -1);
+        std::vector<int32_t> mark(m, -1);
         for (int64_t j = b; j < e; ++j) {
             int64_t d = 0;
-            for_each_lmig_neighbour(g, *fos, inv, j, mark, [&](int32_t) { ++d; });
+            for_each_lmig_neighbour(g, *fos, inv, j, mark.data(), [&](int32_t) { ++d; });
             deg[j] = d;
         }
     });
@@ -200,12 +204,11 @@ int color_fos(const gom_graph_t *g, gom_fos *fos)
 
     // first fit in that order
     std::vector<int32_t> color(m, -1);
-    std::vector<int64_t> mark(m, -1);
     std::vector<int64_t> used; // used[c] == j: colour c taken by a neighbour of j
     int32_t k = 0;
     for (int64_t t = 0; t < m; ++t) {
         const int32_t j = order[t];
-        for_each_lmig_neighbour(g, *fos, inv, j, mark, [&](int32_t j2) {
+        for_each_lmig_neighbour(g, *fos, inv, j, nullptr, [&](int32_t j2) {
             const int32_t c = color[j2];
             if (c >= 0) used[c] = j;
         });

@@ -60,6 +60,7 @@ struct GomDevState {
     int64_t best;      // best fitness after the last generation
     int32_t err;       // device-side error word (0 = none)
     uint32_t call_g0;  // generation counter at the start of the current call
+    int64_t cnt[4];    // counters of the running generation: donorless, accepted, improving
 };
 
 struct GomDevStats { // mirrors gom_gen_stats_t
@@ -79,8 +80,7 @@ struct GomParams {
     int32_t Wv;        // words holding valid individuals, ceil(p/32)
     int32_t m;         // FOS elements
     int32_t k;         // colours
-    int32_t nblk_mix;  // grid of the mixing kernel (partial-sum slots)
-    int32_t pad0;
+    int32_t pad0, pad1;
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population
@@ -90,8 +90,6 @@ struct GomParams {
     GomDevState *st;
     GomDevStats *stats;  // [kStatsCap] ring indexed by generation
     int32_t *order;      // [k] colour visited at position t
-    int64_t *part_f;     // [nblk_mix][32W] per-block fitness deltas of a generation
-    int64_t *part_cnt;   // [nblk_mix][4] donorless, accepted, improving, spare
     const int64_t *row_ptr;
     const int32_t *col;
     const int32_t *wgt;

@@ -180,6 +180,7 @@ __global__ void k_set_state(GomParams P, int64_t fe, int64_t g)
         P.st->improved = 0;
         P.st->done = 0;
         P.st->g = (uint32_t)g;
+        P.st->cnt[0] = P.st->cnt[1] = P.st->cnt[2] = 0;
     }
     for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
 }
@@ -268,8 +269,9 @@ __global__ void k_order(GomParams P)
 //            edge's cut contribution (Sec. 2.2; edges inside F_j listed once)
 //  accept:   delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
 //  write:    one ballot per variable of F_j; lane 0 XORs the accepted flips
-// Fitness deltas and counters are summed per block in shared memory and added
-// into this block's slot of part_f / part_cnt, folded by k_gen_end.
+// Fitness deltas and counters are summed per block in shared memory, then one
+// atomic add per individual (and per counter) per block: integer adds, so the
+// result does not depend on their order.
 __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
 {
     __shared__ long long s_f[1024];
@@ -391,40 +393,19 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
         atomicAdd(&s_cnt[2], (unsigned long long)n_imp);
     }
     __syncthreads();
-    int64_t *pf = P.part_f + (int64_t)blockIdx.x * np;
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
         const long long v = s_f[q];
-        if (v) pf[q] += v;
+        if (v) atomicAdd((unsigned long long *)&P.f[q], (unsigned long long)v);
     }
-    if (threadIdx.x < 3) P.part_cnt[4 * (int64_t)blockIdx.x + threadIdx.x] += (int64_t)s_cnt[threadIdx.x];
+    if (threadIdx.x < 3 && s_cnt[threadIdx.x])
+        atomicAdd((unsigned long long *)&P.st->cnt[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
-// Generation end: fold the per-block fitness deltas, elitist update (strict
-// improvement, lowest index; Sec. 4), counters, target check, g += 1.
+// Generation end: elitist update (strict improvement, lowest index; Sec. 4),
+// counters, target check, g += 1.
 __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 {
-    __shared__ long long s_cnt[3];
     if (P.st->done) return;
-    const int np = 32 * P.W;
-    for (int i = threadIdx.x; i < P.p; i += blockDim.x) {
-        long long s = 0;
-        for (int b = 0; b < P.nblk_mix; ++b) {
-            int64_t *q = P.part_f + (int64_t)b * np + i;
-            s += *q;
-            *q = 0;
-        }
-        P.f[i] += s;
-    }
-    if (threadIdx.x < 3) {
-        long long s = 0;
-        for (int b = 0; b < P.nblk_mix; ++b) {
-            int64_t *q = P.part_cnt + 4 * (int64_t)b + threadIdx.x;
-            s += *q;
-            *q = 0;
-        }
-        s_cnt[threadIdx.x] = s;
-    }
-    __syncthreads();
     int64_t best;
     int arg;
     block_argmax(P.f, P.p, &best, &arg);
@@ -441,10 +422,11 @@ __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
         S.best = best;
         S.elite = st->fe;
         S.trials = (int64_t)P.p * P.m;
-        S.donorless = s_cnt[0];
-        S.accepted = s_cnt[1];
-        S.improving = s_cnt[2];
+        S.donorless = st->cnt[0];
+        S.accepted = st->cnt[1];
+        S.improving = st->cnt[2];
         S.reached = best >= st->target;
+        st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
         st->done = best >= st->target;
         st->g += 1;
     }
