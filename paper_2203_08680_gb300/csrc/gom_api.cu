@@ -29,7 +29,7 @@ int words_for(int32_t p)
 // Byte offsets of every device array inside the workspace.
 struct Layout {
     size_t O, P, f, eqw, xe, st, stats, order;
-    size_t row_ptr, col, wgt, eptr, evars, dep_ptr, dep, seg, cptr, celems;
+    size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
 
@@ -55,13 +55,12 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
-    L.eptr = take(sizeof(int32_t) * (m + 1));
-    L.evars = take(sizeof(int32_t) * total_vars);
-    L.dep_ptr = take(sizeof(int64_t) * (m + 1));
-    L.dep = take(sizeof(int32_t) * 2 * ndeps);
+    L.hdr = take(sizeof(int32_t) * 4 * m);
+    L.fv = take(sizeof(int32_t) * total_vars);
+    L.wout = take(sizeof(int64_t) * total_vars);
     L.seg = take(sizeof(uint16_t) * (total_vars + m));
+    L.dep = take(sizeof(int32_t) * 2 * ndeps);
     L.cptr = take(sizeof(int32_t) * (std::max<int32_t>(k, 0) + 1));
-    L.celems = take(sizeof(int32_t) * m);
     L.total = off;
     return L;
 }
@@ -75,6 +74,7 @@ struct gom_ctx {
     int64_t m = 0;
     int sms = 0;
     int grid_mix = 0, grid_fit = 0, grid_start = 0, grid_order = 0, grid_io = 0;
+    const void *mix_fn = nullptr; // k_mix instance for this population and FOS
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -153,7 +153,7 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         }
         ts[t] = t;
         void *args2[] = {&prm, &ts[t]};
-        e = add_kernel(g, &node, last, (const void *)k_mix, ctx->grid_mix, kMixThreads, 0, args2);
+        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, kMixThreads, 0, args2);
         if (e == cudaSuccess && timed) {
             last = node;
             e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
@@ -336,9 +336,10 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     if (!d_workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
         return GOM_E_WORKSPACE;
 
-    gomh::DepTables deps;
-    rc = gomh::build_deps(g, *fos, &deps);
+    gomh::ElemTables tabs;
+    rc = gomh::build_elem_tables(g, *fos, &tabs);
     if (rc) return rc;
+    if (static_cast<int64_t>(g->num_vertices) * words_for(pop) >= INT_MAX) return GOM_E_LIMIT;
 
     std::unique_ptr<gom_ctx> ctx(new (std::nothrow) gom_ctx());
     if (!ctx) return GOM_E_ARG;
@@ -350,22 +351,29 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->m = fos->m;
     c->k = fos->k;
 
+    // kernel instance: words per item, mask and delta widths
+    const int wpi = std::min(c->W, 4);
+    const bool narrow = tabs.max_s <= 32 && tabs.max_abs_w < (int64_t(1) << 30);
+    c->mix_fn = gom_mix_kernel(wpi, narrow);
+
     int dev = 0;
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
     int occ = 0;
-    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mix, kMixThreads, 0));
+    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, kMixThreads, 0));
     occ = std::max(occ, 1);
-    // mixing grid: enough warps for the largest group, a multiple of W warps
+    // mixing grid: enough warps for the largest group; a multiple of G = W / wpi warps
     int64_t max_group = 1;
     for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
     const int warps_per_block = kMixThreads / 32;
-    const int64_t need_blocks = (max_group * c->W + warps_per_block - 1) / warps_per_block;
+    const int G = c->W / wpi;
+    const int64_t need_blocks = (max_group * G + warps_per_block - 1) / warps_per_block;
     int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
     grid = std::min<int64_t>(grid, kMaxMixBlocks);
-    const int blk_mult = std::max(1, c->W / warps_per_block);
-    grid = std::max<int64_t>(blk_mult, grid / blk_mult * blk_mult);
+    const int mix_mult = std::max(1, G / warps_per_block);
+    grid = std::max<int64_t>(mix_mult, grid / mix_mult * mix_mult);
     c->grid_mix = static_cast<int>(grid);
+    const int blk_mult = std::max(1, c->W / warps_per_block);
     c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
     c->grid_start = c->sms * 4;
     c->grid_io = c->sms * 4;
@@ -395,29 +403,26 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);
-    P.eptr = reinterpret_cast<const int32_t *>(base + L.eptr);
-    P.evars = reinterpret_cast<const int32_t *>(base + L.evars);
-    P.dep_ptr = reinterpret_cast<const int64_t *>(base + L.dep_ptr);
-    P.dep = reinterpret_cast<const int2 *>(base + L.dep);
+    P.hdr = reinterpret_cast<const int4 *>(base + L.hdr);
+    P.fv = reinterpret_cast<const int32_t *>(base + L.fv);
+    P.wout = reinterpret_cast<const int64_t *>(base + L.wout);
     P.seg = reinterpret_cast<const uint16_t *>(base + L.seg);
+    P.dep = reinterpret_cast<const int2 *>(base + L.dep);
     P.cptr = reinterpret_cast<const int32_t *>(base + L.cptr);
-    P.celems = reinterpret_cast<const int32_t *>(base + L.celems);
 
     // uploads (host vectors outlive the copies: the stream is synchronised below)
-    std::vector<int32_t> eptr32(fos->eptr.begin(), fos->eptr.end());
     std::vector<int32_t> cptr32(fos->cptr.begin(), fos->cptr.end());
     cudaStream_t s = c->stream;
     GOM_CUDA(c, cudaMemsetAsync(base, 0, L.row_ptr, s)); // all state arrays
     GOM_CUDA(c, upload_raw(base, L.row_ptr, g->row_ptr, sizeof(int64_t) * (c->n + 1), s));
     GOM_CUDA(c, upload_raw(base, L.col, g->col, sizeof(int32_t) * g->num_adj, s));
     GOM_CUDA(c, upload_raw(base, L.wgt, g->weight, sizeof(int32_t) * g->num_adj, s));
-    GOM_CUDA(c, upload(base, L.eptr, eptr32, s));
-    GOM_CUDA(c, upload(base, L.evars, fos->evars, s));
-    GOM_CUDA(c, upload(base, L.dep_ptr, deps.dep_ptr, s));
-    GOM_CUDA(c, upload(base, L.dep, deps.dep, s));
-    GOM_CUDA(c, upload(base, L.seg, deps.seg, s));
+    GOM_CUDA(c, upload(base, L.hdr, tabs.hdr, s));
+    GOM_CUDA(c, upload(base, L.fv, tabs.fv, s));
+    GOM_CUDA(c, upload(base, L.wout, tabs.wout, s));
+    GOM_CUDA(c, upload(base, L.seg, tabs.seg, s));
+    GOM_CUDA(c, upload(base, L.dep, tabs.dep, s));
     GOM_CUDA(c, upload(base, L.cptr, cptr32, s));
-    GOM_CUDA(c, upload(base, L.celems, fos->celems, s));
 
     k_init_pop<<<c->grid_io, 256, 0, s>>>(P);
     GOM_CUDA(c, cudaGetLastError());

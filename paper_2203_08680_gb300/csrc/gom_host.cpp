@@ -1,7 +1,7 @@
 // gom_host.cpp -- one-time host set-up of parallel GOM: graph validation, the
 // linkage model (FOS, Sec. 4.1), the Welsh-Powell colouring of the linkage
 // model interaction graph (LMIG, Sec. 5.2) and the per-element dependency
-// lists (the edges incident to each element, Alg. 4).
+// tables (the edges incident to each element, Alg. 4, in colour order).
 //
 // Large instances (10^6 elements) are handled without materialising the LMIG:
 // the neighbours of an element are enumerated on the fly through a
@@ -239,57 +239,101 @@ int64_t count_deps(const gom_graph_t *g, const gom_fos &fos)
     return total;
 }
 
-int build_deps(const gom_graph_t *g, const gom_fos &fos, DepTables *out)
+int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
 {
     const int64_t m = fos.m;
-    out->dep_ptr.assign(static_cast<size_t>(m) + 1, 0);
-    out->seg.assign(fos.evars.size() + static_cast<size_t>(m), 0);
+    if (fos.k < 0 || static_cast<int64_t>(fos.celems.size()) != m) return GOM_E_NOT_COLORED;
+    // offsets in colour order
+    std::vector<int64_t> f0(m + 1, 0);
+    for (int64_t q = 0; q < m; ++q) {
+        const int32_t j = fos.celems[q];
+        f0[q + 1] = f0[q] + (fos.eptr[j + 1] - fos.eptr[j]);
+    }
+    const size_t total = static_cast<size_t>(f0[m]);
+    out->hdr.assign(4 * static_cast<size_t>(m), 0);
+    out->fv.assign(total, 0);
+    out->wout.assign(total, 0);
+    out->seg.assign(total + static_cast<size_t>(m), 0);
+    std::vector<int64_t> d0(m + 1, 0);
     std::atomic<int> too_big{0};
+    std::vector<int32_t> smax(m, 0);
+    std::vector<int64_t> wabs(m, 0);
 
-    // pass 1: entries per element (internal edges once) and the segment offsets
+    // pass 1: counts, segment offsets, outside weight sums
     parallel_ranges(m, [&](int64_t b, int64_t e) {
         std::vector<int32_t> pos(fos.n, -1);
-        for (int64_t j = b; j < e; ++j) {
-            const int64_t f0 = fos.eptr[j], s = fos.eptr[j + 1] - f0;
-            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = static_cast<int32_t>(a);
-            uint16_t *seg = out->seg.data() + f0 + j;
-            int64_t cnt = 0;
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t j = fos.celems[q];
+            const int64_t e0 = fos.eptr[j], s = fos.eptr[j + 1] - e0;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = static_cast<int32_t>(a);
+            uint16_t *seg = out->seg.data() + f0[q] + q;
+            int64_t n_out = 0, n_in = 0, sum_abs = 0;
             for (int64_t a = 0; a < s; ++a) {
-                seg[a] = static_cast<uint16_t>(cnt);
-                const int32_t u = fos.evars[f0 + a];
-                for (int64_t q = g->row_ptr[u]; q < g->row_ptr[u + 1]; ++q) {
-                    const int32_t bb = pos[g->col[q]];
-                    if (bb < 0 || bb > a) ++cnt;
+                const int32_t u = fos.evars[e0 + a];
+                out->fv[f0[q] + a] = u;
+                seg[a] = static_cast<uint16_t>(n_out);
+                int64_t wsum = 0;
+                for (int64_t x = g->row_ptr[u]; x < g->row_ptr[u + 1]; ++x) {
+                    const int32_t bb = pos[g->col[x]];
+                    const int64_t w = g->weight[x];
+                    if (bb < 0) {
+                        ++n_out;
+                        wsum += w;
+                        sum_abs += w < 0 ? -w : w;
+                    } else if (bb > a) {
+                        ++n_in;
+                        sum_abs += w < 0 ? -w : w;
+                    }
                 }
-                if (cnt > 65535) too_big = 1;
+                out->wout[f0[q] + a] = wsum;
+                if (n_out > 65535) too_big = 1;
             }
-            seg[s] = static_cast<uint16_t>(cnt);
-            out->dep_ptr[j + 1] = cnt;
-            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = -1;
+            seg[s] = static_cast<uint16_t>(n_out);
+            d0[q + 1] = n_out + n_in;
+            int32_t *h = out->hdr.data() + 4 * q;
+            h[0] = j;
+            h[1] = static_cast<int32_t>(f0[q]);
+            h[3] = static_cast<int32_t>(s | (n_in << 8));
+            smax[q] = static_cast<int32_t>(s);
+            wabs[q] = sum_abs;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = -1;
         }
     });
     if (too_big) return GOM_E_LIMIT;
-    for (int64_t j = 0; j < m; ++j) out->dep_ptr[j + 1] += out->dep_ptr[j];
-    out->dep.resize(2 * static_cast<size_t>(out->dep_ptr[m]));
+    for (int64_t q = 0; q < m; ++q) d0[q + 1] += d0[q];
+    if (d0[m] >= (int64_t(1) << 31)) return GOM_E_LIMIT;
+    out->dep.assign(2 * static_cast<size_t>(d0[m]), 0);
+    out->max_s = m ? *std::max_element(smax.begin(), smax.end()) : 0;
+    out->max_abs_w = m ? *std::max_element(wabs.begin(), wabs.end()) : 0;
 
-    // pass 2: fill
+    // pass 2: the edge lists
     parallel_ranges(m, [&](int64_t b, int64_t e) {
         std::vector<int32_t> pos(fos.n, -1);
-        for (int64_t j = b; j < e; ++j) {
-            const int64_t f0 = fos.eptr[j], s = fos.eptr[j + 1] - f0;
-            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = static_cast<int32_t>(a);
-            int32_t *dst = out->dep.data() + 2 * out->dep_ptr[j];
-            for (int64_t a = 0; a < s; ++a) {
-                const int32_t u = fos.evars[f0 + a];
-                for (int64_t q = g->row_ptr[u]; q < g->row_ptr[u + 1]; ++q) {
-                    const int32_t v = g->col[q];
-                    const int32_t bb = pos[v];
-                    if (bb >= 0 && bb < a) continue; // listed from the other endpoint
-                    *dst++ = bb >= 0 ? -1 - bb : v;
-                    *dst++ = g->weight[q];
+        for (int64_t q = b; q < e; ++q) {
+            const int32_t j = fos.celems[q];
+            const int64_t e0 = fos.eptr[j], s = fos.eptr[j + 1] - e0;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = static_cast<int32_t>(a);
+            out->hdr[4 * q + 2] = static_cast<int32_t>(d0[q]);
+            int32_t *dst = out->dep.data() + 2 * d0[q];
+            for (int64_t a = 0; a < s; ++a) { // outside edges, grouped by a
+                const int32_t u = fos.evars[e0 + a];
+                for (int64_t x = g->row_ptr[u]; x < g->row_ptr[u + 1]; ++x)
+                    if (pos[g->col[x]] < 0) {
+                        *dst++ = g->col[x];
+                        *dst++ = g->weight[x];
+                    }
+            }
+            for (int64_t a = 0; a < s; ++a) { // inside edges, once each (a < b)
+                const int32_t u = fos.evars[e0 + a];
+                for (int64_t x = g->row_ptr[u]; x < g->row_ptr[u + 1]; ++x) {
+                    const int32_t bb = pos[g->col[x]];
+                    if (bb > a) {
+                        *dst++ = static_cast<int32_t>(a | (bb << 8));
+                        *dst++ = g->weight[x];
+                    }
                 }
             }
-            for (int64_t a = 0; a < s; ++a) pos[fos.evars[f0 + a]] = -1;
+            for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = -1;
         }
     });
     return GOM_OK;

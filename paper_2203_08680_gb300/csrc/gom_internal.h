@@ -31,19 +31,29 @@ int build_fos(const gom_graph_t *g, int32_t kind, gom_fos *out);
 int check_fos(int32_t n, const gom_fos &fos);
 int color_fos(const gom_graph_t *g, gom_fos *fos);
 
-// Per-element dependency lists: the edges incident to F_j (Alg. 4's
-// dependent subfunctions), grouped by the F-local index a of the endpoint in
-// F_j, each edge listed once.  Entry = {code, weight}: code >= 0 is the other
-// endpoint (outside F_j); code < 0 is -1 - b with b the F-local index of the
-// other endpoint (inside F_j, b > a).  seg holds, per element, s+1 offsets
-// (relative to dep_ptr[j]) at seg[eptr[j] + j + a].
-struct DepTables {
-    std::vector<int64_t> dep_ptr; // [m+1]
-    std::vector<int32_t> dep;     // 2 ints per entry: code, weight
+// Per-element tables in colour order (position q = rank of the element in
+// the colour-sorted element list, so a colour group is one contiguous range
+// [cptr[c], cptr[c+1])).  For the element j at position q with s variables:
+//   hdr[q]           = {j, f0, d0, s | (n_in << 8)}
+//   fv[f0 + a]       = a-th variable of F_j (ascending)
+//   wout[f0 + a]     = sum of the weights of the edges from F_j[a] to
+//                      variables outside F_j
+//   seg[f0 + q + a]  = start of F_j[a]'s outside edges in dep[d0 ..], a = 0..s
+//                      (seg[f0 + q + s] = n_out)
+//   dep[d0 + x]      = {v, w} for the n_out outside edges grouped by a, then
+//                      {a | (b << 8), w} for the n_in edges inside F_j (a < b)
+// These are the dependent subfunctions of Alg. 4, each edge listed once.
+struct ElemTables {
+    std::vector<int32_t> hdr;     // 4 ints per element
+    std::vector<int32_t> fv;      // [total_vars]
+    std::vector<int64_t> wout;    // [total_vars]
     std::vector<uint16_t> seg;    // [total_vars + m]
+    std::vector<int32_t> dep;     // 2 ints per entry
+    int32_t max_s = 0;            // largest element
+    int64_t max_abs_w = 0;        // largest sum of |w| over one element's edges
 };
 int64_t count_deps(const gom_graph_t *g, const gom_fos &fos); // upper bound of entries
-int build_deps(const gom_graph_t *g, const gom_fos &fos, DepTables *out);
+int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out);
 
 } // namespace gomh
 
@@ -93,11 +103,10 @@ struct GomParams {
     const int64_t *row_ptr;
     const int32_t *col;
     const int32_t *wgt;
-    const int32_t *eptr;   // [m+1]
-    const int32_t *evars;
-    const int64_t *dep_ptr;  // [m+1]
-    const int2 *dep;         // {code, weight}
+    const int4 *hdr;         // [m] element headers in colour order
+    const int32_t *fv;       // [total_vars]
+    const int64_t *wout;     // [total_vars]
     const uint16_t *seg;     // [total_vars + m]
-    const int32_t *cptr;     // [k+1]
-    const int32_t *celems;   // [m]
+    const int2 *dep;         // outside edges {v, w}, then inside edges {a | b << 8, w}
+    const int32_t *cptr;     // [k+1] colour -> positions
 };

@@ -258,132 +258,250 @@ __global__ void k_order(GomParams P)
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->improved = 0; // x_e copied by k_gen_start
 }
 
+// Loads WPI consecutive 32-bit words (16/8/4-byte aligned by construction).
+template <int WPI>
+__device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&x)[WPI])
+{
+    if constexpr (WPI == 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else if constexpr (WPI == 2) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        x[0] = v.x; x[1] = v.y;
+    } else {
+        x[0] = *p;
+    }
+}
+
+// First individual, scanning cyclically upwards from `start` and skipping
+// `self`, whose generation-start bits on F differ from the parent's bits
+// `xf`; 32 candidates per step (one word of each of F's rows of P).  -1 if
+// none.  Called from divergent code: no warp collectives.
+template <typename MaskT>
+__device__ int scan_donor(const GomParams &P, const int32_t *F, int s, MaskT xf, int start, int self)
+{
+    const int W = P.W, Wv = P.Wv, p = P.p;
+    const int ws = start >> 5, bs = start & 31;
+    for (int step = 0; step <= Wv; ++step) {
+        int wc = ws + step;
+        if (wc >= Wv) wc -= Wv;
+        uint32_t diff = 0;
+        for (int a = 0; a < s; ++a)
+            diff |= P.P[F[a] * W + wc] ^ (0u - (uint32_t)((xf >> a) & 1u));
+        const int lim = p - 32 * wc;
+        uint32_t mk = diff & (lim >= 32 ? kFull : ((1u << lim) - 1u));
+        if (wc == (self >> 5)) mk &= ~(1u << (self & 31));
+        if (step == 0)
+            mk &= kFull << bs;
+        else if (step == Wv)
+            mk &= ~(kFull << bs);
+        if (mk) return 32 * wc + __ffs(mk) - 1;
+    }
+    return -1;
+}
+
 // One colour group: all (individual, element) GOM trials (Alg. 2) of group
-// order[t].  Warp = (element, word w), lane = individual 32w+lane.  Elements of
-// one group share no variable and no edge (LMIG colouring), so each warp owns
-// the rows of its element for its word and nothing else of this group touches
-// the closure it reads.
-//  donor:    Philox start, cyclic scan over 32 candidates per step, comparing
-//            P's words on F_j against the parent's bits (word-parallel)
-//  delta:    sum over the element's dependency list of the change of each
-//            edge's cut contribution (Sec. 2.2; edges inside F_j listed once)
-//  accept:   delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
-//  write:    one ballot per variable of F_j; lane 0 XORs the accepted flips
-// Fitness deltas and counters are summed per block in shared memory, then one
-// atomic add per individual (and per counter) per block: integer adds, so the
-// result does not depend on their order.
+// order[t].  A warp item is (element, WPI consecutive words); lane l works on
+// the individuals 32w + l of those words.  Elements of one group share no
+// variable and no edge (LMIG colouring), so the warp owns its element's rows
+// for its words and nothing else in the group touches the closure it reads.
+//  draws:   one Philox call per lane gives 4 words: lane c holds the call
+//           of individuals 4c..4c+3 of the item, fetched with shuffles
+//  donor:   the start candidate's bits on F_j first; if equal to the
+//           parent's, the word-parallel cyclic scan (scan_donor)
+//  delta:   per variable a of F_j that flips, the weighted count S of its
+//           outside neighbours set in the parent gives the cut change of its
+//           outside edges (x_a ? 2S - W_a : W_a - 2S); edges inside F_j are
+//           evaluated directly, once each (Sec. 2.2, Alg. 4)
+//  accept:  delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
+//  write:   one ballot per variable and word; lane 0 XORs the accepted flips
+// MaskT holds one bit per variable of F_j (uint32_t or uint64_t); AccT is
+// the delta type (int32_t when every element's sum of |w| is < 2^30).
+// Fitness deltas and counters are summed per block in shared memory, then
+// added with one atomic per individual (and per counter) per block: integer
+// adds, so the result does not depend on their order.
+template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
 {
     __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
     if (P.st->done) return;
     const int lane = threadIdx.x & 31;
-    const int np = 32 * P.W;
+    const int W = P.W;
+    const int np = 32 * W;
     for (int q = threadIdx.x; q < np; q += blockDim.x) s_f[q] = 0;
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
 
     const int c = P.order[t];
-    const int e0 = P.cptr[c], ne = P.cptr[c + 1] - e0;
-    const int W = P.W;
-    const int64_t gwarp = gthread() >> 5, nwarps = gthreads() >> 5;
-    const int w = (int)(gwarp & (W - 1));
-    const int i = 32 * w + lane;
-    const bool valid = i < P.p;
-    const bool eqflag = (P.eqw[w] >> lane) & 1u;
+    const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
+    const int G = W / WPI; // word groups per element; the warp count is a multiple of G
+    const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
+    const int w0 = (gwarp % G) * WPI;
+    const int p = P.p;
     const uint32_t g = P.st->g;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-    const int p = P.p, Wv = P.Wv;
-    long long facc = 0;
+
+    int iv[WPI];
+    bool eqf[WPI];
+    long long facc[WPI];
+#pragma unroll
+    for (int r = 0; r < WPI; ++r) {
+        iv[r] = 32 * (w0 + r) + lane;
+        eqf[r] = (P.eqw[w0 + r] >> lane) & 1u;
+        facc[r] = 0;
+    }
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
 
-    if (w < Wv) {
-        for (int64_t e = gwarp / W; e < ne; e += nwarps / W) {
-            const int j = P.celems[e0 + e];
-            const int f0 = P.eptr[j];
-            const int s = P.eptr[j + 1] - f0;
-            const int32_t *F = P.evars + f0;
+    if (w0 < P.Wv) {
+        for (int e = gwarp / G; e < ne; e += nwarps / G) {
+            const int q = q0 + e;
+            const int4 h = P.hdr[q];
+            const int j = h.x, f0 = h.y, d0 = h.z;
+            const int s = h.w & 0xFF, n_in = h.w >> 8;
+            const int32_t *F = P.fv + f0;
+            const int fl = lane < s ? F[lane] : 0; // lane a holds F_j[a] (s <= 32 here)
 
             // parent bits on F_j
-            uint64_t xf = 0;
+            MaskT xf[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) xf[r] = 0;
             for (int a = 0; a < s; ++a) {
-                const uint32_t word = P.O[(int64_t)F[a] * W + w];
-                xf |= (uint64_t)((word >> lane) & 1u) << a;
+                const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
+                uint32_t X[WPI];
+                load_words<WPI>(P.O + fa * W + w0, X);
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) xf[r] |= (MaskT)((X[r] >> lane) & 1u) << a;
             }
 
-            // SelectDonorFromPopulation
-            const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)i >> 2, g, kTagDonor), k0, k1);
-            const uint32_t u = __umulhi(pick(r4, i & 3), (uint32_t)(p - 1));
-            int dstart = i + 1 + (int)u;
-            if (dstart >= p) dstart -= p;
-            int donor = -1;
-            if (valid) {
-                const int ws = dstart >> 5, bs = dstart & 31;
-                for (int step = 0; step <= Wv && donor < 0; ++step) {
-                    int wc = ws + step;
-                    if (wc >= Wv) wc -= Wv;
-                    uint32_t diff = 0;
-                    for (int a = 0; a < s; ++a)
-                        diff |= P.P[(int64_t)F[a] * W + wc] ^ (0u - (uint32_t)((xf >> a) & 1u));
-                    const int lim = p - 32 * wc;
-                    uint32_t mk = lim >= 32 ? kFull : ((1u << lim) - 1u);
-                    mk &= diff;
-                    if (wc == w) mk &= ~(1u << lane);
-                    if (step == 0)
-                        mk &= kFull << bs;
-                    else if (step == Wv)
-                        mk &= ~(kFull << bs);
-                    if (mk) donor = 32 * wc + __ffs(mk) - 1;
-                }
+            // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
+            const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+            uint32_t draw[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) {
+                const int src = 8 * r + (lane >> 2);
+                const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
+                const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
+                const int cc = lane & 3;
+                draw[r] = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
             }
 
-            // flips: the donor's bits on F_j that differ from the parent's
-            uint64_t fm = 0;
-            if (donor >= 0) {
-                const int dw = donor >> 5, db = donor & 31;
+            // donors: start candidate, then the scan
+            int donor[WPI];
+            MaskT fm[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) {
+                const uint32_t u = __umulhi(draw[r], (uint32_t)(p - 1));
+                int ds = iv[r] + 1 + (int)u;
+                if (ds >= p) ds -= p;
+                if (iv[r] >= p) ds = 0;
+                const int dw = ds >> 5, db = ds & 31;
+                MaskT pat = 0;
                 for (int a = 0; a < s; ++a) {
-                    const uint32_t word = P.P[(int64_t)F[a] * W + dw];
-                    fm |= (uint64_t)(((word >> db) & 1u) ^ (uint32_t)((xf >> a) & 1u)) << a;
+                    const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
+                    pat |= (MaskT)((P.P[fa * W + dw] >> db) & 1u) << a;
                 }
-            }
-
-            // PartialEvaluation over the element's dependency list
-            long long delta = 0;
-            const int2 *dep = P.dep + P.dep_ptr[j];
-            const uint16_t *seg = P.seg + f0 + j;
-            for (int a = 0; a < s; ++a) {
-                const uint32_t fa = (uint32_t)(fm >> a) & 1u, xa = (uint32_t)(xf >> a) & 1u;
-                const int q1 = seg[a + 1];
-                for (int q = seg[a]; q < q1; ++q) {
-                    const int2 d = dep[q];
-                    uint32_t xb, fb;
-                    if (d.x >= 0) {
-                        xb = (P.O[(int64_t)d.x * W + w] >> lane) & 1u;
-                        fb = 0;
+                donor[r] = -1;
+                fm[r] = 0;
+                if (iv[r] < p) {
+                    if (pat != xf[r]) {
+                        donor[r] = ds;
+                        fm[r] = pat ^ xf[r];
                     } else {
-                        const int b = -1 - d.x;
-                        xb = (uint32_t)(xf >> b) & 1u;
-                        fb = (uint32_t)(fm >> b) & 1u;
+                        const int d = scan_donor<MaskT>(P, F, s, xf[r], ds, iv[r]);
+                        if (d >= 0) {
+                            MaskT pd = 0;
+                            for (int a = 0; a < s; ++a)
+                                pd |= (MaskT)((P.P[F[a] * W + (d >> 5)] >> (d & 31)) & 1u) << a;
+                            donor[r] = d;
+                            fm[r] = pd ^ xf[r];
+                        }
                     }
-                    if (fa ^ fb) delta += (xa ^ xb) ? -(long long)d.y : (long long)d.y;
                 }
             }
 
-            const bool acc = donor >= 0 && (delta > 0 || (delta == 0 && !eqflag));
+            // partial evaluation
+            AccT dl[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) dl[r] = 0;
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) any |= donor[r] >= 0;
+            if (__any_sync(kFull, any)) {
+                const uint16_t *seg = P.seg + f0 + q;
+                const int2 *dep = P.dep + d0;
+                int qb = 0;
+                for (int a = 0; a < s; ++a) {
+                    const int qe = seg[a + 1];
+                    bool flips = false;
+#pragma unroll
+                    for (int r = 0; r < WPI; ++r) flips |= (fm[r] >> a) & 1u;
+                    if (__any_sync(kFull, flips)) {
+                        AccT S[WPI];
+#pragma unroll
+                        for (int r = 0; r < WPI; ++r) S[r] = 0;
+                        for (int x = qb; x < qe; ++x) {
+                            const int2 d = dep[x];
+                            uint32_t X[WPI];
+                            load_words<WPI>(P.O + d.x * W + w0, X);
+#pragma unroll
+                            for (int r = 0; r < WPI; ++r) S[r] += (AccT)d.y * (AccT)((X[r] >> lane) & 1u);
+                        }
+                        const AccT Wa = (AccT)P.wout[f0 + a];
+#pragma unroll
+                        for (int r = 0; r < WPI; ++r)
+                            if ((fm[r] >> a) & 1u) dl[r] += ((xf[r] >> a) & 1u) ? 2 * S[r] - Wa : Wa - 2 * S[r];
+                    }
+                    qb = qe;
+                }
+                for (int x = qb; x < qb + n_in; ++x) {
+                    const int2 d = dep[x];
+                    const int a = d.x & 0xFF, b = d.x >> 8;
+#pragma unroll
+                    for (int r = 0; r < WPI; ++r) {
+                        const MaskT y = xf[r] ^ fm[r];
+                        const int cn = (int)(((y >> a) ^ (y >> b)) & 1u);
+                        const int co = (int)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u);
+                        dl[r] += (AccT)d.y * (AccT)(cn - co);
+                    }
+                }
+            }
+
+            bool acc[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r)
+                acc[r] = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eqf[r]));
             for (int a = 0; a < s; ++a) {
-                const uint32_t mk = __ballot_sync(kFull, acc && ((fm >> a) & 1u));
-                if (lane == 0 && mk) P.O[(int64_t)F[a] * W + w] ^= mk;
+                const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
+                uint32_t mk[WPI];
+                bool anym = false;
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) {
+                    mk[r] = __ballot_sync(kFull, acc[r] && ((fm[r] >> a) & 1u));
+                    anym |= mk[r] != 0;
+                }
+                if (lane == 0 && anym) {
+                    uint32_t *row = P.O + fa * W + w0;
+#pragma unroll
+                    for (int r = 0; r < WPI; ++r)
+                        if (mk[r]) row[r] ^= mk[r];
+                }
             }
-            if (acc) {
-                facc += delta;
-                ++n_acc;
-                if (delta > 0) ++n_imp;
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) {
+                if (acc[r]) {
+                    facc[r] += dl[r];
+                    ++n_acc;
+                    if (dl[r] > 0) ++n_imp;
+                }
+                if (iv[r] < p && donor[r] < 0) ++n_dl;
             }
-            if (valid && donor < 0) ++n_dl;
         }
     }
 
-    if (facc) atomicAdd((unsigned long long *)&s_f[i], (unsigned long long)facc);
+#pragma unroll
+    for (int r = 0; r < WPI; ++r)
+        if (facc[r]) atomicAdd((unsigned long long *)&s_f[iv[r]], (unsigned long long)facc[r]);
     n_dl = __reduce_add_sync(kFull, n_dl);
     n_acc = __reduce_add_sync(kFull, n_acc);
     n_imp = __reduce_add_sync(kFull, n_imp);
@@ -399,6 +517,17 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
     }
     if (threadIdx.x < 3 && s_cnt[threadIdx.x])
         atomicAdd((unsigned long long *)&P.st->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+const void *gom_mix_kernel(int wpi, bool narrow)
+{
+    if (narrow)
+        return wpi == 4 ? (const void *)k_mix<4, uint32_t, int32_t>
+             : wpi == 2 ? (const void *)k_mix<2, uint32_t, int32_t>
+                        : (const void *)k_mix<1, uint32_t, int32_t>;
+    return wpi == 4 ? (const void *)k_mix<4, uint64_t, long long>
+         : wpi == 2 ? (const void *)k_mix<2, uint64_t, long long>
+                    : (const void *)k_mix<1, uint64_t, long long>;
 }
 
 // Generation end: elitist update (strict improvement, lowest index; Sec. 4),

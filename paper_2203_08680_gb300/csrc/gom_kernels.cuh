@@ -13,7 +13,10 @@ __global__ void k_set_state(GomParams P, int64_t fe, int64_t g);
 __global__ void k_begin_call(GomParams P, int64_t target);
 __global__ void k_gen_start(GomParams P);
 __global__ void k_order(GomParams P);
-__global__ void k_mix(GomParams P, int t);
+// The mixing kernel instance for WPI words per warp item (1, 2 or 4) and
+// 32-bit (narrow) or 64-bit masks and deltas; a host-stub address usable as a
+// graph-node function.
+const void *gom_mix_kernel(int wpi, bool narrow);
 __global__ void k_gen_end(GomParams P);
 __global__ void k_export_pop(GomParams P, uint8_t *out);
 __global__ void k_export_elite(GomParams P, uint8_t *out);
