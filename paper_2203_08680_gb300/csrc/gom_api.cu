@@ -75,6 +75,7 @@ struct gom_ctx {
     int sms = 0;
     int grid_mix = 0, grid_fit = 0, grid_start = 0, grid_order = 0, grid_io = 0;
     const void *mix_fn = nullptr; // k_mix instance for this population and FOS
+    size_t mix_smem = 0;          // its dynamic shared memory per block
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -153,7 +154,7 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         }
         ts[t] = t;
         void *args2[] = {&prm, &ts[t]};
-        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, kMixThreads, 0, args2);
+        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, kMixThreads, ctx->mix_smem, args2);
         if (e == cudaSuccess && timed) {
             last = node;
             e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
@@ -359,19 +360,25 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int dev = 0;
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    // per-warp shared memory of k_mix: the rows of P on one element, then
+    // one record per edge (WPI parent words + code + weight, padded)
+    const int es = wpi == 4 ? 8 : 4;
+    const int64_t warp_words = ((static_cast<int64_t>(tabs.max_s) * c->W + 3) & ~int64_t(3)) + tabs.max_edges * es;
+    const int warps_per_block = kMixThreads / 32;
+    const int64_t smem = warp_words * 4 * warps_per_block;
+    if (smem > 200 * 1024) return GOM_E_LIMIT;
+    c->mix_smem = static_cast<size_t>(smem);
+    GOM_CUDA(c, cudaFuncSetAttribute(c->mix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(c->mix_smem)));
     int occ = 0;
-    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, kMixThreads, 0));
+    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, kMixThreads, c->mix_smem));
     occ = std::max(occ, 1);
-    // mixing grid: enough warps for the largest group; a multiple of G = W / wpi warps
+    // mixing grid: one warp per element of the largest group, at most a full wave
     int64_t max_group = 1;
     for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
-    const int warps_per_block = kMixThreads / 32;
-    const int G = c->W / wpi;
-    const int64_t need_blocks = (max_group * G + warps_per_block - 1) / warps_per_block;
+    const int64_t need_blocks = (max_group + warps_per_block - 1) / warps_per_block;
     int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
-    grid = std::min<int64_t>(grid, kMaxMixBlocks);
-    const int mix_mult = std::max(1, G / warps_per_block);
-    grid = std::max<int64_t>(mix_mult, grid / mix_mult * mix_mult);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
     c->grid_mix = static_cast<int>(grid);
     const int blk_mult = std::max(1, c->W / warps_per_block);
     c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
@@ -392,6 +399,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.m = static_cast<int32_t>(fos->m);
     P.k = fos->k;
     P.seed = seed;
+    P.smax = tabs.max_s;
+    P.warp_smem = static_cast<int32_t>(warp_words);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);
     P.f = reinterpret_cast<int64_t *>(base + L.f);

@@ -258,6 +258,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
     std::atomic<int> too_big{0};
     std::vector<int32_t> smax(m, 0);
     std::vector<int64_t> wabs(m, 0);
+    std::vector<int64_t> nedges(m, 0);
 
     // pass 1: counts, segment offsets, outside weight sums
     parallel_ranges(m, [&](int64_t b, int64_t e) {
@@ -296,6 +297,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
             h[3] = static_cast<int32_t>(s | (n_in << 8));
             smax[q] = static_cast<int32_t>(s);
             wabs[q] = sum_abs;
+            nedges[q] = n_out + n_in;
             for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = -1;
         }
     });
@@ -305,6 +307,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
     out->dep.assign(2 * static_cast<size_t>(d0[m]), 0);
     out->max_s = m ? *std::max_element(smax.begin(), smax.end()) : 0;
     out->max_abs_w = m ? *std::max_element(wabs.begin(), wabs.end()) : 0;
+    out->max_edges = m ? *std::max_element(nedges.begin(), nedges.end()) : 0;
 
     // pass 2: the edge lists
     parallel_ranges(m, [&](int64_t b, int64_t e) {

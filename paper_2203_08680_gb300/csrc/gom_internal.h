@@ -50,6 +50,7 @@ struct ElemTables {
     std::vector<uint16_t> seg;    // [total_vars + m]
     std::vector<int32_t> dep;     // 2 ints per entry
     int32_t max_s = 0;            // largest element
+    int64_t max_edges = 0;        // most edges (outside + inside) of one element
     int64_t max_abs_w = 0;        // largest sum of |w| over one element's edges
 };
 int64_t count_deps(const gom_graph_t *g, const gom_fos &fos); // upper bound of entries
@@ -90,7 +91,8 @@ struct GomParams {
     int32_t Wv;        // words holding valid individuals, ceil(p/32)
     int32_t m;         // FOS elements
     int32_t k;         // colours
-    int32_t pad0, pad1;
+    int32_t smax;       // largest element (rows of P staged per warp)
+    int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in k_mix
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population

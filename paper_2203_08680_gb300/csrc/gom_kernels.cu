@@ -275,19 +275,17 @@ __device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&x)[WPI]
 
 // First individual, scanning cyclically upwards from `start` and skipping
 // `self`, whose generation-start bits on F differ from the parent's bits
-// `xf`; 32 candidates per step (one word of each of F's rows of P).  -1 if
-// none.  Called from divergent code: no warp collectives.
+// `xf`; 32 candidates per step from the staged rows sP[a*W + word] of P on
+// F.  -1 if none.  Called from divergent code: no warp collectives.
 template <typename MaskT>
-__device__ int scan_donor(const GomParams &P, const int32_t *F, int s, MaskT xf, int start, int self)
+__device__ int scan_donor(const uint32_t *sP, int W, int Wv, int p, int s, MaskT xf, int start, int self)
 {
-    const int W = P.W, Wv = P.Wv, p = P.p;
     const int ws = start >> 5, bs = start & 31;
     for (int step = 0; step <= Wv; ++step) {
         int wc = ws + step;
         if (wc >= Wv) wc -= Wv;
         uint32_t diff = 0;
-        for (int a = 0; a < s; ++a)
-            diff |= P.P[F[a] * W + wc] ^ (0u - (uint32_t)((xf >> a) & 1u));
+        for (int a = 0; a < s; ++a) diff |= sP[a * W + wc] ^ (0u - (uint32_t)((xf >> a) & 1u));
         const int lim = p - 32 * wc;
         uint32_t mk = diff & (lim >= 32 ? kFull : ((1u << lim) - 1u));
         if (wc == (self >> 5)) mk &= ~(1u << (self & 31));
@@ -300,13 +298,50 @@ __device__ int scan_donor(const GomParams &P, const int32_t *F, int s, MaskT xf,
     return -1;
 }
 
+// Bits of individual `d` on F from the staged rows of P.
+template <typename MaskT>
+__device__ __forceinline__ MaskT pattern_of(const uint32_t *sP, int W, int s, int d)
+{
+    const int dw = d >> 5, db = d & 31;
+    MaskT pat = 0;
+#pragma unroll 4
+    for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + dw] >> db) & 1u) << a;
+    return pat;
+}
+
+// Words per staged edge record in k_mix: WPI parent words, then code and
+// weight, padded to a power of two so the parent words load as one vector.
+template <int WPI>
+struct EdgeStride {
+    static constexpr int value = WPI == 4 ? 8 : 4;
+};
+
+template <int WPI>
+__device__ __forceinline__ void lds_words(const uint32_t *p, uint32_t (&x)[WPI])
+{
+    load_words<WPI>(p, x); // shared-memory pointer: same vector widths
+}
+
+// Value held by lane (a mod 32) of lo (a < 32) or hi (a >= 32): per-variable
+// registers of elements with up to 64 variables.  Warp-uniform a.
+template <bool WIDE, typename T>
+__device__ __forceinline__ T lane_get(T lo, T hi, int a)
+{
+    if (WIDE && a >= 32) return __shfl_sync(kFull, hi, a - 32);
+    return __shfl_sync(kFull, lo, a);
+}
+
 // One colour group: all (individual, element) GOM trials (Alg. 2) of group
-// order[t].  A warp item is (element, WPI consecutive words); lane l works on
-// the individuals 32w + l of those words.  Elements of one group share no
-// variable and no edge (LMIG colouring), so the warp owns its element's rows
-// for its words and nothing else in the group touches the closure it reads.
+// order[t].  One warp per element; it walks the element's population words in
+// groups of WPI (lane l works on individuals 32w + l of those words).
+// Elements of one group share no variable and no edge (LMIG colouring), so
+// the warp owns its element's rows and nothing else in the group touches the
+// closure it reads.  Per element the warp stages, with lane-parallel loads,
+// the generation-start rows of P on F_j and the element's edge list into its
+// slice of shared memory; per word group it stages the parent's words of the
+// outside neighbours, so the trial work below reads no global memory.
 //  draws:   one Philox call per lane gives 4 words: lane c holds the call
-//           of individuals 4c..4c+3 of the item, fetched with shuffles
+//           of individuals 4c..4c+3 of the word group, fetched by shuffles
 //  donor:   the start candidate's bits on F_j first; if equal to the
 //           parent's, the word-parallel cyclic scan (scan_donor)
 //  delta:   per variable a of F_j that flips, the weighted count S of its
@@ -314,107 +349,118 @@ __device__ int scan_donor(const GomParams &P, const int32_t *F, int s, MaskT xf,
 //           outside edges (x_a ? 2S - W_a : W_a - 2S); edges inside F_j are
 //           evaluated directly, once each (Sec. 2.2, Alg. 4)
 //  accept:  delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
-//  write:   one ballot per variable and word; lane 0 XORs the accepted flips
-// MaskT holds one bit per variable of F_j (uint32_t or uint64_t); AccT is
-// the delta type (int32_t when every element's sum of |w| is < 2^30).
-// Fitness deltas and counters are summed per block in shared memory, then
-// added with one atomic per individual (and per counter) per block: integer
-// adds, so the result does not depend on their order.
+//  write:   one ballot per (variable, word); lane a XORs the accepted flips
+//           into row F_j[a]
+// MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
+// s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
+// is < 2^30).  Fitness deltas go to shared-memory accumulators, then one
+// atomic per individual (and per counter) per block: integer adds, so the
+// result does not depend on their order.
 template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
 {
+    constexpr bool WIDE = sizeof(MaskT) == 8;
+    constexpr int ES = EdgeStride<WPI>::value;
+    extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
     if (P.st->done) return;
-    const int lane = threadIdx.x & 31;
-    const int W = P.W;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = P.W, Wv = P.Wv, p = P.p;
+    const int lw = __ffs(W) - 1;
     const int np = 32 * W;
     for (int q = threadIdx.x; q < np; q += blockDim.x) s_f[q] = 0;
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
 
+    uint32_t *sP = s_dyn + wib * P.warp_smem;          // [s][W] rows of P on F_j
+    uint32_t *sE = sP + ((P.smax * W + 3) & ~3);       // [E][ES] edge records
     const int c = P.order[t];
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
-    const int G = W / WPI; // word groups per element; the warp count is a multiple of G
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
-    const int w0 = (gwarp % G) * WPI;
-    const int p = P.p;
     const uint32_t g = P.st->g;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-
-    int iv[WPI];
-    bool eqf[WPI];
-    long long facc[WPI];
-#pragma unroll
-    for (int r = 0; r < WPI; ++r) {
-        iv[r] = 32 * (w0 + r) + lane;
-        eqf[r] = (P.eqw[w0 + r] >> lane) & 1u;
-        facc[r] = 0;
-    }
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
 
-    if (w0 < P.Wv) {
-        for (int e = gwarp / G; e < ne; e += nwarps / G) {
-            const int q = q0 + e;
-            const int4 h = P.hdr[q];
-            const int j = h.x, f0 = h.y, d0 = h.z;
-            const int s = h.w & 0xFF, n_in = h.w >> 8;
-            const int32_t *F = P.fv + f0;
-            const int fl = lane < s ? F[lane] : 0; // lane a holds F_j[a] (s <= 32 here)
+    for (int e = gwarp; e < ne; e += nwarps) {
+        const int q = q0 + e;
+        const int4 h = P.hdr[q];
+        const int j = h.x, f0 = h.y, d0 = h.z;
+        const int s = h.w & 0xFF, n_in = h.w >> 8;
+        // lane a holds F_j[a], the start of its outside edges and their weight sum
+        const int fl = lane < s ? P.fv[f0 + lane] : 0;
+        const int sg = lane <= s ? (int)P.seg[f0 + q + lane] : 0;
+        const AccT wl = lane < s ? (AccT)P.wout[f0 + lane] : 0;
+        int fl2 = 0, sg2 = 0;
+        AccT wl2 = 0;
+        if (WIDE) {
+            fl2 = lane + 32 < s ? P.fv[f0 + 32 + lane] : 0;
+            sg2 = lane + 32 <= s ? (int)P.seg[f0 + q + 32 + lane] : 0;
+            wl2 = lane + 32 < s ? (AccT)P.wout[f0 + 32 + lane] : 0;
+        }
+        const int n_out = (int)P.seg[f0 + q + s];
+        const int ne_tot = n_out + n_in;
+        __syncwarp();
+        for (int x = lane; x < (s << lw); x += 32)
+            sP[x] = P.P[P.fv[f0 + (x >> lw)] * W + (x & (W - 1))];
+        for (int x = lane; x < ne_tot; x += 32) {
+            const int2 d = P.dep[d0 + x];
+            sE[x * ES + WPI] = (uint32_t)d.x;
+            sE[x * ES + WPI + 1] = (uint32_t)d.y;
+        }
+        __syncwarp();
 
-            // parent bits on F_j
+        for (int w0 = 0; w0 < Wv; w0 += WPI) {
+            // parent words of the outside neighbours for this word group
+            for (int x = lane; x < n_out; x += 32) {
+                uint32_t X[WPI];
+                load_words<WPI>(P.O + (int)sE[x * ES + WPI] * W + w0, X);
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) sE[x * ES + r] = X[r];
+            }
+            // parent bits on F_j: lane a loads row F_j[a], then a shuffle transpose
+            uint32_t Xa[WPI], Xa2[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
+            if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
+            if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
             MaskT xf[WPI];
 #pragma unroll
             for (int r = 0; r < WPI; ++r) xf[r] = 0;
             for (int a = 0; a < s; ++a) {
-                const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
-                uint32_t X[WPI];
-                load_words<WPI>(P.O + fa * W + w0, X);
 #pragma unroll
-                for (int r = 0; r < WPI; ++r) xf[r] |= (MaskT)((X[r] >> lane) & 1u) << a;
+                for (int r = 0; r < WPI; ++r)
+                    xf[r] |= (MaskT)((lane_get<WIDE>(Xa[r], Xa2[r], a) >> lane) & 1u) << a;
             }
+            __syncwarp();
 
             // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
             const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
-            uint32_t draw[WPI];
+            int donor[WPI];
+            MaskT fm[WPI];
 #pragma unroll
             for (int r = 0; r < WPI; ++r) {
                 const int src = 8 * r + (lane >> 2);
                 const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
                 const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
                 const int cc = lane & 3;
-                draw[r] = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
-            }
-
-            // donors: start candidate, then the scan
-            int donor[WPI];
-            MaskT fm[WPI];
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) {
-                const uint32_t u = __umulhi(draw[r], (uint32_t)(p - 1));
-                int ds = iv[r] + 1 + (int)u;
-                if (ds >= p) ds -= p;
-                if (iv[r] >= p) ds = 0;
-                const int dw = ds >> 5, db = ds & 31;
-                MaskT pat = 0;
-                for (int a = 0; a < s; ++a) {
-                    const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
-                    pat |= (MaskT)((P.P[fa * W + dw] >> db) & 1u) << a;
-                }
+                const uint32_t draw = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
+                const int i = 32 * (w0 + r) + lane;
                 donor[r] = -1;
                 fm[r] = 0;
-                if (iv[r] < p) {
+                if (i < p) {
+                    const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
+                    int ds = i + 1 + (int)u;
+                    if (ds >= p) ds -= p;
+                    const MaskT pat = pattern_of<MaskT>(sP, W, s, ds);
                     if (pat != xf[r]) {
                         donor[r] = ds;
                         fm[r] = pat ^ xf[r];
                     } else {
-                        const int d = scan_donor<MaskT>(P, F, s, xf[r], ds, iv[r]);
+                        const int d = scan_donor<MaskT>(sP, W, Wv, p, s, xf[r], ds, i);
                         if (d >= 0) {
-                            MaskT pd = 0;
-                            for (int a = 0; a < s; ++a)
-                                pd |= (MaskT)((P.P[F[a] * W + (d >> 5)] >> (d & 31)) & 1u) << a;
                             donor[r] = d;
-                            fm[r] = pd ^ xf[r];
+                            fm[r] = pattern_of<MaskT>(sP, W, s, d) ^ xf[r];
                         }
                     }
                 }
@@ -426,82 +472,85 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
             for (int r = 0; r < WPI; ++r) dl[r] = 0;
             bool any = false;
 #pragma unroll
-            for (int r = 0; r < WPI; ++r) any |= donor[r] >= 0;
+            for (int r = 0; r < WPI; ++r) any |= fm[r] != 0;
             if (__any_sync(kFull, any)) {
-                const uint16_t *seg = P.seg + f0 + q;
-                const int2 *dep = P.dep + d0;
-                int qb = 0;
                 for (int a = 0; a < s; ++a) {
-                    const int qe = seg[a + 1];
                     bool flips = false;
 #pragma unroll
                     for (int r = 0; r < WPI; ++r) flips |= (fm[r] >> a) & 1u;
-                    if (__any_sync(kFull, flips)) {
-                        AccT S[WPI];
+                    const int qb = lane_get<WIDE>(sg, sg2, a);
+                    const int qe = (a + 1 == s) ? n_out : lane_get<WIDE>(sg, sg2, a + 1);
+                    const AccT Wa = lane_get<WIDE>(wl, wl2, a);
+                    if (!__any_sync(kFull, flips)) continue;
+                    AccT S[WPI];
 #pragma unroll
-                        for (int r = 0; r < WPI; ++r) S[r] = 0;
-                        for (int x = qb; x < qe; ++x) {
-                            const int2 d = dep[x];
-                            uint32_t X[WPI];
-                            load_words<WPI>(P.O + d.x * W + w0, X);
+                    for (int r = 0; r < WPI; ++r) S[r] = 0;
+                    for (int x = qb; x < qe; ++x) {
+                        uint32_t X[WPI];
+                        lds_words<WPI>(sE + x * ES, X);
+                        const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
 #pragma unroll
-                            for (int r = 0; r < WPI; ++r) S[r] += (AccT)d.y * (AccT)((X[r] >> lane) & 1u);
-                        }
-                        const AccT Wa = (AccT)P.wout[f0 + a];
-#pragma unroll
-                        for (int r = 0; r < WPI; ++r)
-                            if ((fm[r] >> a) & 1u) dl[r] += ((xf[r] >> a) & 1u) ? 2 * S[r] - Wa : Wa - 2 * S[r];
+                        for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
                     }
-                    qb = qe;
+#pragma unroll
+                    for (int r = 0; r < WPI; ++r)
+                        if ((fm[r] >> a) & 1u) dl[r] += ((xf[r] >> a) & 1u) ? 2 * S[r] - Wa : Wa - 2 * S[r];
                 }
-                for (int x = qb; x < qb + n_in; ++x) {
-                    const int2 d = dep[x];
-                    const int a = d.x & 0xFF, b = d.x >> 8;
+                for (int x = n_out; x < ne_tot; ++x) {
+                    const uint32_t code = sE[x * ES + WPI];
+                    const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
+                    const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
                     for (int r = 0; r < WPI; ++r) {
                         const MaskT y = xf[r] ^ fm[r];
                         const int cn = (int)(((y >> a) ^ (y >> b)) & 1u);
                         const int co = (int)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u);
-                        dl[r] += (AccT)d.y * (AccT)(cn - co);
+                        dl[r] += wx * (AccT)(cn - co);
                     }
                 }
             }
 
+            // accept, fitness, write
             bool acc[WPI];
 #pragma unroll
-            for (int r = 0; r < WPI; ++r)
-                acc[r] = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eqf[r]));
-            for (int a = 0; a < s; ++a) {
-                const int fa = s <= 32 ? __shfl_sync(kFull, fl, a) : F[a];
-                uint32_t mk[WPI];
-                bool anym = false;
-#pragma unroll
-                for (int r = 0; r < WPI; ++r) {
-                    mk[r] = __ballot_sync(kFull, acc[r] && ((fm[r] >> a) & 1u));
-                    anym |= mk[r] != 0;
-                }
-                if (lane == 0 && anym) {
-                    uint32_t *row = P.O + fa * W + w0;
-#pragma unroll
-                    for (int r = 0; r < WPI; ++r)
-                        if (mk[r]) row[r] ^= mk[r];
-                }
-            }
-#pragma unroll
             for (int r = 0; r < WPI; ++r) {
+                const int i = 32 * (w0 + r) + lane;
+                const bool eq = (P.eqw[w0 + r] >> lane) & 1u;
+                acc[r] = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
                 if (acc[r]) {
-                    facc[r] += dl[r];
+                    atomicAdd((unsigned long long *)&s_f[i], (unsigned long long)(long long)dl[r]);
                     ++n_acc;
                     if (dl[r] > 0) ++n_imp;
                 }
-                if (iv[r] < p && donor[r] < 0) ++n_dl;
+                if (i < p && donor[r] < 0) ++n_dl;
             }
+            uint32_t mine[WPI], mine2[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
+            for (int a = 0; a < s; ++a) {
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) {
+                    const uint32_t mk = __ballot_sync(kFull, acc[r] && ((fm[r] >> a) & 1u));
+                    if (lane == a) mine[r] = mk;
+                    if (WIDE && lane + 32 == a) mine2[r] = mk;
+                }
+            }
+#pragma unroll
+            for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
+                const int f = half ? fl2 : fl;
+                if (lane + 32 * half < s) {
+                    uint32_t *row = P.O + f * W + w0;
+#pragma unroll
+                    for (int r = 0; r < WPI; ++r) {
+                        const uint32_t mk = half ? mine2[r] : mine[r];
+                        if (mk) row[r] ^= mk;
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
 
-#pragma unroll
-    for (int r = 0; r < WPI; ++r)
-        if (facc[r]) atomicAdd((unsigned long long *)&s_f[iv[r]], (unsigned long long)facc[r]);
     n_dl = __reduce_add_sync(kFull, n_dl);
     n_acc = __reduce_add_sync(kFull, n_acc);
     n_imp = __reduce_add_sync(kFull, n_imp);

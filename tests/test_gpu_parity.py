@@ -222,3 +222,41 @@ def test_user_stream(oracle):
         st = _gpu_state(P)
     torch.cuda.synchronize()
     _assert_same_state(st, run.get())
+
+
+def test_wide_elements_64bit_masks(oracle):
+    """Elements of 41 variables: the kernel instance with 64-bit masks."""
+    _parity(oracle, I.random_regular(300, 40, seed=5), 70, 4, 4)
+
+
+def test_large_weights_64bit_deltas(oracle):
+    """Sums of |w| above 2^30 per element: the instance with int64 deltas."""
+    g = I.random_regular(500, 6, seed=6, wmin=-(2 ** 29), wmax=2 ** 29)
+    _parity(oracle, g, 40, 8, 5)
+
+
+def _overlapping_fos(n, seed):
+    """Singletons, consecutive pairs and consecutive quads: overlapping
+    elements of mixed sizes, as in a linkage tree (Sec. 4.1)."""
+    sets = [[v] for v in range(n)]
+    sets += [[v, v + 1] for v in range(0, n - 1, 2)]
+    sets += [list(range(v, v + 4)) for v in range(0, n - 3, 4)]
+    ep = np.cumsum([0] + [len(s) for s in sets]).astype(np.int64)
+    ev = np.concatenate([np.array(s, dtype=np.int32) for s in sets])
+    return ep, ev
+
+
+@pytest.mark.parametrize("p", [16, 100])
+def test_custom_overlapping_fos(oracle, p):
+    g = I.torus2d(8, seed=12)
+    ep, ev = _overlapping_fos(g.n, 1)
+    fos = gom.gom_fos_create(g.n, ep, ev)
+    P = gom.Population(g, p, 13, fos=fos)
+    k, co = oracle.color(g, ep, ev)
+    assert P.k == k
+    run = oracle.Run(g, ep, ev, co, k, p, 13)
+    _assert_same_state(_gpu_state(P), run.get(), "init")
+    for _ in range(6):
+        gst, _ = P.generation(1)
+        _assert_same_stats(gst[0], run.generation())
+    _assert_same_state(_gpu_state(P), run.get())
