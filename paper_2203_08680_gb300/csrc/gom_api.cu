@@ -76,6 +76,7 @@ struct gom_ctx {
     int grid_mix = 0, grid_fit = 0, grid_start = 0, grid_order = 0, grid_io = 0;
     const void *mix_fn = nullptr; // k_mix instance for this population and FOS
     size_t mix_smem = 0;          // its dynamic shared memory per block
+    int mix_threads = kMixThreads; // its block size (fewer warps for very large elements)
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -154,7 +155,7 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         }
         ts[t] = t;
         void *args2[] = {&prm, &ts[t]};
-        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, kMixThreads, ctx->mix_smem, args2);
+        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, ctx->mix_threads, ctx->mix_smem, args2);
         if (e == cudaSuccess && timed) {
             last = node;
             e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
@@ -364,14 +365,15 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     // one record per edge (WPI parent words + code + weight, padded)
     const int es = wpi == 4 ? 8 : 4;
     const int64_t warp_words = ((static_cast<int64_t>(tabs.max_s) * c->W + 3) & ~int64_t(3)) + tabs.max_edges * es;
-    const int warps_per_block = kMixThreads / 32;
-    const int64_t smem = warp_words * 4 * warps_per_block;
-    if (smem > 200 * 1024) return GOM_E_LIMIT;
-    c->mix_smem = static_cast<size_t>(smem);
+    constexpr int64_t kSmemBudget = 200 * 1024;
+    const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (warp_words * 4)));
+    if (warps_per_block < 1) return GOM_E_LIMIT;
+    c->mix_threads = 32 * warps_per_block;
+    c->mix_smem = static_cast<size_t>(warp_words * 4 * warps_per_block);
     GOM_CUDA(c, cudaFuncSetAttribute(c->mix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(c->mix_smem)));
     int occ = 0;
-    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, kMixThreads, c->mix_smem));
+    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
     occ = std::max(occ, 1);
     // mixing grid: one warp per element of the largest group, at most a full wave
     int64_t max_group = 1;
@@ -380,7 +382,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
     c->grid_mix = static_cast<int>(grid);
-    const int blk_mult = std::max(1, c->W / warps_per_block);
+    const int blk_mult = std::max(1, c->W / 8);
     c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
     c->grid_start = c->sms * 4;
     c->grid_io = c->sms * 4;
