@@ -99,15 +99,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per mixing launch from the committed ncu summary, if it was
-    taken on this workload with the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "k_mix_traffic.json")
+def profiled_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on this workload with the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(workload)
+    e = d.get(f"{kernel.split()[0]}:{workload}")
     if not e or e.get("kernel_hash") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -250,19 +250,21 @@ def run_gpu(args, wl, rank, world, local):
     g = build()
     seed = SEED + rank
     stream = torch.cuda.current_stream()
-    P = gom.Population(g, p, seed, stream=stream)
+    P = gom.Population(g, p, seed, stream=stream, persistent=None if args.path == "auto" else args.path == "persistent")
     m, k = P.m, P.k
+    persistent = bool(gom.gom_get_option(P.ctx, gom.GOM_OPT_PERSISTENT))
     trials_per_step = p * m
-    launches_per_step = gom.gom_launches_per_generation(P.ctx)
     ex = gom.gom_fos_export(P.fos)
     mix_bytes = mixing_bytes_per_generation(g, ex["elem_ptr"], ex["elem_vars"], p)
+    gen_bytes = mix_bytes + g.n * p // 4 + 16 * p  # + clone of the population, fitness and flags
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     # warm-up generations (untimed)
     P.generation(args.warmup, want_stats=False)
     torch.cuda.synchronize()
-    gom.gom_set_timing(P.ctx, True)
-    gom.gom_read_timing(P.ctx)  # reset
+    if not persistent:
+        gom.gom_set_timing(P.ctx, True)
+        gom.gom_read_timing(P.ctx)  # reset
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     dist_barrier(world)
@@ -275,11 +277,36 @@ def run_gpu(args, wl, rank, world, local):
             ev1[s].record(stream)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    mix_ms, mix_launches = gom.gom_read_timing(P.ctx)
-    gom.gom_set_timing(P.ctx, False)
+    launches_per_step = gom.gom_launches_per_generation(P.ctx) + (0 if persistent else 1)
+    if persistent:
+        dom = {"kernel": "k_run (persistent generation kernel)", "bytes_per_launch": gen_bytes,
+               "avg_ms": sum(step_ms) / len(step_ms), "launches": args.steps}
+    else:
+        mix_ms, mix_launches = gom.gom_read_timing(P.ctx)
+        gom.gom_set_timing(P.ctx, False)
+        dom = {"kernel": "k_mix", "bytes_per_launch": mix_bytes / k, "avg_ms": mix_ms / max(mix_launches, 1),
+               "launches": mix_launches}
     dist_barrier(world)
     total_ms = dist_max(sum(step_ms), world)
     value = world * trials_per_step * args.steps / (total_ms / 1e3)
+
+    # the mixing kernel alone: per-launch events on the graph path
+    mix = None
+    if args.mix_steps > 0:
+        Q = gom.Population(g, p, seed, stream=stream, persistent=False, fos=P.fos)
+        Q.generation(args.warmup, want_stats=False)
+        gom.gom_set_timing(Q.ctx, True)
+        gom.gom_read_timing(Q.ctx)
+        for s in range(args.mix_steps):
+            flush.fill_(s & 0xFF)
+            gom.gom_generation(Q.ctx, 1, gom.INT64_MAX, want_stats=False)
+        mix_ms, mix_launches = gom.gom_read_timing(Q.ctx)
+        peak, peak_kind = peaks()
+        avg = mix_ms / max(mix_launches, 1)
+        ach = (mix_bytes / k) / (avg / 1e3) / 1e9
+        mix = {"kernel": "k_mix", "avg_launch_ms": avg, "launches": mix_launches,
+               "algorithmic_bytes_per_launch": mix_bytes / k, "achieved_gbs": ach, "frac": ach / peak}
+        del Q
 
     # time to target: fresh population, within 0.1% of the closed-form optimum
     # (every edge cut on an even torus) or a generation cap
@@ -297,8 +324,8 @@ def run_gpu(args, wl, rank, world, local):
         cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds)
         cpu = {"value": cval, "unit": "trials/s", "cores": 1, "kind": "oracle",
                "sample": f"{cgens} generations from initialisation ({cel:.1f} s, single thread)"}
-    return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, mix_ms, mix_launches, mix_bytes,
-                  ttt, e2e, launches_per_step, clk, cpu)
+    return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e,
+                  launches_per_step, clk, cpu, persistent)
 
 
 def time_to_target(args, g, p, seed, stream, wl):
@@ -355,27 +382,26 @@ def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step):
             "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
 
 
-def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, mix_ms, mix_launches, mix_bytes, ttt, e2e,
-           launches_per_step, clk, cpu):
+def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e, launches_per_step, clk,
+           cpu, persistent):
     peak, peak_kind = peaks()
-    mix_avg_ms = mix_ms / max(mix_launches, 1)
-    bytes_per_launch = mix_bytes / k
-    achieved = bytes_per_launch / (mix_avg_ms / 1e3) / 1e9 if mix_launches else None
-    traffic = profiled_traffic(wl)
+    achieved = dom["bytes_per_launch"] / (dom["avg_ms"] / 1e3) / 1e9 if dom["launches"] else None
     line = {
         "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl, "description": desc, "population": p, "elements": m, "colours": k,
+                   "path": "persistent" if persistent else "graph",
                    "l2": "flushed between timed generations (2x L2 buffer write)",
                    "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_mix", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": traffic,
-                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_ms": mix_avg_ms, "launches_timed": mix_launches},
+        "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": profiled_traffic(wl, dom["kernel"]),
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom["bytes_per_launch"],
+                     "avg_launch_ms": dom["avg_ms"], "launches_timed": dom["launches"]},
+        "mix_kernel": mix,
         "time_to_target": ttt,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps + args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
@@ -396,6 +422,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
+    ap.add_argument("--path", default="auto", choices=["auto", "persistent", "graph"])
+    ap.add_argument("--mix-steps", type=int, default=50,
+                    help="generations timed per mixing launch on the graph path (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

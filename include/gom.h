@@ -54,7 +54,8 @@ extern "C" {
 #define GOM_E_NOT_COLORED (-3)  /* gom_color_fos has not run on this FOS */
 #define GOM_E_WORKSPACE (-4)    /* workspace null, misaligned or too small */
 #define GOM_E_CUDA (-5)         /* a CUDA call failed; gom_last_cuda_error has it */
-#define GOM_E_TIMEOUT (-6)      /* a bounded device wait gave up */
+#define GOM_E_TIMEOUT (-6)      /* a bounded device wait gave up; the population is then undefined
+                                   until gom_set_population or a new gom_init_population */
 #define GOM_E_STATE (-7)        /* call not valid in the handle's state */
 #define GOM_E_LIMIT (-8)        /* size beyond what this build supports */
 #define GOM_E_FOS (-9)          /* FOS incomplete, out of range or for another graph */
@@ -62,6 +63,13 @@ extern "C" {
 /* FOS kinds for gom_build_fos. */
 #define GOM_FOS_NEIGHBOURHOOD 0 /* F_j = {j} u adj(j), one element per vertex */
 #define GOM_FOS_SINGLETON 1     /* F_j = {j} */
+
+/* Options for gom_set_option / gom_get_option. */
+#define GOM_OPT_PERSISTENT 1 /* 1: each gom_generation call is one persistent cooperative
+                                kernel that runs all its generations, phases separated by
+                                bounded grid barriers (default where the device supports
+                                cooperative launch); 0: one CUDA graph per generation with one
+                                kernel per phase and per colour group */
 
 /* Supported maxima of this build. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
@@ -207,8 +215,8 @@ int gom_get_generation(gom_ctx_t *ctx, int64_t *generation);
 
 /*
  * Kernel timing.  gom_set_timing(ctx, 1) makes each following generation
- * record a CUDA event pair around every mixing launch (event-record nodes in
- * the generation's graph; off by default).  A timed generation's events are
+ * run on the per-generation graph path and record a CUDA event pair around
+ * every mixing launch (event-record nodes in the graph; off by default).  A timed generation's events are
  * read when the next timed generation is enqueued or by gom_read_timing,
  * which waits for the stream and returns the summed mixing-kernel
  * milliseconds and the number of mixing launches run since timing was enabled
@@ -217,8 +225,27 @@ int gom_get_generation(gom_ctx_t *ctx, int64_t *generation);
 int gom_set_timing(gom_ctx_t *ctx, int32_t enable);
 int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches);
 
-/* Kernel launches one generation makes (for launch accounting). */
+/* Kernel launches one generation makes on the current path (for launch
+ * accounting; the persistent path counts its one launch per call as one). */
 int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches);
+
+/* Sets or reads an option (GOM_OPT_*).  GOM_OPT_PERSISTENT = 1 is refused
+ * with GOM_E_STATE where the persistent path is unavailable.  Both paths give
+ * identical results. */
+int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value);
+int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value);
+
+/*
+ * Self-test of the bounded wait in the persistent kernel's grid barrier
+ * (failure detection without a hang): `blocks` co-resident blocks meet at a
+ * barrier that expects blocks + extra arrivals.  With extra = 0 they pass;
+ * with extra > 0 no block is released, each gives up after limit_ns
+ * nanoseconds of wall clock and the kernel returns.  *timed_out reports
+ * whether the error word was set.  d_scratch: caller-owned device memory of
+ * at least 64 bytes, 16-byte aligned.  Waits for cuda_stream.
+ */
+int gom_selftest_barrier(void *d_scratch, int32_t blocks, int32_t extra, int64_t limit_ns, void *cuda_stream,
+                         int32_t *timed_out);
 
 /* Last CUDA error code seen by the handle (0 if none). */
 int gom_last_cuda_error(gom_ctx_t *ctx);

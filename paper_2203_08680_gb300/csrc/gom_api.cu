@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, stats, order;
+    size_t O, P, f, eqw, xe, st, bar, stats, order;
     size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
@@ -50,6 +50,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.eqw = take(sizeof(uint32_t) * W);
     L.xe = take(n);
     L.st = take(sizeof(GomDevState));
+    L.bar = take(sizeof(GomBarrier));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
@@ -77,6 +78,11 @@ struct gom_ctx {
     const void *mix_fn = nullptr; // k_mix instance for this population and FOS
     size_t mix_smem = 0;          // its dynamic shared memory per block
     int mix_threads = kMixThreads; // its block size (fewer warps for very large elements)
+    const void *run_fn = nullptr; // persistent generation kernel (same instance parameters)
+    size_t run_smem = 0;          // its dynamic shared memory (staging or the k group keys)
+    int grid_run = 0;             // its grid: co-resident blocks only
+    bool can_persist = false;     // cooperative launch available and the sizes fit
+    bool persistent = false;      // current path: k_run (true) or the per-generation graph
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -181,6 +187,7 @@ int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *
     GomDevState st;
     GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (st.err) return GOM_E_TIMEOUT;
     const int32_t run = static_cast<int32_t>(st.g - st.call_g0);
     if (run_out) *run_out = run;
     if (host_stats) {
@@ -382,6 +389,24 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
     c->grid_mix = static_cast<int>(grid);
+
+    // persistent path: one cooperative kernel, grid limited to co-resident blocks
+    c->run_fn = gom_run_kernel(wpi, narrow);
+    c->run_smem = std::max(c->mix_smem, sizeof(unsigned long long) * static_cast<size_t>(std::max(c->k, 1)));
+    int coop = 0;
+    GOM_CUDA(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (coop && c->run_smem <= static_cast<size_t>(kSmemBudget)) {
+        GOM_CUDA(c, cudaFuncSetAttribute(c->run_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(c->run_smem)));
+        int occ_run = 0;
+        GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_run, c->run_fn, c->mix_threads, c->run_smem));
+        if (occ_run > 0) {
+            c->grid_run = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_run,
+                                                             std::max<int64_t>(need_blocks, 1)));
+            c->can_persist = true;
+        }
+    }
+    c->persistent = c->can_persist;
     const int blk_mult = std::max(1, c->W / 8);
     c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
     c->grid_start = c->sms * 4;
@@ -409,6 +434,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.eqw = reinterpret_cast<uint32_t *>(base + L.eqw);
     P.xe = reinterpret_cast<uint8_t *>(base + L.xe);
     P.st = reinterpret_cast<GomDevState *>(base + L.st);
+    P.bar = reinterpret_cast<GomBarrier *>(base + L.bar);
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
@@ -465,9 +491,18 @@ int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitne
     do {
         // with host statistics the device ring bounds one chunk
         const int32_t chunk = want ? std::min<int32_t>(remaining, kStatsCap) : remaining;
-        k_begin_call<<<1, 1, 0, ctx->stream>>>(ctx->prm, target_fitness);
-        GOM_CUDA(ctx, cudaGetLastError());
-        for (int32_t q = 0; q < chunk; ++q) {
+        if (ctx->persistent && !ctx->timing) {
+            GomParams prm = ctx->prm;
+            int gens = chunk;
+            int64_t target = target_fitness;
+            void *args[] = {&prm, &gens, &target};
+            GOM_CUDA(ctx, cudaLaunchCooperativeKernel(ctx->run_fn, dim3(ctx->grid_run), dim3(ctx->mix_threads), args,
+                                                      ctx->run_smem, ctx->stream));
+        } else {
+            k_begin_call<<<1, 1, 0, ctx->stream>>>(ctx->prm, target_fitness);
+            GOM_CUDA(ctx, cudaGetLastError());
+        }
+        for (int32_t q = 0; q < chunk && !(ctx->persistent && !ctx->timing); ++q) {
             if (ctx->timing) {
                 // the events of the previous timed generation are read first
                 int rc = accumulate_timing(ctx);
@@ -553,6 +588,7 @@ int gom_get_generation(gom_ctx_t *ctx, int64_t *generation)
     GomDevState st;
     GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (st.err) return GOM_E_TIMEOUT;
     *generation = st.g;
     return GOM_OK;
 }
@@ -593,7 +629,54 @@ int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches)
 int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches)
 {
     if (!ctx || !launches) return GOM_E_ARG;
-    *launches = 3 + static_cast<int64_t>(ctx->k);
+    *launches = (ctx->persistent && !ctx->timing) ? 1 : 3 + static_cast<int64_t>(ctx->k);
+    return GOM_OK;
+}
+
+int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
+{
+    if (!ctx) return GOM_E_ARG;
+    if (option == GOM_OPT_PERSISTENT) {
+        if (value && !ctx->can_persist) return GOM_E_STATE;
+        ctx->persistent = value != 0;
+        return GOM_OK;
+    }
+    return GOM_E_ARG;
+}
+
+int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
+{
+    if (!ctx || !value) return GOM_E_ARG;
+    if (option == GOM_OPT_PERSISTENT) {
+        *value = ctx->persistent ? 1 : 0;
+        return GOM_OK;
+    }
+    return GOM_E_ARG;
+}
+
+int gom_selftest_barrier(void *d_scratch, int32_t blocks, int32_t extra, int64_t limit_ns, void *cuda_stream,
+                         int32_t *timed_out)
+{
+    if (!d_scratch || blocks < 1 || extra < 0 || limit_ns <= 0 || !timed_out) return GOM_E_ARG;
+    if (reinterpret_cast<uintptr_t>(d_scratch) % 16) return GOM_E_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0, coop = 0;
+    GOM_CUDA(nullptr, cudaGetDevice(&dev));
+    GOM_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GOM_CUDA(nullptr, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return GOM_E_STATE;
+    if (blocks > sms) return GOM_E_LIMIT;
+    GomBarrier *bar = static_cast<GomBarrier *>(d_scratch);
+    int *err = reinterpret_cast<int *>(static_cast<char *>(d_scratch) + sizeof(GomBarrier));
+    GOM_CUDA(nullptr, cudaMemsetAsync(d_scratch, 0, sizeof(GomBarrier) + sizeof(int), s));
+    unsigned long long lim = static_cast<unsigned long long>(limit_ns);
+    int ex = extra;
+    void *args[] = {&bar, &err, &ex, &lim};
+    GOM_CUDA(nullptr, cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(blocks), dim3(32), args, 0, s));
+    int herr = 0;
+    GOM_CUDA(nullptr, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GOM_CUDA(nullptr, cudaStreamSynchronize(s));
+    *timed_out = herr != 0;
     return GOM_OK;
 }
 

@@ -74,6 +74,11 @@ struct GomDevState {
     int64_t cnt[4];    // counters of the running generation: donorless, accepted, improving
 };
 
+struct GomBarrier { // grid barrier of the persistent kernel
+    unsigned count;
+    unsigned gen;
+};
+
 struct GomDevStats { // mirrors gom_gen_stats_t
     int64_t generation, best, elite, trials, donorless, accepted, improving, reached;
 };
@@ -100,6 +105,7 @@ struct GomParams {
     uint32_t *eqw;     // [W] generation-start flags P[i] == x_e
     uint8_t *xe;       // [n] elitist
     GomDevState *st;
+    GomBarrier *bar;
     GomDevStats *stats;  // [kStatsCap] ring indexed by generation
     int32_t *order;      // [k] colour visited at position t
     const int64_t *row_ptr;

@@ -7,12 +7,15 @@
 // one GOM trial batch (32 individuals x one element) are whole words.
 //
 // Kernels of one generation (Alg. 3):
-//   k_gen_start  Clone (P <- O), copy of the new elitist, elitist flags
-//   k_order      random order of the colour groups
-//   k_mix        one launch per colour group: every (individual, element)
-//                trial of the group -- donor, partial evaluation, accept, write
-//   k_gen_end    fitness fold, elitist update, counters, target check
-// plus initialisation, full evaluation and import/export kernels.
+//   gen start  Clone (P <- O), copy of the new elitist, elitist flags
+//   order      random order of the colour groups
+//   mix        one phase per colour group: every (individual, element) trial
+//              of the group -- donor, partial evaluation, accept, write
+//   gen end    elitist update, counters, target check
+// Two ways to run them: one kernel per phase in a per-generation CUDA graph
+// (k_gen_start, k_order, k_mix, k_gen_end), or one persistent cooperative
+// kernel (k_run) that runs many generations with grid barriers between the
+// phases.  Plus initialisation, full evaluation and import/export kernels.
 #include <climits>
 #include <cuda_runtime.h>
 
@@ -192,15 +195,66 @@ __global__ void k_begin_call(GomParams P, int64_t target)
     P.st->call_g0 = P.st->g; // first generation of this call
 }
 
+// ----------------------------------------------------------------------------
+// Grid-wide barrier of the persistent generation kernel (all blocks are
+// co-resident: cooperative launch).  Sense counter: the last block to arrive
+// resets the count and bumps the generation word.  A block that waits longer
+// than kBarrierNs (wall clock, %globaltimer) or sees the error word set stops
+// waiting, sets the error word and returns false; every block then leaves the
+// kernel, so a failure ends as an error status, never a hang.
+constexpr unsigned long long kBarrierNs = 2000000000ull; // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err, unsigned expected,
+                             unsigned long long limit_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = gen;
+        volatile int *verr = err;
+        const unsigned g0 = *vgen;
+        int ok = 1;
+        __threadfence();
+        const unsigned prev = atomicAdd(count, 1u);
+        if (prev + 1 == expected) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g0) {
+                if (*verr || global_ns() - t0 > limit_ns) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && *verr == 0;
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+// ----------------------------------------------------------------------------
 // Generation start (Alg. 3 Clone): P <- O.  If the elitist changed in the last
 // generation, its bits are taken from column `argmax` of O (O has not changed
 // since).  eqw[w] bit b ends as 1 iff individual 32w+b equals the elitist on
-// every variable (the flag of the acceptance rule, fixed for the generation).
-// Thread idx handles word idx = v*W + w; the grid stride is a multiple of W.
-__global__ void k_gen_start(GomParams P)
+// every variable (the flag of the acceptance rule, fixed for the generation);
+// eqw starts all ones.  Thread idx handles word idx = v*W + w; the grid
+// stride is a multiple of W.
+__device__ void phase_gen_start(const GomParams &P)
 {
     __shared__ uint32_t s_eq[32];
-    if (P.st->done) return;
     const int improved = P.st->improved;
     const int aw = P.st->argmax >> 5, ab = P.st->argmax & 31;
     const int W = P.W;
@@ -228,16 +282,15 @@ __global__ void k_gen_start(GomParams P)
     const int lane = threadIdx.x & 31;
     if (lane < W) atomicAnd(&s_eq[lane], eq);
     __syncthreads();
-    if (threadIdx.x < W && threadIdx.x < 32) atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
+    if (threadIdx.x < W && threadIdx.x < 32 && s_eq[threadIdx.x] != kFull)
+        atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
 }
 
 // Group order of generation g (Alg. 3, "random order"): colours sorted by
 // their 64-bit Philox key, ties by colour index.  Every block draws all k keys
-// into shared memory and ranks blockDim colours.
-__global__ void k_order(GomParams P)
+// into shared memory s_key[k] and ranks a grid-strided share of the colours.
+__device__ void phase_order(const GomParams &P, unsigned long long *s_key)
 {
-    extern __shared__ unsigned long long s_key[];
-    if (P.st->done) return;
     const uint32_t g = P.st->g;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int c = threadIdx.x; c < P.k; c += blockDim.x) {
@@ -245,8 +298,7 @@ __global__ void k_order(GomParams P)
         s_key[c] = ((unsigned long long)r.x << 32) | r.y;
     }
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < P.k) {
+    for (int c = (int)gthread(); c < P.k; c += (int)gthreads()) {
         const unsigned long long kc = s_key[c];
         int rank = 0;
         for (int c2 = 0; c2 < P.k; ++c2) {
@@ -255,10 +307,46 @@ __global__ void k_order(GomParams P)
         }
         P.order[rank] = c;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->improved = 0; // x_e copied by k_gen_start
+    __syncthreads();
 }
 
-// Loads WPI consecutive 32-bit words (16/8/4-byte aligned by construction).
+// Generation end (one block): elitist update (strict improvement, lowest
+// index of the best; Sec. 4), counters, target check, g += 1.  `improved`
+// records whether this generation replaced the elitist, so the next
+// generation start copies it out of O.
+__device__ void phase_gen_end(const GomParams &P, int64_t target)
+{
+    int64_t best;
+    int arg;
+    block_argmax(P.f, P.p, &best, &arg);
+    if (threadIdx.x == 0) {
+        GomDevState *st = P.st;
+        const int better = best > st->fe;
+        if (better) {
+            st->fe = best;
+            st->argmax = arg;
+        }
+        st->improved = better;
+        st->best = best;
+        GomDevStats &S = P.stats[st->g % kStatsCap];
+        S.generation = st->g;
+        S.best = best;
+        S.elite = st->fe;
+        S.trials = (int64_t)P.p * P.m;
+        S.donorless = st->cnt[0];
+        S.accepted = st->cnt[1];
+        S.improving = st->cnt[2];
+        S.reached = best >= target;
+        st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
+        st->done = best >= target;
+        st->g += 1;
+    }
+    for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
+    __syncthreads();
+}
+
+// Loads WPI consecutive 32-bit words (16/8/4-byte aligned by construction);
+// works on global and shared memory.
 template <int WPI>
 __device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&x)[WPI])
 {
@@ -298,29 +386,13 @@ __device__ int scan_donor(const uint32_t *sP, int W, int Wv, int p, int s, MaskT
     return -1;
 }
 
-// Bits of individual `d` on F from the staged rows of P.
-template <typename MaskT>
-__device__ __forceinline__ MaskT pattern_of(const uint32_t *sP, int W, int s, int d)
-{
-    const int dw = d >> 5, db = d & 31;
-    MaskT pat = 0;
-#pragma unroll 4
-    for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + dw] >> db) & 1u) << a;
-    return pat;
-}
-
-// Words per staged edge record in k_mix: WPI parent words, then code and
-// weight, padded to a power of two so the parent words load as one vector.
+// Words per staged edge record in the mixing phase: WPI parent words, then
+// code and weight, padded to a power of two so the parent words load as one
+// vector.
 template <int WPI>
 struct EdgeStride {
     static constexpr int value = WPI == 4 ? 8 : 4;
 };
-
-template <int WPI>
-__device__ __forceinline__ void lds_words(const uint32_t *p, uint32_t (&x)[WPI])
-{
-    load_words<WPI>(p, x); // shared-memory pointer: same vector widths
-}
 
 // Value held by lane (a mod 32) of lo (a < 32) or hi (a >= 32): per-variable
 // registers of elements with up to 64 variables.  Warp-uniform a.
@@ -331,22 +403,27 @@ __device__ __forceinline__ T lane_get(T lo, T hi, int a)
     return __shfl_sync(kFull, lo, a);
 }
 
+// Number of candidates the mixing phase checks one by one through the
+// pattern table before the word-parallel scan takes over.
+constexpr int kDonorProbe = 4;
+
 // One colour group: all (individual, element) GOM trials (Alg. 2) of group
 // order[t].  One warp per element; it walks the element's population words in
 // groups of WPI (lane l works on individuals 32w + l of those words).
 // Elements of one group share no variable and no edge (LMIG colouring), so
 // the warp owns its element's rows and nothing else in the group touches the
 // closure it reads.  Per element the warp stages, with lane-parallel loads,
-// the generation-start rows of P on F_j and the element's edge list into its
-// slice of shared memory; per word group it stages the parent's words of the
-// outside neighbours, so the trial work below reads no global memory.
+// the generation-start rows of P on F_j, the table patP[d] of every
+// individual's bits on F_j, and the element's edge list into its slice of
+// shared memory; per word group it stages the parent's words of the outside
+// neighbours, so the trial work reads no global memory.
 //  draws:   one Philox call per lane gives 4 words: lane c holds the call
 //           of individuals 4c..4c+3 of the word group, fetched by shuffles
-//  donor:   the start candidate's bits on F_j first; if equal to the
-//           parent's, the word-parallel cyclic scan (scan_donor)
-//  delta:   per variable a of F_j that flips, the weighted count S of its
-//           outside neighbours set in the parent gives the cut change of its
-//           outside edges (x_a ? 2S - W_a : W_a - 2S); edges inside F_j are
+//  donor:   candidates from the start, one by one through patP, then the
+//           word-parallel cyclic scan (scan_donor); flips = patP[d] ^ parent
+//  delta:   per variable a of F_j, the weighted count S of its outside
+//           neighbours set in the parent gives the cut change of its outside
+//           edges if a flips (x_a ? 2S - W_a : W_a - 2S); edges inside F_j are
 //           evaluated directly, once each (Sec. 2.2, Alg. 4)
 //  accept:  delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
 //  write:   one ballot per (variable, word); lane a XORs the accepted flips
@@ -357,14 +434,11 @@ __device__ __forceinline__ T lane_get(T lo, T hi, int a)
 // atomic per individual (and per counter) per block: integer adds, so the
 // result does not depend on their order.
 template <int WPI, typename MaskT, typename AccT>
-__global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
+__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s_dyn, long long *s_f,
+                                          unsigned long long *s_cnt)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
     constexpr int ES = EdgeStride<WPI>::value;
-    extern __shared__ __align__(16) uint32_t s_dyn[];
-    __shared__ long long s_f[1024];
-    __shared__ unsigned long long s_cnt[4];
-    if (P.st->done) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = P.W, Wv = P.Wv, p = P.p;
     const int lw = __ffs(W) - 1;
@@ -373,8 +447,9 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
 
-    uint32_t *sP = s_dyn + wib * P.warp_smem;          // [s][W] rows of P on F_j
-    uint32_t *sE = sP + ((P.smax * W + 3) & ~3);       // [E][ES] edge records
+    uint32_t *sP = s_dyn + wib * P.warp_smem;                         // [s][W] rows of P on F_j
+    MaskT *patP = reinterpret_cast<MaskT *>(sP + ((P.smax * W + 3) & ~3)); // [32 W] bits of P[d] on F_j
+    uint32_t *sE = reinterpret_cast<uint32_t *>(patP + np);           // [E][ES] edge records
     const int c = P.order[t];
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
@@ -407,6 +482,13 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
             const int2 d = P.dep[d0 + x];
             sE[x * ES + WPI] = (uint32_t)d.x;
             sE[x * ES + WPI + 1] = (uint32_t)d.y;
+        }
+        __syncwarp();
+        // pattern table: lane l builds the bits on F_j of individuals 32 wc + l
+        for (int wc = 0; wc < Wv; ++wc) {
+            MaskT pat = 0;
+            for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + wc] >> lane) & 1u) << a;
+            patP[32 * wc + lane] = pat;
         }
         __syncwarp();
 
@@ -450,18 +532,25 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
                 fm[r] = 0;
                 if (i < p) {
                     const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
-                    int ds = i + 1 + (int)u;
-                    if (ds >= p) ds -= p;
-                    const MaskT pat = pattern_of<MaskT>(sP, W, s, ds);
-                    if (pat != xf[r]) {
-                        donor[r] = ds;
+                    int d = i + 1 + (int)u;
+                    if (d >= p) d -= p;
+                    MaskT pat = patP[d];
+                    int probe = 1;
+                    while (pat == xf[r] && probe < kDonorProbe) {
+                        if (++d == p) d = 0;
+                        if (d == i && ++d == p) d = 0;
+                        pat = patP[d];
+                        ++probe;
+                    }
+                    if (pat == xf[r]) { // the rest of the cycle, 32 candidates a step
+                        if (++d == p) d = 0;
+                        if (d == i && ++d == p) d = 0;
+                        d = d == i ? -1 : scan_donor<MaskT>(sP, W, Wv, p, s, xf[r], d, i);
+                        if (d >= 0) pat = patP[d];
+                    }
+                    if (d >= 0 && pat != xf[r]) {
+                        donor[r] = d;
                         fm[r] = pat ^ xf[r];
-                    } else {
-                        const int d = scan_donor<MaskT>(sP, W, Wv, p, s, xf[r], ds, i);
-                        if (d >= 0) {
-                            donor[r] = d;
-                            fm[r] = pattern_of<MaskT>(sP, W, s, d) ^ xf[r];
-                        }
                     }
                 }
             }
@@ -470,43 +559,37 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
             AccT dl[WPI];
 #pragma unroll
             for (int r = 0; r < WPI; ++r) dl[r] = 0;
-            bool any = false;
+            for (int a = 0; a < s; ++a) {
+                const int qb = lane_get<WIDE>(sg, sg2, a);
+                const int qe = (a + 1 == s) ? n_out : lane_get<WIDE>(sg, sg2, a + 1);
+                const AccT Wa = lane_get<WIDE>(wl, wl2, a);
+                AccT S[WPI];
 #pragma unroll
-            for (int r = 0; r < WPI; ++r) any |= fm[r] != 0;
-            if (__any_sync(kFull, any)) {
-                for (int a = 0; a < s; ++a) {
-                    bool flips = false;
-#pragma unroll
-                    for (int r = 0; r < WPI; ++r) flips |= (fm[r] >> a) & 1u;
-                    const int qb = lane_get<WIDE>(sg, sg2, a);
-                    const int qe = (a + 1 == s) ? n_out : lane_get<WIDE>(sg, sg2, a + 1);
-                    const AccT Wa = lane_get<WIDE>(wl, wl2, a);
-                    if (!__any_sync(kFull, flips)) continue;
-                    AccT S[WPI];
-#pragma unroll
-                    for (int r = 0; r < WPI; ++r) S[r] = 0;
-                    for (int x = qb; x < qe; ++x) {
-                        uint32_t X[WPI];
-                        lds_words<WPI>(sE + x * ES, X);
-                        const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
-#pragma unroll
-                        for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
-                    }
-#pragma unroll
-                    for (int r = 0; r < WPI; ++r)
-                        if ((fm[r] >> a) & 1u) dl[r] += ((xf[r] >> a) & 1u) ? 2 * S[r] - Wa : Wa - 2 * S[r];
-                }
-                for (int x = n_out; x < ne_tot; ++x) {
-                    const uint32_t code = sE[x * ES + WPI];
+                for (int r = 0; r < WPI; ++r) S[r] = 0;
+                for (int x = qb; x < qe; ++x) {
+                    uint32_t X[WPI];
+                    load_words<WPI>(sE + x * ES, X);
                     const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
-                    const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
-                    for (int r = 0; r < WPI; ++r) {
-                        const MaskT y = xf[r] ^ fm[r];
-                        const int cn = (int)(((y >> a) ^ (y >> b)) & 1u);
-                        const int co = (int)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u);
-                        dl[r] += wx * (AccT)(cn - co);
-                    }
+                    for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
+                }
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) {
+                    const AccT gain = Wa - 2 * S[r];                      // if x_a = 0
+                    const AccT sx = -(AccT)((xf[r] >> a) & 1u);          // 0 or -1
+                    const AccT sf = -(AccT)((fm[r] >> a) & 1u);
+                    dl[r] += ((gain ^ sx) - sx) & sf;
+                }
+            }
+            for (int x = n_out; x < ne_tot; ++x) {
+                const uint32_t code = sE[x * ES + WPI];
+                const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
+                const int a = code & 0xFF, b = code >> 8;
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) {
+                    const AccT tg = (AccT)(((fm[r] >> a) ^ (fm[r] >> b)) & 1u); // edge toggles
+                    const AccT sc = -(AccT)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u); // cut before
+                    dl[r] += ((wx ^ sc) - sc) & -tg;
                 }
             }
 
@@ -566,6 +649,78 @@ __global__ void __launch_bounds__(kMixThreads) k_mix(GomParams P, int t)
     }
     if (threadIdx.x < 3 && s_cnt[threadIdx.x])
         atomicAdd((unsigned long long *)&P.st->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// Kernels of the per-launch path (one CUDA graph per generation).
+
+__global__ void k_gen_start(GomParams P)
+{
+    if (P.st->done) return;
+    phase_gen_start(P);
+}
+
+__global__ void k_order(GomParams P)
+{
+    extern __shared__ unsigned long long s_key[];
+    if (P.st->done) return;
+    phase_order(P, s_key);
+}
+
+template <int WPI, typename MaskT, typename AccT>
+__global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ long long s_f[1024];
+    __shared__ unsigned long long s_cnt[4];
+    if (P.st->done) return;
+    phase_mix<WPI, MaskT, AccT>(P, t, s_dyn, s_f, s_cnt);
+}
+
+__global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
+{
+    if (P.st->done) return;
+    phase_gen_end(P, P.st->target);
+}
+
+// Persistent path: up to G generations in one cooperative launch, the phases
+// separated by grid barriers (gen start + order | each colour group | gen
+// end).  Stops early once a generation reached the target: done is written
+// by every generation end and read after the following barrier, so every
+// block takes the same decision (the first generation of a call ignores the
+// flag left by an earlier call).
+template <int WPI, typename MaskT, typename AccT>
+__global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ long long s_f[1024];
+    __shared__ unsigned long long s_cnt[4];
+    const unsigned nblk = gridDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.st->call_g0 = P.st->g; // read by the host after the kernel only
+        P.st->target = target;
+    }
+    for (int q = 0; q < G; ++q) {
+        if (q > 0 && *(volatile int32_t *)&P.st->done) return;
+        phase_gen_start(P);
+        phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn));
+        if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+        for (int t = 0; t < P.k; ++t) {
+            phase_mix<WPI, MaskT, AccT>(P, t, s_dyn, s_f, s_cnt);
+            if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+        }
+        if (blockIdx.x == 0) phase_gen_end(P, target);
+        if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+    }
+}
+
+// Self-test of the grid barrier's bounded wait: `blocks` co-resident blocks
+// meet at a barrier that expects `blocks + extra` arrivals; with extra > 0 no
+// block is ever released and every block must give up after limit_ns.
+__global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigned long long limit_ns)
+{
+    grid_barrier(&bar->count, &bar->gen, err, gridDim.x + (unsigned)extra, limit_ns);
 }
 
 const void *gom_mix_kernel(int wpi, bool narrow)
@@ -579,38 +734,18 @@ const void *gom_mix_kernel(int wpi, bool narrow)
                     : (const void *)k_mix<1, uint64_t, long long>;
 }
 
-// Generation end: elitist update (strict improvement, lowest index; Sec. 4),
-// counters, target check, g += 1.
-__global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
+const void *gom_run_kernel(int wpi, bool narrow)
 {
-    if (P.st->done) return;
-    int64_t best;
-    int arg;
-    block_argmax(P.f, P.p, &best, &arg);
-    if (threadIdx.x == 0) {
-        GomDevState *st = P.st;
-        if (best > st->fe) {
-            st->fe = best;
-            st->improved = 1;
-            st->argmax = arg;
-        }
-        st->best = best;
-        GomDevStats &S = P.stats[st->g % kStatsCap];
-        S.generation = st->g;
-        S.best = best;
-        S.elite = st->fe;
-        S.trials = (int64_t)P.p * P.m;
-        S.donorless = st->cnt[0];
-        S.accepted = st->cnt[1];
-        S.improving = st->cnt[2];
-        S.reached = best >= st->target;
-        st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
-        st->done = best >= st->target;
-        st->g += 1;
-    }
-    for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
+    if (narrow)
+        return wpi == 4 ? (const void *)k_run<4, uint32_t, int32_t>
+             : wpi == 2 ? (const void *)k_run<2, uint32_t, int32_t>
+                        : (const void *)k_run<1, uint32_t, int32_t>;
+    return wpi == 4 ? (const void *)k_run<4, uint64_t, long long>
+         : wpi == 2 ? (const void *)k_run<2, uint64_t, long long>
+                    : (const void *)k_run<1, uint64_t, long long>;
 }
 
+// ----------------------------------------------------------------------------
 // uint8 rows out[i*n + v] of the population.
 __global__ void k_export_pop(GomParams P, uint8_t *out)
 {

@@ -17,6 +17,9 @@ __global__ void k_order(GomParams P);
 // 32-bit (narrow) or 64-bit masks and deltas; a host-stub address usable as a
 // graph-node function.
 const void *gom_mix_kernel(int wpi, bool narrow);
+// The persistent generation kernel k_run<WPI, mask, delta>(GomParams, int G, int64_t target).
+const void *gom_run_kernel(int wpi, bool narrow);
+__global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigned long long limit_ns);
 __global__ void k_gen_end(GomParams P);
 __global__ void k_export_pop(GomParams P, uint8_t *out);
 __global__ void k_export_elite(GomParams P, uint8_t *out);

@@ -20,6 +20,7 @@ GOM_FOS_NEIGHBOURHOOD = 0
 GOM_FOS_SINGLETON = 1
 GOM_MAX_POPULATION = 1024
 GOM_MAX_ELEMENT = 64
+GOM_OPT_PERSISTENT = 1
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
@@ -69,6 +70,9 @@ SIGNATURES = [
     ("gom_set_timing", C.c_int, [_P, _I32]),
     ("gom_read_timing", C.c_int, [_P, _P, _P]),
     ("gom_launches_per_generation", C.c_int, [_P, _P]),
+    ("gom_set_option", C.c_int, [_P, _I32, _I64]),
+    ("gom_get_option", C.c_int, [_P, _I32, _P]),
+    ("gom_selftest_barrier", C.c_int, [_P, _I32, _I32, _I64, _P, _P]),
     ("gom_last_cuda_error", C.c_int, [_P]),
     ("gom_destroy", None, [_P]),
     ("gom_strerror", C.c_char_p, [C.c_int]),
@@ -296,6 +300,24 @@ def gom_launches_per_generation(ctx: Ctx) -> int:
     return int(n.value)
 
 
+def gom_set_option(ctx: Ctx, option: int, value: int):
+    _check(load().gom_set_option(ctx.h, option, value), "gom_set_option")
+
+
+def gom_get_option(ctx: Ctx, option: int) -> int:
+    v = C.c_int64()
+    _check(load().gom_get_option(ctx.h, option, C.byref(v)), "gom_get_option")
+    return int(v.value)
+
+
+def gom_selftest_barrier(d_scratch, blocks: int, extra: int, limit_ns: int, stream=None) -> bool:
+    """True if the barrier's bounded wait gave up (expected when extra > 0)."""
+    out = C.c_int32()
+    _check(load().gom_selftest_barrier(_ptr(d_scratch), blocks, extra, limit_ns, _stream(stream), C.byref(out)),
+           "gom_selftest_barrier")
+    return bool(out.value)
+
+
 def gom_last_cuda_error(ctx: Ctx) -> int:
     return int(load().gom_last_cuda_error(ctx.h))
 
@@ -314,7 +336,7 @@ class Population:
     workspace with torch and drives the C ABI above."""
 
     def __init__(self, graph, pop: int, seed: int, kind: int = GOM_FOS_NEIGHBOURHOOD, fos: Fos = None,
-                 stream=None, device=None):
+                 stream=None, device=None, persistent: bool = None):
         import torch
         self.torch = torch
         self.graph = _graph(graph)
@@ -338,6 +360,8 @@ class Population:
         self.ctx = gom_init_population(self.graph, fos, pop, seed, self.workspace.data_ptr() + off, nbytes,
                                        stream)
         self.ctx.workspace = self.workspace
+        if persistent is not None:
+            gom_set_option(self.ctx, GOM_OPT_PERSISTENT, 1 if persistent else 0)
 
     def generation(self, num: int = 1, target: int = INT64_MAX, want_stats: bool = True):
         return gom_generation(self.ctx, num, target, want_stats)

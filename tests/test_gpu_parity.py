@@ -45,20 +45,25 @@ def _assert_same_stats(gst, ost):
 
 
 def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MAX):
-    P = gom.Population(g, p, seed, kind)
+    """Both execution paths (persistent kernel, per-generation graph) against
+    the oracle after every generation."""
+    Ps = [gom.Population(g, p, seed, kind, persistent=True), gom.Population(g, p, seed, kind, persistent=False)]
     run, k = _oracle_run(oracle, g, p, seed, kind)
-    assert P.k == k
-    _assert_same_state(_gpu_state(P), run.get(), "init")
+    for P in Ps:
+        assert P.k == k
+        _assert_same_state(_gpu_state(P), run.get(), "init")
     for gen in range(gens):
-        gst, nrun = P.generation(1, target)
         ost = run.generation(target)
-        assert nrun == 1
-        _assert_same_stats(gst[0], ost)
+        for P in Ps:
+            gst, nrun = P.generation(1, target)
+            assert nrun == 1
+            _assert_same_stats(gst[0], ost)
         if (gen + 1) % check_every == 0 or gen == gens - 1:
-            _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")
-            # incremental fitness equals full re-evaluation on the device
-            assert np.array_equal(P.fitness().cpu().numpy(), run.get()["f"])
-    return P, run
+            for P in Ps:
+                _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")
+                # incremental fitness equals full re-evaluation on the device
+                assert np.array_equal(P.fitness().cpu().numpy(), run.get()["f"])
+    return Ps[0], run
 
 
 def test_config_torus10_p16_every_generation(oracle):
@@ -198,7 +203,7 @@ def test_identical_population_is_all_donorless(oracle):
 
 def test_timing_mode_keeps_results_and_counts_launches(oracle):
     g = I.torus2d(16, seed=7)
-    A = gom.Population(g, 64, 8)
+    A = gom.Population(g, 64, 8, persistent=False)
     gom.gom_set_timing(A.ctx, True)
     A.generation(5)
     ms, launches = gom.gom_read_timing(A.ctx)
@@ -208,6 +213,7 @@ def test_timing_mode_keeps_results_and_counts_launches(oracle):
     sa, sb = _gpu_state(A), _gpu_state(B)
     assert np.array_equal(sa["pop"], sb["pop"]) and np.array_equal(sa["f"], sb["f"])
     assert gom.gom_launches_per_generation(A.ctx) == A.k + 3
+    assert gom.gom_launches_per_generation(B.ctx) == (1 if gom.gom_get_option(B.ctx, gom.GOM_OPT_PERSISTENT) else A.k + 3)
 
 
 def test_user_stream(oracle):
@@ -260,3 +266,33 @@ def test_custom_overlapping_fos(oracle, p):
         gst, _ = P.generation(1)
         _assert_same_stats(gst[0], run.generation())
     _assert_same_state(_gpu_state(P), run.get())
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_long_call_target_stop_both_paths(oracle, persistent):
+    """One call of many generations (the persistent kernel runs them all in
+    one launch) stops at the same generation as the oracle."""
+    g = I.torus2d(12, seed=9)
+    run, _ = _oracle_run(oracle, g, 48, 2)
+    probe = run.run(40)
+    target = probe[25]["best"]
+    P = gom.Population(g, 48, 2, persistent=persistent)
+    run2, _ = _oracle_run(oracle, g, 48, 2)
+    gst, nrun = P.generation(40, target)
+    ost = run2.run(40, target)
+    assert nrun == len(ost)
+    for a, b in zip(gst, ost):
+        _assert_same_stats(a, b)
+    _assert_same_state(_gpu_state(P), run2.get())
+
+
+def test_grid_barrier_bounded_wait():
+    """Failure detection without a hang: a barrier that expects one arrival
+    too many gives up after its wall-clock limit and reports it; the context
+    stays usable."""
+    scratch = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    assert gom.gom_selftest_barrier(scratch, 8, 0, 200_000_000) is False
+    assert gom.gom_selftest_barrier(scratch, 8, 1, 50_000_000) is True
+    assert gom.gom_selftest_barrier(scratch, 8, 0, 200_000_000) is False
+    P = gom.Population(I.torus2d(6), 8, 1)
+    P.generation(2)
