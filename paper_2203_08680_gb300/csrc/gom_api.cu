@@ -368,10 +368,15 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int dev = 0;
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-    // per-warp shared memory of k_mix: the rows of P on one element, then
-    // one record per edge (WPI parent words + code + weight, padded)
+    // per-warp shared memory of the mixing phase (the only definition of its
+    // layout; the kernel takes these offsets): the rows of P on one element,
+    // the table of every individual's bits on it (32 W masks of 4 or 8
+    // bytes), then one record per edge (WPI parent words, code and weight,
+    // padded to 4 or 8 words).  All offsets are multiples of 4 words.
     const int es = wpi == 4 ? 8 : 4;
-    const int64_t warp_words = ((static_cast<int64_t>(tabs.max_s) * c->W + 3) & ~int64_t(3)) + tabs.max_edges * es;
+    const int64_t off_pat = (static_cast<int64_t>(tabs.max_s) * c->W + 3) & ~int64_t(3);
+    const int64_t off_edge = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
+    const int64_t warp_words = off_edge + tabs.max_edges * es;
     constexpr int64_t kSmemBudget = 200 * 1024;
     const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (warp_words * 4)));
     if (warps_per_block < 1) return GOM_E_LIMIT;
@@ -426,8 +431,9 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.m = static_cast<int32_t>(fos->m);
     P.k = fos->k;
     P.seed = seed;
-    P.smax = tabs.max_s;
     P.warp_smem = static_cast<int32_t>(warp_words);
+    P.off_pat = static_cast<int32_t>(off_pat);
+    P.off_edge = static_cast<int32_t>(off_edge);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);
     P.f = reinterpret_cast<int64_t *>(base + L.f);

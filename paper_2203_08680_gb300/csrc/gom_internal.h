@@ -96,8 +96,9 @@ struct GomParams {
     int32_t Wv;        // words holding valid individuals, ceil(p/32)
     int32_t m;         // FOS elements
     int32_t k;         // colours
-    int32_t smax;       // largest element (rows of P staged per warp)
-    int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in k_mix
+    int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in the mixing phase:
+    int32_t off_pat;    //   [0, off_pat) rows of P on F_j, [off_pat, off_edge) pattern
+    int32_t off_edge;   //   table (32 W masks), [off_edge, warp_smem) edge records
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population

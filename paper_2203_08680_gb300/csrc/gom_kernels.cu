@@ -447,9 +447,10 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
 
-    uint32_t *sP = s_dyn + wib * P.warp_smem;                         // [s][W] rows of P on F_j
-    MaskT *patP = reinterpret_cast<MaskT *>(sP + ((P.smax * W + 3) & ~3)); // [32 W] bits of P[d] on F_j
-    uint32_t *sE = reinterpret_cast<uint32_t *>(patP + np);           // [E][ES] edge records
+    // this warp's slice; the host sizes it from the largest element
+    uint32_t *sP = s_dyn + wib * P.warp_smem;                          // [s][W] rows of P on F_j
+    MaskT *patP = reinterpret_cast<MaskT *>(sP + P.off_pat);           // [32 W] bits of P[d] on F_j
+    uint32_t *sE = sP + P.off_edge;                                    // [E][ES] edge records
     const int c = P.order[t];
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);

@@ -99,8 +99,10 @@ def load():
     return _lib
 
 
-def _check(rc: int, what: str):
+def _check(rc: int, what: str, ctx=None):
     if rc != GOM_OK:
+        if rc == -5 and ctx is not None and getattr(ctx, "h", None):
+            what = f"{what} (cudaError {load().gom_last_cuda_error(ctx.h)})"
         raise GomError(rc, what)
 
 
@@ -248,11 +250,11 @@ def gom_generation(ctx: Ctx, num_generations: int, target_fitness: int = INT64_M
     """Returns (list of per-generation stats dicts, generations run); with
     want_stats=False only enqueues and returns (None, None)."""
     if not want_stats:
-        _check(load().gom_generation(ctx.h, num_generations, target_fitness, None, None), "gom_generation")
+        _check(load().gom_generation(ctx.h, num_generations, target_fitness, None, None), "gom_generation", ctx)
         return None, None
     arr = (GenStats * max(num_generations, 1))()
     run = C.c_int32()
-    _check(load().gom_generation(ctx.h, num_generations, target_fitness, arr, C.byref(run)), "gom_generation")
+    _check(load().gom_generation(ctx.h, num_generations, target_fitness, arr, C.byref(run)), "gom_generation", ctx)
     return [arr[q].as_dict() for q in range(run.value)], int(run.value)
 
 
