@@ -247,6 +247,40 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value);
 int gom_selftest_barrier(void *d_scratch, int32_t blocks, int32_t extra, int64_t limit_ns, void *cuda_stream,
                          int32_t *timed_out);
 
+/*
+ * Largest problem of gom_fitness_noalloc: num_vertices * W words, W the
+ * smallest power of two with 32 W >= pop.  The scratch array behind it,
+ * 4 Mi words = 16 MiB, is held by every GPU that loads this library until
+ * the process exits.
+ */
+#define GOM_NOALLOC_MAX_WORDS (4 * 1024 * 1024)
+
+/*
+ * Full fitness (cut weight) of every individual of a caller-given population,
+ * without allocating any device memory -- for callers that must not allocate:
+ * cudaMalloc can synchronise the device and can fail under memory pressure,
+ * and some host programs hand out all device memory through their own
+ * allocator.  It does the same evaluation as gom_fitness but needs no handle
+ * or workspace: its scratch (the population packed 32 individuals per word)
+ * is a fixed array inside the library.  The paper has no counterpart; it is
+ * an interface convenience.
+ *   d_row_ptr[num_vertices+1] (int64), d_col, d_weight (int32): the graph's
+ *     symmetric CSR in device memory, as in gom_graph_t (not validated here);
+ *   d_pop[pop][num_vertices]: uint8 {0,1} rows, device;
+ *   d_fitness_out[pop]: int64, device, overwritten.
+ * Enqueued on cuda_stream (NULL = legacy default stream).  Returns
+ * GOM_E_LIMIT if num_vertices * W > GOM_NOALLOC_MAX_WORDS or
+ * pop > GOM_MAX_POPULATION, GOM_E_ARG on null pointers or non-positive sizes.
+ * The first call on a device looks up the scratch array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  All calls share the one scratch array, which keeps the last
+ * call's contents (every call rewrites the part it reads): calls that overlap
+ * on the GPU, on different streams or threads, race.
+ */
+int gom_fitness_noalloc(const int64_t *d_row_ptr, const int32_t *d_col, const int32_t *d_weight,
+                        int32_t num_vertices, const uint8_t *d_pop, int32_t pop, int64_t *d_fitness_out,
+                        void *cuda_stream);
+
 /* Last CUDA error code seen by the handle (0 if none). */
 int gom_last_cuda_error(gom_ctx_t *ctx);
 

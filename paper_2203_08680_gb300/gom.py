@@ -73,6 +73,7 @@ SIGNATURES = [
     ("gom_set_option", C.c_int, [_P, _I32, _I64]),
     ("gom_get_option", C.c_int, [_P, _I32, _P]),
     ("gom_selftest_barrier", C.c_int, [_P, _I32, _I32, _I64, _P, _P]),
+    ("gom_fitness_noalloc", C.c_int, [_P, _P, _P, _I32, _P, _I32, _P, _P]),
     ("gom_last_cuda_error", C.c_int, [_P]),
     ("gom_destroy", None, [_P]),
     ("gom_strerror", C.c_char_p, [C.c_int]),
@@ -318,6 +319,14 @@ def gom_selftest_barrier(d_scratch, blocks: int, extra: int, limit_ns: int, stre
     _check(load().gom_selftest_barrier(_ptr(d_scratch), blocks, extra, limit_ns, _stream(stream), C.byref(out)),
            "gom_selftest_barrier")
     return bool(out.value)
+
+
+def gom_fitness_noalloc(d_row_ptr, d_col, d_weight, num_vertices: int, d_pop, pop: int, d_fitness_out,
+                        stream=None):
+    """Full fitness of a device uint8 population without any device
+    allocation (the library's fixed scratch array; see include/gom.h)."""
+    _check(load().gom_fitness_noalloc(_ptr(d_row_ptr), _ptr(d_col), _ptr(d_weight), num_vertices, _ptr(d_pop),
+                                      pop, _ptr(d_fitness_out), _stream(stream)), "gom_fitness_noalloc")
 
 
 def gom_last_cuda_error(ctx: Ctx) -> int:
