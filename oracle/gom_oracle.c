@@ -283,15 +283,51 @@ static int cmp_wp(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
+/* Calls of the neighbour enumeration below: every LMIG neighbour jj != j of
+ * element j, through the variables of F_j and of their VIG neighbours and the
+ * elements holding each such variable; seen[] (stamped with j) makes each
+ * neighbour appear once.  The LMIG itself is never stored. */
+typedef struct {
+    int32_t n;
+    const int64_t *rp;
+    const int32_t *col;
+    const int64_t *eptr;
+    const int32_t *evars;
+    int64_t *vptr;
+    int32_t *velems;
+    int64_t *seen;
+} lmig_walk;
+
+static int64_t lmig_degree(lmig_walk *L, int64_t j)
+{
+    int64_t deg = 0;
+    for (int64_t q = L->eptr[j]; q < L->eptr[j + 1]; ++q) {
+        int32_t u = L->evars[q];
+        for (int64_t e = L->rp[u] - 1; e < L->rp[u + 1]; ++e) {
+            int32_t v = (e < L->rp[u]) ? u : L->col[e];
+            for (int64_t r = L->vptr[v]; r < L->vptr[v + 1]; ++r) {
+                int32_t jj = L->velems[r];
+                if (jj == j || L->seen[jj] == j) continue;
+                L->seen[jj] = j;
+                ++deg;
+            }
+        }
+    }
+    return deg;
+}
+
 /* R4.  Returns the number of colours k; color_of_elem[j] in [0,k). */
 int32_t orc_color(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
                   const int64_t *eptr, const int32_t *evars, int32_t *color_of_elem)
 {
-    lmig_t L = build_lmig(n, rp, col, m, eptr, evars);
+    lmig_walk L = {n, rp, col, eptr, evars, NULL, NULL, NULL};
+    invert_fos(n, m, eptr, evars, &L.vptr, &L.velems);
+    L.seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) L.seen[j] = -1;
     int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
     for (int64_t j = 0; j < m; ++j) {
-        deg[j] = L.nptr[j + 1] - L.nptr[j];
+        deg[j] = lmig_degree(&L, j);
         order[j] = (int32_t)j;
         color_of_elem[j] = -1;
     }
@@ -302,9 +338,16 @@ int32_t orc_color(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
     for (int64_t c = 0; c <= m; ++c) used[c] = -1;
     for (int64_t t = 0; t < m; ++t) {
         int32_t j = order[t];
-        for (int64_t q = L.nptr[j]; q < L.nptr[j + 1]; ++q) {
-            int32_t c = color_of_elem[L.nbr[q]];
-            if (c >= 0) used[c] = j;
+        /* colours of the coloured LMIG neighbours of j */
+        for (int64_t q = eptr[j]; q < eptr[j + 1]; ++q) {
+            int32_t u = evars[q];
+            for (int64_t e = rp[u] - 1; e < rp[u + 1]; ++e) {
+                int32_t v = (e < rp[u]) ? u : col[e];
+                for (int64_t r = L.vptr[v]; r < L.vptr[v + 1]; ++r) {
+                    int32_t jj = L.velems[r];
+                    if (jj != j && color_of_elem[jj] >= 0) used[color_of_elem[jj]] = j;
+                }
+            }
         }
         int32_t c = 0;
         while (used[c] == j) ++c;
@@ -314,7 +357,9 @@ int32_t orc_color(int32_t n, const int64_t *rp, const int32_t *col, int64_t m,
     free(used);
     free(order);
     free(deg);
-    free_lmig(&L);
+    free(L.seen);
+    free(L.vptr);
+    free(L.velems);
     return k;
 }
 
@@ -418,9 +463,18 @@ static void elitist_from_scratch(orc_state *s)
 
 /* InitializePopulation (Alg. 3): bit v of individual i is bit (v mod 32) of
  * word (v/32 mod 4) of Philox(ctr = (v/128, i, 0, TAG_INIT)). */
-orc_state *orc_new(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
-                   int64_t m, const int64_t *eptr, const int32_t *evars,
-                   const int32_t *color_of_elem, int32_t k, int32_t p, uint64_t seed)
+void orc_init_individual(uint64_t seed, int32_t i, int32_t n, uint8_t *x)
+{
+    for (int32_t v = 0; v < n; ++v) {
+        uint32_t r = draw(seed, (uint32_t)v >> 7, (uint32_t)i, 0u, ORC_TAG_INIT, (v >> 5) & 3);
+        x[v] = (uint8_t)((r >> (v & 31)) & 1u);
+    }
+}
+
+/* With init = 0 the population is left zero (for orc_load). */
+orc_state *orc_new_ex(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                      int64_t m, const int64_t *eptr, const int32_t *evars,
+                      const int32_t *color_of_elem, int32_t k, int32_t p, uint64_t seed, int32_t init)
 {
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->n = n;
@@ -451,21 +505,31 @@ orc_state *orc_new(int32_t n, const int64_t *rp, const int32_t *col, const int32
     for (int32_t v = 0; v < n; ++v) s->in_f[v] = -1;
     s->stamp = 0;
     s->eq = (uint8_t *)malloc((size_t)p);
+    s->g = 0;
+    if (!init) {
+        memset(s->O, 0, (size_t)p * (size_t)n);
+        memset(s->f, 0, sizeof(int64_t) * (size_t)p);
+        memset(s->xe, 0, (size_t)n);
+        s->fe = 0;
+    }
     {
         int64_t mx = 1;
         for (int64_t j = 0; j < m; ++j)
             if (eptr[j + 1] - eptr[j] > mx) mx = eptr[j + 1] - eptr[j];
         s->ybuf = (uint8_t *)malloc((size_t)mx);
     }
-    for (int32_t i = 0; i < p; ++i)
-        for (int32_t v = 0; v < n; ++v) {
-            uint32_t r = draw(seed, (uint32_t)v >> 7, (uint32_t)i, 0u, ORC_TAG_INIT, (v >> 5) & 3);
-            s->O[(size_t)i * n + v] = (uint8_t)((r >> (v & 31)) & 1u);
-        }
+    if (!init) return s;
+    for (int32_t i = 0; i < p; ++i) orc_init_individual(seed, i, n, s->O + (size_t)i * n);
     for (int32_t i = 0; i < p; ++i) s->f[i] = orc_cut_value(n, rp, col, w, s->O + (size_t)i * n);
     elitist_from_scratch(s);
-    s->g = 0;
     return s;
+}
+
+orc_state *orc_new(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w,
+                   int64_t m, const int64_t *eptr, const int32_t *evars,
+                   const int32_t *color_of_elem, int32_t k, int32_t p, uint64_t seed)
+{
+    return orc_new_ex(n, rp, col, w, m, eptr, evars, color_of_elem, k, p, seed, 1);
 }
 
 void orc_free(orc_state *s)

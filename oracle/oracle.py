@@ -60,6 +60,9 @@ def lib():
         L.orc_group_order.argtypes = [u64, i32, u32, P]
         L.orc_new.argtypes = [i32, P, P, P, i64, P, P, P, i32, i32, u64]
         L.orc_new.restype = P
+        L.orc_new_ex.argtypes = [i32, P, P, P, i64, P, P, P, i32, i32, u64, i32]
+        L.orc_new_ex.restype = P
+        L.orc_init_individual.argtypes = [u64, i32, i32, P]
         L.orc_free.argtypes = [P]
         L.orc_load.argtypes = [P, P, P, P, i64, u32]
         L.orc_get.argtypes = [P, P, P, P, P, P]
@@ -168,16 +171,24 @@ def group_order(seed: int, k: int, g: int):
     return out[:k]
 
 
-class Run:
-    """One parallel-GOMEA run of the oracle (population, fitness, elitist)."""
+def init_individual(seed: int, i: int, n: int):
+    """Initial bits of individual i (InitializePopulation, Alg. 3)."""
+    x = np.zeros(max(n, 1), dtype=np.uint8)
+    lib().orc_init_individual(seed, i, n, _p(x))
+    return x[:n]
 
-    def __init__(self, g, eptr, evars, colors, k: int, p: int, seed: int):
+
+class Run:
+    """One parallel-GOMEA run of the oracle (population, fitness, elitist).
+    With init=False the population starts empty, to be set with load()."""
+
+    def __init__(self, g, eptr, evars, colors, k: int, p: int, seed: int, init: bool = True):
         rp, col, w = _csr(g)
         eptr, evars = _fos_arrays(eptr, evars)
         colors = np.ascontiguousarray(colors, dtype=np.int32)
         self.n, self.p, self.m, self.k = g.n, p, len(eptr) - 1, k
-        self._h = lib().orc_new(g.n, _p(rp), _p(col), _p(w), self.m, _p(eptr), _p(evars),
-                                _p(colors), k, p, seed)
+        self._h = lib().orc_new_ex(g.n, _p(rp), _p(col), _p(w), self.m, _p(eptr), _p(evars),
+                                   _p(colors), k, p, seed, 1 if init else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)
