@@ -21,7 +21,7 @@
  *  R4 Welsh-Powell (Sec. 5.2): visit elements by LMIG degree descending, ties
  *     by ascending index; give each the smallest colour unused by its
  *     already-coloured neighbours.  Groups list their elements ascending.
- *  R5 group order (Alg. 3, "random order"): colours sorted ascending by a
+ *  R5 group order (Alg. 3 visits the groups in random order): colours sorted ascending by a
  *     64-bit Philox key per (colour, generation), ties by colour index.
  *  R6 donor (Sec. 4, SelectDonorFromPopulation): a uniform random start in the
  *     other p-1 individuals of the generation-start population P, then a

@@ -286,7 +286,7 @@ __device__ void phase_gen_start(const GomParams &P)
         atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
 }
 
-// Group order of generation g (Alg. 3, "random order"): colours sorted by
+// Group order of generation g (Alg. 3 visits the groups in random order): colours sorted by
 // their 64-bit Philox key, ties by colour index.  Every block draws all k keys
 // into shared memory s_key[k] and ranks a grid-strided share of the colours.
 __device__ void phase_order(const GomParams &P, unsigned long long *s_key)
