@@ -361,21 +361,36 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->k = fos->k;
 
     // kernel instance: words per item, mask and delta widths
-    const int wpi = std::min(c->W, 4);
     const bool narrow = tabs.max_s <= 32 && tabs.max_abs_w < (int64_t(1) << 30);
-    c->mix_fn = gom_mix_kernel(wpi, narrow);
-
+    int64_t max_group = 1;
+    for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
     int dev = 0;
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    // Work split: one warp per element walking all its words in groups of
+    // wpi = min(W, 4) words, or, when a colour group has too few elements to
+    // fill the GPU, one warp per (element, word group).
+    const int wv = (pop + 31) / 32;
+    int wpi = std::min(c->W, 4);
+    int split = 0;
+    if (max_group < static_cast<int64_t>(c->sms) * 16 && wv > 1) {
+        split = 1;
+        if ((wv + wpi - 1) / wpi == 1) wpi = 1;
+    }
+    const int per = split ? (wv + wpi - 1) / wpi : 1;
+    c->mix_fn = gom_mix_kernel(wpi, narrow);
     // per-warp shared memory of the mixing phase (the only definition of its
     // layout; the kernel takes these offsets): the rows of P on one element,
     // the table of every individual's bits on it (32 W masks of 4 or 8
-    // bytes), then one record per edge (WPI parent words, code and weight,
-    // padded to 4 or 8 words).  All offsets are multiples of 4 words.
+    // bytes), the run starts of that table (W words), one int4 per variable,
+    // then one record per edge (WPI parent words, code and weight, padded to
+    // 4 or 8 words).  All offsets are multiples of 4 words.
     const int es = wpi == 4 ? 8 : 4;
-    const int64_t off_pat = (static_cast<int64_t>(tabs.max_s) * c->W + 3) & ~int64_t(3);
-    const int64_t off_edge = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
+    auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    const int64_t off_pat = round4(static_cast<int64_t>(tabs.max_s) * c->W);
+    const int64_t off_rs = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
+    const int64_t off_var = off_rs + round4(c->W);
+    const int64_t off_edge = off_var + 4 * static_cast<int64_t>(tabs.max_s);
     const int64_t warp_words = off_edge + tabs.max_edges * es;
     constexpr int64_t kSmemBudget = 200 * 1024;
     const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (warp_words * 4)));
@@ -387,10 +402,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int occ = 0;
     GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
     occ = std::max(occ, 1);
-    // mixing grid: one warp per element of the largest group, at most a full wave
-    int64_t max_group = 1;
-    for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
-    const int64_t need_blocks = (max_group + warps_per_block - 1) / warps_per_block;
+    // mixing grid: one warp per item of the largest group, at most a full wave
+    const int64_t need_blocks = (max_group * per + warps_per_block - 1) / warps_per_block;
     int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
     c->grid_mix = static_cast<int>(grid);
@@ -431,8 +444,11 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.m = static_cast<int32_t>(fos->m);
     P.k = fos->k;
     P.seed = seed;
+    P.split = split;
     P.warp_smem = static_cast<int32_t>(warp_words);
     P.off_pat = static_cast<int32_t>(off_pat);
+    P.off_rs = static_cast<int32_t>(off_rs);
+    P.off_var = static_cast<int32_t>(off_var);
     P.off_edge = static_cast<int32_t>(off_edge);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);

@@ -96,9 +96,12 @@ struct GomParams {
     int32_t Wv;        // words holding valid individuals, ceil(p/32)
     int32_t m;         // FOS elements
     int32_t k;         // colours
+    int32_t split;      // mixing items: 0 = one warp per element, 1 = one per (element, word group)
     int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in the mixing phase:
-    int32_t off_pat;    //   [0, off_pat) rows of P on F_j, [off_pat, off_edge) pattern
-    int32_t off_edge;   //   table (32 W masks), [off_edge, warp_smem) edge records
+    int32_t off_pat;    //   [0, off_pat) rows of P on F_j, [off_pat, off_rs) pattern table
+    int32_t off_rs;     //   (32 W masks), [off_rs, off_var) its run starts (W words),
+    int32_t off_var;    //   [off_var, off_edge) one int4 per variable,
+    int32_t off_edge;   //   [off_edge, warp_smem) edge records
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population

@@ -403,31 +403,76 @@ __device__ __forceinline__ T lane_get(T lo, T hi, int a)
     return __shfl_sync(kFull, lo, a);
 }
 
-// Number of candidates the mixing phase checks one by one through the
-// pattern table before the word-parallel scan takes over.
-constexpr int kDonorProbe = 4;
+// First position after d, in cyclic order over [0, p), whose bit is set in
+// rs[0..Wv) (bits >= p are zero); -1 if no bit is set.
+__device__ __forceinline__ int next_set_cyclic(const uint32_t *rs, int Wv, int p, int d)
+{
+    int x = d + 1;
+    if (x >= p) x = 0;
+    int w = x >> 5;
+    uint32_t m = rs[w] & (kFull << (x & 31));
+    for (int step = 0; step <= Wv; ++step) {
+        if (m) return 32 * w + __ffs(m) - 1;
+        if (++w == Wv) w = 0;
+        m = rs[w];
+    }
+    return -1;
+}
+
+// The donor of individual `self` (Sec. 4.2, reading 6): the first candidate in
+// cyclic order from `start`, skipping self, whose generation-start bits on F_j
+// (patP) differ from the parent's bits xf; -1 if there is none.  rs marks the
+// starts of runs of equal patterns (bit d: patP[d] != patP[d-1], cyclically),
+// so a run of candidates equal to the parent is passed in one step.  After a
+// few steps (only possible when the parent's own column interrupts runs)
+// the word-parallel scan over the staged rows finishes the search.  Divergent
+// code: no warp collectives.
+template <typename MaskT>
+__device__ int find_donor(const MaskT *patP, const uint32_t *rs, const uint32_t *sP, int W, int Wv, int p, int s,
+                          MaskT xf, int start, int self)
+{
+    if (patP[start] != xf) return start;
+    int d = start; // patP[d] == xf here
+    for (int it = 0; it < 4; ++it) {
+        const int d2 = next_set_cyclic(rs, Wv, p, d);
+        if (d2 < 0) return -1; // one run: every candidate equals the parent
+        // candidates strictly between d and d2 equal patP[d] == xf; stop if the jump passed start
+        const int dist_d = d - start + (d < start ? p : 0);
+        const int dist_2 = d2 - start + (d2 < start ? p : 0);
+        if (dist_2 <= dist_d) return -1;
+        if (d2 != self) return d2;
+        d = d2 + 1 == p ? 0 : d2 + 1; // skip the parent's own column
+        if (d == start) return -1;
+        if (patP[d] != xf) return d;
+    }
+    // no donor between start and d: continue with a full scan from the next position
+    const int d3 = d + 1 == p ? 0 : d + 1;
+    if (d3 == start) return -1;
+    return scan_donor<MaskT>(sP, W, Wv, p, s, xf, d3, self);
+}
 
 // One colour group: all (individual, element) GOM trials (Alg. 2) of group
-// order[t].  One warp per element; it walks the element's population words in
-// groups of WPI (lane l works on individuals 32w + l of those words).
-// Elements of one group share no variable and no edge (LMIG colouring), so
-// the warp owns its element's rows and nothing else in the group touches the
-// closure it reads.  Per element the warp stages, with lane-parallel loads,
-// the generation-start rows of P on F_j, the table patP[d] of every
-// individual's bits on F_j, and the element's edge list into its slice of
-// shared memory; per word group it stages the parent's words of the outside
-// neighbours, so the trial work reads no global memory.
+// order[t].  A warp item is one element and a range of its population words
+// (all of them, or one word group of WPI words when P.split is set, for small
+// groups); lane l works on individuals 32w + l.  Elements of one group share
+// no variable and no edge (LMIG colouring), so a warp owns its element's rows
+// for its words and nothing else in the group touches the closure it reads.
+// Per item the warp stages, with lane-parallel loads, into its slice of
+// shared memory: the generation-start rows of P on F_j, the table patP[d] of
+// every individual's bits on F_j with the run-start bitmap of that table,
+// one record per variable (its outside-edge range and weight sum), and the
+// element's edge list; per word group it stages the parent's words of the
+// outside neighbours, so the trial work reads no global memory.
 //  draws:   one Philox call per lane gives 4 words: lane c holds the call
 //           of individuals 4c..4c+3 of the word group, fetched by shuffles
-//  donor:   candidates from the start, one by one through patP, then the
-//           word-parallel cyclic scan (scan_donor); flips = patP[d] ^ parent
+//  donor:   find_donor over patP and its run starts; flips = patP[d] ^ parent
 //  delta:   per variable a of F_j, the weighted count S of its outside
 //           neighbours set in the parent gives the cut change of its outside
 //           edges if a flips (x_a ? 2S - W_a : W_a - 2S); edges inside F_j are
 //           evaluated directly, once each (Sec. 2.2, Alg. 4)
 //  accept:  delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
-//  write:   one ballot per (variable, word); lane a XORs the accepted flips
-//           into row F_j[a]
+//  write:   one ballot per (variable, word) when anything was accepted; lane a
+//           XORs the accepted flips into row F_j[a]
 // MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
 // s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
 // is < 2^30).  Fitness deltas go to shared-memory accumulators, then one
@@ -450,33 +495,37 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
     // this warp's slice; the host sizes it from the largest element
     uint32_t *sP = s_dyn + wib * P.warp_smem;                          // [s][W] rows of P on F_j
     MaskT *patP = reinterpret_cast<MaskT *>(sP + P.off_pat);           // [32 W] bits of P[d] on F_j
+    uint32_t *rs = sP + P.off_rs;                                      // [W] run starts of patP
+    int4 *vrec = reinterpret_cast<int4 *>(sP + P.off_var);             // [s] {qb, qe, W_a lo, W_a hi}
     uint32_t *sE = sP + P.off_edge;                                    // [E][ES] edge records
     const int c = P.order[t];
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
+    const int nwg = (Wv + WPI - 1) / WPI;          // word groups per element
+    const int per = P.split ? nwg : 1;             // warp items per element
     const uint32_t g = P.st->g;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
 
-    for (int e = gwarp; e < ne; e += nwarps) {
+    for (int it = gwarp; it < ne * per; it += nwarps) {
+        const int e = it / per, sub = it - e * per;
+        const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
         const int q = q0 + e;
         const int4 h = P.hdr[q];
         const int j = h.x, f0 = h.y, d0 = h.z;
         const int s = h.w & 0xFF, n_in = h.w >> 8;
-        // lane a holds F_j[a], the start of its outside edges and their weight sum
+        // lane a holds F_j[a]
         const int fl = lane < s ? P.fv[f0 + lane] : 0;
-        const int sg = lane <= s ? (int)P.seg[f0 + q + lane] : 0;
-        const AccT wl = lane < s ? (AccT)P.wout[f0 + lane] : 0;
-        int fl2 = 0, sg2 = 0;
-        AccT wl2 = 0;
-        if (WIDE) {
-            fl2 = lane + 32 < s ? P.fv[f0 + 32 + lane] : 0;
-            sg2 = lane + 32 <= s ? (int)P.seg[f0 + q + 32 + lane] : 0;
-            wl2 = lane + 32 < s ? (AccT)P.wout[f0 + 32 + lane] : 0;
-        }
+        int fl2 = 0;
+        if (WIDE) fl2 = lane + 32 < s ? P.fv[f0 + 32 + lane] : 0;
         const int n_out = (int)P.seg[f0 + q + s];
         const int ne_tot = n_out + n_in;
         __syncwarp();
+        for (int a = lane; a < s; a += 32) {
+            const int64_t wa = P.wout[f0 + a];
+            vrec[a] = make_int4((int)P.seg[f0 + q + a], a + 1 == s ? n_out : (int)P.seg[f0 + q + a + 1],
+                                (int)(uint32_t)(uint64_t)wa, (int)((uint64_t)wa >> 32));
+        }
         for (int x = lane; x < (s << lw); x += 32)
             sP[x] = P.P[P.fv[f0 + (x >> lw)] * W + (x & (W - 1))];
         for (int x = lane; x < ne_tot; x += 32) {
@@ -492,8 +541,16 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
             patP[32 * wc + lane] = pat;
         }
         __syncwarp();
+        for (int wc = 0; wc < Wv; ++wc) {
+            const int d = 32 * wc + lane;
+            const bool start = d < p && patP[d] != patP[d == 0 ? p - 1 : d - 1];
+            const uint32_t b = __ballot_sync(kFull, start);
+            if (lane == 0) rs[wc] = b;
+        }
+        __syncwarp();
 
-        for (int w0 = 0; w0 < Wv; w0 += WPI) {
+        for (int wg = wg0; wg < wg1; ++wg) {
+            const int w0 = wg * WPI;
             // parent words of the outside neighbours for this word group
             for (int x = lane; x < n_out; x += 32) {
                 uint32_t X[WPI];
@@ -533,25 +590,12 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
                 fm[r] = 0;
                 if (i < p) {
                     const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
-                    int d = i + 1 + (int)u;
-                    if (d >= p) d -= p;
-                    MaskT pat = patP[d];
-                    int probe = 1;
-                    while (pat == xf[r] && probe < kDonorProbe) {
-                        if (++d == p) d = 0;
-                        if (d == i && ++d == p) d = 0;
-                        pat = patP[d];
-                        ++probe;
-                    }
-                    if (pat == xf[r]) { // the rest of the cycle, 32 candidates a step
-                        if (++d == p) d = 0;
-                        if (d == i && ++d == p) d = 0;
-                        d = d == i ? -1 : scan_donor<MaskT>(sP, W, Wv, p, s, xf[r], d, i);
-                        if (d >= 0) pat = patP[d];
-                    }
-                    if (d >= 0 && pat != xf[r]) {
+                    int ds = i + 1 + (int)u;
+                    if (ds >= p) ds -= p;
+                    const int d = find_donor<MaskT>(patP, rs, sP, W, Wv, p, s, xf[r], ds, i);
+                    if (d >= 0) {
                         donor[r] = d;
-                        fm[r] = pat ^ xf[r];
+                        fm[r] = patP[d] ^ xf[r];
                     }
                 }
             }
@@ -561,13 +605,12 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
 #pragma unroll
             for (int r = 0; r < WPI; ++r) dl[r] = 0;
             for (int a = 0; a < s; ++a) {
-                const int qb = lane_get<WIDE>(sg, sg2, a);
-                const int qe = (a + 1 == s) ? n_out : lane_get<WIDE>(sg, sg2, a + 1);
-                const AccT Wa = lane_get<WIDE>(wl, wl2, a);
+                const int4 vr = vrec[a];
+                const AccT Wa = WIDE ? (AccT)(((int64_t)(uint32_t)vr.w << 32) | (uint32_t)vr.z) : (AccT)vr.z;
                 AccT S[WPI];
 #pragma unroll
                 for (int r = 0; r < WPI; ++r) S[r] = 0;
-                for (int x = qb; x < qe; ++x) {
+                for (int x = vr.x; x < vr.y; ++x) {
                     uint32_t X[WPI];
                     load_words<WPI>(sE + x * ES, X);
                     const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
@@ -595,39 +638,45 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
             }
 
             // accept, fitness, write
-            bool acc[WPI];
+            MaskT afm[WPI]; // accepted flips
+            bool anyacc = false;
 #pragma unroll
             for (int r = 0; r < WPI; ++r) {
                 const int i = 32 * (w0 + r) + lane;
                 const bool eq = (P.eqw[w0 + r] >> lane) & 1u;
-                acc[r] = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
-                if (acc[r]) {
+                const bool acc = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
+                afm[r] = acc ? fm[r] : (MaskT)0;
+                anyacc |= acc;
+                if (acc) {
                     atomicAdd((unsigned long long *)&s_f[i], (unsigned long long)(long long)dl[r]);
                     ++n_acc;
                     if (dl[r] > 0) ++n_imp;
                 }
                 if (i < p && donor[r] < 0) ++n_dl;
             }
-            uint32_t mine[WPI], mine2[WPI];
+            if (__any_sync(kFull, anyacc)) {
+                uint32_t mine[WPI], mine2[WPI];
 #pragma unroll
-            for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
-            for (int a = 0; a < s; ++a) {
-#pragma unroll
-                for (int r = 0; r < WPI; ++r) {
-                    const uint32_t mk = __ballot_sync(kFull, acc[r] && ((fm[r] >> a) & 1u));
-                    if (lane == a) mine[r] = mk;
-                    if (WIDE && lane + 32 == a) mine2[r] = mk;
-                }
-            }
-#pragma unroll
-            for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
-                const int f = half ? fl2 : fl;
-                if (lane + 32 * half < s) {
-                    uint32_t *row = P.O + f * W + w0;
+                for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
+                for (int a = 0; a < s; ++a) {
+                    const bool me = lane == a, me2 = WIDE && lane + 32 == a;
 #pragma unroll
                     for (int r = 0; r < WPI; ++r) {
-                        const uint32_t mk = half ? mine2[r] : mine[r];
-                        if (mk) row[r] ^= mk;
+                        const uint32_t mk = __ballot_sync(kFull, (afm[r] >> a) & 1u);
+                        mine[r] = me ? mk : mine[r];
+                        if (WIDE) mine2[r] = me2 ? mk : mine2[r];
+                    }
+                }
+#pragma unroll
+                for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
+                    const int f = half ? fl2 : fl;
+                    if (lane + 32 * half < s) {
+                        uint32_t *row = P.O + f * W + w0;
+#pragma unroll
+                        for (int r = 0; r < WPI; ++r) {
+                            const uint32_t mk = half ? mine2[r] : mine[r];
+                            if (mk) row[r] ^= mk;
+                        }
                     }
                 }
             }

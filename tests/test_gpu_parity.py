@@ -296,3 +296,37 @@ def test_grid_barrier_bounded_wait():
     assert gom.gom_selftest_barrier(scratch, 8, 0, 200_000_000) is False
     P = gom.Population(I.torus2d(6), 8, 1)
     P.generation(2)
+
+
+def test_large_groups_one_warp_per_element(oracle):
+    """Colour groups of ~2,700 elements: one warp per element walking all its
+    word groups (the small cases above give each word group its own warp)."""
+    _parity(oracle, I.random_regular(40000, 3, seed=12), 96, 6, 4)
+
+
+@pytest.mark.parametrize("p", [64, 200])
+def test_runs_of_identical_individuals(oracle, p):
+    """A population made of long runs of equal individuals: donor search
+    passes whole runs of candidates equal to the parent and skips the parent's
+    own column, exactly as the sequential cyclic scan does."""
+    g = I.torus2d(14, seed=5)
+    run, _ = _oracle_run(oracle, g, p, 3)
+    base = run.get()["pop"]
+    idx = np.repeat(np.arange(5), (p + 4) // 5)[:p]  # 5 runs of individuals 0..4
+    pop = base[idx].copy()
+    f = np.array([oracle.cut_value(g, x) for x in pop], dtype=np.int64)
+    xe = pop[int(np.argmax(f))].copy()
+    dev = torch.device("cuda")
+    run.load(pop, f, xe, int(f.max()), 0)
+    Ps = []
+    for persistent in (True, False):
+        P = gom.Population(g, p, 3, persistent=persistent)
+        P.set_population(torch.from_numpy(pop).to(dev), torch.from_numpy(xe).to(dev), int(f.max()), 0)
+        Ps.append(P)
+    for _ in range(6):
+        ost = run.generation()
+        for P in Ps:
+            gst, _ = P.generation(1)
+            _assert_same_stats(gst[0], ost)
+    for P in Ps:
+        _assert_same_state(_gpu_state(P), run.get())
