@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, bar, stats, order;
+    size_t O, P, f, eqw, xe, st, bar, stats, order, work;
     size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
@@ -53,6 +53,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.bar = take(sizeof(GomBarrier));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
+    L.work = take(sizeof(uint32_t) * std::max<int32_t>(k, 1));
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
@@ -445,6 +446,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.k = fos->k;
     P.seed = seed;
     P.split = split;
+    P.chunk = 4;
     P.warp_smem = static_cast<int32_t>(warp_words);
     P.off_pat = static_cast<int32_t>(off_pat);
     P.off_rs = static_cast<int32_t>(off_rs);
@@ -459,6 +461,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.bar = reinterpret_cast<GomBarrier *>(base + L.bar);
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
+    P.work = reinterpret_cast<uint32_t *>(base + L.work);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);

@@ -197,9 +197,11 @@ __global__ void k_begin_call(GomParams P, int64_t target)
 
 // ----------------------------------------------------------------------------
 // Grid-wide barrier of the persistent generation kernel (all blocks are
-// co-resident: cooperative launch).  Sense counter: the last block to arrive
-// resets the count and bumps the generation word.  A block that waits longer
-// than kBarrierNs (wall clock, %globaltimer) or sees the error word set stops
+// co-resident: cooperative launch).  One monotonic 64-bit arrival counter:
+// a block adds 1 with release semantics and waits, with acquire loads, until
+// the counter reaches the end of its barrier epoch (the next multiple of
+// `expected`); nothing is ever reset.  A block that waits longer than
+// kBarrierNs (wall clock, %globaltimer) or sees the error word set stops
 // waiting, sets the error word and returns false; every block then leaves the
 // kernel, so a failure ends as an error status, never a hang.
 constexpr unsigned long long kBarrierNs = 2000000000ull; // 2 s
@@ -211,35 +213,39 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-__device__ bool grid_barrier(unsigned *count, unsigned *gen, int *err, unsigned expected,
-                             unsigned long long limit_ns)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long *p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ bool grid_barrier(unsigned long long *count, int *err, unsigned expected, unsigned long long limit_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = gen;
         volatile int *verr = err;
-        const unsigned g0 = *vgen;
+        const unsigned long long arrived = atom_add_release_u64(count, 1ull) + 1;
+        const unsigned long long target = (arrived + expected - 1) / expected * expected;
         int ok = 1;
-        __threadfence();
-        const unsigned prev = atomicAdd(count, 1u);
-        if (prev + 1 == expected) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*vgen == g0) {
-                if (*verr || global_ns() - t0 > limit_ns) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(64);
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u64(count) < target) {
+            if (*verr || global_ns() - t0 > limit_ns) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
             }
+            __nanosleep(32);
         }
-        __threadfence();
-        s_ok = ok && *verr == 0;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok;
@@ -284,6 +290,7 @@ __device__ void phase_gen_start(const GomParams &P)
     __syncthreads();
     if (threadIdx.x < W && threadIdx.x < 32 && s_eq[threadIdx.x] != kFull)
         atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
+    for (int64_t c = tid; c < P.k; c += nth) P.work[c] = 0; // mixing work counters of this generation
 }
 
 // Group order of generation g (Alg. 3 visits the groups in random order): colours sorted by
@@ -451,18 +458,100 @@ __device__ int find_donor(const MaskT *patP, const uint32_t *rs, const uint32_t 
     return scan_donor<MaskT>(sP, W, Wv, p, s, xf, d3, self);
 }
 
-// One colour group: all (individual, element) GOM trials (Alg. 2) of group
-// order[t].  A warp item is one element and a range of its population words
-// (all of them, or one word group of WPI words when P.split is set, for small
-// groups); lane l works on individuals 32w + l.  Elements of one group share
-// no variable and no edge (LMIG colouring), so a warp owns its element's rows
-// for its words and nothing else in the group touches the closure it reads.
-// Per item the warp stages, with lane-parallel loads, into its slice of
-// shared memory: the generation-start rows of P on F_j, the table patP[d] of
-// every individual's bits on F_j with the run-start bitmap of that table,
-// one record per variable (its outside-edge range and weight sum), and the
-// element's edge list; per word group it stages the parent's words of the
-// outside neighbours, so the trial work reads no global memory.
+// A warp's current mixing item: one element of a colour group and a range of
+// its population word groups.  Lane a holds the element's variable F_j[a]
+// (and F_j[32 + a] in fl2 for elements of more than 32 variables).
+struct MixItem {
+    int valid;
+    int q, j, d0, s, n_in, n_out;
+    int wg0, wg1;
+    int fl, fl2;
+};
+
+// Item `it` of the group at position t (an element and its word groups).
+__device__ __forceinline__ MixItem mix_item(const GomParams &P, int t, int it, int WPI_)
+{
+    MixItem m;
+    const int lane = threadIdx.x & 31;
+    const int c = P.order[t];
+    const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
+    const int nwg = (P.Wv + WPI_ - 1) / WPI_;
+    const int per = P.split ? nwg : 1;
+    m.valid = it < ne * per;
+    if (!m.valid) return m;
+    const int e = it / per, sub = it - e * per;
+    m.wg0 = P.split ? sub : 0;
+    m.wg1 = P.split ? sub + 1 : nwg;
+    m.q = q0 + e;
+    const int4 h = P.hdr[m.q];
+    m.j = h.x;
+    m.d0 = h.z;
+    m.s = h.w & 0xFF;
+    m.n_in = h.w >> 8;
+    const int f0 = h.y;
+    m.fl = lane < m.s ? P.fv[f0 + lane] : 0;
+    m.fl2 = lane + 32 < m.s ? P.fv[f0 + 32 + lane] : 0;
+    m.n_out = (int)P.seg[f0 + m.q + m.s];
+    return m;
+}
+
+// Items of group t in total (elements times word-group slices).
+__device__ __forceinline__ int mix_items(const GomParams &P, int t, int WPI_)
+{
+    const int c = P.order[t];
+    const int nwg = (P.Wv + WPI_ - 1) / WPI_;
+    return (P.cptr[c + 1] - P.cptr[c]) * (P.split ? nwg : 1);
+}
+
+// Stages the generation-constant half of an item into the warp's slice of
+// shared memory: one record per variable (its outside-edge range and weight
+// sum), the rows of P on F_j, the edge list, the table patP of every
+// individual's bits on F_j and the run starts of that table.  None of it
+// depends on O, so it may run before the barrier that opens the item's group.
+template <int WPI, typename MaskT>
+__device__ __forceinline__ void stage_item(const GomParams &P, const MixItem &m, uint32_t *sP)
+{
+    constexpr int ES = EdgeStride<WPI>::value;
+    const int lane = threadIdx.x & 31;
+    const int W = P.W, Wv = P.Wv, p = P.p;
+    const int lw = __ffs(W) - 1;
+    MaskT *patP = reinterpret_cast<MaskT *>(sP + P.off_pat);
+    uint32_t *rs = sP + P.off_rs;
+    int4 *vrec = reinterpret_cast<int4 *>(sP + P.off_var);
+    uint32_t *sE = sP + P.off_edge;
+    const int s = m.s;
+    const int f0 = P.hdr[m.q].y;
+    __syncwarp();
+    for (int a = lane; a < s; a += 32) {
+        const int64_t wa = P.wout[f0 + a];
+        vrec[a] = make_int4((int)P.seg[f0 + m.q + a], a + 1 == s ? m.n_out : (int)P.seg[f0 + m.q + a + 1],
+                            (int)(uint32_t)(uint64_t)wa, (int)((uint64_t)wa >> 32));
+    }
+    for (int x = lane; x < (s << lw); x += 32)
+        sP[x] = P.P[P.fv[f0 + (x >> lw)] * W + (x & (W - 1))];
+    for (int x = lane; x < m.n_out + m.n_in; x += 32) {
+        const int2 d = P.dep[m.d0 + x];
+        sE[x * ES + WPI] = (uint32_t)d.x;
+        sE[x * ES + WPI + 1] = (uint32_t)d.y;
+    }
+    __syncwarp();
+    // lane l builds the bits on F_j of individuals 32 wc + l
+    for (int wc = 0; wc < Wv; ++wc) {
+        MaskT pat = 0;
+        for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + wc] >> lane) & 1u) << a;
+        patP[32 * wc + lane] = pat;
+    }
+    __syncwarp();
+    for (int wc = 0; wc < Wv; ++wc) {
+        const int d = 32 * wc + lane;
+        const bool start = d < p && patP[d] != patP[d == 0 ? p - 1 : d - 1];
+        const uint32_t b = __ballot_sync(kFull, start);
+        if (lane == 0) rs[wc] = b;
+    }
+    __syncwarp();
+}
+
+// All trials of a staged item (Alg. 2 for each individual of its words):
 //  draws:   one Philox call per lane gives 4 words: lane c holds the call
 //           of individuals 4c..4c+3 of the word group, fetched by shuffles
 //  donor:   find_donor over patP and its run starts; flips = patP[d] ^ parent
@@ -473,214 +562,223 @@ __device__ int find_donor(const MaskT *patP, const uint32_t *rs, const uint32_t 
 //  accept:  delta > 0, or delta == 0 and P[i] is not the elitist (Alg. 2)
 //  write:   one ballot per (variable, word) when anything was accepted; lane a
 //           XORs the accepted flips into row F_j[a]
-// MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
-// s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
-// is < 2^30).  Fitness deltas go to shared-memory accumulators, then one
-// atomic per individual (and per counter) per block: integer adds, so the
-// result does not depend on their order.
+// Fitness deltas go to the block's shared accumulators s_f; counters to
+// per-lane counts.
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s_dyn, long long *s_f,
-                                          unsigned long long *s_cnt)
+__device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, uint32_t *sP, uint32_t g,
+                                         long long *s_f, unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
     constexpr int ES = EdgeStride<WPI>::value;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p;
-    const int lw = __ffs(W) - 1;
-    const int np = 32 * W;
-    for (int q = threadIdx.x; q < np; q += blockDim.x) s_f[q] = 0;
-    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-
-    // this warp's slice; the host sizes it from the largest element
-    uint32_t *sP = s_dyn + wib * P.warp_smem;                          // [s][W] rows of P on F_j
-    MaskT *patP = reinterpret_cast<MaskT *>(sP + P.off_pat);           // [32 W] bits of P[d] on F_j
-    uint32_t *rs = sP + P.off_rs;                                      // [W] run starts of patP
-    int4 *vrec = reinterpret_cast<int4 *>(sP + P.off_var);             // [s] {qb, qe, W_a lo, W_a hi}
-    uint32_t *sE = sP + P.off_edge;                                    // [E][ES] edge records
-    const int c = P.order[t];
-    const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
-    const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
-    const int nwg = (Wv + WPI - 1) / WPI;          // word groups per element
-    const int per = P.split ? nwg : 1;             // warp items per element
-    const uint32_t g = P.st->g;
+    const MaskT *patP = reinterpret_cast<const MaskT *>(sP + P.off_pat);
+    const uint32_t *rs = sP + P.off_rs;
+    const int4 *vrec = reinterpret_cast<const int4 *>(sP + P.off_var);
+    uint32_t *sE = sP + P.off_edge;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-    unsigned n_dl = 0, n_acc = 0, n_imp = 0;
+    const int s = m.s, n_out = m.n_out, ne_tot = m.n_out + m.n_in;
 
-    for (int it = gwarp; it < ne * per; it += nwarps) {
-        const int e = it / per, sub = it - e * per;
-        const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
-        const int q = q0 + e;
-        const int4 h = P.hdr[q];
-        const int j = h.x, f0 = h.y, d0 = h.z;
-        const int s = h.w & 0xFF, n_in = h.w >> 8;
-        // lane a holds F_j[a]
-        const int fl = lane < s ? P.fv[f0 + lane] : 0;
-        int fl2 = 0;
-        if (WIDE) fl2 = lane + 32 < s ? P.fv[f0 + 32 + lane] : 0;
-        const int n_out = (int)P.seg[f0 + q + s];
-        const int ne_tot = n_out + n_in;
+    for (int wg = m.wg0; wg < m.wg1; ++wg) {
+        const int w0 = wg * WPI;
+        // parent words of the outside neighbours for this word group
         __syncwarp();
-        for (int a = lane; a < s; a += 32) {
-            const int64_t wa = P.wout[f0 + a];
-            vrec[a] = make_int4((int)P.seg[f0 + q + a], a + 1 == s ? n_out : (int)P.seg[f0 + q + a + 1],
-                                (int)(uint32_t)(uint64_t)wa, (int)((uint64_t)wa >> 32));
+        for (int x = lane; x < n_out; x += 32) {
+            uint32_t X[WPI];
+            load_words<WPI>(P.O + (int)sE[x * ES + WPI] * W + w0, X);
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) sE[x * ES + r] = X[r];
         }
-        for (int x = lane; x < (s << lw); x += 32)
-            sP[x] = P.P[P.fv[f0 + (x >> lw)] * W + (x & (W - 1))];
-        for (int x = lane; x < ne_tot; x += 32) {
-            const int2 d = P.dep[d0 + x];
-            sE[x * ES + WPI] = (uint32_t)d.x;
-            sE[x * ES + WPI + 1] = (uint32_t)d.y;
-        }
-        __syncwarp();
-        // pattern table: lane l builds the bits on F_j of individuals 32 wc + l
-        for (int wc = 0; wc < Wv; ++wc) {
-            MaskT pat = 0;
-            for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + wc] >> lane) & 1u) << a;
-            patP[32 * wc + lane] = pat;
-        }
-        __syncwarp();
-        for (int wc = 0; wc < Wv; ++wc) {
-            const int d = 32 * wc + lane;
-            const bool start = d < p && patP[d] != patP[d == 0 ? p - 1 : d - 1];
-            const uint32_t b = __ballot_sync(kFull, start);
-            if (lane == 0) rs[wc] = b;
+        // parent bits on F_j: lane a loads row F_j[a], then a shuffle transpose
+        uint32_t Xa[WPI], Xa2[WPI];
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
+        if (lane < s) load_words<WPI>(P.O + m.fl * W + w0, Xa);
+        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + m.fl2 * W + w0, Xa2);
+        MaskT xf[WPI];
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) xf[r] = 0;
+        for (int a = 0; a < s; ++a) {
+#pragma unroll
+            for (int r = 0; r < WPI; ++r)
+                xf[r] |= (MaskT)((lane_get<WIDE>(Xa[r], Xa2[r], a) >> lane) & 1u) << a;
         }
         __syncwarp();
 
-        for (int wg = wg0; wg < wg1; ++wg) {
-            const int w0 = wg * WPI;
-            // parent words of the outside neighbours for this word group
-            for (int x = lane; x < n_out; x += 32) {
+        // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
+        const uint4 r4 = philox10(make_uint4((uint32_t)m.j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+        int donor[WPI];
+        MaskT fm[WPI];
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) {
+            const int src = 8 * r + (lane >> 2);
+            const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
+            const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
+            const int cc = lane & 3;
+            const uint32_t draw = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
+            const int i = 32 * (w0 + r) + lane;
+            donor[r] = -1;
+            fm[r] = 0;
+            if (i < p) {
+                const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
+                int ds = i + 1 + (int)u;
+                if (ds >= p) ds -= p;
+                const int d = find_donor<MaskT>(patP, rs, sP, W, Wv, p, s, xf[r], ds, i);
+                if (d >= 0) {
+                    donor[r] = d;
+                    fm[r] = patP[d] ^ xf[r];
+                }
+            }
+        }
+
+        // partial evaluation
+        AccT dl[WPI];
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) dl[r] = 0;
+        for (int a = 0; a < s; ++a) {
+            const int4 vr = vrec[a];
+            const AccT Wa = WIDE ? (AccT)(((int64_t)(uint32_t)vr.w << 32) | (uint32_t)vr.z) : (AccT)vr.z;
+            AccT S[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) S[r] = 0;
+            for (int x = vr.x; x < vr.y; ++x) {
                 uint32_t X[WPI];
-                load_words<WPI>(P.O + (int)sE[x * ES + WPI] * W + w0, X);
-#pragma unroll
-                for (int r = 0; r < WPI; ++r) sE[x * ES + r] = X[r];
-            }
-            // parent bits on F_j: lane a loads row F_j[a], then a shuffle transpose
-            uint32_t Xa[WPI], Xa2[WPI];
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
-            if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
-            if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
-            MaskT xf[WPI];
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) xf[r] = 0;
-            for (int a = 0; a < s; ++a) {
-#pragma unroll
-                for (int r = 0; r < WPI; ++r)
-                    xf[r] |= (MaskT)((lane_get<WIDE>(Xa[r], Xa2[r], a) >> lane) & 1u) << a;
-            }
-            __syncwarp();
-
-            // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
-            const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
-            int donor[WPI];
-            MaskT fm[WPI];
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) {
-                const int src = 8 * r + (lane >> 2);
-                const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
-                const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
-                const int cc = lane & 3;
-                const uint32_t draw = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
-                const int i = 32 * (w0 + r) + lane;
-                donor[r] = -1;
-                fm[r] = 0;
-                if (i < p) {
-                    const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
-                    int ds = i + 1 + (int)u;
-                    if (ds >= p) ds -= p;
-                    const int d = find_donor<MaskT>(patP, rs, sP, W, Wv, p, s, xf[r], ds, i);
-                    if (d >= 0) {
-                        donor[r] = d;
-                        fm[r] = patP[d] ^ xf[r];
-                    }
-                }
-            }
-
-            // partial evaluation
-            AccT dl[WPI];
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) dl[r] = 0;
-            for (int a = 0; a < s; ++a) {
-                const int4 vr = vrec[a];
-                const AccT Wa = WIDE ? (AccT)(((int64_t)(uint32_t)vr.w << 32) | (uint32_t)vr.z) : (AccT)vr.z;
-                AccT S[WPI];
-#pragma unroll
-                for (int r = 0; r < WPI; ++r) S[r] = 0;
-                for (int x = vr.x; x < vr.y; ++x) {
-                    uint32_t X[WPI];
-                    load_words<WPI>(sE + x * ES, X);
-                    const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
-#pragma unroll
-                    for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
-                }
-#pragma unroll
-                for (int r = 0; r < WPI; ++r) {
-                    const AccT gain = Wa - 2 * S[r];                      // if x_a = 0
-                    const AccT sx = -(AccT)((xf[r] >> a) & 1u);          // 0 or -1
-                    const AccT sf = -(AccT)((fm[r] >> a) & 1u);
-                    dl[r] += ((gain ^ sx) - sx) & sf;
-                }
-            }
-            for (int x = n_out; x < ne_tot; ++x) {
-                const uint32_t code = sE[x * ES + WPI];
+                load_words<WPI>(sE + x * ES, X);
                 const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
-                const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
-                for (int r = 0; r < WPI; ++r) {
-                    const AccT tg = (AccT)(((fm[r] >> a) ^ (fm[r] >> b)) & 1u); // edge toggles
-                    const AccT sc = -(AccT)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u); // cut before
-                    dl[r] += ((wx ^ sc) - sc) & -tg;
-                }
+                for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
             }
-
-            // accept, fitness, write
-            MaskT afm[WPI]; // accepted flips
-            bool anyacc = false;
 #pragma unroll
             for (int r = 0; r < WPI; ++r) {
-                const int i = 32 * (w0 + r) + lane;
-                const bool eq = (P.eqw[w0 + r] >> lane) & 1u;
-                const bool acc = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
-                afm[r] = acc ? fm[r] : (MaskT)0;
-                anyacc |= acc;
-                if (acc) {
-                    atomicAdd((unsigned long long *)&s_f[i], (unsigned long long)(long long)dl[r]);
-                    ++n_acc;
-                    if (dl[r] > 0) ++n_imp;
-                }
-                if (i < p && donor[r] < 0) ++n_dl;
+                const AccT gain = Wa - 2 * S[r];                      // if x_a = 0
+                const AccT sx = -(AccT)((xf[r] >> a) & 1u);          // 0 or -1
+                const AccT sf = -(AccT)((fm[r] >> a) & 1u);
+                dl[r] += ((gain ^ sx) - sx) & sf;
             }
-            if (__any_sync(kFull, anyacc)) {
-                uint32_t mine[WPI], mine2[WPI];
+        }
+        for (int x = n_out; x < ne_tot; ++x) {
+            const uint32_t code = sE[x * ES + WPI];
+            const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
+            const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
-                for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
-                for (int a = 0; a < s; ++a) {
-                    const bool me = lane == a, me2 = WIDE && lane + 32 == a;
+            for (int r = 0; r < WPI; ++r) {
+                const AccT tg = (AccT)(((fm[r] >> a) ^ (fm[r] >> b)) & 1u); // edge toggles
+                const AccT sc = -(AccT)(((xf[r] >> a) ^ (xf[r] >> b)) & 1u); // cut before
+                dl[r] += ((wx ^ sc) - sc) & -tg;
+            }
+        }
+
+        // accept, fitness, write
+        MaskT afm[WPI]; // accepted flips
+        bool anyacc = false;
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) {
+            const int i = 32 * (w0 + r) + lane;
+            const bool eq = (P.eqw[w0 + r] >> lane) & 1u;
+            const bool acc = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
+            afm[r] = acc ? fm[r] : (MaskT)0;
+            anyacc |= acc;
+            if (acc) {
+                atomicAdd((unsigned long long *)&s_f[i], (unsigned long long)(long long)dl[r]);
+                ++n_acc;
+                if (dl[r] > 0) ++n_imp;
+            }
+            if (i < p && donor[r] < 0) ++n_dl;
+        }
+        if (__any_sync(kFull, anyacc)) {
+            uint32_t mine[WPI], mine2[WPI];
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
+            for (int a = 0; a < s; ++a) {
+                const bool me = lane == a, me2 = WIDE && lane + 32 == a;
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) {
+                    const uint32_t mk = __ballot_sync(kFull, (afm[r] >> a) & 1u);
+                    mine[r] = me ? mk : mine[r];
+                    if (WIDE) mine2[r] = me2 ? mk : mine2[r];
+                }
+            }
+#pragma unroll
+            for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
+                const int f = half ? m.fl2 : m.fl;
+                if (lane + 32 * half < s) {
+                    uint32_t *row = P.O + f * W + w0;
 #pragma unroll
                     for (int r = 0; r < WPI; ++r) {
-                        const uint32_t mk = __ballot_sync(kFull, (afm[r] >> a) & 1u);
-                        mine[r] = me ? mk : mine[r];
-                        if (WIDE) mine2[r] = me2 ? mk : mine2[r];
-                    }
-                }
-#pragma unroll
-                for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
-                    const int f = half ? fl2 : fl;
-                    if (lane + 32 * half < s) {
-                        uint32_t *row = P.O + f * W + w0;
-#pragma unroll
-                        for (int r = 0; r < WPI; ++r) {
-                            const uint32_t mk = half ? mine2[r] : mine[r];
-                            if (mk) row[r] ^= mk;
-                        }
+                        const uint32_t mk = half ? mine2[r] : mine[r];
+                        if (mk) row[r] ^= mk;
                     }
                 }
             }
-            __syncwarp();
+        }
+    }
+    __syncwarp();
+}
+
+// Zeroes the block's fitness and counter accumulators.
+__device__ __forceinline__ void acc_zero(const GomParams &P, long long *s_f, unsigned long long *s_cnt)
+{
+    for (int q = threadIdx.x; q < 32 * P.W; q += blockDim.x) s_f[q] = 0;
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+}
+
+// Adds the block's accumulators into the fitness array and the generation's
+// counters: one atomic per individual (and per counter), integer adds, so
+// the result does not depend on their order.
+__device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, unsigned long long *s_cnt)
+{
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * P.W; q += blockDim.x) {
+        const long long v = s_f[q];
+        if (v) atomicAdd((unsigned long long *)&P.f[q], (unsigned long long)v);
+    }
+    if (threadIdx.x < 3 && s_cnt[threadIdx.x])
+        atomicAdd((unsigned long long *)&P.st->cnt[threadIdx.x], s_cnt[threadIdx.x]);
+    __syncthreads();
+}
+
+// One colour group: all (individual, element) GOM trials (Alg. 2) of the
+// group at position t.  Items (an element, or an element's word group when
+// P.split is set) go to warps: the first wave statically (warp w takes item
+// w, which may already be staged: `pre`), the rest in chunks claimed from the
+// group's counter P.work[t].  Elements of one group share no variable and no
+// edge (LMIG colouring), so a warp owns its element's rows for its words and
+// nothing else in the group touches the closure it reads.
+// MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
+// s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
+// is < 2^30).
+template <int WPI, typename MaskT, typename AccT>
+__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g, uint32_t *s_dyn, long long *s_f,
+                                          unsigned long long *s_cnt, const MixItem *pre)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *sP = s_dyn + wib * P.warp_smem; // this warp's slice
+    const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
+    const int total = mix_items(P, t, WPI);
+    const int chunk = P.chunk;
+    unsigned n_dl = 0, n_acc = 0, n_imp = 0;
+
+    MixItem m;
+    if (pre) {
+        m = *pre;
+    } else {
+        m = mix_item(P, t, gwarp, WPI);
+        if (m.valid) stage_item<WPI, MaskT>(P, m, sP);
+    }
+    if (m.valid) run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
+    if (total > nwarps) {
+        for (;;) {
+            int base = 0;
+            if (lane == 0) base = nwarps + (int)atomicAdd(&P.work[t], (unsigned)chunk);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= total) break;
+            const int stop = min(total, base + chunk);
+            for (int it = base; it < stop; ++it) {
+                m = mix_item(P, t, it, WPI);
+                stage_item<WPI, MaskT>(P, m, sP);
+                run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
+            }
         }
     }
 
@@ -692,14 +790,6 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t *s
         atomicAdd(&s_cnt[1], (unsigned long long)n_acc);
         atomicAdd(&s_cnt[2], (unsigned long long)n_imp);
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < np; q += blockDim.x) {
-        const long long v = s_f[q];
-        if (v) atomicAdd((unsigned long long *)&P.f[q], (unsigned long long)v);
-    }
-    if (threadIdx.x < 3 && s_cnt[threadIdx.x])
-        atomicAdd((unsigned long long *)&P.st->cnt[threadIdx.x], s_cnt[threadIdx.x]);
-    __syncthreads();
 }
 
 // ----------------------------------------------------------------------------
@@ -725,7 +815,9 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
     if (P.st->done) return;
-    phase_mix<WPI, MaskT, AccT>(P, t, s_dyn, s_f, s_cnt);
+    acc_zero(P, s_f, s_cnt);
+    phase_mix<WPI, MaskT, AccT>(P, t, P.st->g, s_dyn, s_f, s_cnt, nullptr);
+    acc_flush(P, s_f, s_cnt);
 }
 
 __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
@@ -736,10 +828,15 @@ __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 
 // Persistent path: up to G generations in one cooperative launch, the phases
 // separated by grid barriers (gen start + order | each colour group | gen
-// end).  Stops early once a generation reached the target: done is written
-// by every generation end and read after the following barrier, so every
-// block takes the same decision (the first generation of a call ignores the
-// flag left by an earlier call).
+// end).  Before each barrier that opens a colour group, every warp stages the
+// generation-constant half of its first item of that group (its P rows,
+// pattern table and edge list), so after the barrier only the parent's words
+// remain to be loaded.  The block's fitness accumulators span all groups of a
+// generation and are flushed once before the generation end.  Stops early
+// once a generation reached the target: done is written by every generation
+// end and read after the following barrier, so every block takes the same
+// decision (the first generation of a call ignores the flag left by an
+// earlier call).
 template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
 {
@@ -747,21 +844,31 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
     const unsigned nblk = gridDim.x;
+    const int gwarp = (int)(gthread() >> 5);
+    uint32_t *sP = s_dyn + (threadIdx.x >> 5) * P.warp_smem;
+    const uint32_t g0 = P.st->g;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        P.st->call_g0 = P.st->g; // read by the host after the kernel only
+        P.st->call_g0 = g0; // read by the host after the kernel only
         P.st->target = target;
     }
     for (int q = 0; q < G; ++q) {
         if (q > 0 && *(volatile int32_t *)&P.st->done) return;
+        const uint32_t g = g0 + (uint32_t)q;
         phase_gen_start(P);
         phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn));
-        if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+        acc_zero(P, s_f, s_cnt);
+        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
         for (int t = 0; t < P.k; ++t) {
-            phase_mix<WPI, MaskT, AccT>(P, t, s_dyn, s_f, s_cnt);
-            if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+            // the first item of group t: decode and stage its P side, then wait
+            MixItem m = mix_item(P, t, gwarp, WPI);
+            if (m.valid) stage_item<WPI, MaskT>(P, m, sP);
+            if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+            phase_mix<WPI, MaskT, AccT>(P, t, g, s_dyn, s_f, s_cnt, &m);
         }
+        acc_flush(P, s_f, s_cnt);
+        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
         if (blockIdx.x == 0) phase_gen_end(P, target);
-        if (!grid_barrier(&P.bar->count, &P.bar->gen, &P.st->err, nblk, kBarrierNs)) return;
+        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
     }
 }
 
@@ -770,7 +877,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
 // block is ever released and every block must give up after limit_ns.
 __global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigned long long limit_ns)
 {
-    grid_barrier(&bar->count, &bar->gen, err, gridDim.x + (unsigned)extra, limit_ns);
+    grid_barrier(&bar->count, err, gridDim.x + (unsigned)extra, limit_ns);
 }
 
 const void *gom_mix_kernel(int wpi, bool narrow)
