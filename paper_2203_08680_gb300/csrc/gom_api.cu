@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, bar, stats, order, work;
+    size_t O, P, f, eqw, xe, st, bar, stats, order;
     size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
@@ -53,7 +53,6 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.bar = take(sizeof(GomBarrier));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
-    L.work = take(sizeof(uint32_t) * std::max<int32_t>(k, 1));
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
@@ -369,12 +368,13 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
     // Work split: one warp per element walking all its words in groups of
-    // wpi = min(W, 4) words, or, when a colour group has too few elements to
-    // fill the GPU, one warp per (element, word group).
+    // wpi = min(W, 4) words, or, when the largest colour group has fewer than
+    // about 4 elements per resident warp (~24 per SM), one warp per (element,
+    // word group), so that the static stride over items stays balanced.
     const int wv = (pop + 31) / 32;
     int wpi = std::min(c->W, 4);
     int split = 0;
-    if (max_group < static_cast<int64_t>(c->sms) * 16 && wv > 1) {
+    if (max_group < static_cast<int64_t>(c->sms) * 24 * 4 && wv > 1) {
         split = 1;
         if ((wv + wpi - 1) / wpi == 1) wpi = 1;
     }
@@ -446,7 +446,6 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.k = fos->k;
     P.seed = seed;
     P.split = split;
-    P.chunk = 4;
     P.warp_smem = static_cast<int32_t>(warp_words);
     P.off_pat = static_cast<int32_t>(off_pat);
     P.off_rs = static_cast<int32_t>(off_rs);
@@ -461,7 +460,6 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.bar = reinterpret_cast<GomBarrier *>(base + L.bar);
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
-    P.work = reinterpret_cast<uint32_t *>(base + L.work);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);

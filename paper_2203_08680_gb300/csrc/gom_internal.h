@@ -97,7 +97,7 @@ struct GomParams {
     int32_t m;         // FOS elements
     int32_t k;         // colours
     int32_t split;      // mixing items: 0 = one warp per element, 1 = one per (element, word group)
-    int32_t chunk;      // items a warp claims at a time beyond the first wave
+    int32_t pad0;
     int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in the mixing phase:
     int32_t off_pat;    //   [0, off_pat) rows of P on F_j, [off_pat, off_rs) pattern table
     int32_t off_rs;     //   (32 W masks), [off_rs, off_var) its run starts (W words),
@@ -113,7 +113,6 @@ struct GomParams {
     GomBarrier *bar;
     GomDevStats *stats;  // [kStatsCap] ring indexed by generation
     int32_t *order;      // [k] colour visited at position t
-    uint32_t *work;      // [k] items claimed beyond the first wave, per group position
     const int64_t *row_ptr;
     const int32_t *col;
     const int32_t *wgt;

@@ -290,7 +290,6 @@ __device__ void phase_gen_start(const GomParams &P)
     __syncthreads();
     if (threadIdx.x < W && threadIdx.x < 32 && s_eq[threadIdx.x] != kFull)
         atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
-    for (int64_t c = tid; c < P.k; c += nth) P.work[c] = 0; // mixing work counters of this generation
 }
 
 // Group order of generation g (Alg. 3 visits the groups in random order): colours sorted by
@@ -740,9 +739,8 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 
 // One colour group: all (individual, element) GOM trials (Alg. 2) of the
 // group at position t.  Items (an element, or an element's word group when
-// P.split is set) go to warps: the first wave statically (warp w takes item
-// w, which may already be staged: `pre`), the rest in chunks claimed from the
-// group's counter P.work[t].  Elements of one group share no variable and no
+// P.split is set) go to warps in a static stride: warp w takes items w,
+// w + nwarps, ...; its first item may already be staged (`pre`).  Elements of one group share no variable and no
 // edge (LMIG colouring), so a warp owns its element's rows for its words and
 // nothing else in the group touches the closure it reads.
 // MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
@@ -756,7 +754,6 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g,
     uint32_t *sP = s_dyn + wib * P.warp_smem; // this warp's slice
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
     const int total = mix_items(P, t, WPI);
-    const int chunk = P.chunk;
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
 
     MixItem m;
@@ -767,19 +764,10 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g,
         if (m.valid) stage_item<WPI, MaskT>(P, m, sP);
     }
     if (m.valid) run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
-    if (total > nwarps) {
-        for (;;) {
-            int base = 0;
-            if (lane == 0) base = nwarps + (int)atomicAdd(&P.work[t], (unsigned)chunk);
-            base = __shfl_sync(kFull, base, 0);
-            if (base >= total) break;
-            const int stop = min(total, base + chunk);
-            for (int it = base; it < stop; ++it) {
-                m = mix_item(P, t, it, WPI);
-                stage_item<WPI, MaskT>(P, m, sP);
-                run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
-            }
-        }
+    for (int it = gwarp + nwarps; it < total; it += nwarps) {
+        m = mix_item(P, t, it, WPI);
+        stage_item<WPI, MaskT>(P, m, sP);
+        run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
     }
 
     n_dl = __reduce_add_sync(kFull, n_dl);

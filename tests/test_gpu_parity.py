@@ -299,9 +299,9 @@ def test_grid_barrier_bounded_wait():
 
 
 def test_large_groups_one_warp_per_element(oracle):
-    """Colour groups of ~2,700 elements: one warp per element walking all its
-    word groups (the small cases above give each word group its own warp)."""
-    _parity(oracle, I.random_regular(40000, 3, seed=12), 96, 6, 4)
+    """Colour groups of ~20,000 elements: one warp per element walking all its
+    word groups (smaller groups give each word group its own warp)."""
+    _parity(oracle, I.torus2d(400, seed=12), 96, 6, 3)
 
 
 @pytest.mark.parametrize("p", [64, 200])
