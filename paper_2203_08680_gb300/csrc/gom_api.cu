@@ -47,7 +47,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.O = take(sizeof(uint32_t) * n * W);
     L.P = take(sizeof(uint32_t) * n * W);
     L.f = take(sizeof(int64_t) * 32 * W);
-    L.eqw = take(sizeof(uint32_t) * W);
+    L.eqw = take(sizeof(uint32_t) * 2 * W);
     L.xe = take(n);
     L.st = take(sizeof(GomDevState));
     L.bar = take(sizeof(GomBarrier));

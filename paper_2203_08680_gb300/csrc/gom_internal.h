@@ -107,7 +107,7 @@ struct GomParams {
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population
     int64_t *f;        // [32W] fitness
-    uint32_t *eqw;     // [W] generation-start flags P[i] == x_e
+    uint32_t *eqw;     // [2][W] flags P[i] == x_e of generation g in buffer g mod 2
     uint8_t *xe;       // [n] elitist
     GomDevState *st;
     GomBarrier *bar;

@@ -170,7 +170,7 @@ __global__ void k_elite_init(GomParams P)
         P.st->improved = 1;
         P.st->done = 0;
     }
-    for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
+    for (int w = threadIdx.x; w < 2 * P.W; w += blockDim.x) P.eqw[w] = kFull;
 }
 
 // State after an import: given elitist fitness and generation counter.
@@ -185,7 +185,7 @@ __global__ void k_set_state(GomParams P, int64_t fe, int64_t g)
         P.st->g = (uint32_t)g;
         P.st->cnt[0] = P.st->cnt[1] = P.st->cnt[2] = 0;
     }
-    for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
+    for (int w = threadIdx.x; w < 2 * P.W; w += blockDim.x) P.eqw[w] = kFull;
 }
 
 __global__ void k_begin_call(GomParams P, int64_t target)
@@ -252,22 +252,25 @@ __device__ bool grid_barrier(unsigned long long *count, int *err, unsigned expec
 }
 
 // ----------------------------------------------------------------------------
-// Generation start (Alg. 3 Clone): P <- O.  If the elitist changed in the last
-// generation, its bits are taken from column `argmax` of O (O has not changed
-// since).  eqw[w] bit b ends as 1 iff individual 32w+b equals the elitist on
-// every variable (the flag of the acceptance rule, fixed for the generation);
-// eqw starts all ones.  Thread idx handles word idx = v*W + w; the grid
-// stride is a multiple of W.
-__device__ void phase_gen_start(const GomParams &P)
+// Generation start (Alg. 3 Clone): P <- O.  If the elitist changed at the end
+// of the last generation (`improved`), its bits are taken from column
+// `argmax` of O (O has not changed since).  The elitist flags of generation g
+// live in buffer g mod 2: bit b of eqw[g%2][w] ends as 1 iff individual
+// 32w+b equals the elitist on every variable (the flag of the acceptance
+// rule, fixed for the generation; the buffer starts all ones).  The other
+// buffer is reset to all ones for generation g+1.  Thread idx handles word
+// idx = v*W + w; the grid stride is a multiple of W.
+__device__ void phase_gen_start(const GomParams &P, int improved, int argmax, uint32_t g)
 {
     __shared__ uint32_t s_eq[32];
-    const int improved = P.st->improved;
-    const int aw = P.st->argmax >> 5, ab = P.st->argmax & 31;
+    const int aw = argmax >> 5, ab = argmax & 31;
     const int W = P.W;
     const int lw = __ffs(W) - 1;
     const int64_t total = (int64_t)P.n * W;
     const int64_t tid = gthread(), nth = gthreads();
     const int w = (int)(tid & (W - 1));
+    uint32_t *eqw = P.eqw + (g & 1) * W;
+    if (tid < W) P.eqw[((g + 1) & 1) * W + tid] = kFull;
     uint32_t eq = kFull;
     for (int64_t idx = tid; idx < total; idx += nth) {
         const int64_t v = idx >> lw;
@@ -289,15 +292,14 @@ __device__ void phase_gen_start(const GomParams &P)
     if (lane < W) atomicAnd(&s_eq[lane], eq);
     __syncthreads();
     if (threadIdx.x < W && threadIdx.x < 32 && s_eq[threadIdx.x] != kFull)
-        atomicAnd(&P.eqw[threadIdx.x], s_eq[threadIdx.x]);
+        atomicAnd(&eqw[threadIdx.x], s_eq[threadIdx.x]);
 }
 
 // Group order of generation g (Alg. 3 visits the groups in random order): colours sorted by
 // their 64-bit Philox key, ties by colour index.  Every block draws all k keys
 // into shared memory s_key[k] and ranks a grid-strided share of the colours.
-__device__ void phase_order(const GomParams &P, unsigned long long *s_key)
+__device__ void phase_order(const GomParams &P, unsigned long long *s_key, uint32_t g)
 {
-    const uint32_t g = P.st->g;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int c = threadIdx.x; c < P.k; c += blockDim.x) {
         const uint4 r = philox10(make_uint4((uint32_t)c, 0u, g, kTagOrder), k0, k1);
@@ -316,39 +318,49 @@ __device__ void phase_order(const GomParams &P, unsigned long long *s_key)
     __syncthreads();
 }
 
-// Generation end (one block): elitist update (strict improvement, lowest
-// index of the best; Sec. 4), counters, target check, g += 1.  `improved`
-// records whether this generation replaced the elitist, so the next
-// generation start copies it out of O.
-__device__ void phase_gen_end(const GomParams &P, int64_t target)
+// Generation end: the elitist update (strict improvement, lowest index of
+// the best; Sec. 4), the counters, the target check and g += 1.  Every block
+// that calls it computes the same values from the fitness array; block 0
+// (write_state) records them: the state, and the counters of generation g in
+// the statistics ring.  `improved` tells the next generation start to copy the
+// elitist out of O.  Returns the target check.
+struct GenEnd {
+    int64_t fe;
+    int improved, argmax;
+};
+
+__device__ bool phase_gen_end(const GomParams &P, int64_t target, uint32_t g, GenEnd &e, bool write_state)
 {
     int64_t best;
     int arg;
     block_argmax(P.f, P.p, &best, &arg);
-    if (threadIdx.x == 0) {
+    e.improved = best > e.fe;
+    if (e.improved) {
+        e.fe = best;
+        e.argmax = arg;
+    }
+    const bool reached = best >= target;
+    if (write_state && threadIdx.x == 0) {
         GomDevState *st = P.st;
-        const int better = best > st->fe;
-        if (better) {
-            st->fe = best;
-            st->argmax = arg;
-        }
-        st->improved = better;
+        st->fe = e.fe;
+        st->argmax = e.argmax;
+        st->improved = e.improved;
         st->best = best;
-        GomDevStats &S = P.stats[st->g % kStatsCap];
-        S.generation = st->g;
+        GomDevStats &S = P.stats[g % kStatsCap];
+        S.generation = g;
         S.best = best;
-        S.elite = st->fe;
+        S.elite = e.fe;
         S.trials = (int64_t)P.p * P.m;
         S.donorless = st->cnt[0];
         S.accepted = st->cnt[1];
         S.improving = st->cnt[2];
-        S.reached = best >= target;
+        S.reached = reached;
         st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
-        st->done = best >= target;
-        st->g += 1;
+        st->done = reached;
+        st->g = g + 1;
     }
-    for (int w = threadIdx.x; w < P.W; w += blockDim.x) P.eqw[w] = kFull;
     __syncthreads();
+    return reached;
 }
 
 // Loads WPI consecutive 32-bit words (16/8/4-byte aligned by construction);
@@ -673,7 +685,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, u
 #pragma unroll
         for (int r = 0; r < WPI; ++r) {
             const int i = 32 * (w0 + r) + lane;
-            const bool eq = (P.eqw[w0 + r] >> lane) & 1u;
+            const bool eq = (P.eqw[(g & 1) * W + w0 + r] >> lane) & 1u;
             const bool acc = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
             afm[r] = acc ? fm[r] : (MaskT)0;
             anyacc |= acc;
@@ -786,14 +798,14 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g,
 __global__ void k_gen_start(GomParams P)
 {
     if (P.st->done) return;
-    phase_gen_start(P);
+    phase_gen_start(P, P.st->improved, P.st->argmax, P.st->g);
 }
 
 __global__ void k_order(GomParams P)
 {
     extern __shared__ unsigned long long s_key[];
     if (P.st->done) return;
-    phase_order(P, s_key);
+    phase_order(P, s_key, P.st->g);
 }
 
 template <int WPI, typename MaskT, typename AccT>
@@ -811,20 +823,20 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
 __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 {
     if (P.st->done) return;
-    phase_gen_end(P, P.st->target);
+    GenEnd e{P.st->fe, 0, P.st->argmax};
+    phase_gen_end(P, P.st->target, P.st->g, e, true);
 }
 
 // Persistent path: up to G generations in one cooperative launch, the phases
-// separated by grid barriers (gen start + order | each colour group | gen
-// end).  Before each barrier that opens a colour group, every warp stages the
-// generation-constant half of its first item of that group (its P rows,
-// pattern table and edge list), so after the barrier only the parent's words
-// remain to be loaded.  The block's fitness accumulators span all groups of a
-// generation and are flushed once before the generation end.  Stops early
-// once a generation reached the target: done is written by every generation
-// end and read after the following barrier, so every block takes the same
-// decision (the first generation of a call ignores the flag left by an
-// earlier call).
+// separated by grid barriers: [generation start + group order] | group 0 |
+// ... | group k-1 | and again.  A generation's end is computed by every block
+// from the fitness array right after the barrier that closes its last group
+// (the same values everywhere; block 0 records them), so it needs no phase
+// of its own, and every block takes the same stop decision.  Before each
+// barrier that opens a colour group, every warp stages the generation-constant
+// half of its first item of that group (its P rows, pattern table and edge
+// list).  The block's fitness accumulators span all groups of a generation
+// and are flushed once, before the closing barrier.
 template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
 {
@@ -834,16 +846,16 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     const unsigned nblk = gridDim.x;
     const int gwarp = (int)(gthread() >> 5);
     uint32_t *sP = s_dyn + (threadIdx.x >> 5) * P.warp_smem;
-    const uint32_t g0 = P.st->g;
+    uint32_t g = P.st->g;
+    GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        P.st->call_g0 = g0; // read by the host after the kernel only
+        P.st->call_g0 = g; // read by the host after the kernel only
         P.st->target = target;
     }
     for (int q = 0; q < G; ++q) {
-        if (q > 0 && *(volatile int32_t *)&P.st->done) return;
-        const uint32_t g = g0 + (uint32_t)q;
-        phase_gen_start(P);
-        phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn));
+        if (q > 0 && phase_gen_end(P, target, g - 1, e, blockIdx.x == 0)) return;
+        phase_gen_start(P, e.improved, e.argmax, g);
+        phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
         acc_zero(P, s_f, s_cnt);
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
         for (int t = 0; t < P.k; ++t) {
@@ -855,9 +867,9 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
         }
         acc_flush(P, s_f, s_cnt);
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
-        if (blockIdx.x == 0) phase_gen_end(P, target);
-        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        ++g;
     }
+    if (G > 0 && blockIdx.x == 0) phase_gen_end(P, target, g - 1, e, true);
 }
 
 // Self-test of the grid barrier's bounded wait: `blocks` co-resident blocks
