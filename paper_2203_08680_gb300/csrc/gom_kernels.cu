@@ -52,7 +52,8 @@ __device__ __forceinline__ uint32_t pick(uint4 r, int q)
 __device__ __forceinline__ int64_t gthread() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gthreads() { return (int64_t)gridDim.x * blockDim.x; }
 
-// Lowest index of the maximum of f[0..p) over one block (blockDim <= 1024).
+// Lowest index of the maximum of f[0..p) over one block (blockDim <= 1024);
+// every thread of the block receives the result.
 __device__ void block_argmax(const int64_t *f, int p, int64_t *best_out, int *arg_out)
 {
     __shared__ long long s_best[32];
@@ -90,12 +91,16 @@ __device__ void block_argmax(const int64_t *f, int p, int64_t *best_out, int *ar
                 arg = oa;
             }
         }
-        if (lane == 0) {
-            *best_out = best;
-            *arg_out = arg;
-        }
+    }
+    __syncthreads(); // every warp has read s_best / s_arg
+    if (threadIdx.x == 0) {
+        s_best[0] = best;
+        s_arg[0] = arg;
     }
     __syncthreads();
+    *best_out = s_best[0];
+    *arg_out = s_arg[0];
+    __syncthreads(); // s_best / s_arg may be reused by the next call
 }
 
 } // namespace
