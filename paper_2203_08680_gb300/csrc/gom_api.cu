@@ -59,7 +59,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.hdr = take(sizeof(int32_t) * 4 * m);
     L.fv = take(sizeof(int32_t) * total_vars);
     L.wout = take(sizeof(int64_t) * total_vars);
-    L.seg = take(sizeof(uint16_t) * (total_vars + m));
+    L.seg = take(sizeof(uint32_t) * (total_vars + m));
     L.dep = take(sizeof(int32_t) * 2 * ndeps);
     L.cptr = take(sizeof(int32_t) * (std::max<int32_t>(k, 0) + 1));
     L.total = off;
@@ -380,18 +380,23 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     }
     const int per = split ? (wv + wpi - 1) / wpi : 1;
     c->mix_fn = gom_mix_kernel(wpi, narrow);
-    // per-warp shared memory of the mixing phase (the only definition of its
-    // layout; the kernel takes these offsets): the rows of P on one element,
-    // the table of every individual's bits on it (32 W masks of 4 or 8
-    // bytes), the run starts of that table (W words), one int4 per variable,
-    // then one record per edge (WPI parent words, code and weight, padded to
-    // 4 or 8 words).  All offsets are multiples of 4 words.
+    // One staging slice (one mixing item) in shared memory -- the one
+    // definition of its layout; the kernels take these offsets (words): an
+    // 8-word item header, the element's variables, their outside-edge starts
+    // (s+1), their outside weight sums (int64), the rows of P on the element
+    // (W words each), the pattern table (32 W masks of 4 or 8 bytes), its run
+    // starts (W words), then one record per edge (code, weight, WPI parent
+    // words; 4 or 8 words).  Every offset is a multiple of 4 words (16 bytes).
     const int es = wpi == 4 ? 8 : 4;
     auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
-    const int64_t off_pat = round4(static_cast<int64_t>(tabs.max_s) * c->W);
+    const int64_t smax = tabs.max_s;
+    const int64_t off_fv = 8;
+    const int64_t off_seg = off_fv + round4(smax);
+    const int64_t off_wout = off_seg + round4(smax + 1);
+    const int64_t off_pr = off_wout + round4(2 * smax);
+    const int64_t off_pat = off_pr + round4(smax * c->W);
     const int64_t off_rs = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
-    const int64_t off_var = off_rs + round4(c->W);
-    const int64_t off_edge = off_var + 4 * static_cast<int64_t>(tabs.max_s);
+    const int64_t off_edge = off_rs + round4(c->W);
     const int64_t warp_words = off_edge + tabs.max_edges * es;
     constexpr int64_t kSmemBudget = 200 * 1024;
     const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (warp_words * 4)));
@@ -411,18 +416,44 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
 
     // persistent path: one cooperative kernel, grid limited to co-resident blocks
     c->run_fn = gom_run_kernel(wpi, narrow);
-    c->run_smem = std::max(c->mix_smem, sizeof(unsigned long long) * static_cast<size_t>(std::max(c->k, 1)));
+    const size_t keys_smem = sizeof(unsigned long long) * static_cast<size_t>(std::max(c->k, 1));
     int coop = 0;
     GOM_CUDA(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    if (coop && c->run_smem <= static_cast<size_t>(kSmemBudget)) {
-        GOM_CUDA(c, cudaFuncSetAttribute(c->run_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(c->run_smem)));
+    auto run_grid = [&](size_t smem_bytes, int *out_grid) -> cudaError_t {
+        *out_grid = 0;
+        if (smem_bytes > static_cast<size_t>(kSmemBudget)) return cudaSuccess;
+        cudaError_t e = cudaFuncSetAttribute(c->run_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem_bytes));
+        if (e != cudaSuccess) return e;
         int occ_run = 0;
-        GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_run, c->run_fn, c->mix_threads, c->run_smem));
-        if (occ_run > 0) {
-            c->grid_run = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_run,
-                                                             std::max<int64_t>(need_blocks, 1)));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_run, c->run_fn, c->mix_threads, smem_bytes);
+        if (e != cudaSuccess) return e;
+        *out_grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_run,
+                                                       std::max<int64_t>(need_blocks, 1)));
+        return cudaSuccess;
+    };
+    if (coop) {
+        // stage_all: every warp stages its item of every colour group at the
+        // start of a generation -- when each group fits in one wave of warps
+        // and the k slices per warp fit in shared memory
+        const size_t all_smem = std::max(keys_smem, static_cast<size_t>(c->k) * warp_words * 4 * warps_per_block);
+        int grid_all = 0;
+        GOM_CUDA(c, run_grid(all_smem, &grid_all));
+        if (grid_all > 0 && max_group * per <= static_cast<int64_t>(grid_all) * warps_per_block) {
+            c->run_smem = all_smem;
+            c->grid_run = grid_all;
+            c->prm.stage_all = 1;
             c->can_persist = true;
+        } else {
+            const size_t one_smem = std::max(keys_smem, c->mix_smem);
+            int grid_one = 0;
+            GOM_CUDA(c, run_grid(one_smem, &grid_one));
+            if (grid_one > 0) {
+                c->run_smem = one_smem;
+                c->grid_run = grid_one;
+                c->prm.stage_all = 0;
+                c->can_persist = true;
+            }
         }
     }
     c->persistent = c->can_persist;
@@ -447,9 +478,12 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.seed = seed;
     P.split = split;
     P.warp_smem = static_cast<int32_t>(warp_words);
+    P.off_fv = static_cast<int32_t>(off_fv);
+    P.off_seg = static_cast<int32_t>(off_seg);
+    P.off_wout = static_cast<int32_t>(off_wout);
+    P.off_pr = static_cast<int32_t>(off_pr);
     P.off_pat = static_cast<int32_t>(off_pat);
     P.off_rs = static_cast<int32_t>(off_rs);
-    P.off_var = static_cast<int32_t>(off_var);
     P.off_edge = static_cast<int32_t>(off_edge);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);
@@ -466,7 +500,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.hdr = reinterpret_cast<const int4 *>(base + L.hdr);
     P.fv = reinterpret_cast<const int32_t *>(base + L.fv);
     P.wout = reinterpret_cast<const int64_t *>(base + L.wout);
-    P.seg = reinterpret_cast<const uint16_t *>(base + L.seg);
+    P.seg = reinterpret_cast<const uint32_t *>(base + L.seg);
     P.dep = reinterpret_cast<const int2 *>(base + L.dep);
     P.cptr = reinterpret_cast<const int32_t *>(base + L.cptr);
 

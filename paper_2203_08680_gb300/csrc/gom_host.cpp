@@ -267,12 +267,12 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
             const int32_t j = fos.celems[q];
             const int64_t e0 = fos.eptr[j], s = fos.eptr[j + 1] - e0;
             for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = static_cast<int32_t>(a);
-            uint16_t *seg = out->seg.data() + f0[q] + q;
+            uint32_t *seg = out->seg.data() + f0[q] + q;
             int64_t n_out = 0, n_in = 0, sum_abs = 0;
             for (int64_t a = 0; a < s; ++a) {
                 const int32_t u = fos.evars[e0 + a];
                 out->fv[f0[q] + a] = u;
-                seg[a] = static_cast<uint16_t>(n_out);
+                seg[a] = static_cast<uint32_t>(n_out);
                 int64_t wsum = 0;
                 for (int64_t x = g->row_ptr[u]; x < g->row_ptr[u + 1]; ++x) {
                     const int32_t bb = pos[g->col[x]];
@@ -289,7 +289,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
                 out->wout[f0[q] + a] = wsum;
                 if (n_out > 65535) too_big = 1;
             }
-            seg[s] = static_cast<uint16_t>(n_out);
+            seg[s] = static_cast<uint32_t>(n_out);
             d0[q + 1] = n_out + n_in;
             int32_t *h = out->hdr.data() + 4 * q;
             h[0] = j;

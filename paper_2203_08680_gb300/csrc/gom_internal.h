@@ -47,7 +47,7 @@ struct ElemTables {
     std::vector<int32_t> hdr;     // 4 ints per element
     std::vector<int32_t> fv;      // [total_vars]
     std::vector<int64_t> wout;    // [total_vars]
-    std::vector<uint16_t> seg;    // [total_vars + m]
+    std::vector<uint32_t> seg;    // [total_vars + m]
     std::vector<int32_t> dep;     // 2 ints per entry
     int32_t max_s = 0;            // largest element
     int64_t max_edges = 0;        // most edges (outside + inside) of one element
@@ -97,12 +97,15 @@ struct GomParams {
     int32_t m;         // FOS elements
     int32_t k;         // colours
     int32_t split;      // mixing items: 0 = one warp per element, 1 = one per (element, word group)
-    int32_t pad0;
-    int32_t warp_smem;  // 32-bit words of dynamic shared memory per warp in the mixing phase:
-    int32_t off_pat;    //   [0, off_pat) rows of P on F_j, [off_pat, off_rs) pattern table
-    int32_t off_rs;     //   (32 W masks), [off_rs, off_var) its run starts (W words),
-    int32_t off_var;    //   [off_var, off_edge) one int4 per variable,
-    int32_t off_edge;   //   [off_edge, warp_smem) edge records
+    int32_t stage_all;  // 1: each warp stages its items of all k groups at generation start
+    int32_t warp_smem;  // 32-bit words of one staging slice (one item) in the mixing phase:
+    int32_t off_fv;     //   [0, 8) item header, [off_fv, ..) the element's variables,
+    int32_t off_seg;    //   [off_seg, ..) their outside-edge starts (s+1), [off_wout, ..)
+    int32_t off_wout;   //   their outside weight sums (int64), [off_pr, ..) the rows of P
+    int32_t off_pr;     //   on F_j, [off_pat, ..) the pattern table (32 W masks),
+    int32_t off_pat;    //   [off_rs, ..) its run starts (W words), [off_edge, warp_smem)
+    int32_t off_rs;     //   edge records
+    int32_t off_edge;
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population
@@ -119,7 +122,7 @@ struct GomParams {
     const int4 *hdr;         // [m] element headers in colour order
     const int32_t *fv;       // [total_vars]
     const int64_t *wout;     // [total_vars]
-    const uint16_t *seg;     // [total_vars + m]
+    const uint32_t *seg;     // [total_vars + m]
     const int2 *dep;         // outside edges {v, w}, then inside edges {a | b << 8, w}
     const int32_t *cptr;     // [k+1] colour -> positions
 };

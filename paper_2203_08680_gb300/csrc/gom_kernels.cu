@@ -409,12 +409,16 @@ __device__ int scan_donor(const uint32_t *sP, int W, int Wv, int p, int s, MaskT
     return -1;
 }
 
-// Words per staged edge record in the mixing phase: WPI parent words, then
-// code and weight, padded to a power of two so the parent words load as one
-// vector.
+// Words per staged edge record in the mixing phase: code and weight, then
+// the parent words of WPI individuals-words at offset EdgeX (4 or 2 words,
+// so they load as one vector); the stride is a power of two.
 template <int WPI>
 struct EdgeStride {
     static constexpr int value = WPI == 4 ? 8 : 4;
+};
+template <int WPI>
+struct EdgeX {
+    static constexpr int value = WPI == 4 ? 4 : 2;
 };
 
 // Value held by lane (a mod 32) of lo (a < 32) or hi (a >= 32): per-variable
@@ -474,83 +478,117 @@ __device__ int find_donor(const MaskT *patP, const uint32_t *rs, const uint32_t 
     return scan_donor<MaskT>(sP, W, Wv, p, s, xf, d3, self);
 }
 
-// A warp's current mixing item: one element of a colour group and a range of
-// its population word groups.  Lane a holds the element's variable F_j[a]
-// (and F_j[32 + a] in fl2 for elements of more than 32 variables).
-struct MixItem {
-    int valid;
-    int q, j, d0, s, n_in, n_out;
-    int wg0, wg1;
-    int fl, fl2;
+// Asynchronous global -> shared copies (cp.async): they do not hold registers
+// or stall the warp until cp_wait(), so many can be in flight together.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+// Waits for this thread's copies, then makes the warp's copies visible to the warp.
+__device__ __forceinline__ void cp_wait_warp()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncwarp();
+}
+
+// A staging slice (one mixing item: an element and a range of its words):
+//  hdr[8] = {valid, q, j, d0, s | n_in << 8, n_out, f0, sub}
+//  fv[s] variables, seg[s+1] their outside-edge starts, wout[s] their outside
+//  weight sums (int64), rows of P on F_j [s][W], patP[32 W] every individual's
+//  bits on F_j, rs[W] run starts of patP, edge records [E][ES].
+// Offsets come from the host (the one definition of the layout).
+struct Slice {
+    uint32_t *base;
+    __device__ __forceinline__ int *hdr() const { return reinterpret_cast<int *>(base); }
 };
 
-// Item `it` of the group at position t (an element and its word groups).
-__device__ __forceinline__ MixItem mix_item(const GomParams &P, int t, int it, int WPI_)
+// Decodes item `it` of the group at position t into the slice header (lane 0
+// writes).  Returns validity.  A warp-uniform result.
+__device__ __forceinline__ bool decode_item(const GomParams &P, int t, int it, int WPI_, uint32_t *sl)
 {
-    MixItem m;
-    const int lane = threadIdx.x & 31;
     const int c = P.order[t];
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
     const int nwg = (P.Wv + WPI_ - 1) / WPI_;
     const int per = P.split ? nwg : 1;
-    m.valid = it < ne * per;
-    if (!m.valid) return m;
-    const int e = it / per, sub = it - e * per;
-    m.wg0 = P.split ? sub : 0;
-    m.wg1 = P.split ? sub + 1 : nwg;
-    m.q = q0 + e;
-    const int4 h = P.hdr[m.q];
-    m.j = h.x;
-    m.d0 = h.z;
-    m.s = h.w & 0xFF;
-    m.n_in = h.w >> 8;
-    const int f0 = h.y;
-    m.fl = lane < m.s ? P.fv[f0 + lane] : 0;
-    m.fl2 = lane + 32 < m.s ? P.fv[f0 + 32 + lane] : 0;
-    m.n_out = (int)P.seg[f0 + m.q + m.s];
-    return m;
+    const bool valid = it < ne * per;
+    if ((threadIdx.x & 31) == 0) {
+        int *h = reinterpret_cast<int *>(sl);
+        h[0] = valid;
+        if (valid) {
+            const int e = it / per, sub = it - e * per;
+            const int q = q0 + e;
+            const int4 r = P.hdr[q];
+            const int sv = r.w & 0xFF;
+            h[1] = q;
+            h[2] = r.x;
+            h[3] = r.z;
+            h[4] = r.w;
+            h[5] = (int)P.seg[r.y + q + sv];
+            h[6] = r.y;
+            h[7] = sub;
+        }
+    }
+    return valid;
 }
 
-// Items of group t in total (elements times word-group slices).
-__device__ __forceinline__ int mix_items(const GomParams &P, int t, int WPI_)
-{
-    const int c = P.order[t];
-    const int nwg = (P.Wv + WPI_ - 1) / WPI_;
-    return (P.cptr[c + 1] - P.cptr[c]) * (P.split ? nwg : 1);
-}
-
-// Stages the generation-constant half of an item into the warp's slice of
-// shared memory: one record per variable (its outside-edge range and weight
-// sum), the rows of P on F_j, the edge list, the table patP of every
-// individual's bits on F_j and the run starts of that table.  None of it
-// depends on O, so it may run before the barrier that opens the item's group.
-template <int WPI, typename MaskT>
-__device__ __forceinline__ void stage_item(const GomParams &P, const MixItem &m, uint32_t *sP)
+// Level-1 copies of a decoded item: variables, their edge starts and weight
+// sums, and the edge list (code, weight).
+template <int WPI>
+__device__ __forceinline__ void stage_lists(const GomParams &P, uint32_t *sl)
 {
     constexpr int ES = EdgeStride<WPI>::value;
     const int lane = threadIdx.x & 31;
-    const int W = P.W, Wv = P.Wv, p = P.p;
-    const int lw = __ffs(W) - 1;
-    MaskT *patP = reinterpret_cast<MaskT *>(sP + P.off_pat);
-    uint32_t *rs = sP + P.off_rs;
-    int4 *vrec = reinterpret_cast<int4 *>(sP + P.off_var);
-    uint32_t *sE = sP + P.off_edge;
-    const int s = m.s;
-    const int f0 = P.hdr[m.q].y;
-    __syncwarp();
+    const int *h = reinterpret_cast<const int *>(sl);
+    const int q = h[1], d0 = h[3], s = h[4] & 0xFF, n_in = h[4] >> 8, n_out = h[5], f0 = h[6];
     for (int a = lane; a < s; a += 32) {
-        const int64_t wa = P.wout[f0 + a];
-        vrec[a] = make_int4((int)P.seg[f0 + m.q + a], a + 1 == s ? m.n_out : (int)P.seg[f0 + m.q + a + 1],
-                            (int)(uint32_t)(uint64_t)wa, (int)((uint64_t)wa >> 32));
+        cp_async4(sl + P.off_fv + a, P.fv + f0 + a);
+        cp_async8(sl + P.off_wout + 2 * a, P.wout + f0 + a);
     }
-    for (int x = lane; x < (s << lw); x += 32)
-        sP[x] = P.P[P.fv[f0 + (x >> lw)] * W + (x & (W - 1))];
-    for (int x = lane; x < m.n_out + m.n_in; x += 32) {
-        const int2 d = P.dep[m.d0 + x];
-        sE[x * ES + WPI] = (uint32_t)d.x;
-        sE[x * ES + WPI + 1] = (uint32_t)d.y;
+    for (int a = lane; a <= s; a += 32) cp_async4(sl + P.off_seg + a, P.seg + f0 + q + a);
+    for (int x = lane; x < n_out + n_in; x += 32) cp_async8(sl + P.off_edge + x * ES, P.dep + d0 + x);
+}
+
+// Level-2 copies: the rows of P on F_j (all W words), from the staged variables.
+__device__ __forceinline__ void stage_rows(const GomParams &P, uint32_t *sl)
+{
+    const int lane = threadIdx.x & 31;
+    const int *h = reinterpret_cast<const int *>(sl);
+    const int s = h[4] & 0xFF, W = P.W;
+    const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
+    uint32_t *sP = sl + P.off_pr;
+    if (W >= 4) {
+        const int n4 = (s * W) >> 2, lw4 = __ffs(W >> 2) - 1;
+        for (int x = lane; x < n4; x += 32) {
+            const int a = x >> lw4, w4 = x & ((W >> 2) - 1);
+            cp_async16(sP + 4 * x, P.P + fv[a] * W + 4 * w4);
+        }
+    } else {
+        const int lw = __ffs(W) - 1;
+        for (int x = lane; x < (s << lw); x += 32) cp_async4(sP + x, P.P + fv[x >> lw] * W + (x & (W - 1)));
     }
-    __syncwarp();
+}
+
+// Pattern table and its run starts, from the staged rows (no global memory).
+template <typename MaskT>
+__device__ __forceinline__ void stage_patterns(const GomParams &P, uint32_t *sl)
+{
+    const int lane = threadIdx.x & 31;
+    const int *h = reinterpret_cast<const int *>(sl);
+    const int s = h[4] & 0xFF, W = P.W, Wv = P.Wv, p = P.p;
+    const uint32_t *sP = sl + P.off_pr;
+    MaskT *patP = reinterpret_cast<MaskT *>(sl + P.off_pat);
+    uint32_t *rs = sl + P.off_rs;
     // lane l builds the bits on F_j of individuals 32 wc + l
     for (int wc = 0; wc < Wv; ++wc) {
         MaskT pat = 0;
@@ -567,6 +605,78 @@ __device__ __forceinline__ void stage_item(const GomParams &P, const MixItem &m,
     __syncwarp();
 }
 
+// Stages one item of group t (item index `it`) into a slice: decode, then
+// two levels of asynchronous copies, then the pattern table.  Only
+// generation-constant data: it may run before the barrier that opens group t.
+template <int WPI, typename MaskT>
+__device__ __forceinline__ bool stage_item(const GomParams &P, int t, int it, uint32_t *sl)
+{
+    __syncwarp();
+    const bool valid = decode_item(P, t, it, WPI, sl);
+    if (!valid) return false;
+    __syncwarp();
+    stage_lists<WPI>(P, sl);
+    cp_wait_warp();
+    stage_rows(P, sl);
+    cp_wait_warp();
+    stage_patterns<MaskT>(P, sl);
+    return true;
+}
+
+// Stages this warp's item of every group (one item per group at most) into
+// consecutive slices, overlapping the copies of all of them: decode all
+// (lane t decodes group t), first-level copies of all, second-level copies
+// of all, then the pattern tables.
+template <int WPI, typename MaskT>
+__device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = P.k;
+    __syncwarp();
+    for (int t0 = 0; t0 < k; t0 += 32) {
+        const int t = t0 + lane;
+        if (t < k) {
+            uint32_t *sl = slices + t * P.warp_smem;
+            const int c = P.order[t];
+            const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
+            const int nwg = (P.Wv + WPI - 1) / WPI;
+            const int per = P.split ? nwg : 1;
+            const int it = gwarp;
+            int *h = reinterpret_cast<int *>(sl);
+            const bool valid = it < ne * per;
+            h[0] = valid;
+            if (valid) {
+                const int e = it / per, sub = it - e * per;
+                const int q = q0 + e;
+                const int4 r = P.hdr[q];
+                const int sv = r.w & 0xFF;
+                h[1] = q;
+                h[2] = r.x;
+                h[3] = r.z;
+                h[4] = r.w;
+                h[5] = (int)P.seg[r.y + q + sv];
+                h[6] = r.y;
+                h[7] = sub;
+            }
+        }
+    }
+    __syncwarp();
+    for (int t = 0; t < k; ++t) {
+        uint32_t *sl = slices + t * P.warp_smem;
+        if (sl[0]) stage_lists<WPI>(P, sl);
+    }
+    cp_wait_warp();
+    for (int t = 0; t < k; ++t) {
+        uint32_t *sl = slices + t * P.warp_smem;
+        if (sl[0]) stage_rows(P, sl);
+    }
+    cp_wait_warp();
+    for (int t = 0; t < k; ++t) {
+        uint32_t *sl = slices + t * P.warp_smem;
+        if (sl[0]) stage_patterns<MaskT>(P, sl);
+    }
+}
+
 // All trials of a staged item (Alg. 2 for each individual of its words):
 //  draws:   one Philox call per lane gives 4 words: lane c holds the call
 //           of individuals 4c..4c+3 of the word group, fetched by shuffles
@@ -581,36 +691,45 @@ __device__ __forceinline__ void stage_item(const GomParams &P, const MixItem &m,
 // Fitness deltas go to the block's shared accumulators s_f; counters to
 // per-lane counts.
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, uint32_t *sP, uint32_t g,
-                                         long long *s_f, unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
+__device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint32_t g, long long *s_f,
+                                         unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
-    constexpr int ES = EdgeStride<WPI>::value;
+    constexpr int ES = EdgeStride<WPI>::value, XO = EdgeX<WPI>::value;
     const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p;
-    const MaskT *patP = reinterpret_cast<const MaskT *>(sP + P.off_pat);
-    const uint32_t *rs = sP + P.off_rs;
-    const int4 *vrec = reinterpret_cast<const int4 *>(sP + P.off_var);
-    uint32_t *sE = sP + P.off_edge;
+    const int *h = reinterpret_cast<const int *>(sl);
+    const int j = h[2], s = h[4] & 0xFF, n_in = h[4] >> 8, n_out = h[5], sub = h[7];
+    const int nwg = (Wv + WPI - 1) / WPI;
+    const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
+    const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
+    const uint32_t *sseg = sl + P.off_seg;
+    const int64_t *swout = reinterpret_cast<const int64_t *>(sl + P.off_wout);
+    const uint32_t *sP = sl + P.off_pr;
+    const MaskT *patP = reinterpret_cast<const MaskT *>(sl + P.off_pat);
+    const uint32_t *rs = sl + P.off_rs;
+    uint32_t *sE = sl + P.off_edge;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-    const int s = m.s, n_out = m.n_out, ne_tot = m.n_out + m.n_in;
+    const int ne_tot = n_out + n_in;
+    const int fl = lane < s ? fv[lane] : 0;
+    const int fl2 = (WIDE && lane + 32 < s) ? fv[lane + 32] : 0;
 
-    for (int wg = m.wg0; wg < m.wg1; ++wg) {
+    for (int wg = wg0; wg < wg1; ++wg) {
         const int w0 = wg * WPI;
         // parent words of the outside neighbours for this word group
         __syncwarp();
         for (int x = lane; x < n_out; x += 32) {
             uint32_t X[WPI];
-            load_words<WPI>(P.O + (int)sE[x * ES + WPI] * W + w0, X);
+            load_words<WPI>(P.O + (int)sE[x * ES] * W + w0, X);
 #pragma unroll
-            for (int r = 0; r < WPI; ++r) sE[x * ES + r] = X[r];
+            for (int r = 0; r < WPI; ++r) sE[x * ES + XO + r] = X[r];
         }
         // parent bits on F_j: lane a loads row F_j[a], then a shuffle transpose
         uint32_t Xa[WPI], Xa2[WPI];
 #pragma unroll
         for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
-        if (lane < s) load_words<WPI>(P.O + m.fl * W + w0, Xa);
-        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + m.fl2 * W + w0, Xa2);
+        if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
+        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
         MaskT xf[WPI];
 #pragma unroll
         for (int r = 0; r < WPI; ++r) xf[r] = 0;
@@ -622,7 +741,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, u
         __syncwarp();
 
         // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
-        const uint4 r4 = philox10(make_uint4((uint32_t)m.j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+        const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
         int donor[WPI];
         MaskT fm[WPI];
 #pragma unroll
@@ -652,15 +771,15 @@ __device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, u
 #pragma unroll
         for (int r = 0; r < WPI; ++r) dl[r] = 0;
         for (int a = 0; a < s; ++a) {
-            const int4 vr = vrec[a];
-            const AccT Wa = WIDE ? (AccT)(((int64_t)(uint32_t)vr.w << 32) | (uint32_t)vr.z) : (AccT)vr.z;
+            const int qb = (int)sseg[a], qe = (int)sseg[a + 1];
+            const AccT Wa = (AccT)swout[a];
             AccT S[WPI];
 #pragma unroll
             for (int r = 0; r < WPI; ++r) S[r] = 0;
-            for (int x = vr.x; x < vr.y; ++x) {
+            for (int x = qb; x < qe; ++x) {
                 uint32_t X[WPI];
-                load_words<WPI>(sE + x * ES, X);
-                const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
+                load_words<WPI>(sE + x * ES + XO, X);
+                const AccT wx = (AccT)(int32_t)sE[x * ES + 1];
 #pragma unroll
                 for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
             }
@@ -673,8 +792,8 @@ __device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, u
             }
         }
         for (int x = n_out; x < ne_tot; ++x) {
-            const uint32_t code = sE[x * ES + WPI];
-            const AccT wx = (AccT)(int32_t)sE[x * ES + WPI + 1];
+            const uint32_t code = sE[x * ES];
+            const AccT wx = (AccT)(int32_t)sE[x * ES + 1];
             const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
             for (int r = 0; r < WPI; ++r) {
@@ -716,7 +835,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, const MixItem &m, u
             }
 #pragma unroll
             for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
-                const int f = half ? m.fl2 : m.fl;
+                const int f = half ? fl2 : fl;
                 if (lane + 32 * half < s) {
                     uint32_t *row = P.O + f * W + w0;
 #pragma unroll
@@ -757,36 +876,25 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 // One colour group: all (individual, element) GOM trials (Alg. 2) of the
 // group at position t.  Items (an element, or an element's word group when
 // P.split is set) go to warps in a static stride: warp w takes items w,
-// w + nwarps, ...; its first item may already be staged (`pre`).  Elements of one group share no variable and no
-// edge (LMIG colouring), so a warp owns its element's rows for its words and
+// w + nwarps, ...; its first item may already be staged in its slice
+// (`first_staged`).  Elements of one group share no variable and no edge
+// (LMIG colouring), so a warp owns its element's rows for its words and
 // nothing else in the group touches the closure it reads.
 // MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
 // s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
 // is < 2^30).
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g, uint32_t *s_dyn, long long *s_f,
-                                          unsigned long long *s_cnt, const MixItem *pre)
+__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g, uint32_t *sl, long long *s_f,
+                                          unsigned long long *s_cnt, bool first_staged)
 {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *sP = s_dyn + wib * P.warp_smem; // this warp's slice
+    const int lane = threadIdx.x & 31;
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
-    const int total = mix_items(P, t, WPI);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-
-    MixItem m;
-    if (pre) {
-        m = *pre;
-    } else {
-        m = mix_item(P, t, gwarp, WPI);
-        if (m.valid) stage_item<WPI, MaskT>(P, m, sP);
+    for (int it = gwarp, n = 0;; it += nwarps, ++n) {
+        const bool staged = (n == 0 && first_staged) ? sl[0] != 0 : stage_item<WPI, MaskT>(P, t, it, sl);
+        if (!staged) break;
+        run_item<WPI, MaskT, AccT>(P, sl, g, s_f, n_dl, n_acc, n_imp);
     }
-    if (m.valid) run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
-    for (int it = gwarp + nwarps; it < total; it += nwarps) {
-        m = mix_item(P, t, it, WPI);
-        stage_item<WPI, MaskT>(P, m, sP);
-        run_item<WPI, MaskT, AccT>(P, m, sP, g, s_f, n_dl, n_acc, n_imp);
-    }
-
     n_dl = __reduce_add_sync(kFull, n_dl);
     n_acc = __reduce_add_sync(kFull, n_acc);
     n_imp = __reduce_add_sync(kFull, n_imp);
@@ -821,7 +929,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     __shared__ unsigned long long s_cnt[4];
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
-    phase_mix<WPI, MaskT, AccT>(P, t, P.st->g, s_dyn, s_f, s_cnt, nullptr);
+    phase_mix<WPI, MaskT, AccT>(P, t, P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem, s_f, s_cnt, false);
     acc_flush(P, s_f, s_cnt);
 }
 
@@ -850,7 +958,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     __shared__ unsigned long long s_cnt[4];
     const unsigned nblk = gridDim.x;
     const int gwarp = (int)(gthread() >> 5);
-    uint32_t *sP = s_dyn + (threadIdx.x >> 5) * P.warp_smem;
+    // this warp's staging: one slice, or one per colour group with stage_all
+    uint32_t *slices = s_dyn + (threadIdx.x >> 5) * P.warp_smem * (P.stage_all ? P.k : 1);
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -863,12 +972,13 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
         phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
         acc_zero(P, s_f, s_cnt);
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        if (P.stage_all) stage_all_items<WPI, MaskT>(P, gwarp, slices);
         for (int t = 0; t < P.k; ++t) {
-            // the first item of group t: decode and stage its P side, then wait
-            MixItem m = mix_item(P, t, gwarp, WPI);
-            if (m.valid) stage_item<WPI, MaskT>(P, m, sP);
+            uint32_t *sl = P.stage_all ? slices + t * P.warp_smem : slices;
+            // without stage_all: stage the first item of group t before its barrier
+            if (!P.stage_all) stage_item<WPI, MaskT>(P, t, gwarp, sl);
             if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
-            phase_mix<WPI, MaskT, AccT>(P, t, g, s_dyn, s_f, s_cnt, &m);
+            phase_mix<WPI, MaskT, AccT>(P, t, g, sl, s_f, s_cnt, true);
         }
         acc_flush(P, s_f, s_cnt);
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
