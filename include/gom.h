@@ -71,6 +71,10 @@ extern "C" {
                                 cooperative launch); 0: one CUDA graph per generation with one
                                 kernel per phase and per colour group */
 
+#define GOM_OPT_PHASE_TRACE 2 /* 1: the persistent kernel records wall-clock stamps (ns) of
+                                 the phase boundaries of each generation, read with
+                                 gom_read_phase_trace; 0 (default): off */
+
 /* Supported maxima of this build. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 64      /* variables in one FOS element */
@@ -234,6 +238,18 @@ int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches);
  * identical results. */
 int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value);
 int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value);
+
+/*
+ * Phase trace of the last generation run on the persistent path with
+ * GOM_OPT_PHASE_TRACE on: 5 + 2k wall-clock stamps (%globaltimer, ns), taken
+ * by block 0: [0] generation start, [1] end of the start/order phase, [2]
+ * after its barrier, [3] after staging, then for each colour-group position t:
+ * [4+2t] after the barrier that opens the group, [5+2t] when block 0 finished
+ * its share of the group; [4+2k] after the barrier that closes the
+ * generation.  ns[capacity] host array; *count receives 5 + 2k (GOM_E_ARG if
+ * capacity is smaller).  Waits for the stream.
+ */
+int gom_read_phase_trace(gom_ctx_t *ctx, int64_t *ns, int32_t capacity, int32_t *count);
 
 /*
  * Self-test of the bounded wait in the persistent kernel's grid barrier

@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, bar, stats, order;
+    size_t O, P, f, eqw, xe, st, bar, trace, stats, order;
     size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
@@ -51,6 +51,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.xe = take(n);
     L.st = take(sizeof(GomDevState));
     L.bar = take(sizeof(GomBarrier));
+    L.trace = take(sizeof(unsigned long long) * (5 + 2 * static_cast<size_t>(std::max<int32_t>(k, 1))));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
@@ -83,6 +84,7 @@ struct gom_ctx {
     int grid_run = 0;             // its grid: co-resident blocks only
     bool can_persist = false;     // cooperative launch available and the sizes fit
     bool persistent = false;      // current path: k_run (true) or the per-generation graph
+    unsigned long long *trace_buf = nullptr; // workspace slot of the phase trace
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -492,6 +494,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.xe = reinterpret_cast<uint8_t *>(base + L.xe);
     P.st = reinterpret_cast<GomDevState *>(base + L.st);
     P.bar = reinterpret_cast<GomBarrier *>(base + L.bar);
+    c->trace_buf = reinterpret_cast<unsigned long long *>(base + L.trace);
+    P.trace = nullptr;
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
@@ -698,6 +702,10 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
         ctx->persistent = value != 0;
         return GOM_OK;
     }
+    if (option == GOM_OPT_PHASE_TRACE) {
+        ctx->prm.trace = value ? ctx->trace_buf : nullptr;
+        return GOM_OK;
+    }
     return GOM_E_ARG;
 }
 
@@ -708,7 +716,22 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
         *value = ctx->persistent ? 1 : 0;
         return GOM_OK;
     }
+    if (option == GOM_OPT_PHASE_TRACE) {
+        *value = ctx->prm.trace ? 1 : 0;
+        return GOM_OK;
+    }
     return GOM_E_ARG;
+}
+
+int gom_read_phase_trace(gom_ctx_t *ctx, int64_t *ns, int32_t capacity, int32_t *count)
+{
+    if (!ctx || capacity < 0) return GOM_E_ARG;
+    const int32_t n = 5 + 2 * ctx->k;
+    if (count) *count = n;
+    if (!ns || capacity < n) return GOM_E_ARG;
+    GOM_CUDA(ctx, cudaMemcpyAsync(ns, ctx->trace_buf, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GOM_OK;
 }
 
 int gom_selftest_barrier(void *d_scratch, int32_t blocks, int32_t extra, int64_t limit_ns, void *cuda_stream,

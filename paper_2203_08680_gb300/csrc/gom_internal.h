@@ -114,6 +114,7 @@ struct GomParams {
     uint8_t *xe;       // [n] elitist
     GomDevState *st;
     GomBarrier *bar;
+    unsigned long long *trace; // [5 + 2k] phase stamps of k_run, or null (off)
     GomDevStats *stats;  // [kStatsCap] ring indexed by generation
     int32_t *order;      // [k] colour visited at position t
     const int64_t *row_ptr;

@@ -966,22 +966,32 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
         P.st->call_g0 = g; // read by the host after the kernel only
         P.st->target = target;
     }
+    // optional phase trace (block 0, thread 0): wall-clock stamps of the last
+    // generation of the call, see gom_read_phase_trace
+    const bool tr = P.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
     for (int q = 0; q < G; ++q) {
         if (q > 0 && phase_gen_end(P, target, g - 1, e, blockIdx.x == 0)) return;
+        if (tr) P.trace[0] = global_ns();
         phase_gen_start(P, e.improved, e.argmax, g);
         phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
         acc_zero(P, s_f, s_cnt);
+        if (tr) P.trace[1] = global_ns();
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        if (tr) P.trace[2] = global_ns();
         if (P.stage_all) stage_all_items<WPI, MaskT>(P, gwarp, slices);
+        if (tr) P.trace[3] = global_ns();
         for (int t = 0; t < P.k; ++t) {
             uint32_t *sl = P.stage_all ? slices + t * P.warp_smem : slices;
             // without stage_all: stage the first item of group t before its barrier
             if (!P.stage_all) stage_item<WPI, MaskT>(P, t, gwarp, sl);
             if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+            if (tr) P.trace[4 + 2 * t] = global_ns();
             phase_mix<WPI, MaskT, AccT>(P, t, g, sl, s_f, s_cnt, true);
+            if (tr) P.trace[5 + 2 * t] = global_ns();
         }
         acc_flush(P, s_f, s_cnt);
         if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        if (tr) P.trace[4 + 2 * P.k] = global_ns();
         ++g;
     }
     if (G > 0 && blockIdx.x == 0) phase_gen_end(P, target, g - 1, e, true);

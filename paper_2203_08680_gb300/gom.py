@@ -21,6 +21,7 @@ GOM_FOS_SINGLETON = 1
 GOM_MAX_POPULATION = 1024
 GOM_MAX_ELEMENT = 64
 GOM_OPT_PERSISTENT = 1
+GOM_OPT_PHASE_TRACE = 2
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
@@ -72,6 +73,7 @@ SIGNATURES = [
     ("gom_launches_per_generation", C.c_int, [_P, _P]),
     ("gom_set_option", C.c_int, [_P, _I32, _I64]),
     ("gom_get_option", C.c_int, [_P, _I32, _P]),
+    ("gom_read_phase_trace", C.c_int, [_P, _P, _I32, _P]),
     ("gom_selftest_barrier", C.c_int, [_P, _I32, _I32, _I64, _P, _P]),
     ("gom_fitness_noalloc", C.c_int, [_P, _P, _P, _I32, _P, _I32, _P, _P]),
     ("gom_last_cuda_error", C.c_int, [_P]),
@@ -311,6 +313,15 @@ def gom_get_option(ctx: Ctx, option: int) -> int:
     v = C.c_int64()
     _check(load().gom_get_option(ctx.h, option, C.byref(v)), "gom_get_option")
     return int(v.value)
+
+
+def gom_read_phase_trace(ctx: Ctx):
+    """Phase stamps (ns) of the last persistent-path generation (see include/gom.h)."""
+    cnt = C.c_int32()
+    load().gom_read_phase_trace(ctx.h, None, 0, C.byref(cnt))
+    buf = (C.c_int64 * cnt.value)()
+    _check(load().gom_read_phase_trace(ctx.h, buf, cnt.value, C.byref(cnt)), "gom_read_phase_trace", ctx)
+    return [int(x) for x in buf]
 
 
 def gom_selftest_barrier(d_scratch, blocks: int, extra: int, limit_ns: int, stream=None) -> bool:
