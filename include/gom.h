@@ -75,6 +75,11 @@ extern "C" {
                                  the phase boundaries of each generation, read with
                                  gom_read_phase_trace; 0 (default): off */
 
+#define GOM_OPT_DYNAMIC 3 /* item schedule inside a colour group: 0 = static stride (warp w
+                             takes items w, w + nwarps, ...); 1 = each warp takes item w,
+                             then claims further items from a per-group counter (faster
+                             warps take more; the default).  Same results either way */
+
 /* Supported maxima of this build. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 64      /* variables in one FOS element */
@@ -243,10 +248,12 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value);
  * Phase trace of the last generation run on the persistent path with
  * GOM_OPT_PHASE_TRACE on: 5 + 2k wall-clock stamps (%globaltimer, ns), taken
  * by block 0: [0] generation start, [1] end of the start/order phase, [2]
- * after its barrier, [3] after staging, then for each colour-group position t:
- * [4+2t] after the barrier that opens the group, [5+2t] when block 0 finished
- * its share of the group; [4+2k] after the barrier that closes the
- * generation.  ns[capacity] host array; *count receives 5 + 2k (GOM_E_ARG if
+ * end of the staging of every group's items (stage-all mode, used when every
+ * colour group fits one wave of warps; otherwise no staging happens there),
+ * [3] after the barrier that opens the generation, then for each
+ * colour-group position t: [4+2t] when the group starts (after its barrier
+ * for t > 0), [5+2t] when block 0 finished its share of the group; [4+2k]
+ * after the barrier that closes the generation.  ns[capacity] host array; *count receives 5 + 2k (GOM_E_ARG if
  * capacity is smaller).  Waits for the stream.
  */
 int gom_read_phase_trace(gom_ctx_t *ctx, int64_t *ns, int32_t capacity, int32_t *count);

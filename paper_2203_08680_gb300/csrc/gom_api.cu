@@ -28,7 +28,7 @@ int words_for(int32_t p)
 
 // Byte offsets of every device array inside the workspace.
 struct Layout {
-    size_t O, P, f, eqw, xe, st, bar, trace, stats, order;
+    size_t O, P, f, eqw, xe, st, bar, trace, stats, order, work;
     size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
     size_t total;
 };
@@ -54,10 +54,11 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.trace = take(sizeof(unsigned long long) * (5 + 2 * static_cast<size_t>(std::max<int32_t>(k, 1))));
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
+    L.work = take(sizeof(uint32_t) * std::max<int32_t>(k, 1));
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
-    L.hdr = take(sizeof(int32_t) * 4 * m);
+    L.hdr = take(sizeof(int32_t) * 8 * m);
     L.fv = take(sizeof(int32_t) * total_vars);
     L.wout = take(sizeof(int64_t) * total_vars);
     L.seg = take(sizeof(uint32_t) * (total_vars + m));
@@ -182,6 +183,23 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
     *out_graph = g;
     *out_exec = ex;
     return GOM_OK;
+}
+
+// Rebuilds the per-generation graphs after a change of the parameters they
+// copy (the timed variant only if it exists).  Waits for the stream.
+int rebuild_graphs(gom_ctx *ctx)
+{
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const bool had_timed = ctx->texec != nullptr;
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
+    if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
+    ctx->exec = ctx->texec = nullptr;
+    ctx->graph = ctx->tgraph = nullptr;
+    int rc = build_graph(ctx, false, &ctx->graph, &ctx->exec);
+    if (rc == GOM_OK && had_timed) rc = build_graph(ctx, true, &ctx->tgraph, &ctx->texec);
+    return rc;
 }
 
 int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *run_out)
@@ -380,15 +398,18 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
         split = 1;
         if ((wv + wpi - 1) / wpi == 1) wpi = 1;
     }
-    const int per = split ? (wv + wpi - 1) / wpi : 1;
+    const int nwg = (wv + wpi - 1) / wpi;
+    const int per = split ? nwg : 1;
     c->mix_fn = gom_mix_kernel(wpi, narrow);
     // One staging slice (one mixing item) in shared memory -- the one
     // definition of its layout; the kernels take these offsets (words): an
     // 8-word item header, the element's variables, their outside-edge starts
     // (s+1), their outside weight sums (int64), the rows of P on the element
     // (W words each), the pattern table (32 W masks of 4 or 8 bytes), its run
-    // starts (W words), then one record per edge (code, weight, WPI parent
-    // words; 4 or 8 words).  Every offset is a multiple of 4 words (16 bytes).
+    // starts (W words), one record per edge (code, weight, WPI parent words;
+    // 4 or 8 words), and in stage-all mode the item's donor start positions
+    // (one int per individual of its words).  Every offset is a multiple of 4
+    // words (16 bytes).
     const int es = wpi == 4 ? 8 : 4;
     auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
     const int64_t smax = tabs.max_s;
@@ -399,22 +420,15 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     const int64_t off_pat = off_pr + round4(smax * c->W);
     const int64_t off_rs = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
     const int64_t off_edge = off_rs + round4(c->W);
-    const int64_t warp_words = off_edge + tabs.max_edges * es;
+    const int64_t off_ds = off_edge + tabs.max_edges * es;
+    const int64_t base_words = off_ds;
+    const int64_t all_words = off_ds + int64_t(32) * wpi * (split ? 1 : nwg);
     constexpr int64_t kSmemBudget = 200 * 1024;
-    const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (warp_words * 4)));
+    const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (base_words * 4)));
     if (warps_per_block < 1) return GOM_E_LIMIT;
     c->mix_threads = 32 * warps_per_block;
-    c->mix_smem = static_cast<size_t>(warp_words * 4 * warps_per_block);
-    GOM_CUDA(c, cudaFuncSetAttribute(c->mix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(c->mix_smem)));
-    int occ = 0;
-    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
-    occ = std::max(occ, 1);
-    // mixing grid: one warp per item of the largest group, at most a full wave
+    // one warp per item of the largest group, at most a full wave
     const int64_t need_blocks = (max_group * per + warps_per_block - 1) / warps_per_block;
-    int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
-    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
-    c->grid_mix = static_cast<int>(grid);
 
     // persistent path: one cooperative kernel, grid limited to co-resident blocks
     c->run_fn = gom_run_kernel(wpi, narrow);
@@ -434,20 +448,23 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
                                                        std::max<int64_t>(need_blocks, 1)));
         return cudaSuccess;
     };
+    int64_t warp_words = base_words;
     if (coop) {
         // stage_all: every warp stages its item of every colour group at the
-        // start of a generation -- when each group fits in one wave of warps
-        // and the k slices per warp fit in shared memory
-        const size_t all_smem = std::max(keys_smem, static_cast<size_t>(c->k) * warp_words * 4 * warps_per_block);
+        // start of a generation -- when each group fits in one wave of warps,
+        // the k slices per warp fit in shared memory and k is small enough
+        // for every block to hold the group order
+        const size_t all_smem = static_cast<size_t>(c->k) * all_words * 4 * warps_per_block;
         int grid_all = 0;
-        GOM_CUDA(c, run_grid(all_smem, &grid_all));
+        if (c->k <= kStageAllMaxK) GOM_CUDA(c, run_grid(all_smem, &grid_all));
         if (grid_all > 0 && max_group * per <= static_cast<int64_t>(grid_all) * warps_per_block) {
             c->run_smem = all_smem;
             c->grid_run = grid_all;
             c->prm.stage_all = 1;
             c->can_persist = true;
+            warp_words = all_words;
         } else {
-            const size_t one_smem = std::max(keys_smem, c->mix_smem);
+            const size_t one_smem = std::max(keys_smem, static_cast<size_t>(base_words * 4 * warps_per_block));
             int grid_one = 0;
             GOM_CUDA(c, run_grid(one_smem, &grid_one));
             if (grid_one > 0) {
@@ -458,7 +475,19 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             }
         }
     }
+    c->mix_smem = static_cast<size_t>(warp_words * 4 * warps_per_block);
+    GOM_CUDA(c, cudaFuncSetAttribute(c->mix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(c->mix_smem)));
+    int occ = 0;
+    GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
+    occ = std::max(occ, 1);
+    int64_t grid = std::min<int64_t>(static_cast<int64_t>(c->sms) * occ, need_blocks);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
+    c->grid_mix = static_cast<int>(grid);
     c->persistent = c->can_persist;
+    // dynamic item claims: faster warps take more items (in stage-all mode
+    // every warp has at most one item per group and the schedule is moot)
+    c->prm.dyn = 1;
     const int blk_mult = std::max(1, c->W / 8);
     c->grid_fit = std::max(blk_mult, c->sms * 4 / blk_mult * blk_mult);
     c->grid_start = c->sms * 4;
@@ -487,6 +516,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.off_pat = static_cast<int32_t>(off_pat);
     P.off_rs = static_cast<int32_t>(off_rs);
     P.off_edge = static_cast<int32_t>(off_edge);
+    P.off_ds = static_cast<int32_t>(off_ds);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);
     P.f = reinterpret_cast<int64_t *>(base + L.f);
@@ -498,6 +528,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.trace = nullptr;
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
+    P.work = reinterpret_cast<uint32_t *>(base + L.work);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);
@@ -706,6 +737,12 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
         ctx->prm.trace = value ? ctx->trace_buf : nullptr;
         return GOM_OK;
     }
+    if (option == GOM_OPT_DYNAMIC) {
+        if (value != 0 && value != 1) return GOM_E_ARG;
+        if (ctx->prm.dyn == value) return GOM_OK;
+        ctx->prm.dyn = static_cast<int32_t>(value);
+        return rebuild_graphs(ctx); // the graphs hold a copy of the parameters
+    }
     return GOM_E_ARG;
 }
 
@@ -718,6 +755,10 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
     }
     if (option == GOM_OPT_PHASE_TRACE) {
         *value = ctx->prm.trace ? 1 : 0;
+        return GOM_OK;
+    }
+    if (option == GOM_OPT_DYNAMIC) {
+        *value = ctx->prm.dyn;
         return GOM_OK;
     }
     return GOM_E_ARG;

@@ -250,7 +250,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
         f0[q + 1] = f0[q] + (fos.eptr[j + 1] - fos.eptr[j]);
     }
     const size_t total = static_cast<size_t>(f0[m]);
-    out->hdr.assign(4 * static_cast<size_t>(m), 0);
+    out->hdr.assign(8 * static_cast<size_t>(m), 0);
     out->fv.assign(total, 0);
     out->wout.assign(total, 0);
     out->seg.assign(total + static_cast<size_t>(m), 0);
@@ -291,10 +291,11 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
             }
             seg[s] = static_cast<uint32_t>(n_out);
             d0[q + 1] = n_out + n_in;
-            int32_t *h = out->hdr.data() + 4 * q;
+            int32_t *h = out->hdr.data() + 8 * q;
             h[0] = j;
             h[1] = static_cast<int32_t>(f0[q]);
             h[3] = static_cast<int32_t>(s | (n_in << 8));
+            h[4] = static_cast<int32_t>(n_out);
             smax[q] = static_cast<int32_t>(s);
             wabs[q] = sum_abs;
             nedges[q] = n_out + n_in;
@@ -316,7 +317,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
             const int32_t j = fos.celems[q];
             const int64_t e0 = fos.eptr[j], s = fos.eptr[j + 1] - e0;
             for (int64_t a = 0; a < s; ++a) pos[fos.evars[e0 + a]] = static_cast<int32_t>(a);
-            out->hdr[4 * q + 2] = static_cast<int32_t>(d0[q]);
+            out->hdr[8 * q + 2] = static_cast<int32_t>(d0[q]);
             int32_t *dst = out->dep.data() + 2 * d0[q];
             for (int64_t a = 0; a < s; ++a) { // outside edges, grouped by a
                 const int32_t u = fos.evars[e0 + a];

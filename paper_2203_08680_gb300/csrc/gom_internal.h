@@ -34,7 +34,7 @@ int color_fos(const gom_graph_t *g, gom_fos *fos);
 // Per-element tables in colour order (position q = rank of the element in
 // the colour-sorted element list, so a colour group is one contiguous range
 // [cptr[c], cptr[c+1])).  For the element j at position q with s variables:
-//   hdr[q]           = {j, f0, d0, s | (n_in << 8)}
+//   hdr[8q .. 8q+8)  = {j, f0, d0, s | (n_in << 8), n_out, 0, 0, 0}
 //   fv[f0 + a]       = a-th variable of F_j (ascending)
 //   wout[f0 + a]     = sum of the weights of the edges from F_j[a] to
 //                      variables outside F_j
@@ -44,7 +44,7 @@ int color_fos(const gom_graph_t *g, gom_fos *fos);
 //                      {a | (b << 8), w} for the n_in edges inside F_j (a < b)
 // These are the dependent subfunctions of Alg. 4, each edge listed once.
 struct ElemTables {
-    std::vector<int32_t> hdr;     // 4 ints per element
+    std::vector<int32_t> hdr;     // 8 ints per element (32 bytes)
     std::vector<int32_t> fv;      // [total_vars]
     std::vector<int64_t> wout;    // [total_vars]
     std::vector<uint32_t> seg;    // [total_vars + m]
@@ -85,6 +85,7 @@ struct GomDevStats { // mirrors gom_gen_stats_t
 
 constexpr int kStatsCap = 1024;    // per-generation counters kept on the device
 constexpr int kMixThreads = 256;   // mixing kernel block size (8 warps)
+constexpr int kStageAllMaxK = 128; // most colour groups of the stage-all mode (group order held per block)
 constexpr uint32_t kTagInit = 0x494E4954u;
 constexpr uint32_t kTagDonor = 0x444F4E52u;
 constexpr uint32_t kTagOrder = 0x4F524452u;
@@ -106,6 +107,8 @@ struct GomParams {
     int32_t off_pat;    //   [off_rs, ..) its run starts (W words), [off_edge, warp_smem)
     int32_t off_rs;     //   edge records
     int32_t off_edge;
+    int32_t off_ds;     //   [off_ds, ..) donor start positions (stage-all mode only)
+    int32_t dyn;        // 1: after its first item, a warp claims items from work[t]
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population
@@ -117,10 +120,11 @@ struct GomParams {
     unsigned long long *trace; // [5 + 2k] phase stamps of k_run, or null (off)
     GomDevStats *stats;  // [kStatsCap] ring indexed by generation
     int32_t *order;      // [k] colour visited at position t
+    uint32_t *work;      // [k] item claim counters of the colour-group positions
     const int64_t *row_ptr;
     const int32_t *col;
     const int32_t *wgt;
-    const int4 *hdr;         // [m] element headers in colour order
+    const int4 *hdr;         // [2m] element headers in colour order: {j, f0, d0, s | n_in << 8}, {n_out, 0, 0, 0}
     const int32_t *fv;       // [total_vars]
     const int64_t *wout;     // [total_vars]
     const uint32_t *seg;     // [total_vars + m]

@@ -203,12 +203,16 @@ __global__ void k_begin_call(GomParams P, int64_t target)
 // ----------------------------------------------------------------------------
 // Grid-wide barrier of the persistent generation kernel (all blocks are
 // co-resident: cooperative launch).  One monotonic 64-bit arrival counter:
-// a block adds 1 with release semantics and waits, with acquire loads, until
-// the counter reaches the end of its barrier epoch (the next multiple of
-// `expected`); nothing is ever reset.  A block that waits longer than
-// kBarrierNs (wall clock, %globaltimer) or sees the error word set stops
-// waiting, sets the error word and returns false; every block then leaves the
-// kernel, so a failure ends as an error status, never a hang.
+// a block adds 1 with release semantics (a reduction: nothing comes back)
+// and waits, with acquire loads, until the counter reaches the end of the
+// barrier's epoch; each block's thread 0 keeps the next epoch end (`next`),
+// which starts at the multiple of the block count that follows the counter's
+// value at kernel start (the counter is a multiple of the block count between
+// launches: every launch either passes each barrier with all blocks or stops
+// on the sticky error word).  Nothing is ever reset.  A block that waits
+// longer than kBarrierNs (wall clock, %globaltimer) or sees the error word set
+// stops waiting, sets the error word and returns false; every block then
+// leaves the kernel, so a failure ends as an error status, never a hang.
 constexpr unsigned long long kBarrierNs = 2000000000ull; // 2 s
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -225,21 +229,27 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long *p, unsigned long long v)
+__device__ __forceinline__ void red_add_release_u64(unsigned long long *p, unsigned long long v)
 {
-    unsigned long long old;
-    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ bool grid_barrier(unsigned long long *count, int *err, unsigned expected, unsigned long long limit_ns)
+// End of the first barrier epoch of this launch (thread 0 of each block).
+__device__ __forceinline__ unsigned long long barrier_first(const unsigned long long *count, unsigned nblk)
+{
+    return ld_acquire_u64(count) / nblk * nblk + nblk;
+}
+
+__device__ bool grid_barrier(unsigned long long *count, int *err, unsigned nblk, unsigned long long &next,
+                             unsigned long long limit_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int *verr = err;
-        const unsigned long long arrived = atom_add_release_u64(count, 1ull) + 1;
-        const unsigned long long target = (arrived + expected - 1) / expected * expected;
+        red_add_release_u64(count, 1ull);
+        const unsigned long long target = next;
+        next += nblk;
         int ok = 1;
         const unsigned long long t0 = global_ns();
         while (ld_acquire_u64(count) < target) {
@@ -256,16 +266,12 @@ __device__ bool grid_barrier(unsigned long long *count, int *err, unsigned expec
     return s_ok;
 }
 
-// ----------------------------------------------------------------------------
-// Generation start (Alg. 3 Clone): P <- O.  If the elitist changed at the end
-// of the last generation (`improved`), its bits are taken from column
-// `argmax` of O (O has not changed since).  The elitist flags of generation g
-// live in buffer g mod 2: bit b of eqw[g%2][w] ends as 1 iff individual
-// 32w+b equals the elitist on every variable (the flag of the acceptance
-// rule, fixed for the generation; the buffer starts all ones).  The other
-// buffer is reset to all ones for generation g+1.  Thread idx handles word
-// idx = v*W + w; the grid stride is a multiple of W.
-__device__ void phase_gen_start(const GomParams &P, int improved, int argmax, uint32_t g)
+// Generation start (Alg. 3): P <- O (skipped with copy = false, when every
+// item's generation-start data is staged from O before anything is written),
+// the new elitist copied out of O[argmax] when it changed, the elitist flags
+// eqw[g mod 2] (P[i] == x_e over all variables), the other buffer set for
+// generation g+1, and the item claim counters zeroed.
+__device__ void phase_gen_start(const GomParams &P, int improved, int argmax, uint32_t g, bool copy)
 {
     __shared__ uint32_t s_eq[32];
     const int aw = argmax >> 5, ab = argmax & 31;
@@ -276,11 +282,12 @@ __device__ void phase_gen_start(const GomParams &P, int improved, int argmax, ui
     const int w = (int)(tid & (W - 1));
     uint32_t *eqw = P.eqw + (g & 1) * W;
     if (tid < W) P.eqw[((g + 1) & 1) * W + tid] = kFull;
+    for (int64_t t = tid; t < P.k; t += nth) P.work[t] = 0;
     uint32_t eq = kFull;
     for (int64_t idx = tid; idx < total; idx += nth) {
         const int64_t v = idx >> lw;
         const uint32_t word = P.O[idx];
-        P.P[idx] = word;
+        if (copy) P.P[idx] = word;
         uint32_t xb;
         if (improved) {
             xb = (P.O[v * W + aw] >> ab) & 1u;
@@ -300,10 +307,11 @@ __device__ void phase_gen_start(const GomParams &P, int improved, int argmax, ui
         atomicAnd(&eqw[threadIdx.x], s_eq[threadIdx.x]);
 }
 
-// Group order of generation g (Alg. 3 visits the groups in random order): colours sorted by
-// their 64-bit Philox key, ties by colour index.  Every block draws all k keys
-// into shared memory s_key[k] and ranks a grid-strided share of the colours.
-__device__ void phase_order(const GomParams &P, unsigned long long *s_key, uint32_t g)
+// Group order of generation g (Alg. 3 visits the groups in random order):
+// colours sorted by their 64-bit Philox key, ties by colour index.  Every
+// block draws all k keys into shared memory s_key[k]; rank_of gives the
+// position of colour c.
+__device__ __forceinline__ void order_keys(const GomParams &P, unsigned long long *s_key, uint32_t g)
 {
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     for (int c = threadIdx.x; c < P.k; c += blockDim.x) {
@@ -311,15 +319,32 @@ __device__ void phase_order(const GomParams &P, unsigned long long *s_key, uint3
         s_key[c] = ((unsigned long long)r.x << 32) | r.y;
     }
     __syncthreads();
-    for (int c = (int)gthread(); c < P.k; c += (int)gthreads()) {
-        const unsigned long long kc = s_key[c];
-        int rank = 0;
-        for (int c2 = 0; c2 < P.k; ++c2) {
-            const unsigned long long k2 = s_key[c2];
-            rank += (k2 < kc) || (k2 == kc && c2 < c);
-        }
-        P.order[rank] = c;
+}
+
+__device__ __forceinline__ int rank_of(const unsigned long long *s_key, int k, int c)
+{
+    const unsigned long long kc = s_key[c];
+    int rank = 0;
+    for (int c2 = 0; c2 < k; ++c2) {
+        const unsigned long long k2 = s_key[c2];
+        rank += (k2 < kc) || (k2 == kc && c2 < c);
     }
+    return rank;
+}
+
+// The order into P.order, the colours ranked in a grid-strided share per block.
+__device__ void phase_order(const GomParams &P, unsigned long long *s_key, uint32_t g)
+{
+    order_keys(P, s_key, g);
+    for (int c = (int)gthread(); c < P.k; c += (int)gthreads()) P.order[rank_of(s_key, P.k, c)] = c;
+    __syncthreads();
+}
+
+// The whole order in every block, into shared memory (k <= kStageAllMaxK).
+__device__ void phase_order_block(const GomParams &P, unsigned long long *s_key, int *s_order, uint32_t g)
+{
+    order_keys(P, s_key, g);
+    for (int c = threadIdx.x; c < P.k; c += blockDim.x) s_order[rank_of(s_key, P.k, c)] = c;
     __syncthreads();
 }
 
@@ -506,18 +531,27 @@ __device__ __forceinline__ void cp_wait_warp()
 //  hdr[8] = {valid, q, j, d0, s | n_in << 8, n_out, f0, sub}
 //  fv[s] variables, seg[s+1] their outside-edge starts, wout[s] their outside
 //  weight sums (int64), rows of P on F_j [s][W], patP[32 W] every individual's
-//  bits on F_j, rs[W] run starts of patP, edge records [E][ES].
+//  bits on F_j, rs[W] run starts of patP, edge records [E][ES], and in
+//  stage-all mode the donor start positions of the item's individuals.
 // Offsets come from the host (the one definition of the layout).
-struct Slice {
-    uint32_t *base;
-    __device__ __forceinline__ int *hdr() const { return reinterpret_cast<int *>(base); }
-};
 
-// Decodes item `it` of the group at position t into the slice header (lane 0
-// writes).  Returns validity.  A warp-uniform result.
-__device__ __forceinline__ bool decode_item(const GomParams &P, int t, int it, int WPI_, uint32_t *sl)
+// Header of item (element at position q, word group sub), written by one lane.
+__device__ __forceinline__ void write_item_header(const GomParams &P, int q, int sub, int *h)
 {
-    const int c = P.order[t];
+    const int4 a = P.hdr[2 * q], b = P.hdr[2 * q + 1];
+    h[1] = q;
+    h[2] = a.x;
+    h[3] = a.z;
+    h[4] = a.w;
+    h[5] = b.x;
+    h[6] = a.y;
+    h[7] = sub;
+}
+
+// Decodes item `it` of colour c into the slice header (lane 0 writes).
+// Returns validity.  A warp-uniform result.
+__device__ __forceinline__ bool decode_item(const GomParams &P, int c, int it, int WPI_, uint32_t *sl)
+{
     const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
     const int nwg = (P.Wv + WPI_ - 1) / WPI_;
     const int per = P.split ? nwg : 1;
@@ -525,19 +559,7 @@ __device__ __forceinline__ bool decode_item(const GomParams &P, int t, int it, i
     if ((threadIdx.x & 31) == 0) {
         int *h = reinterpret_cast<int *>(sl);
         h[0] = valid;
-        if (valid) {
-            const int e = it / per, sub = it - e * per;
-            const int q = q0 + e;
-            const int4 r = P.hdr[q];
-            const int sv = r.w & 0xFF;
-            h[1] = q;
-            h[2] = r.x;
-            h[3] = r.z;
-            h[4] = r.w;
-            h[5] = (int)P.seg[r.y + q + sv];
-            h[6] = r.y;
-            h[7] = sub;
-        }
+        if (valid) write_item_header(P, q0 + it / per, it % per, h);
     }
     return valid;
 }
@@ -559,8 +581,10 @@ __device__ __forceinline__ void stage_lists(const GomParams &P, uint32_t *sl)
     for (int x = lane; x < n_out + n_in; x += 32) cp_async8(sl + P.off_edge + x * ES, P.dep + d0 + x);
 }
 
-// Level-2 copies: the rows of P on F_j (all W words), from the staged variables.
-__device__ __forceinline__ void stage_rows(const GomParams &P, uint32_t *sl)
+// Level-2 copies: the rows of the generation-start population on F_j (all W
+// words), from the staged variables; src is P, or O before anything of the
+// generation is written.
+__device__ __forceinline__ void stage_rows(const GomParams &P, uint32_t *sl, const uint32_t *src)
 {
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
@@ -571,11 +595,11 @@ __device__ __forceinline__ void stage_rows(const GomParams &P, uint32_t *sl)
         const int n4 = (s * W) >> 2, lw4 = __ffs(W >> 2) - 1;
         for (int x = lane; x < n4; x += 32) {
             const int a = x >> lw4, w4 = x & ((W >> 2) - 1);
-            cp_async16(sP + 4 * x, P.P + fv[a] * W + 4 * w4);
+            cp_async16(sP + 4 * x, src + fv[a] * W + 4 * w4);
         }
     } else {
         const int lw = __ffs(W) - 1;
-        for (int x = lane; x < (s << lw); x += 32) cp_async4(sP + x, P.P + fv[x >> lw] * W + (x & (W - 1)));
+        for (int x = lane; x < (s << lw); x += 32) cp_async4(sP + x, src + fv[x >> lw] * W + (x & (W - 1)));
     }
 }
 
@@ -605,81 +629,109 @@ __device__ __forceinline__ void stage_patterns(const GomParams &P, uint32_t *sl)
     __syncwarp();
 }
 
-// Stages one item of group t (item index `it`) into a slice: decode, then
+// Donor start positions of the item's individuals (Sec. 4.2, reading 6):
+// individual i of element j starts its cyclic scan at
+// i + 1 + mulhi(r, p - 1) mod p, r word i mod 4 of Philox(j, i / 4, g, DONR).
+// Lane c makes the call of individuals 4c .. 4c+3 of a word group and stores
+// their four starts together, so the start of individual 32 (w0 + r) + l sits
+// at int (wg - wg0) 32 WPI + 32 r + l of the region.
+template <int WPI>
+__device__ __forceinline__ void stage_draws(const GomParams &P, uint32_t *sl, uint32_t g)
+{
+    const int lane = threadIdx.x & 31;
+    const int *h = reinterpret_cast<const int *>(sl);
+    const int j = h[2], sub = h[7];
+    const int nwg = (P.Wv + WPI - 1) / WPI;
+    const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    const int p = P.p;
+    int4 *ds = reinterpret_cast<int4 *>(sl + P.off_ds);
+    for (int wg = wg0; wg < wg1; ++wg) {
+        const int w0 = wg * WPI;
+        if (lane < 8 * WPI) {
+            const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+            const int i0 = 32 * w0 + 4 * lane;
+            int st[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int d = i0 + c + 1 + (int)__umulhi(pick(r4, c), (uint32_t)(p - 1));
+                st[c] = d >= p ? d - p : d;
+            }
+            ds[(wg - wg0) * 8 * WPI + lane] = make_int4(st[0], st[1], st[2], st[3]);
+        }
+    }
+}
+
+// Stages one item of colour c (item index `it`) into a slice: decode, then
 // two levels of asynchronous copies, then the pattern table.  Only
-// generation-constant data: it may run before the barrier that opens group t.
+// generation-constant data: it may run before the barrier that opens the
+// group.
 template <int WPI, typename MaskT>
-__device__ __forceinline__ bool stage_item(const GomParams &P, int t, int it, uint32_t *sl)
+__device__ __forceinline__ bool stage_item(const GomParams &P, int c, int it, uint32_t *sl)
 {
     __syncwarp();
-    const bool valid = decode_item(P, t, it, WPI, sl);
+    const bool valid = decode_item(P, c, it, WPI, sl);
     if (!valid) return false;
     __syncwarp();
     stage_lists<WPI>(P, sl);
     cp_wait_warp();
-    stage_rows(P, sl);
+    stage_rows(P, sl, P.P);
     cp_wait_warp();
     stage_patterns<MaskT>(P, sl);
     return true;
 }
 
-// Stages this warp's item of every group (one item per group at most) into
-// consecutive slices, overlapping the copies of all of them: decode all
-// (lane t decodes group t), first-level copies of all, second-level copies
-// of all, then the pattern tables.
+// Stage-all mode: this warp's item of every colour (one item per colour at
+// most), slice c for colour c, staged at generation start from O (equal to
+// P then) and overlapping the copies of all of them.  The decoded headers and
+// the lists (first level) stay valid for the whole launch and are copied on
+// its first generation only (`lists`); the rows, pattern tables and donor
+// starts are made every generation.
 template <int WPI, typename MaskT>
-__device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices)
+__device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices, uint32_t g, bool lists)
 {
     const int lane = threadIdx.x & 31;
     const int k = P.k;
-    __syncwarp();
-    for (int t0 = 0; t0 < k; t0 += 32) {
-        const int t = t0 + lane;
-        if (t < k) {
-            uint32_t *sl = slices + t * P.warp_smem;
-            const int c = P.order[t];
+    if (lists) {
+        const int nwg = (P.Wv + WPI - 1) / WPI;
+        const int per = P.split ? nwg : 1;
+        __syncwarp();
+        for (int c = lane; c < k; c += 32) { // lane c decodes colour c
+            int *h = reinterpret_cast<int *>(slices + c * P.warp_smem);
             const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
-            const int nwg = (P.Wv + WPI - 1) / WPI;
-            const int per = P.split ? nwg : 1;
-            const int it = gwarp;
-            int *h = reinterpret_cast<int *>(sl);
-            const bool valid = it < ne * per;
+            const bool valid = gwarp < ne * per;
             h[0] = valid;
-            if (valid) {
-                const int e = it / per, sub = it - e * per;
-                const int q = q0 + e;
-                const int4 r = P.hdr[q];
-                const int sv = r.w & 0xFF;
-                h[1] = q;
-                h[2] = r.x;
-                h[3] = r.z;
-                h[4] = r.w;
-                h[5] = (int)P.seg[r.y + q + sv];
-                h[6] = r.y;
-                h[7] = sub;
-            }
+            if (valid) write_item_header(P, q0 + gwarp / per, gwarp % per, h);
         }
+        __syncwarp();
+        for (int c = 0; c < k; ++c) {
+            uint32_t *sl = slices + c * P.warp_smem;
+            if (sl[0]) stage_lists<WPI>(P, sl);
+        }
+        cp_wait_warp();
     }
-    __syncwarp();
-    for (int t = 0; t < k; ++t) {
-        uint32_t *sl = slices + t * P.warp_smem;
-        if (sl[0]) stage_lists<WPI>(P, sl);
+    for (int c = 0; c < k; ++c) {
+        uint32_t *sl = slices + c * P.warp_smem;
+        if (sl[0]) stage_rows(P, sl, P.O);
+    }
+    for (int c = 0; c < k; ++c) { // while the rows are in flight
+        uint32_t *sl = slices + c * P.warp_smem;
+        if (sl[0]) stage_draws<WPI>(P, sl, g);
     }
     cp_wait_warp();
-    for (int t = 0; t < k; ++t) {
-        uint32_t *sl = slices + t * P.warp_smem;
-        if (sl[0]) stage_rows(P, sl);
-    }
-    cp_wait_warp();
-    for (int t = 0; t < k; ++t) {
-        uint32_t *sl = slices + t * P.warp_smem;
+    for (int c = 0; c < k; ++c) {
+        uint32_t *sl = slices + c * P.warp_smem;
         if (sl[0]) stage_patterns<MaskT>(P, sl);
     }
 }
 
 // All trials of a staged item (Alg. 2 for each individual of its words):
-//  draws:   one Philox call per lane gives 4 words: lane c holds the call
-//           of individuals 4c..4c+3 of the word group, fetched by shuffles
+//  loads:   every global load of a word group is issued together: the
+//           parent's rows on F_j, its outside neighbours' words and the
+//           elitist flags
+//  draws:   the staged donor starts (pre), or one Philox call per lane: lane
+//           c holds the call of individuals 4c..4c+3 of the word group,
+//           fetched by shuffles
 //  donor:   find_donor over patP and its run starts; flips = patP[d] ^ parent
 //  delta:   per variable a of F_j, the weighted count S of its outside
 //           neighbours set in the parent gives the cut change of its outside
@@ -691,7 +743,7 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices)
 // Fitness deltas go to the block's shared accumulators s_f; counters to
 // per-lane counts.
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint32_t g, long long *s_f,
+__device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
                                          unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
@@ -708,6 +760,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
     const uint32_t *sP = sl + P.off_pr;
     const MaskT *patP = reinterpret_cast<const MaskT *>(sl + P.off_pat);
     const uint32_t *rs = sl + P.off_rs;
+    const int *sds = reinterpret_cast<const int *>(sl + P.off_ds);
     uint32_t *sE = sl + P.off_edge;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     const int ne_tot = n_out + n_in;
@@ -716,7 +769,14 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
 
     for (int wg = wg0; wg < wg1; ++wg) {
         const int w0 = wg * WPI;
-        // parent words of the outside neighbours for this word group
+        // global loads: the parent's rows on F_j (lane a loads row F_j[a]),
+        // the elitist flags, the outside neighbours' words (to shared memory)
+        uint32_t Xa[WPI], Xa2[WPI], eqv[WPI];
+#pragma unroll
+        for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
+        if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
+        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
+        load_words<WPI>(P.eqw + (g & 1) * W + w0, eqv);
         __syncwarp();
         for (int x = lane; x < n_out; x += 32) {
             uint32_t X[WPI];
@@ -724,12 +784,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
 #pragma unroll
             for (int r = 0; r < WPI; ++r) sE[x * ES + XO + r] = X[r];
         }
-        // parent bits on F_j: lane a loads row F_j[a], then a shuffle transpose
-        uint32_t Xa[WPI], Xa2[WPI];
-#pragma unroll
-        for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
-        if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
-        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
+        // parent bits on F_j: a shuffle transpose of the rows
         MaskT xf[WPI];
 #pragma unroll
         for (int r = 0; r < WPI; ++r) xf[r] = 0;
@@ -740,25 +795,35 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
         }
         __syncwarp();
 
-        // Philox draws: call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
-        const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+        // donor start positions, then the donors
+        int dstart[WPI];
+        if (pre) {
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) dstart[r] = sds[(wg - wg0) * 32 * WPI + 32 * r + lane];
+        } else {
+            // Philox call (j, 8 w0 + lane) covers individuals 32 w0 + 4 lane .. + 3
+            const uint4 r4 = philox10(make_uint4((uint32_t)j, (uint32_t)(8 * w0 + lane), g, kTagDonor), k0, k1);
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) {
+                const int src = 8 * r + (lane >> 2);
+                const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
+                const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
+                const int cc = lane & 3;
+                const uint32_t draw = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
+                const int i = 32 * (w0 + r) + lane;
+                int ds = i + 1 + (int)__umulhi(draw, (uint32_t)(p - 1));
+                dstart[r] = ds >= p ? ds - p : ds;
+            }
+        }
         int donor[WPI];
         MaskT fm[WPI];
 #pragma unroll
         for (int r = 0; r < WPI; ++r) {
-            const int src = 8 * r + (lane >> 2);
-            const uint32_t x = __shfl_sync(kFull, r4.x, src), y = __shfl_sync(kFull, r4.y, src);
-            const uint32_t z = __shfl_sync(kFull, r4.z, src), w = __shfl_sync(kFull, r4.w, src);
-            const int cc = lane & 3;
-            const uint32_t draw = cc == 0 ? x : cc == 1 ? y : cc == 2 ? z : w;
             const int i = 32 * (w0 + r) + lane;
             donor[r] = -1;
             fm[r] = 0;
             if (i < p) {
-                const uint32_t u = __umulhi(draw, (uint32_t)(p - 1));
-                int ds = i + 1 + (int)u;
-                if (ds >= p) ds -= p;
-                const int d = find_donor<MaskT>(patP, rs, sP, W, Wv, p, s, xf[r], ds, i);
+                const int d = find_donor<MaskT>(patP, rs, sP, W, Wv, p, s, xf[r], dstart[r], i);
                 if (d >= 0) {
                     donor[r] = d;
                     fm[r] = patP[d] ^ xf[r];
@@ -809,7 +874,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
 #pragma unroll
         for (int r = 0; r < WPI; ++r) {
             const int i = 32 * (w0 + r) + lane;
-            const bool eq = (P.eqw[(g & 1) * W + w0 + r] >> lane) & 1u;
+            const bool eq = (eqv[r] >> lane) & 1u;
             const bool acc = donor[r] >= 0 && (dl[r] > 0 || (dl[r] == 0 && !eq));
             afm[r] = acc ? fm[r] : (MaskT)0;
             anyacc |= acc;
@@ -874,31 +939,57 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 }
 
 // One colour group: all (individual, element) GOM trials (Alg. 2) of the
-// group at position t.  Items (an element, or an element's word group when
-// P.split is set) go to warps in a static stride: warp w takes items w,
-// w + nwarps, ...; its first item may already be staged in its slice
-// (`first_staged`).  Elements of one group share no variable and no edge
-// (LMIG colouring), so a warp owns its element's rows for its words and
-// nothing else in the group touches the closure it reads.
-// MaskT holds one bit per variable of F_j (uint32_t: s <= 32, uint64_t:
-// s <= 64); AccT is the delta type (int32_t when every element's sum of |w|
-// is < 2^30).
+// group at position t, colour c.  Items (an element, or an element's word
+// group when P.split is set) go to warps: warp w takes item w first (it may
+// already be staged in its slice: `first_staged`), then items w + nwarps,
+// w + 2 nwarps, ... (static stride), or, with P.dyn, items nwarps + x for
+// the claims x it draws from the counter work[t] -- each claim issued one
+// item ahead, so its latency hides behind the item being run.  In stage-all
+// mode (`single`) the staged item, with its precomputed donor starts, is the
+// warp's only item of the group.  Elements of
+// one group share no variable and no edge (LMIG colouring), so a warp owns
+// its element's rows for its words and nothing else in the group touches the
+// closure it reads.  MaskT holds one bit per variable of F_j (uint32_t:
+// s <= 32, uint64_t: s <= 64); AccT is the delta type (int32_t when every
+// element's sum of |w| is < 2^30).  Counters accumulate per lane.
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g, uint32_t *sl, long long *s_f,
-                                          unsigned long long *s_cnt, bool first_staged)
+__device__ __forceinline__ void phase_mix(const GomParams &P, int t, int c, uint32_t g, uint32_t *sl, bool first_staged,
+                                          bool single, long long *s_f, unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
-    unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-    for (int it = gwarp, n = 0;; it += nwarps, ++n) {
-        const bool staged = (n == 0 && first_staged) ? sl[0] != 0 : stage_item<WPI, MaskT>(P, t, it, sl);
-        if (!staged) break;
-        run_item<WPI, MaskT, AccT>(P, sl, g, s_f, n_dl, n_acc, n_imp);
+    bool staged = first_staged ? sl[0] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl);
+    if (single) { // stage-all mode: the staged item is the warp's only one, its slice stays as it is
+        if (staged) run_item<WPI, MaskT, AccT>(P, sl, g, true, s_f, n_dl, n_acc, n_imp);
+        return;
     }
+    const bool pre = false;
+    if (!P.dyn) {
+        for (int it = gwarp + nwarps; staged; it += nwarps) {
+            run_item<WPI, MaskT, AccT>(P, sl, g, pre, s_f, n_dl, n_acc, n_imp);
+            staged = stage_item<WPI, MaskT>(P, c, it, sl);
+        }
+        return;
+    }
+    if (!staged) return;
+    unsigned claim = 0;
+    if (lane == 0) claim = atomicAdd(&P.work[t], 1u);
+    for (;;) {
+        run_item<WPI, MaskT, AccT>(P, sl, g, pre, s_f, n_dl, n_acc, n_imp);
+        const int it = nwarps + (int)__shfl_sync(kFull, claim, 0);
+        // stop on the first claim past the group (items are numbered densely)
+        if (!stage_item<WPI, MaskT>(P, c, it, sl)) break;
+        if (lane == 0) claim = atomicAdd(&P.work[t], 1u);
+    }
+}
+
+// Adds a warp's per-lane counters into the block's counters.
+__device__ __forceinline__ void count_flush(unsigned long long *s_cnt, unsigned n_dl, unsigned n_acc, unsigned n_imp)
+{
     n_dl = __reduce_add_sync(kFull, n_dl);
     n_acc = __reduce_add_sync(kFull, n_acc);
     n_imp = __reduce_add_sync(kFull, n_imp);
-    if (lane == 0 && (n_dl | n_acc | n_imp)) {
+    if ((threadIdx.x & 31) == 0 && (n_dl | n_acc | n_imp)) {
         atomicAdd(&s_cnt[0], (unsigned long long)n_dl);
         atomicAdd(&s_cnt[1], (unsigned long long)n_acc);
         atomicAdd(&s_cnt[2], (unsigned long long)n_imp);
@@ -911,7 +1002,7 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, int t, uint32_t g,
 __global__ void k_gen_start(GomParams P)
 {
     if (P.st->done) return;
-    phase_gen_start(P, P.st->improved, P.st->argmax, P.st->g);
+    phase_gen_start(P, P.st->improved, P.st->argmax, P.st->g, true);
 }
 
 __global__ void k_order(GomParams P)
@@ -929,7 +1020,10 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     __shared__ unsigned long long s_cnt[4];
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
-    phase_mix<WPI, MaskT, AccT>(P, t, P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem, s_f, s_cnt, false);
+    unsigned n_dl = 0, n_acc = 0, n_imp = 0;
+    phase_mix<WPI, MaskT, AccT>(P, t, P.order[t], P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem, false, false,
+                                s_f, n_dl, n_acc, n_imp);
+    count_flush(s_cnt, n_dl, n_acc, n_imp);
     acc_flush(P, s_f, s_cnt);
 }
 
@@ -945,23 +1039,31 @@ __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 // ... | group k-1 | and again.  A generation's end is computed by every block
 // from the fitness array right after the barrier that closes its last group
 // (the same values everywhere; block 0 records them), so it needs no phase
-// of its own, and every block takes the same stop decision.  Before each
-// barrier that opens a colour group, every warp stages the generation-constant
-// half of its first item of that group (its P rows, pattern table and edge
-// list).  The block's fitness accumulators span all groups of a generation
-// and are flushed once, before the closing barrier.
+// of its own, and every block takes the same stop decision.
+// Staging: in stage-all mode every block computes the whole group order and
+// every warp stages its item of every colour from O before the barrier that
+// opens the generation (P itself is then never read, so it is not copied);
+// otherwise every warp stages its first item of group t before the barrier
+// that opens the group.  The block's fitness accumulators and the warps'
+// counters span all groups of a generation and are flushed once, before the
+// closing barrier.
 template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
+    __shared__ unsigned long long s_okey[kStageAllMaxK];
+    __shared__ int s_order[kStageAllMaxK];
     const unsigned nblk = gridDim.x;
     const int gwarp = (int)(gthread() >> 5);
-    // this warp's staging: one slice, or one per colour group with stage_all
-    uint32_t *slices = s_dyn + (threadIdx.x >> 5) * P.warp_smem * (P.stage_all ? P.k : 1);
+    const bool all = P.stage_all != 0;
+    // this warp's staging: one slice, or one per colour with stage_all
+    uint32_t *slices = s_dyn + (threadIdx.x >> 5) * P.warp_smem * (all ? P.k : 1);
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
+    unsigned long long bnext = 0; // next barrier epoch end (thread 0)
+    if (threadIdx.x == 0) bnext = barrier_first(&P.bar->count, nblk);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.st->call_g0 = g; // read by the host after the kernel only
         P.st->target = target;
@@ -972,25 +1074,31 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     for (int q = 0; q < G; ++q) {
         if (q > 0 && phase_gen_end(P, target, g - 1, e, blockIdx.x == 0)) return;
         if (tr) P.trace[0] = global_ns();
-        phase_gen_start(P, e.improved, e.argmax, g);
-        phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
+        phase_gen_start(P, e.improved, e.argmax, g, !all);
+        if (all)
+            phase_order_block(P, s_okey, s_order, g);
+        else
+            phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
         acc_zero(P, s_f, s_cnt);
         if (tr) P.trace[1] = global_ns();
-        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        if (all) stage_all_items<WPI, MaskT>(P, gwarp, slices, g, q == 0);
         if (tr) P.trace[2] = global_ns();
-        if (P.stage_all) stage_all_items<WPI, MaskT>(P, gwarp, slices);
+        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
         if (tr) P.trace[3] = global_ns();
+        unsigned n_dl = 0, n_acc = 0, n_imp = 0;
         for (int t = 0; t < P.k; ++t) {
-            uint32_t *sl = P.stage_all ? slices + t * P.warp_smem : slices;
+            const int c = all ? s_order[t] : P.order[t];
+            uint32_t *sl = all ? slices + c * P.warp_smem : slices;
             // without stage_all: stage the first item of group t before its barrier
-            if (!P.stage_all) stage_item<WPI, MaskT>(P, t, gwarp, sl);
-            if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl);
+            if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
             if (tr) P.trace[4 + 2 * t] = global_ns();
-            phase_mix<WPI, MaskT, AccT>(P, t, g, sl, s_f, s_cnt, true);
+            phase_mix<WPI, MaskT, AccT>(P, t, c, g, sl, true, all, s_f, n_dl, n_acc, n_imp);
             if (tr) P.trace[5 + 2 * t] = global_ns();
         }
+        count_flush(s_cnt, n_dl, n_acc, n_imp);
         acc_flush(P, s_f, s_cnt);
-        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, kBarrierNs)) return;
+        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
         if (tr) P.trace[4 + 2 * P.k] = global_ns();
         ++g;
     }
@@ -1002,7 +1110,10 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
 // block is ever released and every block must give up after limit_ns.
 __global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigned long long limit_ns)
 {
-    grid_barrier(&bar->count, err, gridDim.x + (unsigned)extra, limit_ns);
+    const unsigned expected = gridDim.x + (unsigned)extra;
+    unsigned long long next = 0;
+    if (threadIdx.x == 0) next = barrier_first(&bar->count, expected);
+    grid_barrier(&bar->count, err, expected, next, limit_ns);
 }
 
 const void *gom_mix_kernel(int wpi, bool narrow)

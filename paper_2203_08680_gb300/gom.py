@@ -22,6 +22,7 @@ GOM_MAX_POPULATION = 1024
 GOM_MAX_ELEMENT = 64
 GOM_OPT_PERSISTENT = 1
 GOM_OPT_PHASE_TRACE = 2
+GOM_OPT_DYNAMIC = 3
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
@@ -358,7 +359,7 @@ class Population:
     workspace with torch and drives the C ABI above."""
 
     def __init__(self, graph, pop: int, seed: int, kind: int = GOM_FOS_NEIGHBOURHOOD, fos: Fos = None,
-                 stream=None, device=None, persistent: bool = None):
+                 stream=None, device=None, persistent: bool = None, dynamic: bool = None):
         import torch
         self.torch = torch
         self.graph = _graph(graph)
@@ -384,6 +385,8 @@ class Population:
         self.ctx.workspace = self.workspace
         if persistent is not None:
             gom_set_option(self.ctx, GOM_OPT_PERSISTENT, 1 if persistent else 0)
+        if dynamic is not None:
+            gom_set_option(self.ctx, GOM_OPT_DYNAMIC, 1 if dynamic else 0)
 
     def generation(self, num: int = 1, target: int = INT64_MAX, want_stats: bool = True):
         return gom_generation(self.ctx, num, target, want_stats)

@@ -46,8 +46,11 @@ def _assert_same_stats(gst, ost):
 
 def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MAX):
     """Both execution paths (persistent kernel, per-generation graph) against
-    the oracle after every generation."""
-    Ps = [gom.Population(g, p, seed, kind, persistent=True), gom.Population(g, p, seed, kind, persistent=False)]
+    the oracle after every generation; the graph path with the other item
+    schedule (static stride / dynamic claims) than the persistent default."""
+    A = gom.Population(g, p, seed, kind, persistent=True)
+    dyn = gom.gom_get_option(A.ctx, gom.GOM_OPT_DYNAMIC)
+    Ps = [A, gom.Population(g, p, seed, kind, persistent=False, dynamic=not dyn)]
     run, k = _oracle_run(oracle, g, p, seed, kind)
     for P in Ps:
         assert P.k == k
@@ -298,10 +301,19 @@ def test_grid_barrier_bounded_wait():
     P.generation(2)
 
 
-def test_large_groups_one_warp_per_element(oracle):
+@pytest.mark.parametrize("dynamic", [False, True])
+def test_large_groups_one_warp_per_element(oracle, dynamic):
     """Colour groups of ~20,000 elements: one warp per element walking all its
-    word groups (smaller groups give each word group its own warp)."""
-    _parity(oracle, I.torus2d(400, seed=12), 96, 6, 3)
+    word groups (smaller groups give each word group its own warp), several
+    items per warp, with either item schedule on the persistent path."""
+    g = I.torus2d(400, seed=12)
+    P = gom.Population(g, 96, 6, persistent=True, dynamic=dynamic)
+    run, _ = _oracle_run(oracle, g, 96, 6)
+    for gen in range(3):
+        ost = run.generation()
+        gst, _ = P.generation(1)
+        _assert_same_stats(gst[0], ost)
+    _assert_same_state(_gpu_state(P), run.get(), "gen 3")
 
 
 @pytest.mark.parametrize("p", [64, 200])
