@@ -200,19 +200,26 @@ def dist_barrier(world: int):
         dist.barrier()
 
 
-def oracle_trials_per_sec(g, p: int, seed: int, budget_s: float, warmup: int = 0, steps: int = None):
-    """The CPU oracle as it stands, single-threaded, timed on a bounded sample
-    (generations until budget_s, or `steps` generations after `warmup`)."""
+def oracle_threads() -> int:
+    from oracle import oracle as O
+    return max(1, O.max_threads())
+
+
+def oracle_trials_per_sec(g, p: int, seed: int, budget_s: float, warmup: int = 0, steps: int = None,
+                          threads: int = 1):
+    """The CPU oracle as it stands, timed on a bounded sample (generations
+    until budget_s, or `steps` generations after `warmup`), on `threads`
+    threads (its multi-threaded generation for threads > 1)."""
     from oracle import oracle as O
     ep, ev = O.build_fos(g)
     k, co = O.color(g, ep, ev)
     run = O.Run(g, ep, ev, co, k, p, seed)
     m = len(ep) - 1
     for _ in range(warmup):
-        run.generation()
+        run.generation(threads=threads)
     gens, t0 = 0, time.perf_counter()
     while True:
-        run.generation()
+        run.generation(threads=threads)
         gens += 1
         el = time.perf_counter() - t0
         if (steps is not None and gens >= steps) or (steps is None and el >= budget_s):
@@ -226,13 +233,15 @@ def run_reference(args, wl, rank, world):
         return
     build, p, desc = WORKLOADS[wl]
     g = build()
-    val, gens, el = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps)
+    nth = oracle_threads()
+    val, gens, el = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps, threads=nth)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "trials/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / gens,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": wl, "description": desc},
-            "cpu_baseline": {"value": val, "unit": "trials/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{gens} generations of the workload after {args.warmup} warm-up"},
+            "cpu_baseline": {"value": val, "unit": "trials/s", "cores": nth, "kind": "oracle",
+                             "sample": f"{gens} generations of the workload after {args.warmup} warm-up, "
+                                       f"{nth} threads"},
             "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -321,9 +330,13 @@ def run_gpu(args, wl, rank, world, local):
     # CPU baseline: the oracle, bounded sample, rank 0
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds)
-        cpu = {"value": cval, "unit": "trials/s", "cores": 1, "kind": "oracle",
-               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, single thread)"}
+        nth = oracle_threads()
+        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2, threads=nth)
+        sval, sgens, sel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2)
+        cpu = {"value": cval, "unit": "trials/s", "cores": nth, "kind": "oracle",
+               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, {nth} threads)",
+               "single_thread": {"value": sval, "cores": 1,
+                                 "sample": f"{sgens} generations from initialisation ({sel:.1f} s)"}}
     return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e,
                   launches_per_step, clk, cpu, persistent)
 

@@ -1,7 +1,7 @@
 /*
  * gom_oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded CPU statement of parallel Gene-pool Optimal
+ * A plain, slow CPU statement of parallel Gene-pool Optimal
  * Mixing (GOM) for weighted Max-Cut, written from Bouter & Bosman, "GPU-Accelerated
  * Parallel Gene-pool Optimal Mixing in a Gray-Box Optimization Setting"
  * (arXiv 2203.08680).  It is the checker of the CUDA library, not part of it:
@@ -12,6 +12,11 @@
  * exact and must be matched bit for bit.
  *
  * Population storage is the plainest possible: uint8 x[i*n + v] in {0,1}.
+ *
+ * Single-threaded, except orc_generation_par: the same generation with the
+ * individuals of each colour group split over threads (OpenMP, when built
+ * with it), which must give the identical state; it times the CPU baseline
+ * on all host cores.
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *  R1 objective: f(x) = sum over undirected edges {u,v} of w_uv [x_u != x_v];
@@ -39,6 +44,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TAG_INIT 0x494E4954u  /* 'INIT' */
 #define ORC_TAG_DONOR 0x444F4E52u /* 'DONR' */
@@ -419,6 +427,14 @@ typedef struct {
     int64_t reached;      /* 1 if best >= target */
 } orc_stats;
 
+/* Scratch of one trial: the element's membership stamps and donor bits. */
+typedef struct {
+    int64_t *in_f;    /* [n] stamp of the trial whose element holds v */
+    int32_t *pos_in_f;/* [n] position of v in that element */
+    int64_t stamp;
+    uint8_t *ybuf;    /* [max element size] */
+} orc_scratch;
+
 typedef struct {
     int32_t n;
     int64_t *rp;
@@ -436,12 +452,9 @@ typedef struct {
     uint8_t *xe;
     int64_t fe;
     uint32_t g;
-    /* scratch */
-    int64_t *in_f;
-    int32_t *pos_in_f;
-    int64_t stamp;
-    uint8_t *eq;
-    uint8_t *ybuf; /* [max element size] */
+    uint8_t *eq;     /* [p] P[i] == x_e at generation start */
+    int64_t max_s;   /* largest element */
+    orc_scratch sc;  /* scratch of the single-threaded path */
 } orc_state;
 
 static void *dup_mem(const void *src, size_t bytes)
@@ -469,6 +482,22 @@ void orc_init_individual(uint64_t seed, int32_t i, int32_t n, uint8_t *x)
         uint32_t r = draw(seed, (uint32_t)v >> 7, (uint32_t)i, 0u, ORC_TAG_INIT, (v >> 5) & 3);
         x[v] = (uint8_t)((r >> (v & 31)) & 1u);
     }
+}
+
+static void scratch_init(orc_scratch *sc, int32_t n, int64_t max_s)
+{
+    sc->in_f = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    sc->pos_in_f = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t v = 0; v < n; ++v) sc->in_f[v] = -1;
+    sc->stamp = 0;
+    sc->ybuf = (uint8_t *)malloc((size_t)max_s);
+}
+
+static void scratch_free(orc_scratch *sc)
+{
+    free(sc->in_f);
+    free(sc->pos_in_f);
+    free(sc->ybuf);
 }
 
 /* With init = 0 the population is left zero (for orc_load). */
@@ -500,10 +529,6 @@ orc_state *orc_new_ex(int32_t n, const int64_t *rp, const int32_t *col, const in
     s->P = (uint8_t *)malloc((size_t)p * (size_t)n + 1);
     s->f = (int64_t *)malloc(sizeof(int64_t) * (size_t)p);
     s->xe = (uint8_t *)malloc((size_t)n + 1);
-    s->in_f = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
-    s->pos_in_f = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
-    for (int32_t v = 0; v < n; ++v) s->in_f[v] = -1;
-    s->stamp = 0;
     s->eq = (uint8_t *)malloc((size_t)p);
     s->g = 0;
     if (!init) {
@@ -512,12 +537,10 @@ orc_state *orc_new_ex(int32_t n, const int64_t *rp, const int32_t *col, const in
         memset(s->xe, 0, (size_t)n);
         s->fe = 0;
     }
-    {
-        int64_t mx = 1;
-        for (int64_t j = 0; j < m; ++j)
-            if (eptr[j + 1] - eptr[j] > mx) mx = eptr[j + 1] - eptr[j];
-        s->ybuf = (uint8_t *)malloc((size_t)mx);
-    }
+    s->max_s = 1;
+    for (int64_t j = 0; j < m; ++j)
+        if (eptr[j + 1] - eptr[j] > s->max_s) s->max_s = eptr[j + 1] - eptr[j];
+    scratch_init(&s->sc, n, s->max_s);
     if (!init) return s;
     for (int32_t i = 0; i < p; ++i) orc_init_individual(seed, i, n, s->O + (size_t)i * n);
     for (int32_t i = 0; i < p; ++i) s->f[i] = orc_cut_value(n, rp, col, w, s->O + (size_t)i * n);
@@ -537,7 +560,8 @@ void orc_free(orc_state *s)
     if (!s) return;
     free(s->rp); free(s->col); free(s->w); free(s->eptr); free(s->evars);
     free(s->cptr); free(s->celems); free(s->O); free(s->P); free(s->f); free(s->xe);
-    free(s->in_f); free(s->pos_in_f); free(s->eq); free(s->ybuf);
+    free(s->eq);
+    scratch_free(&s->sc);
     free(s);
 }
 
@@ -590,7 +614,7 @@ void orc_group_order(uint64_t seed, int32_t k, uint32_t g, int32_t *order)
 }
 
 /* One GOM trial (Alg. 2) of individual i with element j. */
-static void gom_trial(orc_state *s, int32_t i, int32_t j, orc_stats *st)
+static void gom_trial(orc_state *s, orc_scratch *sc, int32_t i, int32_t j, orc_stats *st)
 {
     const int32_t n = s->n, p = s->p;
     const int32_t *F = s->evars + s->eptr[j];
@@ -612,14 +636,14 @@ static void gom_trial(orc_state *s, int32_t i, int32_t j, orc_stats *st)
 
     /* PartialEvaluation, R7 */
     const uint8_t *pd = s->P + (size_t)donor * n;
-    uint8_t *y = s->ybuf;
-    s->stamp++;
+    uint8_t *y = sc->ybuf;
+    sc->stamp++;
     for (int32_t q = 0; q < sz; ++q) {
         y[q] = pd[F[q]];
-        s->in_f[F[q]] = s->stamp;
-        s->pos_in_f[F[q]] = q;
+        sc->in_f[F[q]] = sc->stamp;
+        sc->pos_in_f[F[q]] = q;
     }
-    int64_t d = partial_delta(s->rp, s->col, s->w, o, F, sz, y, s->pos_in_f, s->in_f, s->stamp);
+    int64_t d = partial_delta(s->rp, s->col, s->w, o, F, sz, y, sc->pos_in_f, sc->in_f, sc->stamp);
 
     /* acceptance, R8 */
     if (d > 0 || (d == 0 && !s->eq[i])) {
@@ -640,6 +664,31 @@ static uint64_t splitmix_next(uint64_t *x)
     return z ^ (z >> 31);
 }
 
+/* Generation start (Alg. 3): Clone P <- O; R8 flags. */
+static void generation_start(orc_state *s)
+{
+    const int32_t n = s->n, p = s->p;
+    memcpy(s->P, s->O, (size_t)p * n);
+    /* R8: the elitist flag of each individual is fixed at generation start */
+    for (int32_t i = 0; i < p; ++i) s->eq[i] = memcmp(s->P + (size_t)i * n, s->xe, (size_t)n) == 0;
+}
+
+/* Generation end: R9 elitist update, the target check, g += 1. */
+static void generation_end(orc_state *s, int64_t target, orc_stats *st)
+{
+    int64_t best = INT64_MIN;
+    int32_t arg = 0;
+    for (int32_t i = 0; i < s->p; ++i)
+        if (s->f[i] > best) { best = s->f[i]; arg = i; }
+    if (best > s->fe) {
+        s->fe = best;
+        memcpy(s->xe, s->O + (size_t)arg * s->n, (size_t)s->n);
+    }
+    st->best = best;
+    st->elite = s->fe;
+    st->reached = best >= target;
+}
+
 /* One generation of Par-GOMEA (Alg. 3).  `shuffle` != 0 visits the trials of
  * each group in a permuted order; `only`/`n_only` restricts the trials to a
  * subset of individuals (the elitist update is then skipped, since it needs the
@@ -649,11 +698,8 @@ int32_t orc_generation_ex(orc_state *s, int64_t target, uint64_t shuffle, const 
                           int32_t n_only, orc_stats *st)
 {
     memset(st, 0, sizeof(*st));
-    const int32_t n = s->n, p = s->p;
-    /* Clone: P <- O */
-    memcpy(s->P, s->O, (size_t)p * n);
-    /* R8: the elitist flag of each individual is fixed at generation start */
-    for (int32_t i = 0; i < p; ++i) s->eq[i] = memcmp(s->P + (size_t)i * n, s->xe, (size_t)n) == 0;
+    const int32_t p = s->p;
+    generation_start(s);
 
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->k > 0 ? s->k : 1));
     orc_group_order(s->seed, s->k, s->g, order);
@@ -678,27 +724,70 @@ int32_t orc_generation_ex(orc_state *s, int64_t target, uint64_t shuffle, const 
             int32_t j = s->celems[s->cptr[c] + id / n_ind];
             int32_t ii = (int32_t)(id % n_ind);
             int32_t i = only ? only[ii] : ii;
-            gom_trial(s, i, j, st);
+            gom_trial(s, &s->sc, i, j, st);
         }
         free(perm);
     }
     free(order);
 
     st->generation = s->g;
-    if (!only) {
-        /* R9: elitist update at the end of the generation */
-        int64_t best = INT64_MIN;
-        int32_t arg = 0;
-        for (int32_t i = 0; i < p; ++i)
-            if (s->f[i] > best) { best = s->f[i]; arg = i; }
-        if (best > s->fe) {
-            s->fe = best;
-            memcpy(s->xe, s->O + (size_t)arg * n, (size_t)n);
+    if (!only) generation_end(s, target, st);
+    s->g++;
+    return 0;
+}
+
+/* Threads the multi-threaded generation can use (1 without OpenMP). */
+int32_t orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* The same generation with the individuals of each colour group split over
+ * `threads` threads (OpenMP).  The trials of one group are independent of
+ * one another -- its elements share no variable and no edge (LMIG colouring),
+ * donors come from the frozen P, the elitist flags are fixed -- so any order,
+ * and this parallel one, gives the single-threaded result (checked by the
+ * test suite).  Each thread has its own scratch and counters. */
+int32_t orc_generation_par(orc_state *s, int64_t target, int32_t threads, orc_stats *st)
+{
+    memset(st, 0, sizeof(*st));
+    const int32_t p = s->p;
+    if (threads < 1) threads = 1;
+    generation_start(s);
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->k > 0 ? s->k : 1));
+    orc_group_order(s->seed, s->k, s->g, order);
+    orc_scratch *sc = (orc_scratch *)malloc(sizeof(orc_scratch) * (size_t)threads);
+    orc_stats *ts = (orc_stats *)calloc((size_t)threads, sizeof(orc_stats));
+    for (int32_t th = 0; th < threads; ++th) scratch_init(&sc[th], s->n, s->max_s);
+    for (int32_t t = 0; t < s->k; ++t) {
+        const int32_t c = order[t];
+        const int64_t e0 = s->cptr[c], e1 = s->cptr[c + 1];
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int32_t i = 0; i < p; ++i) {
+#ifdef _OPENMP
+            const int th = omp_get_thread_num();
+#else
+            const int th = 0;
+#endif
+            for (int64_t q = e0; q < e1; ++q) gom_trial(s, &sc[th], i, s->celems[q], &ts[th]);
         }
-        st->best = best;
-        st->elite = s->fe;
-        st->reached = best >= target;
     }
+    for (int32_t th = 0; th < threads; ++th) {
+        st->trials += ts[th].trials;
+        st->donorless += ts[th].donorless;
+        st->accepted += ts[th].accepted;
+        st->improving += ts[th].improving;
+        scratch_free(&sc[th]);
+    }
+    free(sc);
+    free(ts);
+    free(order);
+    st->generation = s->g;
+    generation_end(s, target, st);
     s->g++;
     return 0;
 }

@@ -26,8 +26,11 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                               "-o", tmp, _SRC])
+        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC]
+        try:  # with OpenMP where the compiler has it (orc_generation_par), else serial
+            subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +71,10 @@ def lib():
         L.orc_get.argtypes = [P, P, P, P, P, P]
         L.orc_generation_ex.argtypes = [P, i64, u64, P, i32, P]
         L.orc_generation_ex.restype = i32
+        L.orc_generation_par.argtypes = [P, i64, i32, P]
+        L.orc_generation_par.restype = i32
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = i32
         _lib = L
     return _lib
 
@@ -171,6 +178,11 @@ def group_order(seed: int, k: int, g: int):
     return out[:k]
 
 
+def max_threads() -> int:
+    """Threads available to Run.generation(threads=...): 1 without OpenMP."""
+    return int(lib().orc_max_threads())
+
+
 def init_individual(seed: int, i: int, n: int):
     """Initial bits of individual i (InitializePopulation, Alg. 3)."""
     x = np.zeros(max(n, 1), dtype=np.uint8)
@@ -196,9 +208,14 @@ class Run:
             lib().orc_free(h)
             self._h = None
 
-    def generation(self, target: int = 2 ** 63 - 1, shuffle: int = 0, only=None) -> dict:
+    def generation(self, target: int = 2 ** 63 - 1, shuffle: int = 0, only=None, threads: int = 1) -> dict:
+        """One generation; threads > 1 splits each group's individuals over
+        that many threads (same result)."""
         st = Stats()
-        if only is None:
+        if threads > 1:
+            assert not shuffle and only is None
+            lib().orc_generation_par(self._h, target, threads, C.byref(st))
+        elif only is None:
             lib().orc_generation_ex(self._h, target, shuffle, None, 0, C.byref(st))
         else:
             o = np.ascontiguousarray(only, dtype=np.int32)

@@ -436,3 +436,23 @@ def test_gom_subset_replay_matches_full_generation(oracle):
     for i in only:
         assert np.array_equal(part["pop"][i], full["pop"][i])
         assert part["f"][i] == full["f"][i]
+
+
+def test_multithreaded_generation_equals_single_threaded(oracle):
+    """The oracle's multi-threaded generation (individuals of a group split
+    over threads) gives the single-threaded state: trials of one colour group
+    are independent of each other (LMIG colouring, donors from P, fixed
+    elitist flags)."""
+    g = I.torus2d(12, seed=4)
+    ep, ev = oracle.build_fos(g)
+    k, co = oracle.color(g, ep, ev)
+    a = oracle.Run(g, ep, ev, co, k, 37, 9)
+    b = oracle.Run(g, ep, ev, co, k, 37, 9)
+    for _ in range(6):
+        sa = a.generation()
+        sb = b.generation(threads=4)
+        assert sa == sb
+    ra, rb = a.get(), b.get()
+    for key in ("pop", "f", "xe"):
+        assert np.array_equal(ra[key], rb[key])
+    assert ra["fe"] == rb["fe"] and ra["g"] == rb["g"]
