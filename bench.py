@@ -51,6 +51,12 @@ WORKLOADS = {
     "torus1000": (lambda: I.torus2d(1000), 256,
                   "2D torus 1000x1000 (n=1,000,000), int32 weights U[1,100], pop 256"),
 }
+BATCH_WORKLOADS = {
+    "batch256": "256 independent Max-Cut instances in one persistent launch: random d-regular graphs, n "
+                "log-uniform in [1000, 65536] (even), d uniform in 3..8, int32 weights U[1,100], pop uniform "
+                "over {32, 64, 128, 256}, graph and Philox seeds 1..256",
+}
+BATCH_CONFIGS = [(1, 2), (2, 2), (2, 3), (4, 2), (4, 3), (8, 3)]
 SEED = 1
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "GOM trials/sec (plain parallel GOM, weighted Max-Cut)"
@@ -231,6 +237,24 @@ def run_reference(args, wl, rank, world):
     """Reference arm: the CPU oracle on this workload, rank 0 only."""
     if rank != 0:
         return
+    if wl in BATCH_WORKLOADS:
+        # steps: one oracle generation each of the first warmup + steps instances of the mix
+        mix = I.batch_mix(seed=SEED)[: args.warmup + args.steps]
+        graphs = [I.random_regular(n, d, s) for n, d, p, s in mix]
+        nth = oracle_threads()
+        oracle_batch_sample(graphs[: args.warmup], mix[: args.warmup], float("inf"), nth)
+        val, ninst, done, el = oracle_batch_sample(graphs[args.warmup:], mix[args.warmup:], float("inf"), nth)
+        line = {"impl": "reference", "metric": "GOM trials/sec (batched parallel GOM, weighted Max-Cut)",
+                "value": val, "unit": "trials/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * el / max(ninst, 1), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": wl, "description": BATCH_WORKLOADS[wl]},
+                "cpu_baseline": {"value": val, "unit": "trials/s", "cores": nth, "kind": "oracle",
+                                 "sample": f"one generation of each of instances {args.warmup}.."
+                                           f"{args.warmup + ninst - 1} of the mix, {nth} threads"},
+                "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     build, p, desc = WORKLOADS[wl]
     g = build()
     nth = oracle_threads()
@@ -341,6 +365,157 @@ def run_gpu(args, wl, rank, world, local):
                   launches_per_step, clk, cpu, persistent)
 
 
+def oracle_batch_sample(graphs, mix, budget_s: float, threads: int, max_instances: int = None):
+    """The oracle on the instances of a batch taken in order, one generation
+    each, until budget_s seconds of generations (set-up not timed) or
+    max_instances; returns (trials/s, instances, trials, seconds)."""
+    from oracle import oracle as O
+    done, el, ninst = 0, 0.0, 0
+    for g, (n, d, p, sd) in zip(graphs, mix):
+        ep, ev = O.build_fos(g)
+        kk, co = O.color(g, ep, ev)
+        run = O.Run(g, ep, ev, co, kk, p, sd)
+        t0 = time.perf_counter()
+        run.generation(threads=threads)
+        el += time.perf_counter() - t0
+        done += p * (len(ep) - 1)
+        ninst += 1
+        if el > budget_s or (max_instances is not None and ninst >= max_instances):
+            break
+    return done / el, ninst, done, el
+
+
+def run_batch(args, wl, rank, world, local):
+    """Batched GOM: every instance of the mix, one persistent launch per
+    generation (gom_batch_generation); beside it the same instances run one
+    after another with their own gom_generation calls (plain GPU GOM).  Both
+    give every instance the same generations bit for bit, so the ratio of
+    their generation times is also their ratio of time to any target."""
+    import torch
+
+    from paper_2203_08680_gb300 import gom
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    mix = I.batch_mix(seed=SEED + rank)
+    graphs = [I.random_regular(n, d, s) for n, d, p, s in mix]
+    pops = [gom.Population(g, p, s, stream=stream) for g, (n, d, p, s) in zip(graphs, mix)]
+    ctxs = [P.ctx for P in pops]
+    trials_per_step = sum(P.p * P.m for P in pops)
+    mix_bytes = 0
+    for g, P in zip(graphs, pops):
+        ex = gom.gom_fos_export(P.fos)
+        mix_bytes += mixing_bytes_per_generation(g, ex["elem_ptr"], ex["elem_vars"], P.p) + g.n * P.p // 4 + 16 * P.p
+    # autotuner: the configuration with the fastest generations (state restored after every trial)
+    scratch = torch.empty(gom.gom_batch_scratch_bytes(ctxs) + 256, dtype=torch.uint8, device=dev)
+    scratch = scratch[(-scratch.data_ptr()) % 256:]
+    best, tune_ms = gom.gom_batch_autotune(ctxs, BATCH_CONFIGS, 2, scratch, stream)
+    del scratch
+    ws = torch.empty(gom.gom_batch_workspace_bytes(len(ctxs)) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    batch = gom.gom_batch_create(ctxs, BATCH_CONFIGS[best], ws, stream)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gom.gom_batch_generation(batch, 1, want_counts=False)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            ev0[s].record(stream)
+            gom.gom_batch_generation(batch, 1, want_counts=False)
+            ev1[s].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    dist_barrier(world)
+    total_ms = dist_max(sum(step_ms), world)
+    value = world * trials_per_step * args.steps / (total_ms / 1e3)
+    # plain GPU GOM: the instances one after another, each its own persistent launch
+    plain_steps = max(1, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_ms = 0.0
+    for s in range(plain_steps):
+        flush.fill_(s & 0xFF)
+        e0.record(stream)
+        for P in pops:
+            gom.gom_generation(P.ctx, 1, gom.INT64_MAX, want_stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+    plain_ms /= plain_steps
+    batch_ms = total_ms / args.steps
+    # end to end through the C ABI from host buffers: FOS, colouring, uploads, the
+    # batch, args.steps batched generations, populations and fitness back to host
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hctx, keep, h2d, d2h = [], [], 0, 0
+        for g, (n, d, p, sd) in zip(graphs, mix):
+            G = gom.Graph(g)
+            fos = gom.gom_build_fos(G)
+            gom.gom_color_fos(G, fos)
+            nb = gom.gom_workspace_bytes(G, fos, p)
+            w = torch.empty(nb, dtype=torch.uint8, device=dev)
+            hctx.append(gom.gom_init_population(G, fos, p, sd, w, nb, stream))
+            keep.append((G, fos))
+            h2d += G.row_ptr.nbytes + G.col.nbytes + G.weight.nbytes
+        w2 = torch.empty(gom.gom_batch_workspace_bytes(len(hctx)) + 256, dtype=torch.uint8, device=dev)
+        w2 = w2[(-w2.data_ptr()) % 256:]
+        b2 = gom.gom_batch_create(hctx, BATCH_CONFIGS[best], w2, stream)
+        gom.gom_batch_generation(b2, args.steps)
+        outs = []
+        for c, (n, d, p, sd) in zip(hctx, mix):
+            dpop = torch.empty((p, n), dtype=torch.uint8, device=dev)
+            dfit = torch.empty(p, dtype=torch.int64, device=dev)
+            gom.gom_get_population(c, dpop, dfit, False)
+            outs.append((dpop.to("cpu"), dfit.to("cpu")))
+            d2h += p * n + 8 * p
+        torch.cuda.synchronize()
+        e2e_s = dist_max(time.perf_counter() - t0, world)
+        e2e = {"value": trials_per_step * args.steps * world / e2e_s, "unit": "trials/s",
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+        del b2, hctx, outs
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        # the oracle on instances of the mix taken in order, one generation each, within the budget
+        nth = oracle_threads()
+        val, ninst, done, el = oracle_batch_sample(graphs, mix, args.cpu_seconds, nth)
+        cpu = {"value": val, "unit": "trials/s", "cores": nth, "kind": "oracle",
+               "sample": f"one generation of each of the first {ninst} instances of the mix ({done} trials in "
+                         f"{el:.1f} s of generations, {nth} threads)"}
+    peak, peak_kind = peaks()
+    achieved = mix_bytes / (batch_ms / 1e3) / 1e9
+    line = {
+        "metric": "GOM trials/sec (batched parallel GOM, weighted Max-Cut)", "value": value, "unit": "trials/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl, "description": BATCH_WORKLOADS[wl], "instances": len(pops),
+                   "trials_per_generation": trials_per_step, "batch_config": list(BATCH_CONFIGS[best]),
+                   "autotune_ms_per_generation": dict(zip([f"{w}x{m}" for w, m in BATCH_CONFIGS], tune_ms)),
+                   "grid": gom.gom_batch_layout(batch, 0)[2],
+                   "l2": "flushed between timed generations (2x L2 buffer write)",
+                   "parallelism": f"replicas{world}"},
+        "plain_gpu": {"ms_per_generation": plain_ms, "trials_per_sec": trials_per_step / (plain_ms / 1e3),
+                      "launches_per_generation": len(pops), "generations_timed": plain_steps,
+                      "speedup_of_batch": plain_ms / batch_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_batch (batched persistent generation kernel)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(wl, "k_batch"), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": mix_bytes, "avg_launch_ms": batch_ms,
+                     "launches_timed": args.steps},
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def time_to_target(args, g, p, seed, stream, wl):
     import torch
 
@@ -428,7 +603,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gom", choices=["gom", "reference"])
-    ap.add_argument("--workload", default="torus100", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="torus100", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -444,6 +619,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, args.workload, rank, world)
+    elif args.workload in BATCH_WORKLOADS:
+        run_batch(args, args.workload, rank, world, local)
     else:
         run_gpu(args, args.workload, rank, world, local)
     if world > 1:

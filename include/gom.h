@@ -307,6 +307,81 @@ int gom_fitness_noalloc(const int64_t *d_row_ptr, const int32_t *d_col, const in
 /* Last CUDA error code seen by the handle (0 if none). */
 int gom_last_cuda_error(gom_ctx_t *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched GOM: many independent instances in one persistent launch.
+ *
+ * The paper runs one problem at a time (Sec. 6); a small instance then leaves
+ * most of the GPU idle, and its experiments show the GPU gaining little on
+ * small graphs (Sec. 6.3).  A batch runs several contexts made by
+ * gom_init_population in one cooperative launch: each instance gets its own
+ * range of blocks, its own grid barrier and its own target, and goes through
+ * exactly the generations (Alg. 3) that gom_generation would run for it --
+ * the same population, fitness, elitist and counters bit for bit, whatever
+ * the batch configuration.  Instances never wait for one another.  The paper
+ * has no batched form.
+ */
+typedef struct gom_batch gom_batch_t;
+
+typedef struct gom_batch_config {
+    int32_t warps_per_block; /* 1, 2, 4 or 8 */
+    int32_t min_blocks;      /* register budget: 2 (128 registers a thread, no spills) or 3 (85) */
+} gom_batch_config_t;
+
+/* Device bytes of a batch of `num` instances (their parameter blocks, the
+ * instance table and one barrier counter each). */
+size_t gom_batch_workspace_bytes(int32_t num);
+
+/*
+ * A batch over ctxs[0..num) (num >= 1, each context at most once), all made
+ * on cuda_stream on the current device; cfg NULL means {4, 3}.  Blocks go to
+ * instances in proportion to their estimated work per generation (at least
+ * one each, at most what their largest colour group can use).  d_workspace:
+ * caller-owned device memory of gom_batch_workspace_bytes(num) bytes,
+ * 256-byte aligned.  The contexts stay the caller's, must outlive the batch
+ * and can still be used on their own.  GOM_E_LIMIT if the device cannot hold
+ * one block per instance at once or an element does not fit the
+ * configuration's shared memory; GOM_E_STATE without cooperative launch.
+ */
+int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config_t *cfg, void *d_workspace,
+                     size_t ws_bytes, void *cuda_stream, gom_batch_t **out);
+
+/*
+ * Up to num_generations generations of every instance in one launch;
+ * instance b stops after the first generation whose best fitness reaches
+ * targets[b] (host array, or NULL for no target).  generations_run (host
+ * [num], or NULL for an asynchronous call) receives the generations each
+ * instance ran; the call then waits for the stream.  GOM_E_TIMEOUT if the
+ * grid-barrier wait of any instance timed out (that context's error is
+ * sticky).
+ */
+int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int64_t *targets,
+                         int32_t *generations_run);
+
+/* Counters of the generations instance b ran in the last call, into
+ * host_stats[0..capacity); *count receives their number.  Waits. */
+int gom_batch_stats(gom_batch_t *batch, int32_t b, gom_gen_stats_t *host_stats, int32_t capacity, int32_t *count);
+
+/* The blocks of instance b ([*blk0, *blk0 + *nblk)) and the launch's grid. */
+int gom_batch_layout(const gom_batch_t *batch, int32_t b, int32_t *blk0, int32_t *nblk, int32_t *grid);
+
+void gom_batch_destroy(gom_batch_t *batch);
+
+/*
+ * Autotuner of the batch configuration: for each of cfgs[0..num_cfg) it
+ * builds the batch and times `generations` generations of every instance
+ * (CUDA events), all from the same starting state -- the instances' states
+ * are saved to d_scratch first and restored after every trial, so tuning
+ * changes no result.  *best receives the index of the fastest configuration,
+ * ms[c] (host, may be NULL) the milliseconds per generation of each (a
+ * configuration that cannot be built gets a negative value).  d_scratch:
+ * gom_batch_scratch_bytes(ctxs, num) bytes of device memory, 256-byte
+ * aligned.  Waits for cuda_stream.
+ */
+size_t gom_batch_scratch_bytes(gom_ctx_t *const *ctxs, int32_t num);
+int gom_batch_autotune(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config_t *cfgs, int32_t num_cfg,
+                       int32_t generations, void *d_scratch, size_t scratch_bytes, void *cuda_stream,
+                       int32_t *best, double *ms);
+
 void gom_destroy(gom_ctx_t *ctx);
 
 const char *gom_strerror(int code);

@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 
+#include "gom_ctx.h"
 #include "gom_internal.h"
 #include "gom_kernels.cuh"
 
@@ -67,51 +68,6 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.total = off;
     return L;
 }
-
-} // namespace
-
-struct gom_ctx {
-    GomParams prm{};
-    cudaStream_t stream = nullptr;
-    int32_t n = 0, p = 0, W = 0, k = 0;
-    int64_t m = 0;
-    int sms = 0;
-    int grid_mix = 0, grid_fit = 0, grid_start = 0, grid_order = 0, grid_io = 0;
-    const void *mix_fn = nullptr; // k_mix instance for this population and FOS
-    size_t mix_smem = 0;          // its dynamic shared memory per block
-    int mix_threads = kMixThreads; // its block size (fewer warps for very large elements)
-    const void *run_fn = nullptr; // persistent generation kernel (same instance parameters)
-    size_t run_smem = 0;          // its dynamic shared memory (staging or the k group keys)
-    int grid_run = 0;             // its grid: co-resident blocks only
-    bool can_persist = false;     // cooperative launch available and the sizes fit
-    bool persistent = false;      // current path: k_run (true) or the per-generation graph
-    unsigned long long *trace_buf = nullptr; // workspace slot of the phase trace
-    size_t order_smem = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t tgraph = nullptr; // variant with event records around each mixing launch
-    cudaGraphExec_t texec = nullptr;
-    std::vector<cudaEvent_t> events;
-    bool timing = false;
-    bool timing_pending = false; // the events hold a generation not yet added to mix_ms
-    double mix_ms = 0.0;
-    int64_t timing_g0 = 0;       // generation counter when timing was (re)started
-    int last_cuda = 0;
-};
-
-namespace {
-
-int cuda_fail(gom_ctx *ctx, cudaError_t e)
-{
-    if (ctx) ctx->last_cuda = static_cast<int>(e);
-    return GOM_E_CUDA;
-}
-
-#define GOM_CUDA(ctx, call)                          \
-    do {                                             \
-        cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
-    } while (0)
 
 template <class T>
 cudaError_t upload(void *base, size_t off, const std::vector<T> &v, cudaStream_t s)
@@ -202,7 +158,25 @@ int rebuild_graphs(gom_ctx *ctx)
     return rc;
 }
 
-int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *run_out)
+
+int accumulate_timing(gom_ctx *ctx)
+{
+    if (!ctx->timing_pending) return GOM_OK;
+    ctx->timing_pending = false;
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int t = 0; t < ctx->k; ++t) {
+        float ms = 0.f;
+        GOM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * t], ctx->events[2 * t + 1]));
+        ctx->mix_ms += ms;
+    }
+    return GOM_OK;
+}
+
+} // namespace
+
+// The counters of the generations of the context's last call (host_stats
+// may be null), and their number.  Waits for the stream.
+int ctx_read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *run_out)
 {
     GomDevState st;
     GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
@@ -231,21 +205,6 @@ int read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *
     }
     return GOM_OK;
 }
-
-int accumulate_timing(gom_ctx *ctx)
-{
-    if (!ctx->timing_pending) return GOM_OK;
-    ctx->timing_pending = false;
-    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int t = 0; t < ctx->k; ++t) {
-        float ms = 0.f;
-        GOM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * t], ctx->events[2 * t + 1]));
-        ctx->mix_ms += ms;
-    }
-    return GOM_OK;
-}
-
-} // namespace
 
 extern "C" {
 
@@ -438,8 +397,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     auto run_grid = [&](size_t smem_bytes, int *out_grid) -> cudaError_t {
         *out_grid = 0;
         if (smem_bytes > static_cast<size_t>(kSmemBudget)) return cudaSuccess;
-        cudaError_t e = cudaFuncSetAttribute(c->run_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem_bytes));
+        cudaError_t e = raise_smem_limit(c->run_fn, smem_bytes);
         if (e != cudaSuccess) return e;
         int occ_run = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_run, c->run_fn, c->mix_threads, smem_bytes);
@@ -476,8 +434,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
         }
     }
     c->mix_smem = static_cast<size_t>(warp_words * 4 * warps_per_block);
-    GOM_CUDA(c, cudaFuncSetAttribute(c->mix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(c->mix_smem)));
+    GOM_CUDA(c, raise_smem_limit(c->mix_fn, c->mix_smem));
     int occ = 0;
     GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
     occ = std::max(occ, 1);
@@ -485,6 +442,18 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxMixBlocks));
     c->grid_mix = static_cast<int>(grid);
     c->persistent = c->can_persist;
+    c->wpi = wpi;
+    c->narrow = narrow;
+    c->max_items = std::max<int64_t>(1, max_group * per);
+    {
+        // per-trial cost ~ element variables + edges + a constant, summed over elements
+        double per_gen = 0.0;
+        for (int64_t q = 0; q < c->m; ++q) {
+            const int32_t *h = tabs.hdr.data() + 8 * q;
+            per_gen += 8.0 + (h[3] & 0xFF) + (h[3] >> 8) + h[4];
+        }
+        c->work = per_gen * pop;
+    }
     // dynamic item claims: faster warps take more items (in stage-all mode
     // every warp has at most one item per group and the schedule is moot)
     c->prm.dyn = 1;
@@ -495,10 +464,11 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->grid_order = (c->k + 255) / 256;
     c->order_smem = sizeof(unsigned long long) * std::max(c->k, 1);
     if (c->order_smem > 48 * 1024)
-        GOM_CUDA(c, cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(c->order_smem)));
+        GOM_CUDA(c, raise_smem_limit((const void *)k_order, c->order_smem));
 
     char *base = static_cast<char *>(d_workspace);
+    c->base = base;
+    c->state_bytes = L.row_ptr;
     GomParams &P = c->prm;
     P.n = c->n;
     P.p = pop;
@@ -608,7 +578,7 @@ int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitne
         remaining -= chunk;
         if (want) {
             int32_t run = 0;
-            int rc = read_stats(ctx, chunk, stats_out, &run);
+            int rc = ctx_read_stats(ctx, chunk, stats_out, &run);
             if (rc) return rc;
             done_total += run;
             if (stats_out) stats_out += chunk;

@@ -1,0 +1,348 @@
+// gom_batch.cu -- batched GOM: many independent instances (contexts made by
+// gom_init_population) in one persistent cooperative launch, each on its own
+// range of blocks with its own grid barrier (k_batch), plus the autotuner of
+// the batch configuration.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <queue>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gom_ctx.h"
+#include "gom_internal.h"
+#include "gom_kernels.cuh"
+
+struct gom_batch {
+    std::vector<gom_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    int32_t B = 0;
+    gom_batch_config_t cfg{4, 3};
+    const void *fn = nullptr;  // k_batch<min_blocks>
+    int grid = 0;              // blocks of the launch
+    int threads = 0;           // threads per block
+    size_t smem = 0;           // dynamic shared memory per block
+    int32_t f_words = 0;       // its first part: the fitness accumulators (32-bit words)
+    GomParams *d_params = nullptr;
+    GomBatchInst *d_inst = nullptr;
+    GomBarrier *d_bars = nullptr;
+    std::vector<GomParams> params; // host copies (uploaded once)
+    std::vector<GomBatchInst> inst; // host copy of the instance table
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kBatchSmemBudget = 200 * 1024;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct BatchLayout {
+    size_t params, inst, bars, total;
+};
+
+BatchLayout batch_layout(int32_t num)
+{
+    BatchLayout L{};
+    size_t off = 0;
+    L.params = off;
+    off = align_up(off + sizeof(GomParams) * static_cast<size_t>(num));
+    L.inst = off;
+    off = align_up(off + sizeof(GomBatchInst) * static_cast<size_t>(num));
+    L.bars = off;
+    off = align_up(off + sizeof(GomBarrier) * static_cast<size_t>(num));
+    L.total = off;
+    return L;
+}
+
+bool valid_config(const gom_batch_config_t &c)
+{
+    const int w = c.warps_per_block;
+    return (w == 1 || w == 2 || w == 4 || w == 8) && (c.min_blocks == 2 || c.min_blocks == 3);
+}
+
+// Blocks per instance: one each, then one at a time to the instance with the
+// largest estimated work per block, up to what its largest colour group can
+// use (one warp per item) or until the device is full.
+std::vector<int32_t> allocate_blocks(const std::vector<gom_ctx *> &ctx, int total_blocks, int warps_per_block)
+{
+    const size_t B = ctx.size();
+    std::vector<int32_t> nb(B, 1);
+    std::priority_queue<std::pair<double, size_t>> heap;
+    std::vector<int64_t> need(B);
+    for (size_t b = 0; b < B; ++b) {
+        need[b] = (ctx[b]->max_items + warps_per_block - 1) / warps_per_block;
+        if (need[b] > 1) heap.push({ctx[b]->work, b});
+    }
+    int64_t left = static_cast<int64_t>(total_blocks) - static_cast<int64_t>(B);
+    while (left > 0 && !heap.empty()) {
+        const size_t b = heap.top().second;
+        heap.pop();
+        ++nb[b];
+        --left;
+        if (nb[b] < need[b]) heap.push({ctx[b]->work / nb[b], b});
+    }
+    return nb;
+}
+
+} // namespace
+
+extern "C" {
+
+size_t gom_batch_workspace_bytes(int32_t num) { return num < 1 ? 0 : batch_layout(num).total; }
+
+int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config_t *cfg, void *d_workspace,
+                     size_t ws_bytes, void *cuda_stream, gom_batch_t **out)
+{
+    if (!ctxs || num < 1 || !out) return GOM_E_ARG;
+    const gom_batch_config_t conf = cfg ? *cfg : gom_batch_config_t{4, 3};
+    if (!valid_config(conf)) return GOM_E_ARG;
+    const BatchLayout L = batch_layout(num);
+    if (!d_workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
+        return GOM_E_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<gom_ctx *> cs(ctxs, ctxs + num);
+    {
+        std::vector<gom_ctx *> sorted(cs);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return GOM_E_ARG;
+    }
+    for (gom_ctx *c : cs)
+        if (!c || c->stream != s) return GOM_E_ARG;
+
+    int dev = 0, sms = 0, coop = 0;
+    GOM_CUDA(nullptr, cudaGetDevice(&dev));
+    GOM_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GOM_CUDA(nullptr, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return GOM_E_STATE;
+
+    // shared memory: the fitness accumulators (32 W of the widest instance,
+    // int64), then one staging slice per warp (the largest slice of any
+    // instance), or the colour-group keys of the instance with most colours
+    int maxW = 1, maxk = 1;
+    int64_t max_warp_words = 8;
+    for (gom_ctx *c : cs) {
+        maxW = std::max(maxW, c->W);
+        maxk = std::max(maxk, c->k);
+        max_warp_words = std::max<int64_t>(max_warp_words, c->prm.warp_smem);
+    }
+    const int32_t f_words = 2 * 32 * maxW;
+    const int64_t slices = std::max<int64_t>(int64_t(8) * maxk,
+                                             int64_t(4) * max_warp_words * conf.warps_per_block);
+    const int64_t smem = int64_t(4) * f_words + slices;
+    if (smem > kBatchSmemBudget) return GOM_E_LIMIT;
+
+    const void *fn = gom_batch_kernel(conf.min_blocks);
+    const int threads = 32 * conf.warps_per_block;
+    GOM_CUDA(nullptr, raise_smem_limit(fn, static_cast<size_t>(smem)));
+    int occ = 0;
+    GOM_CUDA(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, static_cast<size_t>(smem)));
+    const int total = sms * occ;
+    if (total < num) return GOM_E_LIMIT;
+
+    std::unique_ptr<gom_batch> bt(new (std::nothrow) gom_batch());
+    if (!bt) return GOM_E_ARG;
+    gom_batch *B = bt.get();
+    B->ctx = cs;
+    B->stream = s;
+    B->B = num;
+    B->cfg = conf;
+    B->fn = fn;
+    B->threads = threads;
+    B->smem = static_cast<size_t>(smem);
+    B->f_words = f_words;
+    char *base = static_cast<char *>(d_workspace);
+    B->d_params = reinterpret_cast<GomParams *>(base + L.params);
+    B->d_inst = reinterpret_cast<GomBatchInst *>(base + L.inst);
+    B->d_bars = reinterpret_cast<GomBarrier *>(base + L.bars);
+
+    const std::vector<int32_t> nb = allocate_blocks(cs, total, conf.warps_per_block);
+    B->params.resize(num);
+    B->inst.resize(num);
+    int32_t blk = 0;
+    for (int32_t b = 0; b < num; ++b) {
+        GomParams P = cs[b]->prm;
+        P.stage_all = 0; // one staging slice per warp
+        P.dyn = 1;
+        P.trace = nullptr;
+        P.bar = B->d_bars + b;
+        B->params[b] = P;
+        GomBatchInst &I = B->inst[b];
+        I = GomBatchInst{};
+        I.blk0 = blk;
+        I.nblk = nb[b];
+        I.wpi = cs[b]->wpi;
+        I.narrow = cs[b]->narrow ? 1 : 0;
+        I.target = INT64_MAX;
+        blk += nb[b];
+    }
+    B->grid = blk;
+    GOM_CUDA(nullptr, cudaMemcpyAsync(B->d_params, B->params.data(), sizeof(GomParams) * num,
+                                      cudaMemcpyHostToDevice, s));
+    GOM_CUDA(nullptr, cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(GomBatchInst) * num,
+                                      cudaMemcpyHostToDevice, s));
+    GOM_CUDA(nullptr, cudaMemsetAsync(B->d_bars, 0, sizeof(GomBarrier) * num, s));
+    GOM_CUDA(nullptr, cudaStreamSynchronize(s));
+    *out = bt.release();
+    return GOM_OK;
+}
+
+int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int64_t *targets,
+                         int32_t *generations_run)
+{
+    if (!batch || num_generations < 0) return GOM_E_ARG;
+    gom_batch *B = batch;
+    if (num_generations == 0) {
+        if (generations_run) std::fill(generations_run, generations_run + B->B, 0);
+        return GOM_OK;
+    }
+    for (int32_t b = 0; b < B->B; ++b) B->inst[b].target = targets ? targets[b] : INT64_MAX;
+    // pageable source: the copy has read it when the call returns
+    GOM_CUDA(nullptr, cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(GomBatchInst) * B->B,
+                                      cudaMemcpyHostToDevice, B->stream));
+    GomParams *dp = B->d_params;
+    GomBatchInst *di = B->d_inst;
+    GomBarrier *db = B->d_bars;
+    int nB = B->B, G = num_generations, fw = B->f_words;
+    void *args[] = {&dp, &di, &db, &nB, &G, &fw};
+    GOM_CUDA(nullptr, cudaLaunchCooperativeKernel(B->fn, dim3(B->grid), dim3(B->threads), args, B->smem, B->stream));
+    k_batch_collect<<<(B->B + 255) / 256, 256, 0, B->stream>>>(B->d_params, B->d_inst, B->B);
+    GOM_CUDA(nullptr, cudaGetLastError());
+    if (!generations_run) return GOM_OK;
+    std::vector<GomBatchInst> back(B->B);
+    GOM_CUDA(nullptr, cudaMemcpyAsync(back.data(), B->d_inst, sizeof(GomBatchInst) * B->B,
+                                      cudaMemcpyDeviceToHost, B->stream));
+    GOM_CUDA(nullptr, cudaStreamSynchronize(B->stream));
+    bool timed_out = false;
+    for (int32_t b = 0; b < B->B; ++b) {
+        generations_run[b] = back[b].gens_run;
+        timed_out |= back[b].err != 0;
+    }
+    return timed_out ? GOM_E_TIMEOUT : GOM_OK;
+}
+
+int gom_batch_stats(gom_batch_t *batch, int32_t b, gom_gen_stats_t *host_stats, int32_t capacity, int32_t *count)
+{
+    if (!batch || b < 0 || b >= batch->B || capacity < 0 || (capacity > 0 && !host_stats)) return GOM_E_ARG;
+    gom_ctx *c = batch->ctx[b];
+    int32_t run = 0;
+    int rc = ctx_read_stats(c, 0, nullptr, &run);
+    if (rc) return rc;
+    if (run > kStatsCap) return GOM_E_LIMIT; // the device ring keeps the last kStatsCap generations
+    rc = ctx_read_stats(c, std::min(capacity, run), host_stats, &run);
+    if (rc) return rc;
+    if (count) *count = run;
+    return GOM_OK;
+}
+
+int gom_batch_layout(const gom_batch_t *batch, int32_t b, int32_t *blk0, int32_t *nblk, int32_t *grid)
+{
+    if (!batch || b < 0 || b >= batch->B) return GOM_E_ARG;
+    if (blk0) *blk0 = batch->inst[b].blk0;
+    if (nblk) *nblk = batch->inst[b].nblk;
+    if (grid) *grid = batch->grid;
+    return GOM_OK;
+}
+
+void gom_batch_destroy(gom_batch_t *batch)
+{
+    if (!batch) return;
+    cudaStreamSynchronize(batch->stream);
+    delete batch;
+}
+
+size_t gom_batch_scratch_bytes(gom_ctx_t *const *ctxs, int32_t num)
+{
+    if (!ctxs || num < 1) return 0;
+    size_t total = 0;
+    for (int32_t b = 0; b < num; ++b) {
+        if (!ctxs[b]) return 0;
+        total += align_up(ctxs[b]->state_bytes);
+    }
+    return total + batch_layout(num).total;
+}
+
+namespace {
+
+// Copies every instance's state arrays to (save) or from (restore) the scratch.
+int copy_states(gom_ctx_t *const *ctxs, int32_t num, char *scratch, bool save, cudaStream_t s)
+{
+    size_t off = 0;
+    for (int32_t b = 0; b < num; ++b) {
+        gom_ctx *c = ctxs[b];
+        void *dst = save ? static_cast<void *>(scratch + off) : static_cast<void *>(c->base);
+        const void *src = save ? static_cast<const void *>(c->base) : static_cast<const void *>(scratch + off);
+        GOM_CUDA(nullptr, cudaMemcpyAsync(dst, src, c->state_bytes, cudaMemcpyDeviceToDevice, s));
+        off += align_up(c->state_bytes);
+    }
+    return GOM_OK;
+}
+
+} // namespace
+
+int gom_batch_autotune(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config_t *cfgs, int32_t num_cfg,
+                       int32_t generations, void *d_scratch, size_t scratch_bytes, void *cuda_stream,
+                       int32_t *best, double *ms)
+{
+    if (!ctxs || num < 1 || !cfgs || num_cfg < 1 || generations < 1 || !best) return GOM_E_ARG;
+    const size_t need = gom_batch_scratch_bytes(ctxs, num);
+    if (!need || !d_scratch || scratch_bytes < need || reinterpret_cast<uintptr_t>(d_scratch) % kAlign)
+        return GOM_E_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    char *scratch = static_cast<char *>(d_scratch);
+    size_t states = 0;
+    for (int32_t b = 0; b < num; ++b) states += align_up(ctxs[b]->state_bytes);
+    char *ws = scratch + states;
+    const size_t ws_bytes = need - states;
+    int rc = copy_states(ctxs, num, scratch, true, s);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GOM_CUDA(nullptr, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GOM_E_CUDA;
+    }
+    int32_t arg = -1;
+    double best_ms = 0.0;
+    for (int32_t c = 0; c < num_cfg && rc == GOM_OK; ++c) {
+        if (ms) ms[c] = -1.0;
+        gom_batch_t *bt = nullptr;
+        const int brc = gom_batch_create(ctxs, num, &cfgs[c], ws, ws_bytes, cuda_stream, &bt);
+        if (brc == GOM_E_LIMIT || brc == GOM_E_ARG) continue; // not buildable: skipped
+        if (brc) {
+            rc = brc;
+            break;
+        }
+        // one untimed generation (first launch of the kernel variant), then the timed ones
+        rc = gom_batch_generation(bt, 1, nullptr, nullptr);
+        if (rc == GOM_OK) rc = copy_states(ctxs, num, scratch, false, s);
+        if (rc == GOM_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = GOM_E_CUDA;
+        if (rc == GOM_OK) rc = gom_batch_generation(bt, generations, nullptr, nullptr);
+        if (rc == GOM_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = GOM_E_CUDA;
+        if (rc == GOM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = GOM_E_CUDA;
+        float el = 0.f;
+        if (rc == GOM_OK && cudaEventElapsedTime(&el, e0, e1) != cudaSuccess) rc = GOM_E_CUDA;
+        gom_batch_destroy(bt);
+        const int rrc = copy_states(ctxs, num, scratch, false, s);
+        if (rc == GOM_OK) rc = rrc;
+        if (rc) break;
+        const double per = static_cast<double>(el) / generations;
+        if (ms) ms[c] = per;
+        if (arg < 0 || per < best_ms) {
+            arg = c;
+            best_ms = per;
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (arg < 0) return GOM_E_LIMIT;
+    *best = arg;
+    return GOM_OK;
+}
+
+} // extern "C"

@@ -79,6 +79,17 @@ struct GomBarrier { // grid barrier of the persistent kernel: monotonic arrival 
     unsigned long long pad;
 };
 
+// One instance of a batched launch (gom_batch_*): its blocks, kernel variant
+// and target; gens_run and err are filled after each call.
+struct GomBatchInst {
+    int32_t blk0, nblk; // its blocks [blk0, blk0 + nblk) of the launch
+    int32_t wpi;        // words per item of its mixing (1, 2, 4)
+    int32_t narrow;     // 1: elements of <= 32 variables and |w| sums < 2^30
+    int64_t target;     // target fitness of the current call
+    int32_t gens_run;   // generations run by the last call
+    int32_t err;        // the instance's device error word after the last call
+};
+
 struct GomDevStats { // mirrors gom_gen_stats_t
     int64_t generation, best, elite, trials, donorless, accepted, improving, reached;
 };

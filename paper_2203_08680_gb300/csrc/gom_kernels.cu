@@ -52,6 +52,15 @@ __device__ __forceinline__ uint32_t pick(uint4 r, int q)
 __device__ __forceinline__ int64_t gthread() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gthreads() { return (int64_t)gridDim.x * blockDim.x; }
 
+// The blocks that run one problem: the whole grid, or, in a batched launch,
+// the range of blocks given to one instance (block `blk` of `nblk`).
+struct VGrid {
+    int blk, nblk;
+    __device__ __forceinline__ int64_t thread() const { return (int64_t)blk * blockDim.x + threadIdx.x; }
+    __device__ __forceinline__ int64_t threads() const { return (int64_t)nblk * blockDim.x; }
+};
+__device__ __forceinline__ VGrid whole_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+
 // Lowest index of the maximum of f[0..p) over one block (blockDim <= 1024);
 // every thread of the block receives the result.
 __device__ void block_argmax(const int64_t *f, int p, int64_t *best_out, int *arg_out)
@@ -271,14 +280,14 @@ __device__ bool grid_barrier(unsigned long long *count, int *err, unsigned nblk,
 // the new elitist copied out of O[argmax] when it changed, the elitist flags
 // eqw[g mod 2] (P[i] == x_e over all variables), the other buffer set for
 // generation g+1, and the item claim counters zeroed.
-__device__ void phase_gen_start(const GomParams &P, int improved, int argmax, uint32_t g, bool copy)
+__device__ void phase_gen_start(const GomParams &P, const VGrid &V, int improved, int argmax, uint32_t g, bool copy)
 {
     __shared__ uint32_t s_eq[32];
     const int aw = argmax >> 5, ab = argmax & 31;
     const int W = P.W;
     const int lw = __ffs(W) - 1;
     const int64_t total = (int64_t)P.n * W;
-    const int64_t tid = gthread(), nth = gthreads();
+    const int64_t tid = V.thread(), nth = V.threads();
     const int w = (int)(tid & (W - 1));
     uint32_t *eqw = P.eqw + (g & 1) * W;
     if (tid < W) P.eqw[((g + 1) & 1) * W + tid] = kFull;
@@ -333,10 +342,10 @@ __device__ __forceinline__ int rank_of(const unsigned long long *s_key, int k, i
 }
 
 // The order into P.order, the colours ranked in a grid-strided share per block.
-__device__ void phase_order(const GomParams &P, unsigned long long *s_key, uint32_t g)
+__device__ void phase_order(const GomParams &P, const VGrid &V, unsigned long long *s_key, uint32_t g)
 {
     order_keys(P, s_key, g);
-    for (int c = (int)gthread(); c < P.k; c += (int)gthreads()) P.order[rank_of(s_key, P.k, c)] = c;
+    for (int c = (int)V.thread(); c < P.k; c += (int)V.threads()) P.order[rank_of(s_key, P.k, c)] = c;
     __syncthreads();
 }
 
@@ -953,11 +962,12 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 // s <= 32, uint64_t: s <= 64); AccT is the delta type (int32_t when every
 // element's sum of |w| is < 2^30).  Counters accumulate per lane.
 template <int WPI, typename MaskT, typename AccT>
-__device__ __forceinline__ void phase_mix(const GomParams &P, int t, int c, uint32_t g, uint32_t *sl, bool first_staged,
-                                          bool single, long long *s_f, unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
+__device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *sl,
+                                          bool first_staged, bool single, long long *s_f, unsigned &n_dl,
+                                          unsigned &n_acc, unsigned &n_imp)
 {
     const int lane = threadIdx.x & 31;
-    const int gwarp = (int)(gthread() >> 5), nwarps = (int)(gthreads() >> 5);
+    const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
     bool staged = first_staged ? sl[0] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl);
     if (single) { // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (staged) run_item<WPI, MaskT, AccT>(P, sl, g, true, s_f, n_dl, n_acc, n_imp);
@@ -1002,14 +1012,14 @@ __device__ __forceinline__ void count_flush(unsigned long long *s_cnt, unsigned 
 __global__ void k_gen_start(GomParams P)
 {
     if (P.st->done) return;
-    phase_gen_start(P, P.st->improved, P.st->argmax, P.st->g, true);
+    phase_gen_start(P, whole_grid(), P.st->improved, P.st->argmax, P.st->g, true);
 }
 
 __global__ void k_order(GomParams P)
 {
     extern __shared__ unsigned long long s_key[];
     if (P.st->done) return;
-    phase_order(P, s_key, P.st->g);
+    phase_order(P, whole_grid(), s_key, P.st->g);
 }
 
 template <int WPI, typename MaskT, typename AccT>
@@ -1021,8 +1031,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-    phase_mix<WPI, MaskT, AccT>(P, t, P.order[t], P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem, false, false,
-                                s_f, n_dl, n_acc, n_imp);
+    phase_mix<WPI, MaskT, AccT>(P, whole_grid(), t, P.order[t], P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem,
+                                false, false, s_f, n_dl, n_acc, n_imp);
     count_flush(s_cnt, n_dl, n_acc, n_imp);
     acc_flush(P, s_f, s_cnt);
 }
@@ -1046,7 +1056,72 @@ __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 // otherwise every warp stages its first item of group t before the barrier
 // that opens the group.  The block's fitness accumulators and the warps'
 // counters span all groups of a generation and are flushed once, before the
-// closing barrier.
+// closing barrier.  V is the set of blocks that run this problem (the whole
+// grid, or one instance's blocks in a batched launch); `bar` is their
+// barrier counter.
+struct RunShared {
+    uint32_t *dyn;              // staging slices (and the group keys outside stage-all mode)
+    long long *f;               // [32 W] the block's fitness accumulators
+    unsigned long long *cnt;    // [4] the block's counters
+    unsigned long long *okey;   // [kStageAllMaxK] stage-all group keys
+    int *order;                 // [kStageAllMaxK] stage-all group order
+};
+
+template <int WPI, typename MaskT, typename AccT>
+__device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *bar, int G, int64_t target,
+                                const RunShared &S)
+{
+    const unsigned nblk = (unsigned)V.nblk;
+    const int gwarp = (int)(V.thread() >> 5);
+    const bool all = P.stage_all != 0;
+    const bool lead = V.blk == 0;
+    // this warp's staging: one slice, or one per colour with stage_all
+    uint32_t *slices = S.dyn + (threadIdx.x >> 5) * P.warp_smem * (all ? P.k : 1);
+    uint32_t g = P.st->g;
+    GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
+    unsigned long long bnext = 0; // next barrier epoch end (thread 0)
+    if (threadIdx.x == 0) bnext = barrier_first(&bar->count, nblk);
+    if (lead && threadIdx.x == 0) {
+        P.st->call_g0 = g; // read by the host after the kernel only
+        P.st->target = target;
+    }
+    // optional phase trace (block 0, thread 0): wall-clock stamps of the last
+    // generation of the call, see gom_read_phase_trace
+    const bool tr = P.trace != nullptr && lead && threadIdx.x == 0;
+    for (int q = 0; q < G; ++q) {
+        if (q > 0 && phase_gen_end(P, target, g - 1, e, lead)) return;
+        if (tr) P.trace[0] = global_ns();
+        phase_gen_start(P, V, e.improved, e.argmax, g, !all);
+        if (all)
+            phase_order_block(P, S.okey, S.order, g);
+        else
+            phase_order(P, V, reinterpret_cast<unsigned long long *>(S.dyn), g);
+        acc_zero(P, S.f, S.cnt);
+        if (tr) P.trace[1] = global_ns();
+        if (all) stage_all_items<WPI, MaskT>(P, gwarp, slices, g, q == 0);
+        if (tr) P.trace[2] = global_ns();
+        if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (tr) P.trace[3] = global_ns();
+        unsigned n_dl = 0, n_acc = 0, n_imp = 0;
+        for (int t = 0; t < P.k; ++t) {
+            const int c = all ? S.order[t] : P.order[t];
+            uint32_t *sl = all ? slices + c * P.warp_smem : slices;
+            // without stage_all: stage the first item of group t before its barrier
+            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl);
+            if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+            if (tr) P.trace[4 + 2 * t] = global_ns();
+            phase_mix<WPI, MaskT, AccT>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);
+            if (tr) P.trace[5 + 2 * t] = global_ns();
+        }
+        count_flush(S.cnt, n_dl, n_acc, n_imp);
+        acc_flush(P, S.f, S.cnt);
+        if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (tr) P.trace[4 + 2 * P.k] = global_ns();
+        ++g;
+    }
+    if (G > 0 && lead) phase_gen_end(P, target, g - 1, e, true);
+}
+
 template <int WPI, typename MaskT, typename AccT>
 __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
 {
@@ -1055,54 +1130,87 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     __shared__ unsigned long long s_cnt[4];
     __shared__ unsigned long long s_okey[kStageAllMaxK];
     __shared__ int s_order[kStageAllMaxK];
-    const unsigned nblk = gridDim.x;
-    const int gwarp = (int)(gthread() >> 5);
-    const bool all = P.stage_all != 0;
-    // this warp's staging: one slice, or one per colour with stage_all
-    uint32_t *slices = s_dyn + (threadIdx.x >> 5) * P.warp_smem * (all ? P.k : 1);
-    uint32_t g = P.st->g;
-    GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
-    unsigned long long bnext = 0; // next barrier epoch end (thread 0)
-    if (threadIdx.x == 0) bnext = barrier_first(&P.bar->count, nblk);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        P.st->call_g0 = g; // read by the host after the kernel only
-        P.st->target = target;
-    }
-    // optional phase trace (block 0, thread 0): wall-clock stamps of the last
-    // generation of the call, see gom_read_phase_trace
-    const bool tr = P.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
-    for (int q = 0; q < G; ++q) {
-        if (q > 0 && phase_gen_end(P, target, g - 1, e, blockIdx.x == 0)) return;
-        if (tr) P.trace[0] = global_ns();
-        phase_gen_start(P, e.improved, e.argmax, g, !all);
-        if (all)
-            phase_order_block(P, s_okey, s_order, g);
-        else
-            phase_order(P, reinterpret_cast<unsigned long long *>(s_dyn), g);
-        acc_zero(P, s_f, s_cnt);
-        if (tr) P.trace[1] = global_ns();
-        if (all) stage_all_items<WPI, MaskT>(P, gwarp, slices, g, q == 0);
-        if (tr) P.trace[2] = global_ns();
-        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
-        if (tr) P.trace[3] = global_ns();
-        unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-        for (int t = 0; t < P.k; ++t) {
-            const int c = all ? s_order[t] : P.order[t];
-            uint32_t *sl = all ? slices + c * P.warp_smem : slices;
-            // without stage_all: stage the first item of group t before its barrier
-            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl);
-            if (t > 0 && !grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
-            if (tr) P.trace[4 + 2 * t] = global_ns();
-            phase_mix<WPI, MaskT, AccT>(P, t, c, g, sl, true, all, s_f, n_dl, n_acc, n_imp);
-            if (tr) P.trace[5 + 2 * t] = global_ns();
+    const RunShared S{s_dyn, s_f, s_cnt, s_okey, s_order};
+    run_generations<WPI, MaskT, AccT>(P, whole_grid(), P.bar, G, target, S);
+}
+
+// One kernel variant of the batched path, compiled as its own function so
+// that each variant gets its own register allocation.
+template <int WPI, typename MaskT, typename AccT>
+__device__ __noinline__ void batch_variant(const GomParams &P, const VGrid V, GomBarrier *bar, int G, int64_t target,
+                                           const RunShared &S)
+{
+    run_generations<WPI, MaskT, AccT>(P, V, bar, G, target, S);
+}
+
+// Batched path: many independent instances in one cooperative launch.  Each
+// instance owns a range of blocks and runs its own generations on them, with
+// its own barrier counter and its own stop decision, exactly as its
+// persistent kernel would; instances never wait for one another.  Ps[b] is
+// instance b's parameter block (one-slice staging), inst[b] its blocks,
+// kernel variant and target.  The dynamic shared memory holds the block's
+// fitness accumulators (f_words 32-bit words, 32 W of the widest instance)
+// and then the warps' staging slices.
+// MINB: resident blocks of 256 threads the register budget is cut for (2: no
+// spills, 3: more warps per SM).
+template <int MINB>
+__global__ void __launch_bounds__(kMixThreads, MINB)
+    k_batch(const GomParams *Ps, const GomBatchInst *inst, GomBarrier *bars, int B, int G, int f_words)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ GomParams sP;
+    __shared__ unsigned long long s_cnt[4];
+    __shared__ int s_b;
+    if (threadIdx.x == 0) {
+        // the instance of this block: the last b with blk0 <= blockIdx.x
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].blk0 <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
         }
-        count_flush(s_cnt, n_dl, n_acc, n_imp);
-        acc_flush(P, s_f, s_cnt);
-        if (!grid_barrier(&P.bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
-        if (tr) P.trace[4 + 2 * P.k] = global_ns();
-        ++g;
+        s_b = lo;
+        sP = Ps[lo];
     }
-    if (G > 0 && blockIdx.x == 0) phase_gen_end(P, target, g - 1, e, true);
+    __syncthreads();
+    const int b = s_b;
+    const GomBatchInst I = inst[b];
+    if ((int)blockIdx.x >= I.blk0 + I.nblk) return; // a block past every range (none by construction)
+    const VGrid V{(int)blockIdx.x - I.blk0, I.nblk};
+    const RunShared S{s_dyn + f_words, reinterpret_cast<long long *>(s_dyn), s_cnt, nullptr, nullptr};
+    GomBarrier *bar = bars + b;
+    if (I.narrow) {
+        if (I.wpi == 4)
+            batch_variant<4, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
+        else if (I.wpi == 2)
+            batch_variant<2, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
+        else
+            batch_variant<1, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
+    } else {
+        if (I.wpi == 4)
+            batch_variant<4, uint64_t, long long>(sP, V, bar, G, I.target, S);
+        else if (I.wpi == 2)
+            batch_variant<2, uint64_t, long long>(sP, V, bar, G, I.target, S);
+        else
+            batch_variant<1, uint64_t, long long>(sP, V, bar, G, I.target, S);
+    }
+}
+
+const void *gom_batch_kernel(int minb)
+{
+    return minb >= 3 ? (const void *)k_batch<3> : (const void *)k_batch<2>;
+}
+
+// After a batched call: each instance's generation count and error word.
+__global__ void k_batch_collect(const GomParams *Ps, GomBatchInst *inst, int B)
+{
+    for (int b = (int)gthread(); b < B; b += (int)gthreads()) {
+        const GomDevState *st = Ps[b].st;
+        inst[b].gens_run = (int32_t)(st->g - st->call_g0);
+        inst[b].err = st->err;
+    }
 }
 
 // Self-test of the grid barrier's bounded wait: `blocks` co-resident blocks

@@ -19,6 +19,11 @@ __global__ void k_order(GomParams P);
 const void *gom_mix_kernel(int wpi, bool narrow);
 // The persistent generation kernel k_run<WPI, mask, delta>(GomParams, int G, int64_t target).
 const void *gom_run_kernel(int wpi, bool narrow);
+// Batched path: instances on block ranges of one cooperative launch.
+// k_batch<MINB>(const GomParams *Ps, const GomBatchInst *inst, GomBarrier *bars, int B, int G, int f_words),
+// registers cut for MINB (2 or 3) resident blocks of 256 threads.
+const void *gom_batch_kernel(int minb);
+__global__ void k_batch_collect(const GomParams *Ps, GomBatchInst *inst, int B);
 __global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigned long long limit_ns);
 __global__ void k_gen_end(GomParams P);
 __global__ void k_export_pop(GomParams P, uint8_t *out);

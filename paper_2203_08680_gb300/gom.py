@@ -78,6 +78,14 @@ SIGNATURES = [
     ("gom_selftest_barrier", C.c_int, [_P, _I32, _I32, _I64, _P, _P]),
     ("gom_fitness_noalloc", C.c_int, [_P, _P, _P, _I32, _P, _I32, _P, _P]),
     ("gom_last_cuda_error", C.c_int, [_P]),
+    ("gom_batch_workspace_bytes", _SZ, [_I32]),
+    ("gom_batch_create", C.c_int, [_P, _I32, _P, _P, _SZ, _P, _P]),
+    ("gom_batch_generation", C.c_int, [_P, _I32, _P, _P]),
+    ("gom_batch_stats", C.c_int, [_P, _I32, _P, _I32, _P]),
+    ("gom_batch_layout", C.c_int, [_P, _I32, _P, _P, _P]),
+    ("gom_batch_destroy", None, [_P]),
+    ("gom_batch_scratch_bytes", _SZ, [_P, _I32]),
+    ("gom_batch_autotune", C.c_int, [_P, _I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P]),
     ("gom_destroy", None, [_P]),
     ("gom_strerror", C.c_char_p, [C.c_int]),
 ]
@@ -144,6 +152,10 @@ class Graph:
 
 def _graph(g):
     return g if isinstance(g, Graph) else Graph(g)
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("min_blocks", C.c_int32)]
 
 
 class Fos:
@@ -349,6 +361,92 @@ def gom_destroy(ctx: Ctx):
     if ctx.h:
         load().gom_destroy(ctx.h)
         ctx.h = None
+
+
+class Batch:
+    """Owning wrapper of a gom_batch_t handle; keeps its contexts and workspace alive."""
+
+    def __init__(self, handle, ctxs, workspace):
+        self.h = handle
+        self.ctxs = list(ctxs)
+        self.workspace = workspace
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gom_batch_destroy(self.h)
+            self.h = None
+
+
+def _ctx_array(ctxs):
+    arr = (C.c_void_p * len(ctxs))()
+    for b, c in enumerate(ctxs):
+        arr[b] = c.h.value if isinstance(c.h, C.c_void_p) else c.h
+    return arr
+
+
+def gom_batch_workspace_bytes(num: int) -> int:
+    return int(load().gom_batch_workspace_bytes(num))
+
+
+def gom_batch_create(ctxs, config=None, workspace=None, stream=None) -> Batch:
+    """ctxs: Ctx handles made on `stream`; config: (warps_per_block, min_blocks)
+    or None; workspace: a CUDA tensor of at least gom_batch_workspace_bytes(len(ctxs))
+    bytes, 256-byte aligned."""
+    arr = _ctx_array(ctxs)
+    cfg = BatchConfig(*config) if config is not None else None
+    nbytes = workspace.numel() * workspace.element_size()
+    h = C.c_void_p()
+    _check(load().gom_batch_create(arr, len(ctxs), C.byref(cfg) if cfg is not None else None, _ptr(workspace),
+                                   nbytes, _stream(stream), C.byref(h)), "gom_batch_create")
+    return Batch(h, ctxs, workspace)
+
+
+def gom_batch_generation(batch: Batch, num_generations: int, targets=None, want_counts: bool = True):
+    """Returns the generations each instance ran (numpy int32), or None when
+    want_counts is False (asynchronous)."""
+    B = len(batch.ctxs)
+    t = None
+    if targets is not None:
+        t = np.ascontiguousarray(targets, dtype=np.int64)
+        assert len(t) == B
+    runs = np.zeros(B, dtype=np.int32) if want_counts else None
+    _check(load().gom_batch_generation(batch.h, num_generations, t.ctypes.data if t is not None else None,
+                                       runs.ctypes.data if runs is not None else None), "gom_batch_generation")
+    return runs
+
+
+def gom_batch_stats(batch: Batch, b: int, capacity: int):
+    arr = (GenStats * max(capacity, 1))()
+    cnt = C.c_int32()
+    _check(load().gom_batch_stats(batch.h, b, arr, capacity, C.byref(cnt)), "gom_batch_stats")
+    return [arr[q].as_dict() for q in range(cnt.value)]
+
+
+def gom_batch_layout(batch: Batch, b: int):
+    b0, nb, grid = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().gom_batch_layout(batch.h, b, C.byref(b0), C.byref(nb), C.byref(grid)), "gom_batch_layout")
+    return int(b0.value), int(nb.value), int(grid.value)
+
+
+def gom_batch_destroy(batch: Batch):
+    if batch.h:
+        load().gom_batch_destroy(batch.h)
+        batch.h = None
+
+
+def gom_batch_scratch_bytes(ctxs) -> int:
+    return int(load().gom_batch_scratch_bytes(_ctx_array(ctxs), len(ctxs)))
+
+
+def gom_batch_autotune(ctxs, configs, generations: int, scratch, stream=None):
+    """Returns (index of the fastest configuration, ms per generation of each)."""
+    cfgs = (BatchConfig * len(configs))(*[BatchConfig(*c) for c in configs])
+    ms = (C.c_double * len(configs))()
+    best = C.c_int32()
+    nbytes = scratch.numel() * scratch.element_size()
+    _check(load().gom_batch_autotune(_ctx_array(ctxs), len(ctxs), cfgs, len(configs), generations, _ptr(scratch),
+                                     nbytes, _stream(stream), C.byref(best), ms), "gom_batch_autotune")
+    return int(best.value), [float(x) for x in ms]
 
 
 # ---------------------------------------------------------------------------

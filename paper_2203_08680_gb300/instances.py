@@ -175,6 +175,22 @@ def empty_graph(n: int) -> Graph:
                  np.zeros(0, dtype=np.int32), f"empty_{n}")
 
 
+def batch_mix(count: int = 256, seed: int = 1, nmin: int = 1000, nmax: int = 65536, dmin: int = 3,
+              dmax: int = 8, pops=(32, 64, 128, 256)):
+    """Shapes of a batch of independent random d-regular Max-Cut instances:
+    n log-uniform in [nmin, nmax] (rounded up to even), d uniform in
+    {dmin..dmax}, population uniform over `pops`, graph and Philox seeds
+    1..count.  Returns a list of (n, d, p, seed); graphs are built with
+    random_regular(n, d, seed)."""
+    idx = np.arange(count, dtype=np.uint64)
+    u = (_hash(seed, 0x2001, idx) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    n = np.ceil(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    n = np.minimum(n + (n & 1), nmax)
+    d = dmin + (_hash(seed, 0x2002, idx) % np.uint64(dmax - dmin + 1)).astype(np.int64)
+    p = np.asarray(pops, dtype=np.int64)[(_hash(seed, 0x2003, idx) % np.uint64(len(pops))).astype(np.int64)]
+    return [(int(n[b]), int(d[b]), int(p[b]), b + 1) for b in range(count)]
+
+
 # The workload shapes of the benchmark configurations, by name.
 def workload(name: str) -> Graph:
     """Named synthetic workloads: 'torus10' (10x10), 'torus100' (100x100),
