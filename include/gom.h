@@ -63,6 +63,8 @@ extern "C" {
 /* FOS kinds for gom_build_fos. */
 #define GOM_FOS_NEIGHBOURHOOD 0 /* F_j = {j} u adj(j), one element per vertex */
 #define GOM_FOS_SINGLETON 1     /* F_j = {j} */
+#define GOM_FOS_BFLT 2          /* bounded fixed linkage tree: UPGMA on the edge weights, sets of
+                                   at most `param` variables (Sec. 4.1) */
 
 /* Options for gom_set_option / gom_get_option. */
 #define GOM_OPT_PERSISTENT 1 /* 1: each gom_generation call is one persistent cooperative
@@ -118,9 +120,21 @@ typedef struct gom_gen_stats {
 
 /*
  * Builds the linkage model (FOS, Sec. 4.1) of a graph.  kind is
- * GOM_FOS_NEIGHBOURHOOD (element j = {j} u adj(j), variables ascending) or
- * GOM_FOS_SINGLETON; param is reserved (pass 0).  Validates the graph
- * (GOM_E_GRAPH).  *out receives a handle to free with gom_fos_destroy.
+ * GOM_FOS_NEIGHBOURHOOD (element j = {j} u adj(j), variables ascending),
+ * GOM_FOS_SINGLETON (param 0 for both), or GOM_FOS_BFLT with param = the
+ * largest linkage set (>= 1).  GOM_FOS_BFLT is the paper's model (Sec. 4.1,
+ * used for every GOMEA version in Sec. 6.1): a fixed linkage tree learned once
+ * by UPGMA with the edge weights as similarity -- from the singletons,
+ * repeatedly merge the two clusters of highest average pairwise weight,
+ * sum over u in A, v in B of w_uv divided by |A||B| -- bounded: a merge above
+ * param variables is never made.  Readings: only clusters joined by an edge
+ * are merged (the tree stops when none fits the bound), the set of all
+ * variables is left out (Sec. 4.1), ties go to the pair of smaller creation
+ * ids (singletons 0..n-1, then merges in order).  Elements: the n
+ * singletons, then the merged sets in creation order, variables ascending.
+ * The mixing kernels take elements of up to GOM_MAX_ELEMENT variables.
+ * Validates the graph (GOM_E_GRAPH).  *out receives a handle to free with
+ * gom_fos_destroy.
  */
 int gom_build_fos(const gom_graph_t *g, int32_t kind, int32_t param, gom_fos_t **out);
 
@@ -325,6 +339,11 @@ typedef struct gom_batch gom_batch_t;
 typedef struct gom_batch_config {
     int32_t warps_per_block; /* 1, 2, 4 or 8 */
     int32_t min_blocks;      /* register budget: 2 (128 registers a thread, no spills) or 3 (85) */
+    int32_t max_blocks;      /* most blocks of the launch (0: every block that can be resident) */
+    int32_t item_cost;       /* block allocation: a warp's time for one element is taken as
+                                item_cost + (population words) x (variables + edges), so
+                                item_cost is the fixed cost of an item (staging, draws,
+                                memory round trips); 0 means 300 */
 } gom_batch_config_t;
 
 /* Device bytes of a batch of `num` instances (their parameter blocks, the
@@ -333,9 +352,10 @@ size_t gom_batch_workspace_bytes(int32_t num);
 
 /*
  * A batch over ctxs[0..num) (num >= 1, each context at most once), all made
- * on cuda_stream on the current device; cfg NULL means {4, 3}.  Blocks go to
- * instances in proportion to their estimated work per generation (at least
- * one each, at most what their largest colour group can use).  d_workspace:
+ * on cuda_stream on the current device; cfg NULL means {4, 3, 0, 0}.  Blocks go
+ * to instances in proportion to their estimated time per generation (the
+ * item_cost model; at least one each, at most what their largest colour group
+ * can use).  d_workspace:
  * caller-owned device memory of gom_batch_workspace_bytes(num) bytes,
  * 256-byte aligned.  The contexts stay the caller's, must outlive the batch
  * and can still be used on their own.  GOM_E_LIMIT if the device cannot hold

@@ -40,6 +40,9 @@
  *     lowest-index individual attaining max f.
  *  R10 random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
  *     (seed low, seed high), counters as in the functions below.
+ *  R11 bounded fixed linkage tree (Sec. 4.1): UPGMA on the edge weights, linked
+ *     pairs only, merges above the bound never made, ties by creation ids
+ *     (orc_build_bflt).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -180,6 +183,87 @@ void orc_build_fos(int32_t n, const int64_t *rp, const int32_t *col, int32_t kin
         if (!placed) evars[pos++] = j;
     }
     eptr[n] = pos;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bounded fixed linkage tree (Sec. 4.1), R11: UPGMA on the Max-Cut graph with
+ * the edge weights as similarity (Sec. 6.1 uses it for every GOMEA version).
+ * Starting from the n singletons, repeatedly merge the pair of clusters with
+ * the highest average pairwise similarity, sum of w_uv over u in A, v in B,
+ * divided by |A||B|.  Readings: only clusters joined by at least one edge are
+ * candidates (non-adjacent pairs have no dependence to link); a merge whose
+ * result would exceed `bound` variables is never made, and the tree stops
+ * when no candidate remains; a cluster holding all n variables is not a
+ * linkage set (Sec. 4.1); ties go to the pair with the smaller first id,
+ * then the smaller second id, ids numbering clusters in creation order
+ * (singletons 0..n-1).  Elements: the singletons, then the merged clusters in
+ * creation order, variables ascending.  Plain O(c^2) rescans per merge: for
+ * the small graphs of the tests.  eptr[2n], evars[n * bound] (upper bounds);
+ * returns the number of elements m. */
+
+/* weight of edge {u,v}, and whether it exists */
+static int edge_weight(const int64_t *rp, const int32_t *col, const int32_t *w, int32_t u, int32_t v,
+                       int64_t *out)
+{
+    for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
+        if (col[e] == v) { *out = w[e]; return 1; }
+    return 0;
+}
+
+int64_t orc_build_bflt(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *w, int32_t bound,
+                       int64_t *eptr, int32_t *evars)
+{
+    int64_t cap = 2 * (int64_t)n;
+    int32_t *size = (int32_t *)calloc((size_t)cap + 1, sizeof(int32_t));
+    uint8_t *alive = (uint8_t *)calloc((size_t)cap + 1, 1);
+    int64_t *mptr = (int64_t *)calloc((size_t)cap + 2, sizeof(int64_t)); /* members of cluster c */
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n * (size_t)(bound > 0 ? bound : 1) + 1));
+    int64_t nc = 0, nm = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        mptr[nc] = nm;
+        mem[nm++] = v;
+        size[nc] = 1;
+        alive[nc] = 1;
+        ++nc;
+    }
+    mptr[nc] = nm;
+    for (;;) {
+        int64_t ba = -1, bb = -1, bs = 0, bn = 1;
+        for (int64_t a = 0; a < nc; ++a) {
+            if (!alive[a]) continue;
+            for (int64_t b = a + 1; b < nc; ++b) {
+                if (!alive[b] || size[a] + size[b] > bound) continue;
+                int64_t S = 0;
+                int linked = 0;
+                for (int64_t x = mptr[a]; x < mptr[a + 1]; ++x)
+                    for (int64_t y = mptr[b]; y < mptr[b + 1]; ++y) {
+                        int64_t wv;
+                        if (edge_weight(rp, col, w, mem[x], mem[y], &wv)) { S += wv; linked = 1; }
+                    }
+                if (!linked) continue;
+                int64_t N = (int64_t)size[a] * size[b];
+                /* S / N > bs / bn, exactly (128-bit products) */
+                if (ba < 0 || (__int128)S * bn > (__int128)bs * N) { ba = a; bb = b; bs = S; bn = N; }
+            }
+        }
+        if (ba < 0 || size[ba] + size[bb] >= n) break; /* nothing to merge, or the root */
+        /* the new cluster: members of both, ascending */
+        int64_t i = mptr[ba], j = mptr[bb];
+        mptr[nc] = nm;
+        while (i < mptr[ba + 1] || j < mptr[bb + 1]) {
+            if (j >= mptr[bb + 1] || (i < mptr[ba + 1] && mem[i] < mem[j])) mem[nm++] = mem[i++];
+            else mem[nm++] = mem[j++];
+        }
+        size[nc] = size[ba] + size[bb];
+        alive[nc] = 1;
+        alive[ba] = alive[bb] = 0;
+        ++nc;
+        mptr[nc] = nm;
+    }
+    for (int64_t c = 0; c <= nc; ++c) eptr[c] = mptr[c];
+    memcpy(evars, mem, sizeof(int32_t) * (size_t)nm);
+    free(size); free(alive); free(mptr); free(mem);
+    return nc;
 }
 
 /* ------------------------------------------------------------------------ */

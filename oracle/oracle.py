@@ -54,6 +54,8 @@ def lib():
         L.orc_fos_total.argtypes = [i32, P, i32]
         L.orc_fos_total.restype = i64
         L.orc_build_fos.argtypes = [i32, P, P, i32, P, P]
+        L.orc_build_bflt.argtypes = [i32, P, P, P, i32, P, P]
+        L.orc_build_bflt.restype = i64
         L.orc_lmig_edges.argtypes = [i32, P, P, i64, P, P, P, i64]
         L.orc_lmig_edges.restype = i64
         L.orc_color.argtypes = [i32, P, P, i64, P, P, P]
@@ -135,6 +137,16 @@ def build_fos(g, kind: int = NEIGHBOURHOOD):
     evars = np.zeros(max(total, 1), dtype=np.int32)
     lib().orc_build_fos(g.n, _p(rp), _p(col), kind, _p(eptr), _p(evars))
     return eptr, evars[:total]
+
+
+def build_bflt(g, bound: int):
+    """Bounded fixed linkage tree: UPGMA on the edge weights (reading R11)."""
+    rp, col, w = _csr(g)
+    n = g.n
+    eptr = np.zeros(2 * n + 2, dtype=np.int64)
+    evars = np.zeros(max(n * max(bound, 1), 1), dtype=np.int32)
+    m = int(lib().orc_build_bflt(n, _p(rp), _p(col), _p(w), bound, _p(eptr), _p(evars)))
+    return eptr[: m + 1].copy(), evars[: eptr[m]].copy()
 
 
 def _fos_arrays(eptr, evars):

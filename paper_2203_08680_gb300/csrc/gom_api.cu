@@ -227,13 +227,14 @@ const char *gom_strerror(int code)
 
 int gom_build_fos(const gom_graph_t *g, int32_t kind, int32_t param, gom_fos_t **out)
 {
-    if (!g || !out || param != 0) return GOM_E_ARG;
-    if (kind != GOM_FOS_NEIGHBOURHOOD && kind != GOM_FOS_SINGLETON) return GOM_E_ARG;
+    if (!g || !out) return GOM_E_ARG;
+    if (kind == GOM_FOS_BFLT ? param < 1 : param != 0) return GOM_E_ARG;
+    if (kind != GOM_FOS_NEIGHBOURHOOD && kind != GOM_FOS_SINGLETON && kind != GOM_FOS_BFLT) return GOM_E_ARG;
     int rc = gomh::validate_graph(g);
     if (rc) return rc;
     std::unique_ptr<gom_fos> fos(new (std::nothrow) gom_fos());
     if (!fos) return GOM_E_ARG;
-    rc = gomh::build_fos(g, kind, fos.get());
+    rc = kind == GOM_FOS_BFLT ? gomh::build_bflt(g, param, fos.get()) : gomh::build_fos(g, kind, fos.get());
     if (rc) return rc;
     *out = fos.release();
     return GOM_OK;
@@ -346,42 +347,18 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     int dev = 0;
     GOM_CUDA(c, cudaGetDevice(&dev));
     GOM_CUDA(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-    // Work split: one warp per element walking all its words in groups of
-    // wpi = min(W, 4) words, or, when the largest colour group has fewer than
-    // about 4 elements per resident warp (~24 per SM), one warp per (element,
-    // word group), so that the static stride over items stays balanced.
+    // Work split for the whole grid (~24 resident warps per SM).
     const int wv = (pop + 31) / 32;
-    int wpi = std::min(c->W, 4);
-    int split = 0;
-    if (max_group < static_cast<int64_t>(c->sms) * 24 * 4 && wv > 1) {
-        split = 1;
-        if ((wv + wpi - 1) / wpi == 1) wpi = 1;
-    }
+    int wpi = 1, split = 0;
+    item_split(c->W, pop, max_group, static_cast<int64_t>(c->sms) * 24, &wpi, &split);
     const int nwg = (wv + wpi - 1) / wpi;
     const int per = split ? nwg : 1;
     c->mix_fn = gom_mix_kernel(wpi, narrow);
-    // One staging slice (one mixing item) in shared memory -- the one
-    // definition of its layout; the kernels take these offsets (words): an
-    // 8-word item header, the element's variables, their outside-edge starts
-    // (s+1), their outside weight sums (int64), the rows of P on the element
-    // (W words each), the pattern table (32 W masks of 4 or 8 bytes), its run
-    // starts (W words), one record per edge (code, weight, WPI parent words;
-    // 4 or 8 words), and in stage-all mode the item's donor start positions
-    // (one int per individual of its words).  Every offset is a multiple of 4
-    // words (16 bytes).
-    const int es = wpi == 4 ? 8 : 4;
-    auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
-    const int64_t smax = tabs.max_s;
-    const int64_t off_fv = 8;
-    const int64_t off_seg = off_fv + round4(smax);
-    const int64_t off_wout = off_seg + round4(smax + 1);
-    const int64_t off_pr = off_wout + round4(2 * smax);
-    const int64_t off_pat = off_pr + round4(smax * c->W);
-    const int64_t off_rs = off_pat + int64_t(32) * c->W * (narrow ? 1 : 2);
-    const int64_t off_edge = off_rs + round4(c->W);
-    const int64_t off_ds = off_edge + tabs.max_edges * es;
-    const int64_t base_words = off_ds;
-    const int64_t all_words = off_ds + int64_t(32) * wpi * (split ? 1 : nwg);
+    const SliceLayout SL = slice_layout(tabs.max_s, tabs.max_edges, c->W, wpi, narrow, split != 0, nwg);
+    const int64_t off_fv = SL.off_fv, off_seg = SL.off_seg, off_wout = SL.off_wout, off_pr = SL.off_pr;
+    const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_edge = SL.off_edge, off_ds = SL.off_ds;
+    const int64_t base_words = SL.base_words;
+    const int64_t all_words = SL.all_words;
     constexpr int64_t kSmemBudget = 200 * 1024;
     const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (base_words * 4)));
     if (warps_per_block < 1) return GOM_E_LIMIT;
@@ -445,14 +422,12 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->wpi = wpi;
     c->narrow = narrow;
     c->max_items = std::max<int64_t>(1, max_group * per);
-    {
-        // per-trial cost ~ element variables + edges + a constant, summed over elements
-        double per_gen = 0.0;
-        for (int64_t q = 0; q < c->m; ++q) {
-            const int32_t *h = tabs.hdr.data() + 8 * q;
-            per_gen += 8.0 + (h[3] & 0xFF) + (h[3] >> 8) + h[4];
-        }
-        c->work = per_gen * pop;
+    c->max_group = max_group;
+    c->max_s = tabs.max_s;
+    c->max_edges = tabs.max_edges;
+    for (int64_t q = 0; q < c->m; ++q) {
+        const int32_t *h = tabs.hdr.data() + 8 * q;
+        c->sum_se += (h[3] & 0xFF) + (h[3] >> 8) + h[4];
     }
     // dynamic item claims: faster warps take more items (in stage-all mode
     // every warp has at most one item per group and the schedule is moot)

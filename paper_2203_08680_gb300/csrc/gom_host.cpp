@@ -10,7 +10,9 @@
 #include <atomic>
 #include <cstring>
 #include <numeric>
+#include <queue>
 #include <thread>
+#include <utility>
 #include <vector_types.h>
 
 #include "gom_internal.h"
@@ -109,6 +111,92 @@ int build_fos(const gom_graph_t *g, int32_t kind, gom_fos *out)
             std::memcpy(dst + split + 1, nb + split, sizeof(int32_t) * (d - split));
         }
     });
+    return GOM_OK;
+}
+
+int build_bflt(const gom_graph_t *g, int32_t bound, gom_fos *out)
+{
+    if (bound < 1) return GOM_E_ARG;
+    const int32_t n = g->num_vertices;
+    // candidate merge: clusters a < b joined by at least one edge, summed weight S, N = |a| |b|
+    struct Cand {
+        int64_t S, N;
+        int32_t a, b;
+    };
+    // lower priority: smaller average S/N (exact, 128-bit products), then larger a, then larger b
+    auto lower = [](const Cand &x, const Cand &y) {
+        const __int128 lx = static_cast<__int128>(x.S) * y.N, ly = static_cast<__int128>(y.S) * x.N;
+        if (lx != ly) return lx < ly;
+        if (x.a != y.a) return x.a > y.a;
+        return x.b > y.b;
+    };
+    std::priority_queue<Cand, std::vector<Cand>, decltype(lower)> pq(lower);
+    std::vector<int32_t> size(n, 1);
+    std::vector<uint8_t> alive(n, 1);
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> adj(n); // neighbour cluster -> weight sum, ascending
+    std::vector<std::vector<int32_t>> members(n);
+    for (int32_t v = 0; v < n; ++v) {
+        members[v] = {v};
+        for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {
+            adj[v].push_back({g->col[e], g->weight[e]});
+            if (v < g->col[e] && bound >= 2) pq.push({g->weight[e], 1, v, g->col[e]});
+        }
+    }
+    while (!pq.empty()) {
+        const Cand top = pq.top();
+        pq.pop();
+        if (!alive[top.a] || !alive[top.b]) continue; // stale: a cluster was merged since
+        const int32_t a = top.a, b = top.b;
+        if (size[a] + size[b] >= n) break; // the set of all variables is no linkage set
+        const int32_t c = static_cast<int32_t>(size.size());
+        size.push_back(size[a] + size[b]);
+        alive.push_back(1);
+        alive[a] = alive[b] = 0;
+        std::vector<int32_t> mc(members[a].size() + members[b].size());
+        std::merge(members[a].begin(), members[a].end(), members[b].begin(), members[b].end(), mc.begin());
+        members.push_back(std::move(mc));
+        // neighbours of the new cluster: those of a and b (summed), without a and b
+        std::vector<std::pair<int32_t, int64_t>> ac;
+        {
+            const auto &A = adj[a], &Bv = adj[b];
+            size_t i = 0, j = 0;
+            while (i < A.size() || j < Bv.size()) {
+                std::pair<int32_t, int64_t> x;
+                if (j >= Bv.size() || (i < A.size() && A[i].first < Bv[j].first))
+                    x = A[i++];
+                else if (i >= A.size() || Bv[j].first < A[i].first)
+                    x = Bv[j++];
+                else {
+                    x = {A[i].first, A[i].second + Bv[j].second};
+                    ++i;
+                    ++j;
+                }
+                if (x.first != a && x.first != b) ac.push_back(x);
+            }
+        }
+        for (const auto &xs : ac) {
+            auto &ax = adj[xs.first];
+            ax.erase(std::remove_if(ax.begin(), ax.end(),
+                                    [&](const std::pair<int32_t, int64_t> &y) { return y.first == a || y.first == b; }),
+                     ax.end());
+            ax.push_back({c, xs.second}); // c is the largest id: the list stays ascending
+            if (size[c] + size[xs.first] <= bound)
+                pq.push({xs.second, static_cast<int64_t>(size[c]) * size[xs.first], xs.first, c});
+        }
+        adj.push_back(std::move(ac));
+        adj[a].clear();
+        adj[a].shrink_to_fit();
+        adj[b].clear();
+        adj[b].shrink_to_fit();
+    }
+    out->n = n;
+    out->m = static_cast<int64_t>(members.size());
+    out->k = -1;
+    out->eptr.assign(static_cast<size_t>(out->m) + 1, 0);
+    for (int64_t j = 0; j < out->m; ++j) out->eptr[j + 1] = out->eptr[j] + static_cast<int64_t>(members[j].size());
+    out->evars.resize(static_cast<size_t>(out->eptr[out->m]));
+    for (int64_t j = 0; j < out->m; ++j)
+        std::copy(members[j].begin(), members[j].end(), out->evars.begin() + out->eptr[j]);
     return GOM_OK;
 }
 

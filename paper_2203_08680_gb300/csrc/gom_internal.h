@@ -28,6 +28,7 @@ namespace gomh {
 // Host set-up steps (gom_host.cpp).
 int validate_graph(const gom_graph_t *g);
 int build_fos(const gom_graph_t *g, int32_t kind, gom_fos *out);
+int build_bflt(const gom_graph_t *g, int32_t bound, gom_fos *out);
 int check_fos(int32_t n, const gom_fos &fos);
 int color_fos(const gom_graph_t *g, gom_fos *fos);
 

@@ -18,6 +18,7 @@ from . import build as _build
 GOM_OK = 0
 GOM_FOS_NEIGHBOURHOOD = 0
 GOM_FOS_SINGLETON = 1
+GOM_FOS_BFLT = 2
 GOM_MAX_POPULATION = 1024
 GOM_MAX_ELEMENT = 64
 GOM_OPT_PERSISTENT = 1
@@ -155,7 +156,8 @@ def _graph(g):
 
 
 class BatchConfig(C.Structure):
-    _fields_ = [("warps_per_block", C.c_int32), ("min_blocks", C.c_int32)]
+    _fields_ = [("warps_per_block", C.c_int32), ("min_blocks", C.c_int32), ("max_blocks", C.c_int32),
+                ("item_cost", C.c_int32)]
 
 
 class Fos:
@@ -389,8 +391,8 @@ def gom_batch_workspace_bytes(num: int) -> int:
 
 
 def gom_batch_create(ctxs, config=None, workspace=None, stream=None) -> Batch:
-    """ctxs: Ctx handles made on `stream`; config: (warps_per_block, min_blocks)
-    or None; workspace: a CUDA tensor of at least gom_batch_workspace_bytes(len(ctxs))
+    """ctxs: Ctx handles made on `stream`; config: (warps_per_block, min_blocks[,
+    max_blocks[, item_cost]]) or None; workspace: a CUDA tensor of at least gom_batch_workspace_bytes(len(ctxs))
     bytes, 256-byte aligned."""
     arr = _ctx_array(ctxs)
     cfg = BatchConfig(*config) if config is not None else None

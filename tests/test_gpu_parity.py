@@ -342,3 +342,26 @@ def test_runs_of_identical_individuals(oracle, p):
             _assert_same_stats(gst[0], ost)
     for P in Ps:
         _assert_same_state(_gpu_state(P), run.get())
+
+
+@pytest.mark.parametrize("name,bound,p", [("torus12", 10, 50), ("rreg300_d5", 20, 100), ("rreg200_d4", 64, 40)])
+def test_bflt_fos(oracle, name, bound, p):
+    """The paper's own linkage model (Sec. 4.1): a bounded fixed linkage tree
+    learned by UPGMA on the edge weights -- nested sets of 1 to `bound`
+    variables (64: 64-bit masks) -- on both execution paths, every generation."""
+    g = {"torus12": lambda: I.torus2d(12, seed=21), "rreg300_d5": lambda: I.random_regular(300, 5, seed=22),
+         "rreg200_d4": lambda: I.random_regular(200, 4, seed=23)}[name]()
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
+    ep, ev = oracle.build_bflt(g, bound)
+    k, co = oracle.color(g, ep, ev)
+    run = oracle.Run(g, ep, ev, co, k, p, 31)
+    Ps = [gom.Population(g, p, 31, fos=fos, persistent=True), gom.Population(g, p, 31, fos=fos, persistent=False)]
+    for P in Ps:
+        assert P.k == k
+        _assert_same_state(_gpu_state(P), run.get(), "init")
+    for gen in range(6):
+        ost = run.generation()
+        for P in Ps:
+            gst, _ = P.generation(1)
+            _assert_same_stats(gst[0], ost)
+            _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")

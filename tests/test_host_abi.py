@@ -72,6 +72,30 @@ def test_host_fos_and_coloring_equal_oracle(oracle, name, kind):
         assert np.array_equal(grp, np.nonzero(co == c)[0])
 
 
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("bound", [1, 2, 5, 10, 64])
+def test_host_bflt_equal_oracle(oracle, name, bound):
+    """The bounded fixed linkage tree (UPGMA on the weights) and its colouring
+    equal the oracle's."""
+    g = GRAPHS[name]()
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
+    k = gom.gom_color_fos(g, fos)
+    ex = gom.gom_fos_export(fos)
+    ep, ev = oracle.build_bflt(g, bound)
+    assert np.array_equal(ex["elem_ptr"], ep)
+    assert np.array_equal(ex["elem_vars"], ev)
+    ko, co = oracle.color(g, ep, ev)
+    assert k == ko and np.array_equal(ex["color_of_elem"], co)
+
+
+def test_bflt_arguments():
+    g = I.torus2d(5)
+    with pytest.raises(gom.GomError):
+        gom.gom_build_fos(g, gom.GOM_FOS_BFLT, 0)
+    with pytest.raises(gom.GomError):
+        gom.gom_build_fos(g, gom.GOM_FOS_NEIGHBOURHOOD, 3)
+
+
 def test_custom_fos_figure2_coloring(oracle):
     # the linkage tree of the paper's Figure 2 over the VIG of Figure 1
     g = I.from_edges(5, [0, 0, 1, 2, 2, 3], [1, 2, 2, 3, 4, 4], np.ones(6, dtype=np.int32))

@@ -456,3 +456,94 @@ def test_multithreaded_generation_equals_single_threaded(oracle):
     for key in ("pop", "f", "xe"):
         assert np.array_equal(ra[key], rb[key])
     assert ra["fe"] == rb["fe"] and ra["g"] == rb["g"]
+
+
+# ---------------------------------------------------------------------------
+# Bounded fixed linkage tree (Sec. 4.1): UPGMA on the edge weights
+
+def _bflt_sets(oracle, g, bound):
+    ep, ev = oracle.build_bflt(g, bound)
+    return [tuple(int(x) for x in ev[ep[j]:ep[j + 1]]) for j in range(len(ep) - 1)]
+
+
+def test_bflt_hand_example(oracle):
+    """Path 0-1-2-3-4 with weights 5, 1, 5, 2, worked by hand from the UPGMA
+    definition: {0,1} (average 5, before the tied {2,3} by the smaller id),
+    {2,3} (5), then {2,3,4} (2/2 = 1 beats {0,1}+{2,3} at 1/4); the last merge
+    would hold all five variables and is left out."""
+    g = I.from_edges(5, np.array([0, 1, 2, 3]), np.array([1, 2, 3, 4]), np.array([5, 1, 5, 2]))
+    single = [(0,), (1,), (2,), (3,), (4,)]
+    assert _bflt_sets(oracle, g, 1) == single
+    assert _bflt_sets(oracle, g, 2) == single + [(0, 1), (2, 3)]
+    assert _bflt_sets(oracle, g, 3) == single + [(0, 1), (2, 3), (2, 3, 4)]
+    assert _bflt_sets(oracle, g, 4) == single + [(0, 1), (2, 3), (2, 3, 4)]
+    assert _bflt_sets(oracle, g, 5) == single + [(0, 1), (2, 3), (2, 3, 4)]
+    # one more vertex (edge 4-5 of weight 1): {4,5} and {4,{2,3}} tie at
+    # average 1, the smaller second id (vertex 5) wins; then {2,3}+{4,5}
+    # (2/4) beats {0,1}+{2,3} (1/4); the six-variable root is left out
+    g6 = I.from_edges(6, np.array([0, 1, 2, 3, 4]), np.array([1, 2, 3, 4, 5]), np.array([5, 1, 5, 2, 1]))
+    assert _bflt_sets(oracle, g6, 6) == [(i,) for i in range(6)] + [(0, 1), (2, 3), (4, 5), (2, 3, 4, 5)]
+
+
+def test_bflt_average_not_single_linkage(oracle):
+    """After {0,1} forms (weight 50), vertex 2 (one edge of 10 to 0) has
+    average 10/2 = 5 to it and vertex 3 (edges of 6 to 0 and to 1) has 12/2 = 6:
+    average linkage takes 3 first; single linkage would take 2."""
+    u = np.array([0, 0, 0, 1])
+    v = np.array([1, 2, 3, 3])
+    w = np.array([50, 10, 6, 6])
+    g = I.from_edges(5, np.append(u, 2), np.append(v, 4), np.append(w, 1))
+    sets = _bflt_sets(oracle, g, 3)
+    assert sets[5] == (0, 1) and sets[6] == (0, 1, 3)
+
+
+def _upgma_replay(g, bound):
+    """Independent replay with exact fractions: at every step the merged pair
+    is the best linked pair under the rule (highest average, then smaller ids)."""
+    from fractions import Fraction
+    n = g.n
+    W = {}
+    for a in range(n):
+        for e in range(g.row_ptr[a], g.row_ptr[a + 1]):
+            W[(a, int(g.col[e]))] = int(g.weight[e])
+    clusters = {i: (i,) for i in range(n)}
+    out = [(i,) for i in range(n)]
+    nxt = n
+    while True:
+        best = None
+        ids = sorted(clusters)
+        for i, a in enumerate(ids):
+            for b in ids[i + 1:]:
+                A, B = clusters[a], clusters[b]
+                if len(A) + len(B) > bound:
+                    continue
+                pairs = [(x, y) for x in A for y in B if (x, y) in W]
+                if not pairs:
+                    continue
+                avg = Fraction(sum(W[p] for p in pairs), len(A) * len(B))
+                if best is None or avg > best[0]:
+                    best = (avg, a, b)
+        if best is None or len(clusters[best[1]]) + len(clusters[best[2]]) >= n:
+            return out
+        merged = tuple(sorted(clusters.pop(best[1]) + clusters.pop(best[2])))
+        clusters[nxt] = merged
+        out.append(merged)
+        nxt += 1
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("bound", [2, 4, 7, 40])
+def test_bflt_replay_and_tree_properties(oracle, seed, bound):
+    g = I.random_regular(24, 3, seed=seed, wmin=-5, wmax=9)
+    sets = _bflt_sets(oracle, g, bound)
+    assert sets == _upgma_replay(g, bound)
+    n = g.n
+    assert sets[:n] == [(i,) for i in range(n)]  # complete: every singleton
+    for j, s in enumerate(sets[n:], start=n):
+        assert 2 <= len(s) <= bound and len(s) < n
+        # the union of exactly two disjoint earlier sets (Sec. 4.1)
+        earlier = [set(x) for x in sets[:j]]
+        splits = [(a, b) for ia, a in enumerate(earlier) for b in earlier[ia + 1:]
+                  if not (a & b) and (a | b) == set(s)]
+        assert len(splits) >= 1
+    assert len(set(sets)) == len(sets)
