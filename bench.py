@@ -56,7 +56,8 @@ BATCH_WORKLOADS = {
                 "log-uniform in [1000, 65536] (even), d uniform in 3..8, int32 weights U[1,100], pop uniform "
                 "over {32, 64, 128, 256}, graph and Philox seeds 1..256",
 }
-BATCH_CONFIGS = [(1, 2), (2, 2), (2, 3), (4, 2), (4, 3), (8, 3)]
+# autotuner candidates: (warps per block, register budget in resident blocks, grid cap, item cost)
+BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300)]
 SEED = 1
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "GOM trials/sec (plain parallel GOM, weighted Max-Cut)"
@@ -495,7 +496,7 @@ def run_batch(args, wl, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl, "description": BATCH_WORKLOADS[wl], "instances": len(pops),
                    "trials_per_generation": trials_per_step, "batch_config": list(BATCH_CONFIGS[best]),
-                   "autotune_ms_per_generation": dict(zip([f"{w}x{m}" for w, m in BATCH_CONFIGS], tune_ms)),
+                   "autotune_ms_per_generation": dict(zip(["x".join(map(str, c)) for c in BATCH_CONFIGS], tune_ms)),
                    "grid": gom.gom_batch_layout(batch, 0)[2],
                    "l2": "flushed between timed generations (2x L2 buffer write)",
                    "parallelism": f"replicas{world}"},

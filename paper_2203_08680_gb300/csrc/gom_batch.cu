@@ -20,7 +20,7 @@ struct gom_batch {
     std::vector<gom_ctx *> ctx;
     cudaStream_t stream = nullptr;
     int32_t B = 0;
-    gom_batch_config_t cfg{4, 3};
+    gom_batch_config_t cfg{4, 3, 0, 0};
     const void *fn = nullptr;  // k_batch<min_blocks>
     int grid = 0;              // blocks of the launch
     int threads = 0;           // threads per block
@@ -61,21 +61,43 @@ BatchLayout batch_layout(int32_t num)
 bool valid_config(const gom_batch_config_t &c)
 {
     const int w = c.warps_per_block;
-    return (w == 1 || w == 2 || w == 4 || w == 8) && (c.min_blocks == 2 || c.min_blocks == 3);
+    return (w == 1 || w == 2 || w == 4 || w == 8) && (c.min_blocks == 2 || c.min_blocks == 3) && c.max_blocks >= 0 &&
+           c.item_cost >= 0;
+}
+
+// Items of the largest colour group of an instance when split as finely as
+// item_split allows (one warp per (element, word group)).
+int64_t max_split_items(const gom_ctx *c)
+{
+    int wpi = 1, split = 0;
+    item_split(c->W, c->p, c->max_group, INT64_MAX / 8, &wpi, &split);
+    const int wv = (c->p + 31) / 32;
+    return c->max_group * (split ? (wv + wpi - 1) / wpi : 1);
+}
+
+// Estimated warp time of one generation of an instance: per element, a fixed
+// item cost plus (population words) x (variables + edges).
+double instance_cost(const gom_ctx *c, int item_cost)
+{
+    const int wv = (c->p + 31) / 32;
+    return static_cast<double>(c->m) * item_cost + static_cast<double>(wv) * c->sum_se;
 }
 
 // Blocks per instance: one each, then one at a time to the instance with the
-// largest estimated work per block, up to what its largest colour group can
+// largest estimated time per block, up to what its largest colour group can
 // use (one warp per item) or until the device is full.
-std::vector<int32_t> allocate_blocks(const std::vector<gom_ctx *> &ctx, int total_blocks, int warps_per_block)
+std::vector<int32_t> allocate_blocks(const std::vector<gom_ctx *> &ctx, int total_blocks, int warps_per_block,
+                                     int item_cost)
 {
     const size_t B = ctx.size();
     std::vector<int32_t> nb(B, 1);
+    std::vector<double> cost(B);
     std::priority_queue<std::pair<double, size_t>> heap;
     std::vector<int64_t> need(B);
     for (size_t b = 0; b < B; ++b) {
-        need[b] = (ctx[b]->max_items + warps_per_block - 1) / warps_per_block;
-        if (need[b] > 1) heap.push({ctx[b]->work, b});
+        cost[b] = instance_cost(ctx[b], item_cost);
+        need[b] = (max_split_items(ctx[b]) + warps_per_block - 1) / warps_per_block;
+        if (need[b] > 1) heap.push({cost[b], b});
     }
     int64_t left = static_cast<int64_t>(total_blocks) - static_cast<int64_t>(B);
     while (left > 0 && !heap.empty()) {
@@ -83,7 +105,7 @@ std::vector<int32_t> allocate_blocks(const std::vector<gom_ctx *> &ctx, int tota
         heap.pop();
         ++nb[b];
         --left;
-        if (nb[b] < need[b]) heap.push({ctx[b]->work / nb[b], b});
+        if (nb[b] < need[b]) heap.push({cost[b] / nb[b], b});
     }
     return nb;
 }
@@ -98,7 +120,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
                      size_t ws_bytes, void *cuda_stream, gom_batch_t **out)
 {
     if (!ctxs || num < 1 || !out) return GOM_E_ARG;
-    const gom_batch_config_t conf = cfg ? *cfg : gom_batch_config_t{4, 3};
+    const gom_batch_config_t conf = cfg ? *cfg : gom_batch_config_t{4, 3, 0, 0};
     if (!valid_config(conf)) return GOM_E_ARG;
     const BatchLayout L = batch_layout(num);
     if (!d_workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
@@ -121,13 +143,21 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
 
     // shared memory: the fitness accumulators (32 W of the widest instance,
     // int64), then one staging slice per warp (the largest slice of any
-    // instance), or the colour-group keys of the instance with most colours
+    // instance, whichever item split its allocation gets), or the colour-group
+    // keys of the instance with most colours
     int maxW = 1, maxk = 1;
     int64_t max_warp_words = 8;
     for (gom_ctx *c : cs) {
         maxW = std::max(maxW, c->W);
         maxk = std::max(maxk, c->k);
-        max_warp_words = std::max<int64_t>(max_warp_words, c->prm.warp_smem);
+        const int wv = (c->p + 31) / 32;
+        for (int64_t warps : {int64_t(1), INT64_MAX / 8}) {
+            int wpi = 1, split = 0;
+            item_split(c->W, c->p, c->max_group, warps, &wpi, &split);
+            const SliceLayout SL =
+                slice_layout(c->max_s, c->max_edges, c->W, wpi, c->narrow, split != 0, (wv + wpi - 1) / wpi);
+            max_warp_words = std::max<int64_t>(max_warp_words, SL.base_words);
+        }
     }
     const int32_t f_words = 2 * 32 * maxW;
     const int64_t slices = std::max<int64_t>(int64_t(8) * maxk,
@@ -140,7 +170,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
     GOM_CUDA(nullptr, raise_smem_limit(fn, static_cast<size_t>(smem)));
     int occ = 0;
     GOM_CUDA(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, static_cast<size_t>(smem)));
-    const int total = sms * occ;
+    const int total = conf.max_blocks > 0 ? std::min(sms * occ, conf.max_blocks) : sms * occ;
     if (total < num) return GOM_E_LIMIT;
 
     std::unique_ptr<gom_batch> bt(new (std::nothrow) gom_batch());
@@ -159,22 +189,39 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
     B->d_inst = reinterpret_cast<GomBatchInst *>(base + L.inst);
     B->d_bars = reinterpret_cast<GomBarrier *>(base + L.bars);
 
-    const std::vector<int32_t> nb = allocate_blocks(cs, total, conf.warps_per_block);
+    const std::vector<int32_t> nb =
+        allocate_blocks(cs, total, conf.warps_per_block, conf.item_cost > 0 ? conf.item_cost : 300);
     B->params.resize(num);
     B->inst.resize(num);
     int32_t blk = 0;
     for (int32_t b = 0; b < num; ++b) {
-        GomParams P = cs[b]->prm;
+        const gom_ctx *c = cs[b];
+        // the item split for this instance's warps, and its slice layout
+        int wpi = 1, split = 0;
+        item_split(c->W, c->p, c->max_group, int64_t(nb[b]) * conf.warps_per_block, &wpi, &split);
+        const int wv = (c->p + 31) / 32;
+        const SliceLayout SL =
+            slice_layout(c->max_s, c->max_edges, c->W, wpi, c->narrow, split != 0, (wv + wpi - 1) / wpi);
+        GomParams P = c->prm;
         P.stage_all = 0; // one staging slice per warp
+        P.split = split;
+        P.warp_smem = static_cast<int32_t>(SL.base_words);
+        P.off_fv = static_cast<int32_t>(SL.off_fv);
+        P.off_seg = static_cast<int32_t>(SL.off_seg);
+        P.off_wout = static_cast<int32_t>(SL.off_wout);
+        P.off_pr = static_cast<int32_t>(SL.off_pr);
+        P.off_pat = static_cast<int32_t>(SL.off_pat);
+        P.off_rs = static_cast<int32_t>(SL.off_rs);
+        P.off_edge = static_cast<int32_t>(SL.off_edge);
+        P.off_ds = static_cast<int32_t>(SL.off_ds);
         P.dyn = 1;
-        P.trace = nullptr;
-        P.bar = B->d_bars + b;
+        P.bar = B->d_bars + b; // (P.trace: the context's phase trace, when switched on)
         B->params[b] = P;
         GomBatchInst &I = B->inst[b];
         I = GomBatchInst{};
         I.blk0 = blk;
         I.nblk = nb[b];
-        I.wpi = cs[b]->wpi;
+        I.wpi = wpi;
         I.narrow = cs[b]->narrow ? 1 : 0;
         I.target = INT64_MAX;
         blk += nb[b];

@@ -39,7 +39,10 @@ struct gom_ctx {
     int wpi = 1;                 // words per mixing item
     bool narrow = true;          // 32-bit masks and deltas
     int64_t max_items = 1;       // mixing items of the largest colour group
-    double work = 0.0;           // cost estimate of one generation (trial-weighted element sizes)
+    double sum_se = 0.0;         // sum over elements of (variables + edges)
+    int64_t max_group = 1;       // elements of the largest colour group
+    int64_t max_s = 0;           // variables of the largest element
+    int64_t max_edges = 0;       // most edges of one element
     char *base = nullptr;        // the workspace
     size_t state_bytes = 0;      // its state arrays: [0, state_bytes) (population, fitness, elitist, ...)
 };
@@ -49,6 +52,56 @@ inline int cuda_fail(gom_ctx *ctx, cudaError_t e)
 {
     if (ctx) ctx->last_cuda = static_cast<int>(e);
     return GOM_E_CUDA;
+}
+
+// One staging slice (one mixing item) in shared memory -- the one definition
+// of its layout; the kernels take these offsets (32-bit words): an 8-word
+// item header, the element's variables, their outside-edge starts (s+1),
+// their outside weight sums (int64), the rows of P on the element (W words
+// each), the pattern table (32 W masks of 4 or 8 bytes), its run starts (W
+// words), one record per edge (code, weight, WPI parent words; 4 or 8
+// words), and in stage-all mode the item's donor start positions (one int
+// per individual of its words).  Every offset is a multiple of 4 words.
+struct SliceLayout {
+    int64_t off_fv, off_seg, off_wout, off_pr, off_pat, off_rs, off_edge, off_ds;
+    int64_t base_words; // a slice without the donor starts
+    int64_t all_words;  // with them (stage-all mode)
+};
+
+inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi, bool narrow, bool split,
+                                int nwg)
+{
+    auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    const int es = wpi == 4 ? 8 : 4;
+    SliceLayout L{};
+    L.off_fv = 8;
+    L.off_seg = L.off_fv + round4(max_s);
+    L.off_wout = L.off_seg + round4(max_s + 1);
+    L.off_pr = L.off_wout + round4(2 * max_s);
+    L.off_pat = L.off_pr + round4(max_s * W);
+    L.off_rs = L.off_pat + int64_t(32) * W * (narrow ? 1 : 2);
+    L.off_edge = L.off_rs + round4(W);
+    L.off_ds = L.off_edge + max_edges * es;
+    L.base_words = L.off_ds;
+    L.all_words = L.off_ds + int64_t(32) * wpi * (split ? 1 : nwg);
+    return L;
+}
+
+// Words per item and split mode for p individuals when `warps` warps share
+// the items of the largest colour group of `max_group` elements: one warp per
+// element walking all its words in groups of min(W, 4) words, or, with fewer
+// than about 4 elements per warp, one warp per (element, word group) so that
+// the warps stay busy (then single words if the population has only one
+// group of min(W, 4) words).
+inline void item_split(int W, int32_t p, int64_t max_group, int64_t warps, int *wpi, int *split)
+{
+    const int wv = (p + 31) / 32;
+    *wpi = W < 4 ? W : 4;
+    *split = 0;
+    if (max_group < 4 * warps && wv > 1) {
+        *split = 1;
+        if ((wv + *wpi - 1) / *wpi == 1) *wpi = 1;
+    }
 }
 
 // Raises a kernel's dynamic shared memory limit to at least `bytes`, never
