@@ -377,6 +377,54 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
 int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int64_t *targets,
                          int32_t *generations_run);
 
+/* As gom_batch_generation, with a generation count per instance:
+ * num_generations[b] (host [num], each >= 0) for instance b. */
+int gom_batch_generation_each(gom_batch_t *batch, const int32_t *num_generations, const int64_t *targets,
+                              int32_t *generations_run);
+
+/* ---------------------------------------------------------------------------
+ * Interleaved Multi-start Scheme (Sec. 6.3): populations P_0, P_1, ... of
+ * base_pop * 2^i individuals (up to max_pop), P_i seeded with seed + i; one
+ * generation of P_i is made each time P_{i-1} has made c more generations (the
+ * paper's default c = 4).  All populations are made at creation (a population
+ * made later would be the same: its initialisation depends on its seed only)
+ * and run together on the batched path.
+ */
+typedef struct gom_ims gom_ims_t;
+
+typedef struct gom_ims_result {
+    int64_t steps;              /* generations made by P_0 so far */
+    int64_t best_fitness;       /* best fitness of any generation of this call */
+    int32_t reached;            /* 1 if a generation of this call reached the target */
+    int32_t reached_population; /* the first to reach it in the scheme's order, -1 if none */
+    int64_t reached_step;       /* the P_0 generation count at which that happened */
+    int64_t reached_generation; /* that population's generation index */
+} gom_ims_result_t;
+
+/* Device bytes for gom_ims_create (every population's workspace and the batch). */
+size_t gom_ims_workspace_bytes(const gom_graph_t *g, const gom_fos_t *fos, int32_t base_pop, int32_t max_pop);
+
+/* The scheme on a coloured FOS; base_pop >= 2, c >= 1, max_pop <= GOM_MAX_POPULATION.
+ * d_workspace: caller-owned, gom_ims_workspace_bytes bytes, 256-byte aligned. */
+int gom_ims_create(const gom_graph_t *g, const gom_fos_t *fos, int32_t base_pop, int32_t c, int32_t max_pop,
+                   uint64_t seed, void *d_workspace, size_t ws_bytes, void *cuda_stream, gom_ims_t **out);
+
+/*
+ * Advances the scheme by `steps` generations of P_0 (0..1024), every other
+ * population by its share, in one batched launch.  A population that reaches
+ * `target` stops there; res (host, may be NULL) reports the first reach in the
+ * scheme's own order -- P_i's r-th generation comes at P_0's generation
+ * r * c^i, after those of the smaller populations -- and the best fitness.
+ * The scheme as stated stops every population at that first reach; here the
+ * other populations run on to their own share or target.  Waits.
+ */
+int gom_ims_run(gom_ims_t *ims, int32_t steps, int64_t target, gom_ims_result_t *res);
+
+/* Population i of the scheme (owned by it), for export or inspection. */
+int gom_ims_population(gom_ims_t *ims, int32_t i, gom_ctx_t **ctx);
+int32_t gom_ims_num_populations(const gom_ims_t *ims);
+void gom_ims_destroy(gom_ims_t *ims);
+
 /* Counters of the generations instance b ran in the last call, into
  * host_stats[0..capacity); *count receives their number.  Waits. */
 int gom_batch_stats(gom_batch_t *batch, int32_t b, gom_gen_stats_t *host_stats, int32_t capacity, int32_t *count);

@@ -237,24 +237,26 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
     return GOM_OK;
 }
 
-int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int64_t *targets,
-                         int32_t *generations_run)
+namespace {
+
+int batch_run(gom_batch *B, int32_t G, const int32_t *gens, const int64_t *targets, int32_t *generations_run)
 {
-    if (!batch || num_generations < 0) return GOM_E_ARG;
-    gom_batch *B = batch;
-    if (num_generations == 0) {
+    if (G == 0) {
         if (generations_run) std::fill(generations_run, generations_run + B->B, 0);
         return GOM_OK;
     }
-    for (int32_t b = 0; b < B->B; ++b) B->inst[b].target = targets ? targets[b] : INT64_MAX;
+    for (int32_t b = 0; b < B->B; ++b) {
+        B->inst[b].target = targets ? targets[b] : INT64_MAX;
+        B->inst[b].gens = gens ? gens[b] : G;
+    }
     // pageable source: the copy has read it when the call returns
     GOM_CUDA(nullptr, cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(GomBatchInst) * B->B,
                                       cudaMemcpyHostToDevice, B->stream));
     GomParams *dp = B->d_params;
     GomBatchInst *di = B->d_inst;
     GomBarrier *db = B->d_bars;
-    int nB = B->B, G = num_generations, fw = B->f_words;
-    void *args[] = {&dp, &di, &db, &nB, &G, &fw};
+    int nB = B->B, nG = G, fw = B->f_words;
+    void *args[] = {&dp, &di, &db, &nB, &nG, &fw};
     GOM_CUDA(nullptr, cudaLaunchCooperativeKernel(B->fn, dim3(B->grid), dim3(B->threads), args, B->smem, B->stream));
     k_batch_collect<<<(B->B + 255) / 256, 256, 0, B->stream>>>(B->d_params, B->d_inst, B->B);
     GOM_CUDA(nullptr, cudaGetLastError());
@@ -269,6 +271,27 @@ int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int6
         timed_out |= back[b].err != 0;
     }
     return timed_out ? GOM_E_TIMEOUT : GOM_OK;
+}
+
+} // namespace
+
+int gom_batch_generation(gom_batch_t *batch, int32_t num_generations, const int64_t *targets,
+                         int32_t *generations_run)
+{
+    if (!batch || num_generations < 0) return GOM_E_ARG;
+    return batch_run(batch, num_generations, nullptr, targets, generations_run);
+}
+
+int gom_batch_generation_each(gom_batch_t *batch, const int32_t *num_generations, const int64_t *targets,
+                              int32_t *generations_run)
+{
+    if (!batch || !num_generations) return GOM_E_ARG;
+    int32_t G = 0;
+    for (int32_t b = 0; b < batch->B; ++b) {
+        if (num_generations[b] < 0) return GOM_E_ARG;
+        G = std::max(G, num_generations[b]);
+    }
+    return batch_run(batch, G, num_generations, targets, generations_run);
 }
 
 int gom_batch_stats(gom_batch_t *batch, int32_t b, gom_gen_stats_t *host_stats, int32_t capacity, int32_t *count)

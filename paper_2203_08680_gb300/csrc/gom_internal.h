@@ -87,6 +87,8 @@ struct GomBatchInst {
     int32_t wpi;        // words per item of its mixing (1, 2, 4)
     int32_t narrow;     // 1: elements of <= 32 variables and |w| sums < 2^30
     int64_t target;     // target fitness of the current call
+    int32_t gens;       // generations of the current call for this instance
+    int32_t pad;
     int32_t gens_run;   // generations run by the last call
     int32_t err;        // the instance's device error word after the last call
 };

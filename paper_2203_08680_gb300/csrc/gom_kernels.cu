@@ -537,24 +537,28 @@ __device__ __forceinline__ void cp_wait_warp()
 }
 
 // A staging slice (one mixing item: an element and a range of its words):
-//  hdr[8] = {valid, q, j, d0, s | n_in << 8, n_out, f0, sub}
+//  hdr[8] = {valid, q, sub, n_out, j, f0, d0, s | n_in << 8}
 //  fv[s] variables, seg[s+1] their outside-edge starts, wout[s] their outside
 //  weight sums (int64), rows of P on F_j [s][W], patP[32 W] every individual's
 //  bits on F_j, rs[W] run starts of patP, edge records [E][ES], and in
 //  stage-all mode the donor start positions of the item's individuals.
 // Offsets come from the host (the one definition of the layout).
 
+// Slice header words: validity, element position q, word group, outside
+// edges, then the element header {j, f0, d0, s | n_in << 8}.
+enum : int { H_VALID = 0, H_Q = 1, H_SUB = 2, H_NOUT = 3, H_J = 4, H_F0 = 5, H_D0 = 6, H_SN = 7 };
+
 // Header of item (element at position q, word group sub), written by one lane.
 __device__ __forceinline__ void write_item_header(const GomParams &P, int q, int sub, int *h)
 {
     const int4 a = P.hdr[2 * q], b = P.hdr[2 * q + 1];
-    h[1] = q;
-    h[2] = a.x;
-    h[3] = a.z;
-    h[4] = a.w;
-    h[5] = b.x;
-    h[6] = a.y;
-    h[7] = sub;
+    h[H_Q] = q;
+    h[H_SUB] = sub;
+    h[H_NOUT] = b.x;
+    h[H_J] = a.x;
+    h[H_F0] = a.y;
+    h[H_D0] = a.z;
+    h[H_SN] = a.w;
 }
 
 // Decodes item `it` of colour c into the slice header (lane 0 writes).
@@ -567,7 +571,7 @@ __device__ __forceinline__ bool decode_item(const GomParams &P, int c, int it, i
     const bool valid = it < ne * per;
     if ((threadIdx.x & 31) == 0) {
         int *h = reinterpret_cast<int *>(sl);
-        h[0] = valid;
+        h[H_VALID] = valid;
         if (valid) write_item_header(P, q0 + it / per, it % per, h);
     }
     return valid;
@@ -581,7 +585,7 @@ __device__ __forceinline__ void stage_lists(const GomParams &P, uint32_t *sl)
     constexpr int ES = EdgeStride<WPI>::value;
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
-    const int q = h[1], d0 = h[3], s = h[4] & 0xFF, n_in = h[4] >> 8, n_out = h[5], f0 = h[6];
+    const int q = h[H_Q], d0 = h[H_D0], s = h[H_SN] & 0xFF, n_in = h[H_SN] >> 8, n_out = h[H_NOUT], f0 = h[H_F0];
     for (int a = lane; a < s; a += 32) {
         cp_async4(sl + P.off_fv + a, P.fv + f0 + a);
         cp_async8(sl + P.off_wout + 2 * a, P.wout + f0 + a);
@@ -597,7 +601,7 @@ __device__ __forceinline__ void stage_rows(const GomParams &P, uint32_t *sl, con
 {
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
-    const int s = h[4] & 0xFF, W = P.W;
+    const int s = h[H_SN] & 0xFF, W = P.W;
     const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
     uint32_t *sP = sl + P.off_pr;
     if (W >= 4) {
@@ -618,7 +622,7 @@ __device__ __forceinline__ void stage_patterns(const GomParams &P, uint32_t *sl)
 {
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
-    const int s = h[4] & 0xFF, W = P.W, Wv = P.Wv, p = P.p;
+    const int s = h[H_SN] & 0xFF, W = P.W, Wv = P.Wv, p = P.p;
     const uint32_t *sP = sl + P.off_pr;
     MaskT *patP = reinterpret_cast<MaskT *>(sl + P.off_pat);
     uint32_t *rs = sl + P.off_rs;
@@ -649,7 +653,7 @@ __device__ __forceinline__ void stage_draws(const GomParams &P, uint32_t *sl, ui
 {
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
-    const int j = h[2], sub = h[7];
+    const int j = h[H_J], sub = h[H_SUB];
     const int nwg = (P.Wv + WPI - 1) / WPI;
     const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
@@ -709,7 +713,7 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
             int *h = reinterpret_cast<int *>(slices + c * P.warp_smem);
             const int q0 = P.cptr[c], ne = P.cptr[c + 1] - q0;
             const bool valid = gwarp < ne * per;
-            h[0] = valid;
+            h[H_VALID] = valid;
             if (valid) write_item_header(P, q0 + gwarp / per, gwarp % per, h);
         }
         __syncwarp();
@@ -760,7 +764,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
     const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p;
     const int *h = reinterpret_cast<const int *>(sl);
-    const int j = h[2], s = h[4] & 0xFF, n_in = h[4] >> 8, n_out = h[5], sub = h[7];
+    const int j = h[H_J], s = h[H_SN] & 0xFF, n_in = h[H_SN] >> 8, n_out = h[H_NOUT], sub = h[H_SUB];
     const int nwg = (Wv + WPI - 1) / WPI;
     const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
     const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
@@ -955,12 +959,12 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 // the claims x it draws from the counter work[t] -- each claim issued one
 // item ahead, so its latency hides behind the item being run.  In stage-all
 // mode (`single`) the staged item, with its precomputed donor starts, is the
-// warp's only item of the group.  Elements of
-// one group share no variable and no edge (LMIG colouring), so a warp owns
-// its element's rows for its words and nothing else in the group touches the
-// closure it reads.  MaskT holds one bit per variable of F_j (uint32_t:
-// s <= 32, uint64_t: s <= 64); AccT is the delta type (int32_t when every
-// element's sum of |w| is < 2^30).  Counters accumulate per lane.
+// warp's only item of the group.  Elements of one group share no variable and no edge (LMIG
+// colouring), so a warp owns its element's rows for its words and nothing
+// else in the group touches the closure it reads.  MaskT holds one bit per
+// variable of F_j (uint32_t: s <= 32, uint64_t: s <= 64); AccT is the delta
+// type (int32_t when every element's sum of |w| is < 2^30).  Counters
+// accumulate per lane.
 template <int WPI, typename MaskT, typename AccT>
 __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *sl,
                                           bool first_staged, bool single, long long *s_f, unsigned &n_dl,
@@ -968,7 +972,7 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
-    bool staged = first_staged ? sl[0] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl);
+    bool staged = first_staged ? sl[H_VALID] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl);
     if (single) { // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (staged) run_item<WPI, MaskT, AccT>(P, sl, g, true, s_f, n_dl, n_acc, n_imp);
         return;
@@ -991,6 +995,12 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
         if (!stage_item<WPI, MaskT>(P, c, it, sl)) break;
         if (lane == 0) claim = atomicAdd(&P.work[t], 1u);
     }
+}
+
+// Shared-memory words of one warp's staging: k slices in stage-all mode, else one.
+__device__ __forceinline__ int warp_words(const GomParams &P, bool all)
+{
+    return all ? P.k * P.warp_smem : P.warp_smem;
 }
 
 // Adds a warp's per-lane counters into the block's counters.
@@ -1031,8 +1041,9 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-    phase_mix<WPI, MaskT, AccT>(P, whole_grid(), t, P.order[t], P.st->g, s_dyn + (threadIdx.x >> 5) * P.warp_smem,
-                                false, false, s_f, n_dl, n_acc, n_imp);
+    phase_mix<WPI, MaskT, AccT>(P, whole_grid(), t, P.order[t], P.st->g,
+                                s_dyn + (threadIdx.x >> 5) * warp_words(P, false), false, false, s_f, n_dl, n_acc,
+                                n_imp);
     count_flush(s_cnt, n_dl, n_acc, n_imp);
     acc_flush(P, s_f, s_cnt);
 }
@@ -1076,7 +1087,7 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
     const bool all = P.stage_all != 0;
     const bool lead = V.blk == 0;
     // this warp's staging: one slice, or one per colour with stage_all
-    uint32_t *slices = S.dyn + (threadIdx.x >> 5) * P.warp_smem * (all ? P.k : 1);
+    uint32_t *slices = S.dyn + (threadIdx.x >> 5) * warp_words(P, all);
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
     unsigned long long bnext = 0; // next barrier epoch end (thread 0)
@@ -1148,7 +1159,7 @@ __device__ __noinline__ void batch_variant(const GomParams &P, const VGrid V, Go
 // its own barrier counter and its own stop decision, exactly as its
 // persistent kernel would; instances never wait for one another.  Ps[b] is
 // instance b's parameter block (one-slice staging), inst[b] its blocks,
-// kernel variant and target.  The dynamic shared memory holds the block's
+// kernel variant, target and generation count (at most G).  The dynamic shared memory holds the block's
 // fitness accumulators (f_words 32-bit words, 32 W of the widest instance)
 // and then the warps' staging slices.
 // MINB: resident blocks of 256 threads the register budget is cut for (2: no
@@ -1181,6 +1192,7 @@ __global__ void __launch_bounds__(kMixThreads, MINB)
     const VGrid V{(int)blockIdx.x - I.blk0, I.nblk};
     const RunShared S{s_dyn + f_words, reinterpret_cast<long long *>(s_dyn), s_cnt, nullptr, nullptr};
     GomBarrier *bar = bars + b;
+    G = min(G, I.gens);
     if (I.narrow) {
         if (I.wpi == 4)
             batch_variant<4, uint32_t, int32_t>(sP, V, bar, G, I.target, S);

@@ -82,9 +82,16 @@ SIGNATURES = [
     ("gom_batch_workspace_bytes", _SZ, [_I32]),
     ("gom_batch_create", C.c_int, [_P, _I32, _P, _P, _SZ, _P, _P]),
     ("gom_batch_generation", C.c_int, [_P, _I32, _P, _P]),
+    ("gom_batch_generation_each", C.c_int, [_P, _P, _P, _P]),
     ("gom_batch_stats", C.c_int, [_P, _I32, _P, _I32, _P]),
     ("gom_batch_layout", C.c_int, [_P, _I32, _P, _P, _P]),
     ("gom_batch_destroy", None, [_P]),
+    ("gom_ims_workspace_bytes", _SZ, [_P, _P, _I32, _I32]),
+    ("gom_ims_create", C.c_int, [_P, _P, _I32, _I32, _I32, _U64, _P, _SZ, _P, _P]),
+    ("gom_ims_run", C.c_int, [_P, _I32, _I64, _P]),
+    ("gom_ims_population", C.c_int, [_P, _I32, _P]),
+    ("gom_ims_num_populations", _I32, [_P]),
+    ("gom_ims_destroy", None, [_P]),
     ("gom_batch_scratch_bytes", _SZ, [_P, _I32]),
     ("gom_batch_autotune", C.c_int, [_P, _I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P]),
     ("gom_destroy", None, [_P]),
@@ -155,6 +162,14 @@ def _graph(g):
     return g if isinstance(g, Graph) else Graph(g)
 
 
+class ImsResult(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("best_fitness", C.c_int64), ("reached", C.c_int32),
+                ("reached_population", C.c_int32), ("reached_step", C.c_int64), ("reached_generation", C.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class BatchConfig(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("min_blocks", C.c_int32), ("max_blocks", C.c_int32),
                 ("item_cost", C.c_int32)]
@@ -173,17 +188,19 @@ class Fos:
 
 
 class Ctx:
-    """Owning wrapper of a gom_ctx_t handle; keeps its workspace alive."""
+    """Wrapper of a gom_ctx_t handle; keeps its workspace alive.  A non-owning
+    view (owner = the object that owns the handle) does not destroy it."""
 
-    def __init__(self, handle, workspace, n: int, p: int):
+    def __init__(self, handle, workspace, n: int, p: int, owner=None):
         self.h = handle
         self.workspace = workspace
         self.n, self.p = n, p
+        self.owner = owner
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
+        if getattr(self, "h", None) and _lib is not None and getattr(self, "owner", None) is None:
             _lib.gom_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 # ---------------------------------------------------------------------------
@@ -417,6 +434,22 @@ def gom_batch_generation(batch: Batch, num_generations: int, targets=None, want_
     return runs
 
 
+def gom_batch_generation_each(batch: Batch, num_generations, targets=None, want_counts: bool = True):
+    """Generation counts per instance (sequence of len(batch.ctxs) ints)."""
+    B = len(batch.ctxs)
+    gens = np.ascontiguousarray(num_generations, dtype=np.int32)
+    assert len(gens) == B
+    t = None
+    if targets is not None:
+        t = np.ascontiguousarray(targets, dtype=np.int64)
+        assert len(t) == B
+    runs = np.zeros(B, dtype=np.int32) if want_counts else None
+    _check(load().gom_batch_generation_each(batch.h, gens.ctypes.data, t.ctypes.data if t is not None else None,
+                                            runs.ctypes.data if runs is not None else None),
+           "gom_batch_generation_each")
+    return runs
+
+
 def gom_batch_stats(batch: Batch, b: int, capacity: int):
     arr = (GenStats * max(capacity, 1))()
     cnt = C.c_int32()
@@ -434,6 +467,51 @@ def gom_batch_destroy(batch: Batch):
     if batch.h:
         load().gom_batch_destroy(batch.h)
         batch.h = None
+
+
+class Ims:
+    """Owning wrapper of a gom_ims_t handle; keeps its workspace alive."""
+
+    def __init__(self, handle, workspace, graph, fos):
+        self.h = handle
+        self.workspace = workspace
+        self.graph, self.fos = graph, fos
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gom_ims_destroy(self.h)
+            self.h = None
+
+
+def gom_ims_workspace_bytes(g, fos: Fos, base_pop: int, max_pop: int) -> int:
+    return int(load().gom_ims_workspace_bytes(_graph(g).ref(), fos.h, base_pop, max_pop))
+
+
+def gom_ims_create(g, fos: Fos, base_pop: int, c: int, max_pop: int, seed: int, workspace, stream=None) -> Ims:
+    """workspace: a CUDA tensor of at least gom_ims_workspace_bytes(...) bytes, 256-byte aligned."""
+    G = _graph(g)
+    h = C.c_void_p()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().gom_ims_create(G.ref(), fos.h, base_pop, c, max_pop, seed & 0xFFFFFFFFFFFFFFFF, _ptr(workspace),
+                                 nbytes, _stream(stream), C.byref(h)), "gom_ims_create")
+    return Ims(h, workspace, G, fos)
+
+
+def gom_ims_run(ims: Ims, steps: int, target: int = INT64_MAX) -> dict:
+    res = ImsResult()
+    _check(load().gom_ims_run(ims.h, steps, target, C.byref(res)), "gom_ims_run")
+    return res.as_dict()
+
+
+def gom_ims_population(ims: Ims, i: int) -> Ctx:
+    """Population i as a non-owning Ctx view (the scheme owns it)."""
+    h = C.c_void_p()
+    _check(load().gom_ims_population(ims.h, i, C.byref(h)), "gom_ims_population")
+    return Ctx(h, None, ims.graph.n, 0, owner=ims)
+
+
+def gom_ims_num_populations(ims: Ims) -> int:
+    return int(load().gom_ims_num_populations(ims.h))
 
 
 def gom_batch_scratch_bytes(ctxs) -> int:
