@@ -347,6 +347,8 @@ def run_gpu(args, wl, rank, world, local):
     ttt = None
     if not args.no_ttt:
         ttt = time_to_target(args, g, p, seed, stream, wl)
+        if wl.startswith("torus"):
+            ttt["ims"] = ims_time_to_target(args, g, seed, stream)
 
     e2e = None
     if not args.no_e2e:
@@ -538,6 +540,44 @@ def time_to_target(args, g, p, seed, stream, wl):
     return ttt
 
 
+def ims_time_to_target(args, g, seed, stream):
+    """Time to target of the Interleaved Multi-start Scheme (Sec. 6.3):
+    populations of base_pop * 2^i individuals (up to 1024), P_i one generation
+    per c of P_{i-1}, advanced in batched calls of up to 1024 P_0 generations
+    until a population reaches the target or the time budget runs out."""
+    import torch
+
+    from paper_2203_08680_gb300 import gom
+    tw = g.total_weight()
+    target = int(math.ceil(0.999 * tw))
+    fos = gom.gom_build_fos(g)
+    gom.gom_color_fos(g, fos)
+    nb = gom.gom_ims_workspace_bytes(g, fos, args.ims_base, 1024)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    ims = gom.gom_ims_create(g, fos, args.ims_base, args.ims_c, 1024, seed, ws, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    best, res = None, None
+    while True:
+        res = gom.gom_ims_run(ims, 1024, target)
+        best = res["best_fitness"] if best is None else max(best, res["best_fitness"])
+        if res["reached"] or time.perf_counter() - t0 > args.ims_seconds:
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"target": target, "closed_form_optimum": tw, "reached": bool(res["reached"]), "ms": e0.elapsed_time(e1),
+           "p0_generations": res["steps"], "best": best, "base_pop": args.ims_base, "c": args.ims_c,
+           "max_pop": 1024, "populations": gom.gom_ims_num_populations(ims)}
+    if res["reached"]:
+        out.update(reached_step=res["reached_step"], reached_population=res["reached_population"],
+                   reached_generation=res["reached_generation"])
+    del ims
+    return out
+
+
 def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step):
     """End to end through the C ABI from host buffers: FOS, colouring, upload,
     generations with host statistics, population and fitness back to host."""
@@ -608,6 +648,9 @@ def main():
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ims-base", type=int, default=16, help="IMS base population (time-to-target run)")
+    ap.add_argument("--ims-c", type=int, default=4, help="IMS generation ratio c")
+    ap.add_argument("--ims-seconds", type=float, default=20.0, help="IMS time-to-target budget")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
