@@ -356,7 +356,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->mix_fn = gom_mix_kernel(wpi, narrow);
     const SliceLayout SL = slice_layout(tabs.max_s, tabs.max_edges, c->W, wpi, narrow, split != 0, nwg);
     const int64_t off_fv = SL.off_fv, off_seg = SL.off_seg, off_wout = SL.off_wout, off_pr = SL.off_pr;
-    const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_edge = SL.off_edge, off_ds = SL.off_ds;
+    const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_ds = SL.off_ds;
     const int64_t base_words = SL.base_words;
     const int64_t all_words = SL.all_words;
     constexpr int64_t kSmemBudget = 200 * 1024;
@@ -460,7 +460,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.off_pr = static_cast<int32_t>(off_pr);
     P.off_pat = static_cast<int32_t>(off_pat);
     P.off_rs = static_cast<int32_t>(off_rs);
-    P.off_edge = static_cast<int32_t>(off_edge);
+    P.off_cw = static_cast<int32_t>(SL.off_cw);
+    P.off_xw = static_cast<int32_t>(SL.off_xw);
     P.off_ds = static_cast<int32_t>(off_ds);
     P.O = reinterpret_cast<uint32_t *>(base + L.O);
     P.P = reinterpret_cast<uint32_t *>(base + L.P);

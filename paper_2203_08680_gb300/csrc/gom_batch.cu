@@ -212,7 +212,8 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         P.off_pr = static_cast<int32_t>(SL.off_pr);
         P.off_pat = static_cast<int32_t>(SL.off_pat);
         P.off_rs = static_cast<int32_t>(SL.off_rs);
-        P.off_edge = static_cast<int32_t>(SL.off_edge);
+        P.off_cw = static_cast<int32_t>(SL.off_cw);
+        P.off_xw = static_cast<int32_t>(SL.off_xw);
         P.off_ds = static_cast<int32_t>(SL.off_ds);
         P.dyn = 1;
         P.bar = B->d_bars + b; // (P.trace: the context's phase trace, when switched on)

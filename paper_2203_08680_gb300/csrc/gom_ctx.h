@@ -59,11 +59,12 @@ inline int cuda_fail(gom_ctx *ctx, cudaError_t e)
 // item header, the element's variables, their outside-edge starts (s+1),
 // their outside weight sums (int64), the rows of P on the element (W words
 // each), the pattern table (32 W masks of 4 or 8 bytes), its run starts (W
-// words), one record per edge (code, weight, WPI parent words; 4 or 8
-// words), and in stage-all mode the item's donor start positions (one int
-// per individual of its words).  Every offset is a multiple of 4 words.
+// words), each edge's {code, weight} (two words), each outside edge's parent
+// words (WPI words), and in stage-all mode the item's donor start positions
+// (one int per individual of its words).  Every offset is a multiple of 4
+// words.
 struct SliceLayout {
-    int64_t off_fv, off_seg, off_wout, off_pr, off_pat, off_rs, off_edge, off_ds;
+    int64_t off_fv, off_seg, off_wout, off_pr, off_pat, off_rs, off_cw, off_xw, off_ds;
     int64_t base_words; // a slice without the donor starts
     int64_t all_words;  // with them (stage-all mode)
 };
@@ -72,7 +73,6 @@ inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi
                                 int nwg)
 {
     auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
-    const int es = wpi == 4 ? 8 : 4;
     SliceLayout L{};
     L.off_fv = 8;
     L.off_seg = L.off_fv + round4(max_s);
@@ -80,8 +80,9 @@ inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi
     L.off_pr = L.off_wout + round4(2 * max_s);
     L.off_pat = L.off_pr + round4(max_s * W);
     L.off_rs = L.off_pat + int64_t(32) * W * (narrow ? 1 : 2);
-    L.off_edge = L.off_rs + round4(W);
-    L.off_ds = L.off_edge + max_edges * es;
+    L.off_cw = L.off_rs + round4(W);
+    L.off_xw = L.off_cw + round4(2 * max_edges);
+    L.off_ds = L.off_xw + round4(max_edges * wpi);
     L.base_words = L.off_ds;
     L.all_words = L.off_ds + int64_t(32) * wpi * (split ? 1 : nwg);
     return L;

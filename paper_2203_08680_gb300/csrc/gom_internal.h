@@ -118,9 +118,10 @@ struct GomParams {
     int32_t off_seg;    //   [off_seg, ..) their outside-edge starts (s+1), [off_wout, ..)
     int32_t off_wout;   //   their outside weight sums (int64), [off_pr, ..) the rows of P
     int32_t off_pr;     //   on F_j, [off_pat, ..) the pattern table (32 W masks),
-    int32_t off_pat;    //   [off_rs, ..) its run starts (W words), [off_edge, warp_smem)
-    int32_t off_rs;     //   edge records
-    int32_t off_edge;
+    int32_t off_pat;    //   [off_rs, ..) its run starts (W words), [off_cw, ..) each edge's
+    int32_t off_rs;     //   {code, weight}, [off_xw, ..) each outside edge's WPI parent words
+    int32_t off_cw;
+    int32_t off_xw;
     int32_t off_ds;     //   [off_ds, ..) donor start positions (stage-all mode only)
     int32_t dyn;        // 1: after its first item, a warp claims items from work[t]
     uint64_t seed;

@@ -418,6 +418,19 @@ __device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&x)[WPI]
     }
 }
 
+// Stores WPI consecutive 32-bit words (aligned as in load_words).
+template <int WPI>
+__device__ __forceinline__ void store_words(uint32_t *p, const uint32_t (&x)[WPI])
+{
+    if constexpr (WPI == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (WPI == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(x[0], x[1]);
+    } else {
+        *p = x[0];
+    }
+}
+
 // First individual, scanning cyclically upwards from `start` and skipping
 // `self`, whose generation-start bits on F differ from the parent's bits
 // `xf`; 32 candidates per step from the staged rows sP[a*W + word] of P on
@@ -442,18 +455,6 @@ __device__ int scan_donor(const uint32_t *sP, int W, int Wv, int p, int s, MaskT
     }
     return -1;
 }
-
-// Words per staged edge record in the mixing phase: code and weight, then
-// the parent words of WPI individuals-words at offset EdgeX (4 or 2 words,
-// so they load as one vector); the stride is a power of two.
-template <int WPI>
-struct EdgeStride {
-    static constexpr int value = WPI == 4 ? 8 : 4;
-};
-template <int WPI>
-struct EdgeX {
-    static constexpr int value = WPI == 4 ? 4 : 2;
-};
 
 // Value held by lane (a mod 32) of lo (a < 32) or hi (a >= 32): per-variable
 // registers of elements with up to 64 variables.  Warp-uniform a.
@@ -540,8 +541,9 @@ __device__ __forceinline__ void cp_wait_warp()
 //  hdr[8] = {valid, q, sub, n_out, j, f0, d0, s | n_in << 8}
 //  fv[s] variables, seg[s+1] their outside-edge starts, wout[s] their outside
 //  weight sums (int64), rows of P on F_j [s][W], patP[32 W] every individual's
-//  bits on F_j, rs[W] run starts of patP, edge records [E][ES], and in
-//  stage-all mode the donor start positions of the item's individuals.
+//  bits on F_j, rs[W] run starts of patP, cw[E] each edge's {code, weight},
+//  xw[E_out][WPI] the outside edges' parent words, and in stage-all mode the
+//  donor start positions of the item's individuals.
 // Offsets come from the host (the one definition of the layout).
 
 // Slice header words: validity, element position q, word group, outside
@@ -582,7 +584,6 @@ __device__ __forceinline__ bool decode_item(const GomParams &P, int c, int it, i
 template <int WPI>
 __device__ __forceinline__ void stage_lists(const GomParams &P, uint32_t *sl)
 {
-    constexpr int ES = EdgeStride<WPI>::value;
     const int lane = threadIdx.x & 31;
     const int *h = reinterpret_cast<const int *>(sl);
     const int q = h[H_Q], d0 = h[H_D0], s = h[H_SN] & 0xFF, n_in = h[H_SN] >> 8, n_out = h[H_NOUT], f0 = h[H_F0];
@@ -591,7 +592,7 @@ __device__ __forceinline__ void stage_lists(const GomParams &P, uint32_t *sl)
         cp_async8(sl + P.off_wout + 2 * a, P.wout + f0 + a);
     }
     for (int a = lane; a <= s; a += 32) cp_async4(sl + P.off_seg + a, P.seg + f0 + q + a);
-    for (int x = lane; x < n_out + n_in; x += 32) cp_async8(sl + P.off_edge + x * ES, P.dep + d0 + x);
+    for (int x = lane; x < n_out + n_in; x += 32) cp_async8(sl + P.off_cw + 2 * x, P.dep + d0 + x);
 }
 
 // Level-2 copies: the rows of the generation-start population on F_j (all W
@@ -760,7 +761,6 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
                                          unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
-    constexpr int ES = EdgeStride<WPI>::value, XO = EdgeX<WPI>::value;
     const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p;
     const int *h = reinterpret_cast<const int *>(sl);
@@ -774,7 +774,8 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
     const MaskT *patP = reinterpret_cast<const MaskT *>(sl + P.off_pat);
     const uint32_t *rs = sl + P.off_rs;
     const int *sds = reinterpret_cast<const int *>(sl + P.off_ds);
-    uint32_t *sE = sl + P.off_edge;
+    const int2 *cw = reinterpret_cast<const int2 *>(sl + P.off_cw);
+    uint32_t *xw = sl + P.off_xw;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     const int ne_tot = n_out + n_in;
     const int fl = lane < s ? fv[lane] : 0;
@@ -793,9 +794,8 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
         __syncwarp();
         for (int x = lane; x < n_out; x += 32) {
             uint32_t X[WPI];
-            load_words<WPI>(P.O + (int)sE[x * ES] * W + w0, X);
-#pragma unroll
-            for (int r = 0; r < WPI; ++r) sE[x * ES + XO + r] = X[r];
+            load_words<WPI>(P.O + cw[x].x * W + w0, X);
+            store_words<WPI>(xw + x * WPI, X);
         }
         // parent bits on F_j: a shuffle transpose of the rows
         MaskT xf[WPI];
@@ -856,8 +856,8 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
             for (int r = 0; r < WPI; ++r) S[r] = 0;
             for (int x = qb; x < qe; ++x) {
                 uint32_t X[WPI];
-                load_words<WPI>(sE + x * ES + XO, X);
-                const AccT wx = (AccT)(int32_t)sE[x * ES + 1];
+                load_words<WPI>(xw + x * WPI, X);
+                const AccT wx = (AccT)cw[x].y;
 #pragma unroll
                 for (int r = 0; r < WPI; ++r) S[r] += wx * (AccT)((X[r] >> lane) & 1u);
             }
@@ -870,8 +870,9 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
             }
         }
         for (int x = n_out; x < ne_tot; ++x) {
-            const uint32_t code = sE[x * ES];
-            const AccT wx = (AccT)(int32_t)sE[x * ES + 1];
+            const int2 e = cw[x];
+            const uint32_t code = (uint32_t)e.x;
+            const AccT wx = (AccT)e.y;
             const int a = code & 0xFF, b = code >> 8;
 #pragma unroll
             for (int r = 0; r < WPI; ++r) {
@@ -972,28 +973,19 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
-    bool staged = first_staged ? sl[H_VALID] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl);
-    if (single) { // stage-all mode: the staged item is the warp's only one, its slice stays as it is
-        if (staged) run_item<WPI, MaskT, AccT>(P, sl, g, true, s_f, n_dl, n_acc, n_imp);
-        return;
-    }
-    const bool pre = false;
-    if (!P.dyn) {
-        for (int it = gwarp + nwarps; staged; it += nwarps) {
-            run_item<WPI, MaskT, AccT>(P, sl, g, pre, s_f, n_dl, n_acc, n_imp);
-            staged = stage_item<WPI, MaskT>(P, c, it, sl);
-        }
-        return;
-    }
-    if (!staged) return;
+    if (!(first_staged ? sl[H_VALID] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl))) return;
+    // one call site of run_item and of stage_item (the loop body is the hot code)
+    const bool dyn = P.dyn && !single;
     unsigned claim = 0;
-    if (lane == 0) claim = atomicAdd(&P.work[t], 1u);
-    for (;;) {
-        run_item<WPI, MaskT, AccT>(P, sl, g, pre, s_f, n_dl, n_acc, n_imp);
-        const int it = nwarps + (int)__shfl_sync(kFull, claim, 0);
-        // stop on the first claim past the group (items are numbered densely)
+    if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
+    for (int next = gwarp + nwarps;; next += nwarps) {
+        run_item<WPI, MaskT, AccT>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
+        // stage-all mode: the staged item is the warp's only one, its slice stays as it is
+        if (single) break;
+        // stop on the first item past the group (items are numbered densely)
+        const int it = dyn ? nwarps + (int)__shfl_sync(kFull, claim, 0) : next;
         if (!stage_item<WPI, MaskT>(P, c, it, sl)) break;
-        if (lane == 0) claim = atomicAdd(&P.work[t], 1u);
+        if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     }
 }
 
