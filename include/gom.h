@@ -57,7 +57,7 @@ extern "C" {
 #define GOM_E_TIMEOUT (-6)      /* a bounded device wait gave up; the population is then undefined
                                    until gom_set_population or a new gom_init_population */
 #define GOM_E_STATE (-7)        /* call not valid in the handle's state */
-#define GOM_E_LIMIT (-8)        /* size beyond what this build supports */
+#define GOM_E_LIMIT (-8)        /* size beyond what the library supports */
 #define GOM_E_FOS (-9)          /* FOS incomplete, out of range or for another graph */
 
 /* FOS kinds for gom_build_fos. */
@@ -82,7 +82,7 @@ extern "C" {
                              then claims further items from a per-group counter (faster
                              warps take more; the default).  Same results either way */
 
-/* Supported maxima of this build. */
+/* Supported maxima of the library. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 64      /* variables in one FOS element */
 #define GOM_MAX_COLORS 28000    /* colour groups */

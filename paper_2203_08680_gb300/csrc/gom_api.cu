@@ -219,7 +219,7 @@ const char *gom_strerror(int code)
     case GOM_E_CUDA: return "CUDA call failed";
     case GOM_E_TIMEOUT: return "bounded device wait gave up";
     case GOM_E_STATE: return "call not valid in this state";
-    case GOM_E_LIMIT: return "size beyond this build's limits";
+    case GOM_E_LIMIT: return "size beyond the library's limits";
     case GOM_E_FOS: return "FOS incomplete, out of range or for another graph";
     default: return "unknown error";
     }
