@@ -401,7 +401,7 @@ def run_batch(args, wl, rank, world, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    mix = I.batch_mix(seed=SEED + rank)
+    mix = I.batch_mix(seed=SEED + rank)[: args.batch_count]
     graphs = [I.random_regular(n, d, s) for n, d, p, s in mix]
     pops = [gom.Population(g, p, s, stream=stream) for g, (n, d, p, s) in zip(graphs, mix)]
     ctxs = [P.ctx for P in pops]
@@ -497,7 +497,8 @@ def run_batch(args, wl, rank, world, local):
         "metric": "GOM trials/sec (batched parallel GOM, weighted Max-Cut)", "value": value, "unit": "trials/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl, "description": BATCH_WORKLOADS[wl], "instances": len(pops),
+        "config": {"workload": wl if len(pops) == 256 else f"{wl}[:{len(pops)}]", "description": BATCH_WORKLOADS[wl],
+                   "instances": len(pops),
                    "trials_per_generation": trials_per_step, "batch_config": list(BATCH_CONFIGS[best]),
                    "autotune_ms_per_generation": dict(zip(["x".join(map(str, c)) for c in BATCH_CONFIGS], tune_ms)),
                    "grid": gom.gom_batch_layout(batch, 0)[2],
@@ -649,6 +650,8 @@ def main():
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="batch workloads: the first N instances of the mix (a smaller case for profiling)")
     ap.add_argument("--ims-base", type=int, default=16, help="IMS base population (time-to-target run)")
     ap.add_argument("--ims-c", type=int, default=4, help="IMS generation ratio c")
     ap.add_argument("--ims-seconds", type=float, default=20.0, help="IMS time-to-target budget")
