@@ -383,6 +383,71 @@ int gom_batch_generation_each(gom_batch_t *batch, const int32_t *num_generations
                               int32_t *generations_run);
 
 /* ---------------------------------------------------------------------------
+ * Learned trial filter (not in the paper).  A small MLP -- 16 features of an
+ * FOS element, 64 ReLU units, one logit; bf16 weights, fp32 accumulation --
+ * trained on accept/reject samples that GOM itself logs, skips the trials of
+ * elements predicted to accept nothing.  Every change that is kept is still
+ * decided by the exact integer partial evaluation of Alg. 2; skipping only
+ * removes trials.  One in 16 elements the filter would skip is run anyway (an
+ * audit); when the estimated recall (useful elements run / all useful ones)
+ * of a generation falls below min_recall the filter turns itself off and the
+ * run goes on as plain GOM.  Features of element j in generation g: its size,
+ * outside and inside edge counts, its accepted, donor-less and improving
+ * trials of generation g-1 (fractions of p), whether it accepted none or had no
+ * donor at all, log2(1+g), the population's accept, improve and donor-less
+ * rates of generation g-1, and a constant.
+ *
+ * Modes: 0 off (plain GOM); 1 history and training log (results identical to
+ * plain GOM); 2 also skip.  Mode 2 is not available to a context whose
+ * persistent path stages all groups at once (small problems): GOM_E_STATE.
+ */
+typedef struct gom_filter_train {
+    int64_t samples;      /* logged samples trained on */
+    int64_t useful;       /* of which accepted at least one trial */
+    double loss;          /* mean weighted logistic loss of the last epoch */
+    float threshold;      /* logit below which an element is skipped */
+    double skip_fraction; /* of the logged samples below the threshold */
+    double recall;        /* useful logged samples at or above the threshold */
+} gom_filter_train_t;
+
+typedef struct gom_filter_stats {
+    int32_t mode, enabled, disabled_at; /* disabled_at: generation the filter turned itself off, -1 never */
+    float threshold;
+    int64_t log_count;                  /* samples offered to the log */
+    int64_t last[5];                    /* last generation's items: run, run useful, skipped, audited, audited useful */
+    int64_t total[5];                   /* the same since attach */
+} gom_filter_stats_t;
+
+/* Device bytes of the filter state: per-element history (24 bytes per element),
+ * the MLP and its optimiser, and a training log of log_capacity samples (38 bytes each). */
+size_t gom_filter_workspace_bytes(gom_ctx_t *ctx, int64_t log_capacity);
+
+/* Attaches caller-owned device memory (256-byte aligned) as the filter state; mode 0. */
+int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_t log_capacity);
+
+/* Mode 0, 1 or 2 (above).  Waits for the stream. */
+int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode);
+
+/* Skip threshold (logit) and the recall under which the filter turns itself off. */
+int gom_filter_configure(gom_ctx_t *ctx, float threshold, float min_recall);
+
+/*
+ * Trains the MLP from scratch on the logged samples: `epochs` full-batch Adam
+ * steps on the logistic loss with positive samples weighted by pos_weight
+ * (hand-written kernels; weights initialised from `seed`), then sets the
+ * threshold to the largest logit that keeps target_recall of the useful
+ * logged samples.  *out (may be NULL) reports it.  GOM_E_STATE with an empty
+ * log.  Waits.
+ */
+int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float pos_weight, float target_recall,
+                     uint64_t seed, gom_filter_train_t *out);
+
+int gom_filter_stats(gom_ctx_t *ctx, gom_filter_stats_t *out);
+
+/* The elements skipped in the last generation: host_mask[j] = 1 (host, [m]). */
+int gom_filter_skipped(gom_ctx_t *ctx, uint8_t *host_mask);
+
+/* ---------------------------------------------------------------------------
  * Interleaved Multi-start Scheme (Sec. 6.3): populations P_0, P_1, ... of
  * base_pop * 2^i individuals (up to max_pop), P_i seeded with seed + i; one
  * generation of P_i is made each time P_{i-1} has made c more generations (the

@@ -778,8 +778,25 @@ static void generation_end(orc_state *s, int64_t target, orc_stats *st)
  * subset of individuals (the elitist update is then skipped, since it needs the
  * whole population).  A run stops once a generation ends with max f >= target;
  * that stop is the caller's loop, st->reached reports it. */
+static int32_t generation_impl(orc_state *s, int64_t target, uint64_t shuffle, const int32_t *only,
+                               int32_t n_only, const uint8_t *skip_elem, orc_stats *st);
+
 int32_t orc_generation_ex(orc_state *s, int64_t target, uint64_t shuffle, const int32_t *only,
                           int32_t n_only, orc_stats *st)
+{
+    return generation_impl(s, target, shuffle, only, n_only, NULL, st);
+}
+
+/* The generation with the trials of the elements marked in skip_elem[j] left
+ * out (a replay of a run whose learned filter skipped them); everything else
+ * is the plain generation. */
+int32_t orc_generation_skip(orc_state *s, int64_t target, const uint8_t *skip_elem, orc_stats *st)
+{
+    return generation_impl(s, target, 0, NULL, 0, skip_elem, st);
+}
+
+static int32_t generation_impl(orc_state *s, int64_t target, uint64_t shuffle, const int32_t *only,
+                               int32_t n_only, const uint8_t *skip_elem, orc_stats *st)
 {
     memset(st, 0, sizeof(*st));
     const int32_t p = s->p;
@@ -808,6 +825,7 @@ int32_t orc_generation_ex(orc_state *s, int64_t target, uint64_t shuffle, const 
             int32_t j = s->celems[s->cptr[c] + id / n_ind];
             int32_t ii = (int32_t)(id % n_ind);
             int32_t i = only ? only[ii] : ii;
+            if (skip_elem && skip_elem[j]) continue;
             gom_trial(s, &s->sc, i, j, st);
         }
         free(perm);

@@ -73,6 +73,8 @@ def lib():
         L.orc_get.argtypes = [P, P, P, P, P, P]
         L.orc_generation_ex.argtypes = [P, i64, u64, P, i32, P]
         L.orc_generation_ex.restype = i32
+        L.orc_generation_skip.argtypes = [P, i64, P, P]
+        L.orc_generation_skip.restype = i32
         L.orc_generation_par.argtypes = [P, i64, i32, P]
         L.orc_generation_par.restype = i32
         L.orc_max_threads.argtypes = []
@@ -232,6 +234,14 @@ class Run:
         else:
             o = np.ascontiguousarray(only, dtype=np.int32)
             lib().orc_generation_ex(self._h, target, shuffle, _p(o), len(o), C.byref(st))
+        return st.as_dict()
+
+    def generation_skip(self, skip_elem, target: int = 2 ** 63 - 1) -> dict:
+        """One generation without the trials of the elements marked in skip_elem[j]."""
+        sk = np.ascontiguousarray(skip_elem, dtype=np.uint8)
+        assert len(sk) == self.m
+        st = Stats()
+        lib().orc_generation_skip(self._h, target, _p(sk), C.byref(st))
         return st.as_dict()
 
     def run(self, generations: int, target: int = 2 ** 63 - 1):

@@ -141,22 +141,6 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
     return GOM_OK;
 }
 
-// Rebuilds the per-generation graphs after a change of the parameters they
-// copy (the timed variant only if it exists).  Waits for the stream.
-int rebuild_graphs(gom_ctx *ctx)
-{
-    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const bool had_timed = ctx->texec != nullptr;
-    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
-    if (ctx->graph) cudaGraphDestroy(ctx->graph);
-    if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
-    if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
-    ctx->exec = ctx->texec = nullptr;
-    ctx->graph = ctx->tgraph = nullptr;
-    int rc = build_graph(ctx, false, &ctx->graph, &ctx->exec);
-    if (rc == GOM_OK && had_timed) rc = build_graph(ctx, true, &ctx->tgraph, &ctx->texec);
-    return rc;
-}
 
 
 int accumulate_timing(gom_ctx *ctx)
@@ -173,6 +157,23 @@ int accumulate_timing(gom_ctx *ctx)
 }
 
 } // namespace
+
+// Rebuilds the per-generation graphs after a change of the parameters they
+// copy (the timed variant only if it exists).  Waits for the stream.
+int rebuild_graphs(gom_ctx *ctx)
+{
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const bool had_timed = ctx->texec != nullptr;
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->texec) cudaGraphExecDestroy(ctx->texec);
+    if (ctx->tgraph) cudaGraphDestroy(ctx->tgraph);
+    ctx->exec = ctx->texec = nullptr;
+    ctx->graph = ctx->tgraph = nullptr;
+    int rc = build_graph(ctx, false, &ctx->graph, &ctx->exec);
+    if (rc == GOM_OK && had_timed) rc = build_graph(ctx, true, &ctx->tgraph, &ctx->texec);
+    return rc;
+}
 
 // The counters of the generations of the context's last call (host_stats
 // may be null), and their number.  Waits for the stream.
@@ -423,6 +424,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->narrow = narrow;
     c->max_items = std::max<int64_t>(1, max_group * per);
     c->max_group = max_group;
+    c->celems.assign(fos->celems.begin(), fos->celems.end());
     c->max_s = tabs.max_s;
     c->max_edges = tabs.max_edges;
     for (int64_t q = 0; q < c->m; ++q) {

@@ -43,6 +43,9 @@ struct gom_ctx {
     int64_t max_group = 1;       // elements of the largest colour group
     int64_t max_s = 0;           // variables of the largest element
     int64_t max_edges = 0;       // most edges of one element
+    std::vector<int32_t> celems; // element index at each colour-order position
+    char *filter_base = nullptr; // learned-filter workspace (gom_filter_attach), or null
+    int64_t filter_cap = 0;      // its training-log capacity
     char *base = nullptr;        // the workspace
     size_t state_bytes = 0;      // its state arrays: [0, state_bytes) (population, fitness, elitist, ...)
 };
@@ -128,3 +131,7 @@ inline cudaError_t raise_smem_limit(const void *fn, size_t bytes)
 // host_stats[0..num) (may be null) and their number (*run_out).  Waits for
 // the stream.  GOM_E_TIMEOUT if the context's device error word is set.
 int ctx_read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32_t *run_out);
+
+// Rebuilds the per-generation graphs after a change of the parameters they
+// copy (the timed variant only if it exists).  Waits for the stream.
+int rebuild_graphs(gom_ctx *ctx);

@@ -93,6 +93,38 @@ struct GomBatchInst {
     int32_t err;        // the instance's device error word after the last call
 };
 
+// Learned trial filter (gom_filter_*): a 16 -> 64 -> 1 MLP with bf16 weights
+// that skips the trials of elements predicted to accept nothing, with
+// per-element history of the last two generations and audit counters.
+constexpr int kFilterIn = 16;
+constexpr int kFilterHidden = 64;
+enum : int { FC_RUN = 0, FC_RUN_USEFUL = 1, FC_SKIPPED = 2, FC_AUDITED = 3, FC_AUDITED_USEFUL = 4, FC_N = 5 };
+
+struct GomFilterState {
+    int32_t enabled;                   // 1 while the filter skips elements
+    int32_t disabled_at;               // generation at which it turned itself off, -1 never
+    float threshold;                   // skip when the logit is below it
+    float min_recall;                  // estimated recall under which the filter turns itself off
+    unsigned long long log_count;      // samples offered to the log (those past its capacity are dropped)
+    unsigned long long cnt[FC_N];      // items of the running generation: run, run with an acceptance,
+                                       // skipped, audited, audited with an acceptance
+    unsigned long long last[FC_N];     // the same for the last finished generation
+    unsigned long long total[FC_N];    // since the filter was attached
+};
+
+struct GomFilter {
+    GomFilterState *st;
+    uint32_t *hist;       // [2][3][m] accepted, donor-less and improving trials per element position, by g mod 2
+    uint8_t *skipped;     // [m] elements (by position) skipped in the last generation
+    const uint16_t *w1;   // [64][16] bf16 bits
+    const float *b1;      // [64]
+    const uint16_t *w2;   // [64] bf16 bits
+    const float *b2;      // [1]
+    uint16_t *log_x;      // [cap][16] bf16 features
+    uint8_t *log_y;       // [cap] label: the item accepted at least one trial
+    int64_t log_cap;
+};
+
 struct GomDevStats { // mirrors gom_gen_stats_t
     int64_t generation, best, elite, trials, donorless, accepted, improving, reached;
 };
@@ -124,6 +156,8 @@ struct GomParams {
     int32_t off_xw;
     int32_t off_ds;     //   [off_ds, ..) donor start positions (stage-all mode only)
     int32_t dyn;        // 1: after its first item, a warp claims items from work[t]
+    int32_t learn;      // learned filter: 0 off, 1 history and training log, 2 also skip elements
+    GomFilter flt;
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population

@@ -17,6 +17,7 @@
 // kernel (k_run) that runs many generations with grid barriers between the
 // phases.  Plus initialisation, full evaluation and import/export kernels.
 #include <climits>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "gom_internal.h"
@@ -292,6 +293,12 @@ __device__ void phase_gen_start(const GomParams &P, const VGrid &V, int improved
     uint32_t *eqw = P.eqw + (g & 1) * W;
     if (tid < W) P.eqw[((g + 1) & 1) * W + tid] = kFull;
     for (int64_t t = tid; t < P.k; t += nth) P.work[t] = 0;
+    if (P.learn) { // the learned filter's history and skip marks of generation g, and its counters
+        uint32_t *cur = P.flt.hist + (size_t)(g & 1) * 3 * (size_t)P.m;
+        for (int64_t x = tid; x < 3 * (int64_t)P.m; x += nth) cur[x] = 0;
+        for (int64_t x = tid; x < P.m; x += nth) P.flt.skipped[x] = 0;
+        if (tid < FC_N) P.flt.st->cnt[tid] = 0;
+    }
     uint32_t eq = kFull;
     for (int64_t idx = tid; idx < total; idx += nth) {
         const int64_t v = idx >> lw;
@@ -368,6 +375,29 @@ struct GenEnd {
     int improved, argmax;
 };
 
+// The learned filter at the end of generation g (one thread): the counters
+// into last/total, and the recall check.  Recall is estimated as useful items
+// run / (useful items run + skipped items x the useful fraction of the
+// audited ones); below min_recall (with at least 16 audits) the filter turns
+// itself off and the run goes on as plain GOM.
+__device__ void filter_generation_end(const GomParams &P, uint32_t g)
+{
+    GomFilterState *st = P.flt.st;
+    for (int x = 0; x < FC_N; ++x) {
+        st->last[x] = st->cnt[x];
+        st->total[x] += st->cnt[x];
+    }
+    if (P.learn == 2 && st->enabled && st->last[FC_AUDITED] >= 16) {
+        const double miss = (double)st->last[FC_AUDITED_USEFUL] / (double)st->last[FC_AUDITED];
+        const double found = (double)st->last[FC_RUN_USEFUL];
+        const double lost = (double)st->last[FC_SKIPPED] * miss;
+        if (found + lost > 0.0 && found / (found + lost) < (double)st->min_recall) {
+            st->enabled = 0;
+            st->disabled_at = (int32_t)g;
+        }
+    }
+}
+
 __device__ bool phase_gen_end(const GomParams &P, int64_t target, uint32_t g, GenEnd &e, bool write_state)
 {
     int64_t best;
@@ -397,6 +427,7 @@ __device__ bool phase_gen_end(const GomParams &P, int64_t target, uint32_t g, Ge
         st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
         st->done = reached;
         st->g = g + 1;
+        if (P.learn) filter_generation_end(P, g);
     }
     __syncthreads();
     return reached;
@@ -676,23 +707,119 @@ __device__ __forceinline__ void stage_draws(const GomParams &P, uint32_t *sl, ui
     }
 }
 
+// ----------------------------------------------------------------------------
+// Learned trial filter.  Features of the element at position q for
+// generation g (the same in every lane): its size and edge counts, its
+// accepted / donor-less / improving trials of the previous generation (as
+// fractions of p), whether it accepted nothing or had no donor at all, the
+// generation, the population's accept / improve / donor-less rates of the
+// previous generation, and a constant.
+__device__ __forceinline__ float bf16_bits_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+__device__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x)[kFilterIn])
+{
+    const int4 a = P.hdr[2 * q], b = P.hdr[2 * q + 1];
+    const int s = a.w & 0xFF, n_in = a.w >> 8, n_out = b.x;
+    const float inv_p = 1.f / (float)P.p;
+    const uint32_t *prev = P.flt.hist + (size_t)((g + 1) & 1) * 3 * (size_t)P.m;
+    const uint32_t acc = prev[q], dl = prev[P.m + q], imp = prev[2 * (size_t)P.m + q];
+    x[0] = (float)s / 16.f;
+    x[1] = (float)n_out / 64.f;
+    x[2] = (float)n_in / 32.f;
+    x[3] = (float)acc * inv_p;
+    x[4] = (float)dl * inv_p;
+    x[5] = (float)imp * inv_p;
+    x[6] = acc == 0 ? 1.f : 0.f;
+    x[7] = dl >= (uint32_t)P.p ? 1.f : 0.f;
+    x[8] = log2f(1.f + (float)g) / 16.f;
+    x[9] = x[10] = x[11] = 0.f;
+    if (g > 0) {
+        const GomDevStats &S = P.stats[(g - 1) % kStatsCap];
+        const float tr = (float)S.trials;
+        x[9] = (float)S.accepted / tr;
+        x[10] = (float)S.improving / tr;
+        x[11] = (float)S.donorless / tr;
+    }
+    x[12] = 1.f;
+    x[13] = x[14] = x[15] = 0.f;
+}
+
+// The MLP's output (logit): 64 ReLU units over the 16 features, bf16 weights,
+// fp32 accumulation, two units per lane and a fixed-order warp sum.
+__device__ float filter_logit(const GomParams &P, const float (&x)[kFilterIn])
+{
+    const int lane = threadIdx.x & 31;
+    float part = 0.f;
+    for (int h = lane; h < kFilterHidden; h += 32) {
+        float z = P.flt.b1[h];
+#pragma unroll
+        for (int k = 0; k < kFilterIn; ++k) z = fmaf(bf16_bits_to_f32(P.flt.w1[h * kFilterIn + k]), x[k], z);
+        part = fmaf(bf16_bits_to_f32(P.flt.w2[h]), fmaxf(z, 0.f), part);
+    }
+    for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
+    return part + P.flt.b2[0];
+}
+
+// One in 16 elements of a generation whose trials the filter would skip is run
+// anyway (an audit), to estimate how many useful elements it skips.
+__device__ __forceinline__ bool filter_audit(int q, uint32_t g)
+{
+    uint32_t h = (uint32_t)q * 0x9E3779B1u ^ (g * 0x85EBCA77u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return (h & 15u) == 0;
+}
+
+// One in 32 elements of a generation gives a training sample.
+__device__ __forceinline__ bool filter_sample(int q, uint32_t g)
+{
+    uint32_t h = (uint32_t)q * 0xCC9E2D51u ^ (g * 0x1B873593u);
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    return (h & 31u) == 0;
+}
+
+// Slice validity states: no item, staged, skipped by the filter, staged for an audit.
+enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
+
 // Stages one item of colour c (item index `it`) into a slice: decode, then
 // two levels of asynchronous copies, then the pattern table.  Only
 // generation-constant data: it may run before the barrier that opens the
-// group.
+// group.  With the learned filter on, an element predicted to accept nothing
+// is not staged (IT_SKIPPED) unless it is audited.  Returns the slice state.
 template <int WPI, typename MaskT>
-__device__ __forceinline__ bool stage_item(const GomParams &P, int c, int it, uint32_t *sl)
+__device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uint32_t *sl, uint32_t g)
 {
     __syncwarp();
     const bool valid = decode_item(P, c, it, WPI, sl);
-    if (!valid) return false;
+    if (!valid) return IT_NONE;
     __syncwarp();
+    int state = IT_STAGED;
+    if (P.learn == 2 && P.flt.st->enabled) {
+        const int *h = reinterpret_cast<const int *>(sl);
+        const int q = h[H_Q];
+        float x[kFilterIn];
+        filter_features(P, q, g, x);
+        if (filter_logit(P, x) < P.flt.st->threshold) {
+            state = filter_audit(q, g) ? IT_AUDIT : IT_SKIPPED;
+            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) {
+                P.flt.skipped[q] = 1;
+                atomicAdd(&P.flt.st->cnt[FC_SKIPPED], 1ull);
+            }
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) sl[H_VALID] = (uint32_t)state;
+        __syncwarp();
+        if (state == IT_SKIPPED) return state;
+    }
     stage_lists<WPI>(P, sl);
     cp_wait_warp();
     stage_rows(P, sl, P.P);
     cp_wait_warp();
     stage_patterns<MaskT>(P, sl);
-    return true;
+    return state;
 }
 
 // Stage-all mode: this warp's item of every colour (one item per colour at
@@ -739,6 +866,47 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
     }
 }
 
+// Learned filter bookkeeping after an item ran: the element's accepted,
+// donor-less and improving trials into this generation's history, the item
+// counters (run, useful, audited), and for sampled elements a training
+// sample (the features as at the decision, label: the item accepted a trial).
+__device__ void item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl, unsigned imp)
+{
+    const int lane = threadIdx.x & 31;
+    acc = __reduce_add_sync(kFull, acc);
+    dl = __reduce_add_sync(kFull, dl);
+    imp = __reduce_add_sync(kFull, imp);
+    const int q = h[H_Q];
+    const bool audited = h[H_VALID] == IT_AUDIT, first = h[H_SUB] == 0;
+    if (lane == 0) {
+        uint32_t *cur = P.flt.hist + (size_t)(g & 1) * 3 * (size_t)P.m;
+        if (acc) atomicAdd(&cur[q], acc);
+        if (dl) atomicAdd(&cur[P.m + q], dl);
+        if (imp) atomicAdd(&cur[2 * (size_t)P.m + q], imp);
+        GomFilterState *st = P.flt.st;
+        atomicAdd(&st->cnt[FC_RUN], 1ull);
+        if (acc) atomicAdd(&st->cnt[FC_RUN_USEFUL], 1ull);
+        if (audited) {
+            atomicAdd(&st->cnt[FC_AUDITED], 1ull);
+            if (acc) atomicAdd(&st->cnt[FC_AUDITED_USEFUL], 1ull);
+        }
+    }
+    if (first && filter_sample(q, g)) {
+        float x[kFilterIn];
+        filter_features(P, q, g, x);
+        unsigned long long idx = 0;
+        if (lane == 0) idx = atomicAdd(&P.flt.st->log_count, 1ull);
+        idx = __shfl_sync(kFull, idx, 0);
+        if ((long long)idx < P.flt.log_cap) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < kFilterIn; ++k) v = lane == k ? x[k] : v;
+            if (lane < kFilterIn) P.flt.log_x[idx * kFilterIn + lane] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+            if (lane == 0) P.flt.log_y[idx] = acc ? 1 : 0;
+        }
+    }
+}
+
 // All trials of a staged item (Alg. 2 for each individual of its words):
 //  loads:   every global load of a word group is issued together: the
 //           parent's rows on F_j, its outside neighbours' words and the
@@ -778,6 +946,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
     uint32_t *xw = sl + P.off_xw;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     const int ne_tot = n_out + n_in;
+    const unsigned acc0 = n_acc, dl0 = n_dl, imp0 = n_imp; // this item's counts, for the learned filter
     const int fl = lane < s ? fv[lane] : 0;
     const int fl2 = (WIDE && lane + 32 < s) ? fv[lane + 32] : 0;
 
@@ -926,6 +1095,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
             }
         }
     }
+    if (P.learn) item_record(P, h, g, n_acc - acc0, n_dl - dl0, n_imp - imp0);
     __syncwarp();
 }
 
@@ -973,18 +1143,20 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
-    if (!(first_staged ? sl[H_VALID] != 0 : stage_item<WPI, MaskT>(P, c, gwarp, sl))) return;
+    int state = first_staged ? (int)sl[H_VALID] : stage_item<WPI, MaskT>(P, c, gwarp, sl, g);
+    if (state == IT_NONE) return;
     // one call site of run_item and of stage_item (the loop body is the hot code)
     const bool dyn = P.dyn && !single;
     unsigned claim = 0;
     if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     for (int next = gwarp + nwarps;; next += nwarps) {
-        run_item<WPI, MaskT, AccT>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
+        if (state != IT_SKIPPED) run_item<WPI, MaskT, AccT>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
         // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (single) break;
         // stop on the first item past the group (items are numbered densely)
         const int it = dyn ? nwarps + (int)__shfl_sync(kFull, claim, 0) : next;
-        if (!stage_item<WPI, MaskT>(P, c, it, sl)) break;
+        state = stage_item<WPI, MaskT>(P, c, it, sl, g);
+        if (state == IT_NONE) break;
         if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     }
 }
@@ -1110,7 +1282,7 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
             const int c = all ? S.order[t] : P.order[t];
             uint32_t *sl = all ? slices + c * P.warp_smem : slices;
             // without stage_all: stage the first item of group t before its barrier
-            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl);
+            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl, g);
             if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
             if (tr) P.trace[4 + 2 * t] = global_ns();
             phase_mix<WPI, MaskT, AccT>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);

@@ -86,6 +86,13 @@ SIGNATURES = [
     ("gom_batch_stats", C.c_int, [_P, _I32, _P, _I32, _P]),
     ("gom_batch_layout", C.c_int, [_P, _I32, _P, _P, _P]),
     ("gom_batch_destroy", None, [_P]),
+    ("gom_filter_workspace_bytes", _SZ, [_P, _I64]),
+    ("gom_filter_attach", C.c_int, [_P, _P, _SZ, _I64]),
+    ("gom_filter_set_mode", C.c_int, [_P, _I32]),
+    ("gom_filter_configure", C.c_int, [_P, C.c_float, C.c_float]),
+    ("gom_filter_train", C.c_int, [_P, _I32, C.c_float, C.c_float, C.c_float, _U64, _P]),
+    ("gom_filter_stats", C.c_int, [_P, _P]),
+    ("gom_filter_skipped", C.c_int, [_P, _P]),
     ("gom_ims_workspace_bytes", _SZ, [_P, _P, _I32, _I32]),
     ("gom_ims_create", C.c_int, [_P, _P, _I32, _I32, _I32, _U64, _P, _SZ, _P, _P]),
     ("gom_ims_run", C.c_int, [_P, _I32, _I64, _P]),
@@ -160,6 +167,25 @@ class Graph:
 
 def _graph(g):
     return g if isinstance(g, Graph) else Graph(g)
+
+
+class FilterTrain(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("useful", C.c_int64), ("loss", C.c_double), ("threshold", C.c_float),
+                ("skip_fraction", C.c_double), ("recall", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class FilterStats(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("enabled", C.c_int32), ("disabled_at", C.c_int32), ("threshold", C.c_float),
+                ("log_count", C.c_int64), ("last", C.c_int64 * 5), ("total", C.c_int64 * 5)]
+
+    def as_dict(self):
+        names = ("run", "run_useful", "skipped", "audited", "audited_useful")
+        return {"mode": self.mode, "enabled": self.enabled, "disabled_at": self.disabled_at,
+                "threshold": self.threshold, "log_count": self.log_count,
+                "last": dict(zip(names, list(self.last))), "total": dict(zip(names, list(self.total)))}
 
 
 class ImsResult(C.Structure):
@@ -467,6 +493,45 @@ def gom_batch_destroy(batch: Batch):
     if batch.h:
         load().gom_batch_destroy(batch.h)
         batch.h = None
+
+
+def gom_filter_workspace_bytes(ctx: Ctx, log_capacity: int) -> int:
+    return int(load().gom_filter_workspace_bytes(ctx.h, log_capacity))
+
+
+def gom_filter_attach(ctx: Ctx, workspace, log_capacity: int):
+    """workspace: a CUDA tensor (kept alive by the handle), 256-byte aligned."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(load().gom_filter_attach(ctx.h, _ptr(workspace), nbytes, log_capacity), "gom_filter_attach", ctx)
+    ctx.filter_workspace = workspace
+
+
+def gom_filter_set_mode(ctx: Ctx, mode: int):
+    _check(load().gom_filter_set_mode(ctx.h, mode), "gom_filter_set_mode", ctx)
+
+
+def gom_filter_configure(ctx: Ctx, threshold: float, min_recall: float):
+    _check(load().gom_filter_configure(ctx.h, threshold, min_recall), "gom_filter_configure", ctx)
+
+
+def gom_filter_train(ctx: Ctx, epochs: int = 200, learning_rate: float = 0.01, pos_weight: float = 1.0,
+                     target_recall: float = 0.95, seed: int = 1) -> dict:
+    out = FilterTrain()
+    _check(load().gom_filter_train(ctx.h, epochs, learning_rate, pos_weight, target_recall, seed, C.byref(out)),
+           "gom_filter_train", ctx)
+    return out.as_dict()
+
+
+def gom_filter_stats(ctx: Ctx) -> dict:
+    out = FilterStats()
+    _check(load().gom_filter_stats(ctx.h, C.byref(out)), "gom_filter_stats", ctx)
+    return out.as_dict()
+
+
+def gom_filter_skipped(ctx: Ctx, m: int):
+    mask = np.zeros(m, dtype=np.uint8)
+    _check(load().gom_filter_skipped(ctx.h, mask.ctypes.data), "gom_filter_skipped", ctx)
+    return mask
 
 
 class Ims:

@@ -547,3 +547,23 @@ def test_bflt_replay_and_tree_properties(oracle, seed, bound):
                   if not (a & b) and (a | b) == set(s)]
         assert len(splits) >= 1
     assert len(set(sets)) == len(sets)
+
+
+def test_generation_skip_mask(oracle):
+    """The replay of a filtered generation: an all-zero mask is the plain
+    generation; an all-one mask runs no trial and changes nothing but the
+    generation counter."""
+    g = I.torus2d(8, seed=7)
+    ep, ev = oracle.build_fos(g)
+    k, co = oracle.color(g, ep, ev)
+    a = oracle.Run(g, ep, ev, co, k, 12, 4)
+    b = oracle.Run(g, ep, ev, co, k, 12, 4)
+    m = len(ep) - 1
+    assert a.generation() == b.generation_skip(np.zeros(m, dtype=np.uint8))
+    ra, rb = a.get(), b.get()
+    assert np.array_equal(ra["pop"], rb["pop"]) and np.array_equal(ra["f"], rb["f"])
+    before = b.get()
+    st = b.generation_skip(np.ones(m, dtype=np.uint8))
+    after = b.get()
+    assert st["trials"] == 0 and st["accepted"] == 0
+    assert np.array_equal(before["pop"], after["pop"]) and after["g"] == before["g"] + 1
