@@ -313,11 +313,11 @@ int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float 
         }
     float thr = -INFINITY;
     if (!pos.empty()) {
+        // skipping strictly below the (may_lose+1)-th smallest useful logit
+        // loses at most may_lose useful samples, ties included
         std::sort(pos.begin(), pos.end());
         const int64_t may_lose = static_cast<int64_t>(std::floor((1.0 - target_recall) * useful));
-        thr = may_lose > 0 ? pos[static_cast<size_t>(may_lose - 1)] : -INFINITY;
-        // skip strictly below: samples at the threshold are kept
-        if (may_lose > 0) thr = std::nextafter(thr, INFINITY);
+        thr = pos[static_cast<size_t>(std::min<int64_t>(may_lose, useful - 1))];
     }
     int64_t skipped = 0, lost = 0;
     for (int64_t n = 0; n < N; ++n)

@@ -744,11 +744,15 @@ __device__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x
     x[13] = x[14] = x[15] = 0.f;
 }
 
-// The MLP's output (logit): 64 ReLU units over the 16 features, bf16 weights,
-// fp32 accumulation, two units per lane and a fixed-order warp sum.
-__device__ float filter_logit(const GomParams &P, const float (&x)[kFilterIn])
+// The MLP's output (logit): 64 ReLU units over the 16 features (rounded to
+// bf16, as logged), bf16 weights, fp32 accumulation, two units per lane and a
+// fixed-order warp sum -- the order of the training code's evaluation.
+__device__ float filter_logit(const GomParams &P, const float (&x0)[kFilterIn])
 {
     const int lane = threadIdx.x & 31;
+    float x[kFilterIn]; // the features as the training log holds them (bf16)
+#pragma unroll
+    for (int k = 0; k < kFilterIn; ++k) x[k] = __bfloat162float(__float2bfloat16_rn(x0[k]));
     float part = 0.f;
     for (int h = lane; h < kFilterHidden; h += 32) {
         float z = P.flt.b1[h];
