@@ -58,6 +58,11 @@ BATCH_WORKLOADS = {
                 "over {32, 64, 128, 256}, graph and Philox seeds 1..256",
 }
 # autotuner candidates: (warps per block, register budget in resident blocks, grid cap, item cost)
+LEARNED_WORKLOADS = {
+    "learned1000": "learned trial filter on the 2D torus 1000x1000 (n=1,000,000), int32 weights U[1,100], pop 256: "
+                   "MLP (16 features, 64 hidden, bf16 weights, fp32 accumulation) trained on the accept/reject "
+                   "log of 50 plain generations, then run to the fitness plain GOM reaches at generation 200",
+}
 BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300)]
 SEED = 1
 L2_BYTES = 129 * 1024 * 1024
@@ -257,7 +262,8 @@ def run_reference(args, wl, rank, world):
                 "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    build, p, desc = WORKLOADS[wl]
+    # the learned workload's reference is the oracle on its graph (plain GOM, no filter)
+    build, p, desc = WORKLOADS["torus1000" if wl in LEARNED_WORKLOADS else wl]
     g = build()
     nth = oracle_threads()
     val, gens, el = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps, threads=nth)
@@ -521,6 +527,72 @@ def run_batch(args, wl, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args, wl, rank, world, local):
+    """Learned trial filter against plain GOM on the same GPU: both start from
+    the same population; plain runs 200 generations, whose final best fitness
+    is the target; the learned run logs 50 plain generations, trains its MLP,
+    then runs with the filter until the target (at most 400 generations in
+    all).  Times are wall clock with the device synchronised, training
+    included."""
+    import torch
+
+    from paper_2203_08680_gb300 import gom
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    g = I.torus2d(1000)
+    p, seed, warm, total = 256, SEED + rank, 50, 200
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    A = gom.Population(g, p, seed, stream=stream)
+    (stA, nA), tA = timed(lambda: A.generation(total))
+    target = stA[-1]["best_fitness"]
+    trials_plain = p * A.m * nA
+
+    B = gom.Population(g, p, seed, stream=stream, fos=A.fos)
+    cap = 1 << 20
+    ws = torch.empty(gom.gom_filter_workspace_bytes(B.ctx, cap) + 256, dtype=torch.uint8, device=dev)
+    ws = ws[(-ws.data_ptr()) % 256:]
+    gom.gom_filter_attach(B.ctx, ws, cap)
+    gom.gom_filter_set_mode(B.ctx, 1)
+    (stB1, n1), t1 = timed(lambda: B.generation(warm, target))
+    tr, t2 = timed(lambda: gom.gom_filter_train(B.ctx, epochs=200, learning_rate=0.02, pos_weight=1.0,
+                                                target_recall=args.learn_recall))
+    gom.gom_filter_configure(B.ctx, tr["threshold"], args.learn_min_recall)
+    gom.gom_filter_set_mode(B.ctx, 2)
+    reached, n2, t3, best = bool(stB1 and stB1[-1]["reached_target"]), 0, 0.0, stB1[-1]["best_fitness"]
+    while not reached and n1 + n2 < 2 * total:
+        (st, n), dt = timed(lambda: B.generation(25, target))
+        n2 += n
+        t3 += dt
+        best = st[-1]["best_fitness"]
+        reached = bool(st[-1]["reached_target"])
+    fs = gom.gom_filter_stats(B.ctx)
+    learned_s = t1 + t2 + t3
+    line = {
+        "metric": "time to target cut (learned trial filter vs plain GOM, same GPU)", "value": learned_s * 1e3,
+        "unit": "ms", "n_gpus": world, "steps": n1 + n2, "warmup": 0, "ms_per_step": learned_s * 1e3 / max(n1 + n2, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl, "description": LEARNED_WORKLOADS[wl], "population": p, "elements": A.m,
+                   "target": target, "target_source": f"plain GOM best fitness at generation {total}",
+                   "parallelism": f"replicas{world}"},
+        "plain": {"ms": tA * 1e3, "generations": nA, "trials_per_sec": trials_plain / tA},
+        "learned": {"reached": reached, "best": best, "generations_logged": n1, "generations_filtered": n2,
+                    "log_ms": t1 * 1e3, "train_ms": t2 * 1e3, "filtered_ms": t3 * 1e3,
+                    "ms_per_filtered_generation": t3 * 1e3 / max(n2, 1), "train": tr, "filter": fs},
+        "speedup_vs_plain": tA / learned_s if reached else None,
+        "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def time_to_target(args, g, p, seed, stream, wl):
     import torch
 
@@ -646,7 +718,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gom", choices=["gom", "reference"])
-    ap.add_argument("--workload", default="torus100", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default="torus100",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(LEARNED_WORKLOADS))
+    ap.add_argument("--learn-recall", type=float, default=0.95, help="learned filter: training recall target")
+    ap.add_argument("--learn-min-recall", type=float, default=0.8, help="learned filter: self-disable recall")
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -669,6 +744,8 @@ def main():
         run_reference(args, args.workload, rank, world)
     elif args.workload in BATCH_WORKLOADS:
         run_batch(args, args.workload, rank, world, local)
+    elif args.workload in LEARNED_WORKLOADS:
+        run_learned(args, args.workload, rank, world, local)
     else:
         run_gpu(args, args.workload, rank, world, local)
     if world > 1:
