@@ -788,6 +788,31 @@ __device__ __forceinline__ bool filter_sample(int q, uint32_t g)
 // Slice validity states: no item, staged, skipped by the filter, staged for an audit.
 enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
 
+// The filter's decision on a decoded item (warp-wide; kept out of line, so
+// the mixing loop stays small when the filter is off): IT_STAGED, IT_SKIPPED
+// (the element is marked skipped and counted) or IT_AUDIT; written to the
+// slice header.
+__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
+{
+    int state = IT_STAGED;
+    if (P.flt.st->enabled) {
+        const int q = reinterpret_cast<const int *>(sl)[H_Q];
+        float x[kFilterIn];
+        filter_features(P, q, g, x);
+        if (filter_logit(P, x) < P.flt.st->threshold) {
+            state = filter_audit(q, g) ? IT_AUDIT : IT_SKIPPED;
+            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) {
+                P.flt.skipped[q] = 1;
+                atomicAdd(&P.flt.st->cnt[FC_SKIPPED], 1ull);
+            }
+        }
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) sl[H_VALID] = (uint32_t)state;
+    __syncwarp();
+    return state;
+}
+
 // Stages one item of colour c (item index `it`) into a slice: decode, then
 // two levels of asynchronous copies, then the pattern table.  Only
 // generation-constant data: it may run before the barrier that opens the
@@ -801,21 +826,8 @@ __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uin
     if (!valid) return IT_NONE;
     __syncwarp();
     int state = IT_STAGED;
-    if (P.learn == 2 && P.flt.st->enabled) {
-        const int *h = reinterpret_cast<const int *>(sl);
-        const int q = h[H_Q];
-        float x[kFilterIn];
-        filter_features(P, q, g, x);
-        if (filter_logit(P, x) < P.flt.st->threshold) {
-            state = filter_audit(q, g) ? IT_AUDIT : IT_SKIPPED;
-            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) {
-                P.flt.skipped[q] = 1;
-                atomicAdd(&P.flt.st->cnt[FC_SKIPPED], 1ull);
-            }
-        }
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) sl[H_VALID] = (uint32_t)state;
-        __syncwarp();
+    if (P.learn == 2) {
+        state = filter_decide(P, sl, g);
         if (state == IT_SKIPPED) return state;
     }
     stage_lists<WPI>(P, sl);
@@ -874,7 +886,8 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
 // donor-less and improving trials into this generation's history, the item
 // counters (run, useful, audited), and for sampled elements a training
 // sample (the features as at the decision, label: the item accepted a trial).
-__device__ void item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl, unsigned imp)
+__device__ __noinline__ void item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
+                                        unsigned imp)
 {
     const int lane = threadIdx.x & 31;
     acc = __reduce_add_sync(kFull, acc);
