@@ -111,7 +111,8 @@ typedef struct gom_gen_stats {
     int64_t generation;     /* index g of the generation (0 = first after init) */
     int64_t best_fitness;   /* max_i f[i] at its end */
     int64_t elite_fitness;  /* fitness of the elitist at its end */
-    int64_t trials;         /* (individual, element) pairs = p * m, donor-less included */
+    int64_t trials;         /* (individual, element) trials made: p * m, less those a learned
+                               filter skipped; donor-less ones included */
     int64_t donorless;      /* trials with no donor differing on the element */
     int64_t accepted;       /* trials whose change was kept */
     int64_t improving;      /* accepted trials with a positive delta */

@@ -72,7 +72,7 @@ struct GomDevState {
     int64_t best;      // best fitness after the last generation
     int32_t err;       // device-side error word (0 = none)
     uint32_t call_g0;  // generation counter at the start of the current call
-    int64_t cnt[4];    // counters of the running generation: donorless, accepted, improving
+    int64_t cnt[4];    // counters of the running generation: donorless, accepted, improving, trials skipped
 };
 
 struct GomBarrier { // grid barrier of the persistent kernel: monotonic arrival count

@@ -198,7 +198,7 @@ __global__ void k_set_state(GomParams P, int64_t fe, int64_t g)
         P.st->improved = 0;
         P.st->done = 0;
         P.st->g = (uint32_t)g;
-        P.st->cnt[0] = P.st->cnt[1] = P.st->cnt[2] = 0;
+        P.st->cnt[0] = P.st->cnt[1] = P.st->cnt[2] = P.st->cnt[3] = 0;
     }
     for (int w = threadIdx.x; w < 2 * P.W; w += blockDim.x) P.eqw[w] = kFull;
 }
@@ -419,12 +419,12 @@ __device__ bool phase_gen_end(const GomParams &P, int64_t target, uint32_t g, Ge
         S.generation = g;
         S.best = best;
         S.elite = e.fe;
-        S.trials = (int64_t)P.p * P.m;
+        S.trials = (int64_t)P.p * P.m - st->cnt[3]; // minus the trials a learned filter skipped
         S.donorless = st->cnt[0];
         S.accepted = st->cnt[1];
         S.improving = st->cnt[2];
         S.reached = reached;
-        st->cnt[0] = st->cnt[1] = st->cnt[2] = 0;
+        st->cnt[0] = st->cnt[1] = st->cnt[2] = st->cnt[3] = 0;
         st->done = reached;
         st->g = g + 1;
         if (P.learn) filter_generation_end(P, g);
@@ -792,7 +792,7 @@ enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
 // the mixing loop stays small when the filter is off): IT_STAGED, IT_SKIPPED
 // (the element is marked skipped and counted) or IT_AUDIT; written to the
 // slice header.
-__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
+__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g, int item_trials)
 {
     int state = IT_STAGED;
     if (P.flt.st->enabled) {
@@ -804,6 +804,7 @@ __device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint
             if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) {
                 P.flt.skipped[q] = 1;
                 atomicAdd(&P.flt.st->cnt[FC_SKIPPED], 1ull);
+                atomicAdd((unsigned long long *)&P.st->cnt[3], (unsigned long long)item_trials); // trials not made
             }
         }
     }
@@ -827,7 +828,9 @@ __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uin
     __syncwarp();
     int state = IT_STAGED;
     if (P.learn == 2) {
-        state = filter_decide(P, sl, g);
+        const int sub = reinterpret_cast<const int *>(sl)[H_SUB], w = 32 * WPI;
+        const int trials = P.split ? min(P.p, w * (sub + 1)) - w * sub : P.p;
+        state = filter_decide(P, sl, g, trials);
         if (state == IT_SKIPPED) return state;
     }
     stage_lists<WPI>(P, sl);

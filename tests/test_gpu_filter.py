@@ -19,7 +19,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from test_gpu_parity import _assert_same_state, _gpu_state, _oracle_run  # noqa: E402
 
 STAT_KEYS = [("best_fitness", "best"), ("elite_fitness", "elite"), ("donorless", "donorless"),
-             ("accepted", "accepted"), ("improving", "improving")]
+             ("accepted", "accepted"), ("improving", "improving"), ("trials", "trials")]
 
 
 def _attach(P, cap=1 << 16):
