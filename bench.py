@@ -564,7 +564,7 @@ def run_learned(args, wl, rank, world, local):
     (stB1, n1), t1 = timed(lambda: B.generation(warm, target))
     tr, t2 = timed(lambda: gom.gom_filter_train(B.ctx, epochs=200, learning_rate=0.02, pos_weight=1.0,
                                                 target_recall=args.learn_recall))
-    gom.gom_filter_configure(B.ctx, tr["threshold"], args.learn_min_recall)
+    gom.gom_filter_configure(B.ctx, tr["threshold"], args.learn_recall, args.learn_min_recall)
     gom.gom_filter_set_mode(B.ctx, 2)
     reached, n2, t3, best = bool(stB1 and stB1[-1]["reached_target"]), 0, 0.0, stB1[-1]["best_fitness"]
     while not reached and n1 + n2 < 2 * total:
@@ -720,8 +720,8 @@ def main():
     ap.add_argument("--impl", default="gom", choices=["gom", "reference"])
     ap.add_argument("--workload", default="torus100",
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(LEARNED_WORKLOADS))
-    ap.add_argument("--learn-recall", type=float, default=0.95, help="learned filter: training recall target")
-    ap.add_argument("--learn-min-recall", type=float, default=0.8, help="learned filter: self-disable recall")
+    ap.add_argument("--learn-recall", type=float, default=0.9, help="learned filter: recall target")
+    ap.add_argument("--learn-min-recall", type=float, default=0.5, help="learned filter: self-disable recall")
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -390,9 +390,11 @@ int gom_batch_generation_each(gom_batch_t *batch, const int32_t *num_generations
  * elements predicted to accept nothing.  Every change that is kept is still
  * decided by the exact integer partial evaluation of Alg. 2; skipping only
  * removes trials.  One in 16 elements the filter would skip is run anyway (an
- * audit); when the estimated recall (useful elements run / all useful ones)
- * of a generation falls below min_recall the filter turns itself off and the
- * run goes on as plain GOM.  Features of element j in generation g: its size,
+ * audit).  From the audits each generation estimates the recall (useful
+ * elements run / all useful ones); the skip threshold steps down while the
+ * estimate is under target_recall and up while it is well over it, and when
+ * it stays under min_recall for two generations the filter turns itself off
+ * and the run goes on as plain GOM.  Features of element j in generation g: its size,
  * outside and inside edge counts, its accepted, donor-less and improving
  * trials of generation g-1 (fractions of p), whether it accepted none or had no
  * donor at all, log2(1+g), the population's accept, improve and donor-less
@@ -429,15 +431,18 @@ int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_
 /* Mode 0, 1 or 2 (above).  Waits for the stream. */
 int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode);
 
-/* Skip threshold (logit) and the recall under which the filter turns itself off. */
-int gom_filter_configure(gom_ctx_t *ctx, float threshold, float min_recall);
+/* Skip threshold (logit), the recall the threshold follows, and the recall
+ * under which the filter turns itself off (defaults after attach: none, 0.9, 0.5). */
+int gom_filter_configure(gom_ctx_t *ctx, float threshold, float target_recall, float min_recall);
 
 /*
  * Trains the MLP from scratch on the logged samples: `epochs` full-batch Adam
  * steps on the logistic loss with positive samples weighted by pos_weight
  * (hand-written kernels; weights initialised from `seed`), then sets the
  * threshold to the largest logit that keeps target_recall of the useful
- * logged samples.  *out (may be NULL) reports it.  GOM_E_STATE with an empty
+ * logged samples (and target_recall as the recall the threshold follows).
+ * The log is a ring: it holds the latest log_capacity samples.  *out (may be
+ * NULL) reports it.  GOM_E_STATE with an empty
  * log.  Waits.
  */
 int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float pos_weight, float target_recall,

@@ -220,7 +220,9 @@ int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_
     st.enabled = 0;
     st.disabled_at = -1;
     st.threshold = -INFINITY;
-    st.min_recall = 0.9f;
+    st.min_recall = 0.5f;
+    st.target_recall = 0.9f;
+    st.low_streak = 0;
     GOM_CUDA(ctx, cudaMemcpyAsync(F.st, &st, sizeof(st), cudaMemcpyHostToDevice, ctx->stream));
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->prm.learn = 0;
@@ -242,12 +244,18 @@ int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode)
     return rebuild_graphs(ctx);
 }
 
-int gom_filter_configure(gom_ctx_t *ctx, float threshold, float min_recall)
+int gom_filter_configure(gom_ctx_t *ctx, float threshold, float target_recall, float min_recall)
 {
-    if (!ctx || !ctx->filter_base || !(min_recall >= 0.f && min_recall <= 1.f)) return GOM_E_ARG;
+    if (!ctx || !ctx->filter_base || !(min_recall >= 0.f && min_recall <= 1.f) ||
+        !(target_recall >= 0.f && target_recall <= 1.f))
+        return GOM_E_ARG;
     GomFilterState *st = ctx->prm.flt.st;
+    const int32_t zero = 0;
     GOM_CUDA(ctx, cudaMemcpyAsync(&st->threshold, &threshold, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st->target_recall, &target_recall, sizeof(float), cudaMemcpyHostToDevice,
+                                  ctx->stream));
     GOM_CUDA(ctx, cudaMemcpyAsync(&st->min_recall, &min_recall, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st->low_streak, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream));
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return GOM_OK;
 }
@@ -327,6 +335,7 @@ int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float 
         }
     GomFilterState *d_st = ctx->prm.flt.st;
     GOM_CUDA(ctx, cudaMemcpyAsync(&d_st->threshold, &thr, sizeof(float), cudaMemcpyHostToDevice, s));
+    GOM_CUDA(ctx, cudaMemcpyAsync(&d_st->target_recall, &target_recall, sizeof(float), cudaMemcpyHostToDevice, s));
     GOM_CUDA(ctx, cudaStreamSynchronize(s));
     if (out) {
         out->samples = N;

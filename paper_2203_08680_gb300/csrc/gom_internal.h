@@ -104,7 +104,10 @@ struct GomFilterState {
     int32_t enabled;                   // 1 while the filter skips elements
     int32_t disabled_at;               // generation at which it turned itself off, -1 never
     float threshold;                   // skip when the logit is below it
-    float min_recall;                  // estimated recall under which the filter turns itself off
+    float min_recall;                  // estimated recall under which (two generations running) the
+                                       // filter turns itself off
+    float target_recall;               // the threshold follows the audits towards this recall
+    int32_t low_streak;                // generations in a row below min_recall
     unsigned long long log_count;      // samples offered to the log (those past its capacity are dropped)
     unsigned long long cnt[FC_N];      // items of the running generation: run, run with an acceptance,
                                        // skipped, audited, audited with an acceptance

@@ -376,10 +376,12 @@ struct GenEnd {
 };
 
 // The learned filter at the end of generation g (one thread): the counters
-// into last/total, and the recall check.  Recall is estimated as useful items
-// run / (useful items run + skipped items x the useful fraction of the
-// audited ones); below min_recall (with at least 16 audits) the filter turns
-// itself off and the run goes on as plain GOM.
+// into last/total, then, with at least 16 audits, the recall estimate --
+// useful items run / (useful items run + skipped items x the useful fraction
+// of the audited ones).  The threshold steps down (skip less) while the
+// estimate is under target_recall and up while it is well over it; two
+// generations in a row under min_recall turn the filter off, and the run goes
+// on as plain GOM.
 __device__ void filter_generation_end(const GomParams &P, uint32_t g)
 {
     GomFilterState *st = P.flt.st;
@@ -391,7 +393,13 @@ __device__ void filter_generation_end(const GomParams &P, uint32_t g)
         const double miss = (double)st->last[FC_AUDITED_USEFUL] / (double)st->last[FC_AUDITED];
         const double found = (double)st->last[FC_RUN_USEFUL];
         const double lost = (double)st->last[FC_SKIPPED] * miss;
-        if (found + lost > 0.0 && found / (found + lost) < (double)st->min_recall) {
+        const double recall = found + lost > 0.0 ? found / (found + lost) : 1.0;
+        if (recall < (double)st->target_recall)
+            st->threshold -= 0.25f;
+        else if (recall > (double)st->target_recall + 0.03)
+            st->threshold += 0.125f;
+        st->low_streak = recall < (double)st->min_recall ? st->low_streak + 1 : 0;
+        if (st->low_streak >= 2) {
             st->enabled = 0;
             st->disabled_at = (int32_t)g;
         }
@@ -917,7 +925,8 @@ __device__ __noinline__ void item_record(const GomParams &P, const int *h, uint3
         unsigned long long idx = 0;
         if (lane == 0) idx = atomicAdd(&P.flt.st->log_count, 1ull);
         idx = __shfl_sync(kFull, idx, 0);
-        if ((long long)idx < P.flt.log_cap) {
+        if (P.flt.log_cap > 0) { // a ring: the log keeps the latest log_cap samples
+            idx %= (unsigned long long)P.flt.log_cap;
             float v = 0.f;
 #pragma unroll
             for (int k = 0; k < kFilterIn; ++k) v = lane == k ? x[k] : v;

@@ -89,7 +89,7 @@ SIGNATURES = [
     ("gom_filter_workspace_bytes", _SZ, [_P, _I64]),
     ("gom_filter_attach", C.c_int, [_P, _P, _SZ, _I64]),
     ("gom_filter_set_mode", C.c_int, [_P, _I32]),
-    ("gom_filter_configure", C.c_int, [_P, C.c_float, C.c_float]),
+    ("gom_filter_configure", C.c_int, [_P, C.c_float, C.c_float, C.c_float]),
     ("gom_filter_train", C.c_int, [_P, _I32, C.c_float, C.c_float, C.c_float, _U64, _P]),
     ("gom_filter_stats", C.c_int, [_P, _P]),
     ("gom_filter_skipped", C.c_int, [_P, _P]),
@@ -510,8 +510,8 @@ def gom_filter_set_mode(ctx: Ctx, mode: int):
     _check(load().gom_filter_set_mode(ctx.h, mode), "gom_filter_set_mode", ctx)
 
 
-def gom_filter_configure(ctx: Ctx, threshold: float, min_recall: float):
-    _check(load().gom_filter_configure(ctx.h, threshold, min_recall), "gom_filter_configure", ctx)
+def gom_filter_configure(ctx: Ctx, threshold: float, target_recall: float = 0.9, min_recall: float = 0.5):
+    _check(load().gom_filter_configure(ctx.h, threshold, target_recall, min_recall), "gom_filter_configure", ctx)
 
 
 def gom_filter_train(ctx: Ctx, epochs: int = 200, learning_rate: float = 0.01, pos_weight: float = 1.0,

@@ -53,7 +53,7 @@ def test_filter_log_mode_is_plain_and_filtered_mode_replays(oracle, persistent):
     assert fs["log_count"] > 1000 and fs["last"]["skipped"] == 0
     tr = gom.gom_filter_train(P.ctx, epochs=150, learning_rate=0.02, pos_weight=1.0, target_recall=0.9)
     assert tr["samples"] == min(fs["log_count"], 1 << 16) and tr["recall"] >= 0.9
-    gom.gom_filter_configure(P.ctx, tr["threshold"], 0.0)  # never turns itself off here
+    gom.gom_filter_configure(P.ctx, tr["threshold"], 0.9, 0.0)  # never turns itself off here
     gom.gom_filter_set_mode(P.ctx, 2)
     skipped_any = False
     for gen in range(4):
@@ -79,11 +79,11 @@ def test_filter_turns_itself_off_when_recall_drops(oracle):
     gom.gom_filter_set_mode(P.ctx, 1)
     P.generation(3)
     gom.gom_filter_train(P.ctx, epochs=20)
-    gom.gom_filter_configure(P.ctx, 1e30, 0.5)
+    gom.gom_filter_configure(P.ctx, 1e30, 0.9, 0.5)
     gom.gom_filter_set_mode(P.ctx, 2)
-    P.generation(1)
+    P.generation(2)  # two generations under min_recall
     fs = gom.gom_filter_stats(P.ctx)
-    assert fs["enabled"] == 0 and fs["disabled_at"] == 3
+    assert fs["enabled"] == 0 and fs["disabled_at"] == 4
     assert fs["last"]["audited"] > 0 and fs["last"]["audited_useful"] > 0
     # plain from here: the next generation skips nothing
     P.generation(1)
