@@ -354,7 +354,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     item_split(c->W, pop, max_group, static_cast<int64_t>(c->sms) * 24, &wpi, &split);
     const int nwg = (wv + wpi - 1) / wpi;
     const int per = split ? nwg : 1;
-    c->mix_fn = gom_mix_kernel(wpi, narrow);
+    c->mix_fn = gom_mix_kernel(wpi, narrow, false);
     const SliceLayout SL = slice_layout(tabs.max_s, tabs.max_edges, c->W, wpi, narrow, split != 0, nwg);
     const int64_t off_fv = SL.off_fv, off_seg = SL.off_seg, off_wout = SL.off_wout, off_pr = SL.off_pr;
     const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_ds = SL.off_ds;
@@ -368,7 +368,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     const int64_t need_blocks = (max_group * per + warps_per_block - 1) / warps_per_block;
 
     // persistent path: one cooperative kernel, grid limited to co-resident blocks
-    c->run_fn = gom_run_kernel(wpi, narrow);
+    c->run_fn = gom_run_kernel(wpi, narrow, false);
     const size_t keys_smem = sizeof(unsigned long long) * static_cast<size_t>(std::max(c->k, 1));
     int coop = 0;
     GOM_CUDA(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));

@@ -216,6 +216,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         P.off_xw = static_cast<int32_t>(SL.off_xw);
         P.off_ds = static_cast<int32_t>(SL.off_ds);
         P.dyn = 1;
+        P.learn = 0; // the learned filter is not active inside batched launches
         P.bar = B->d_bars + b; // (P.trace: the context's phase trace, when switched on)
         B->params[b] = P;
         GomBatchInst &I = B->inst[b];

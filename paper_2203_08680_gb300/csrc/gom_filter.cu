@@ -14,6 +14,7 @@
 
 #include "gom_ctx.h"
 #include "gom_internal.h"
+#include "gom_kernels.cuh"
 
 namespace {
 
@@ -234,12 +235,25 @@ int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode)
     if (!ctx || mode < 0 || mode > 2) return GOM_E_ARG;
     if (mode > 0 && !ctx->filter_base) return GOM_E_STATE;
     if (mode == 2 && ctx->prm.stage_all && ctx->persistent) return GOM_E_STATE;
+    // the kernel instances with (or without) the filter's bookkeeping, on the same grids
+    const bool learn = mode > 0;
+    const void *mix = gom_mix_kernel(ctx->wpi, ctx->narrow, learn);
+    const void *run = gom_run_kernel(ctx->wpi, ctx->narrow, learn);
+    GOM_CUDA(ctx, raise_smem_limit(mix, ctx->mix_smem));
+    if (ctx->can_persist) {
+        GOM_CUDA(ctx, raise_smem_limit(run, ctx->run_smem));
+        int occ = 0;
+        GOM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, run, ctx->mix_threads, ctx->run_smem));
+        if (static_cast<int64_t>(occ) * ctx->sms < ctx->grid_run) return GOM_E_STATE;
+    }
     if (mode > 0) {
         const int32_t on = mode == 2 ? 1 : 0;
         GOM_CUDA(ctx, cudaMemcpyAsync(&ctx->prm.flt.st->enabled, &on, sizeof(on), cudaMemcpyHostToDevice,
                                       ctx->stream));
         GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
+    ctx->mix_fn = mix;
+    ctx->run_fn = run;
     ctx->prm.learn = mode;
     return rebuild_graphs(ctx);
 }

@@ -827,7 +827,7 @@ __device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint
 // generation-constant data: it may run before the barrier that opens the
 // group.  With the learned filter on, an element predicted to accept nothing
 // is not staged (IT_SKIPPED) unless it is audited.  Returns the slice state.
-template <int WPI, typename MaskT>
+template <int WPI, typename MaskT, bool LEARN>
 __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uint32_t *sl, uint32_t g)
 {
     __syncwarp();
@@ -835,7 +835,7 @@ __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uin
     if (!valid) return IT_NONE;
     __syncwarp();
     int state = IT_STAGED;
-    if (P.learn == 2) {
+    if (LEARN && P.learn == 2) {
         const int sub = reinterpret_cast<const int *>(sl)[H_SUB], w = 32 * WPI;
         const int trials = P.split ? min(P.p, w * (sub + 1)) - w * sub : P.p;
         state = filter_decide(P, sl, g, trials);
@@ -953,7 +953,7 @@ __device__ __noinline__ void item_record(const GomParams &P, const int *h, uint3
 //           XORs the accepted flips into row F_j[a]
 // Fitness deltas go to the block's shared accumulators s_f; counters to
 // per-lane counts.
-template <int WPI, typename MaskT, typename AccT>
+template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
                                          unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
@@ -1124,7 +1124,7 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
             }
         }
     }
-    if (P.learn) item_record(P, h, g, n_acc - acc0, n_dl - dl0, n_imp - imp0);
+    if (LEARN && P.learn) item_record(P, h, g, n_acc - acc0, n_dl - dl0, n_imp - imp0);
     __syncwarp();
 }
 
@@ -1165,26 +1165,26 @@ __device__ __forceinline__ void acc_flush(const GomParams &P, long long *s_f, un
 // variable of F_j (uint32_t: s <= 32, uint64_t: s <= 64); AccT is the delta
 // type (int32_t when every element's sum of |w| is < 2^30).  Counters
 // accumulate per lane.
-template <int WPI, typename MaskT, typename AccT>
+template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *sl,
                                           bool first_staged, bool single, long long *s_f, unsigned &n_dl,
                                           unsigned &n_acc, unsigned &n_imp)
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
-    int state = first_staged ? (int)sl[H_VALID] : stage_item<WPI, MaskT>(P, c, gwarp, sl, g);
+    int state = first_staged ? (int)sl[H_VALID] : stage_item<WPI, MaskT, LEARN>(P, c, gwarp, sl, g);
     if (state == IT_NONE) return;
     // one call site of run_item and of stage_item (the loop body is the hot code)
     const bool dyn = P.dyn && !single;
     unsigned claim = 0;
     if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     for (int next = gwarp + nwarps;; next += nwarps) {
-        if (state != IT_SKIPPED) run_item<WPI, MaskT, AccT>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
+        if (state != IT_SKIPPED) run_item<WPI, MaskT, AccT, LEARN>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
         // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (single) break;
         // stop on the first item past the group (items are numbered densely)
         const int it = dyn ? nwarps + (int)__shfl_sync(kFull, claim, 0) : next;
-        state = stage_item<WPI, MaskT>(P, c, it, sl, g);
+        state = stage_item<WPI, MaskT, LEARN>(P, c, it, sl, g);
         if (state == IT_NONE) break;
         if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     }
@@ -1225,7 +1225,7 @@ __global__ void k_order(GomParams P)
     phase_order(P, whole_grid(), s_key, P.st->g);
 }
 
-template <int WPI, typename MaskT, typename AccT>
+template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
@@ -1234,7 +1234,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-    phase_mix<WPI, MaskT, AccT>(P, whole_grid(), t, P.order[t], P.st->g,
+    phase_mix<WPI, MaskT, AccT, LEARN>(P, whole_grid(), t, P.order[t], P.st->g,
                                 s_dyn + (threadIdx.x >> 5) * warp_words(P, false), false, false, s_f, n_dl, n_acc,
                                 n_imp);
     count_flush(s_cnt, n_dl, n_acc, n_imp);
@@ -1271,7 +1271,7 @@ struct RunShared {
     int *order;                 // [kStageAllMaxK] stage-all group order
 };
 
-template <int WPI, typename MaskT, typename AccT>
+template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *bar, int G, int64_t target,
                                 const RunShared &S)
 {
@@ -1311,10 +1311,10 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
             const int c = all ? S.order[t] : P.order[t];
             uint32_t *sl = all ? slices + c * P.warp_smem : slices;
             // without stage_all: stage the first item of group t before its barrier
-            if (!all) stage_item<WPI, MaskT>(P, c, gwarp, sl, g);
+            if (!all) stage_item<WPI, MaskT, LEARN>(P, c, gwarp, sl, g);
             if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
             if (tr) P.trace[4 + 2 * t] = global_ns();
-            phase_mix<WPI, MaskT, AccT>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);
+            phase_mix<WPI, MaskT, AccT, LEARN>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);
             if (tr) P.trace[5 + 2 * t] = global_ns();
         }
         count_flush(S.cnt, n_dl, n_acc, n_imp);
@@ -1326,7 +1326,7 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
     if (G > 0 && lead) phase_gen_end(P, target, g - 1, e, true);
 }
 
-template <int WPI, typename MaskT, typename AccT>
+template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
@@ -1335,7 +1335,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run(GomParams P, int G, int6
     __shared__ unsigned long long s_okey[kStageAllMaxK];
     __shared__ int s_order[kStageAllMaxK];
     const RunShared S{s_dyn, s_f, s_cnt, s_okey, s_order};
-    run_generations<WPI, MaskT, AccT>(P, whole_grid(), P.bar, G, target, S);
+    run_generations<WPI, MaskT, AccT, LEARN>(P, whole_grid(), P.bar, G, target, S);
 }
 
 // One kernel variant of the batched path, compiled as its own function so
@@ -1344,7 +1344,7 @@ template <int WPI, typename MaskT, typename AccT>
 __device__ __noinline__ void batch_variant(const GomParams &P, const VGrid V, GomBarrier *bar, int G, int64_t target,
                                            const RunShared &S)
 {
-    run_generations<WPI, MaskT, AccT>(P, V, bar, G, target, S);
+    run_generations<WPI, MaskT, AccT, false>(P, V, bar, G, target, S);
 }
 
 // Batched path: many independent instances in one cooperative launch.  Each
@@ -1429,26 +1429,38 @@ __global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigne
     grid_barrier(&bar->count, err, expected, next, limit_ns);
 }
 
-const void *gom_mix_kernel(int wpi, bool narrow)
+template <bool LEARN>
+const void *mix_kernel(int wpi, bool narrow)
 {
     if (narrow)
-        return wpi == 4 ? (const void *)k_mix<4, uint32_t, int32_t>
-             : wpi == 2 ? (const void *)k_mix<2, uint32_t, int32_t>
-                        : (const void *)k_mix<1, uint32_t, int32_t>;
-    return wpi == 4 ? (const void *)k_mix<4, uint64_t, long long>
-         : wpi == 2 ? (const void *)k_mix<2, uint64_t, long long>
-                    : (const void *)k_mix<1, uint64_t, long long>;
+        return wpi == 4 ? (const void *)k_mix<4, uint32_t, int32_t, LEARN>
+             : wpi == 2 ? (const void *)k_mix<2, uint32_t, int32_t, LEARN>
+                        : (const void *)k_mix<1, uint32_t, int32_t, LEARN>;
+    return wpi == 4 ? (const void *)k_mix<4, uint64_t, long long, LEARN>
+         : wpi == 2 ? (const void *)k_mix<2, uint64_t, long long, LEARN>
+                    : (const void *)k_mix<1, uint64_t, long long, LEARN>;
 }
 
-const void *gom_run_kernel(int wpi, bool narrow)
+template <bool LEARN>
+const void *run_kernel(int wpi, bool narrow)
 {
     if (narrow)
-        return wpi == 4 ? (const void *)k_run<4, uint32_t, int32_t>
-             : wpi == 2 ? (const void *)k_run<2, uint32_t, int32_t>
-                        : (const void *)k_run<1, uint32_t, int32_t>;
-    return wpi == 4 ? (const void *)k_run<4, uint64_t, long long>
-         : wpi == 2 ? (const void *)k_run<2, uint64_t, long long>
-                    : (const void *)k_run<1, uint64_t, long long>;
+        return wpi == 4 ? (const void *)k_run<4, uint32_t, int32_t, LEARN>
+             : wpi == 2 ? (const void *)k_run<2, uint32_t, int32_t, LEARN>
+                        : (const void *)k_run<1, uint32_t, int32_t, LEARN>;
+    return wpi == 4 ? (const void *)k_run<4, uint64_t, long long, LEARN>
+         : wpi == 2 ? (const void *)k_run<2, uint64_t, long long, LEARN>
+                    : (const void *)k_run<1, uint64_t, long long, LEARN>;
+}
+
+const void *gom_mix_kernel(int wpi, bool narrow, bool learn)
+{
+    return learn ? mix_kernel<true>(wpi, narrow) : mix_kernel<false>(wpi, narrow);
+}
+
+const void *gom_run_kernel(int wpi, bool narrow, bool learn)
+{
+    return learn ? run_kernel<true>(wpi, narrow) : run_kernel<false>(wpi, narrow);
 }
 
 // ----------------------------------------------------------------------------
