@@ -800,7 +800,7 @@ enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
 // the mixing loop stays small when the filter is off): IT_STAGED, IT_SKIPPED
 // (the element is marked skipped and counted) or IT_AUDIT; written to the
 // slice header.
-__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g, int item_trials)
+__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
 {
     int state = IT_STAGED;
     if (P.flt.st->enabled) {
@@ -809,11 +809,7 @@ __device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint
         filter_features(P, q, g, x);
         if (filter_logit(P, x) < P.flt.st->threshold) {
             state = filter_audit(q, g) ? IT_AUDIT : IT_SKIPPED;
-            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) {
-                P.flt.skipped[q] = 1;
-                atomicAdd(&P.flt.st->cnt[FC_SKIPPED], 1ull);
-                atomicAdd((unsigned long long *)&P.st->cnt[3], (unsigned long long)item_trials); // trials not made
-            }
+            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) P.flt.skipped[q] = 1;
         }
     }
     __syncwarp();
@@ -836,9 +832,7 @@ __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uin
     __syncwarp();
     int state = IT_STAGED;
     if (LEARN && P.learn == 2) {
-        const int sub = reinterpret_cast<const int *>(sl)[H_SUB], w = 32 * WPI;
-        const int trials = P.split ? min(P.p, w * (sub + 1)) - w * sub : P.p;
-        state = filter_decide(P, sl, g, trials);
+        state = filter_decide(P, sl, g);
         if (state == IT_SKIPPED) return state;
     }
     stage_lists<WPI>(P, sl);
@@ -894,11 +888,12 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
 }
 
 // Learned filter bookkeeping after an item ran: the element's accepted,
-// donor-less and improving trials into this generation's history, the item
-// counters (run, useful, audited), and for sampled elements a training
-// sample (the features as at the decision, label: the item accepted a trial).
-__device__ __noinline__ void item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
-                                        unsigned imp)
+// donor-less and improving trials into this generation's history, and for
+// sampled elements a training sample (the features as at the decision,
+// label: the item accepted a trial).  Returns the item's counter increments
+// (bits: run, useful, audited, audited and useful) for the caller to sum.
+__device__ __noinline__ unsigned item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
+                                            unsigned imp)
 {
     const int lane = threadIdx.x & 31;
     acc = __reduce_add_sync(kFull, acc);
@@ -911,13 +906,6 @@ __device__ __noinline__ void item_record(const GomParams &P, const int *h, uint3
         if (acc) atomicAdd(&cur[q], acc);
         if (dl) atomicAdd(&cur[P.m + q], dl);
         if (imp) atomicAdd(&cur[2 * (size_t)P.m + q], imp);
-        GomFilterState *st = P.flt.st;
-        atomicAdd(&st->cnt[FC_RUN], 1ull);
-        if (acc) atomicAdd(&st->cnt[FC_RUN_USEFUL], 1ull);
-        if (audited) {
-            atomicAdd(&st->cnt[FC_AUDITED], 1ull);
-            if (acc) atomicAdd(&st->cnt[FC_AUDITED_USEFUL], 1ull);
-        }
     }
     if (first && filter_sample(q, g)) {
         float x[kFilterIn];
@@ -934,6 +922,8 @@ __device__ __noinline__ void item_record(const GomParams &P, const int *h, uint3
             if (lane == 0) P.flt.log_y[idx] = acc ? 1 : 0;
         }
     }
+    // the item's counter increments: run, run with an acceptance, audited, audited with an acceptance
+    return 1u | (acc ? 2u : 0u) | (audited ? 4u : 0u) | (audited && acc ? 8u : 0u);
 }
 
 // All trials of a staged item (Alg. 2 for each individual of its words):
@@ -954,7 +944,7 @@ __device__ __noinline__ void item_record(const GomParams &P, const int *h, uint3
 // Fitness deltas go to the block's shared accumulators s_f; counters to
 // per-lane counts.
 template <int WPI, typename MaskT, typename AccT, bool LEARN>
-__device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
+__device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
                                          unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
     constexpr bool WIDE = sizeof(MaskT) == 8;
@@ -1124,8 +1114,10 @@ __device__ __forceinline__ void run_item(const GomParams &P, uint32_t *sl, uint3
             }
         }
     }
-    if (LEARN && P.learn) item_record(P, h, g, n_acc - acc0, n_dl - dl0, n_imp - imp0);
+    unsigned flags = 0;
+    if (LEARN && P.learn) flags = item_record(P, h, g, n_acc - acc0, n_dl - dl0, n_imp - imp0);
     __syncwarp();
+    return flags;
 }
 
 // Zeroes the block's fitness and counter accumulators.
@@ -1177,9 +1169,22 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
     // one call site of run_item and of stage_item (the loop body is the hot code)
     const bool dyn = P.dyn && !single;
     unsigned claim = 0;
+    unsigned fc[FC_N] = {}, skipped_trials = 0; // learned filter: this warp's counters of the group
     if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     for (int next = gwarp + nwarps;; next += nwarps) {
-        if (state != IT_SKIPPED) run_item<WPI, MaskT, AccT, LEARN>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
+        if (state != IT_SKIPPED) {
+            const unsigned f = run_item<WPI, MaskT, AccT, LEARN>(P, sl, g, single, s_f, n_dl, n_acc, n_imp);
+            if (LEARN) {
+                fc[FC_RUN] += f & 1u;
+                fc[FC_RUN_USEFUL] += (f >> 1) & 1u;
+                fc[FC_AUDITED] += (f >> 2) & 1u;
+                fc[FC_AUDITED_USEFUL] += (f >> 3) & 1u;
+            }
+        } else if (LEARN) {
+            const int sub = reinterpret_cast<const int *>(sl)[H_SUB], w = 32 * WPI;
+            ++fc[FC_SKIPPED];
+            skipped_trials += P.split ? min(P.p, w * (sub + 1)) - w * sub : P.p;
+        }
         // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (single) break;
         // stop on the first item past the group (items are numbered densely)
@@ -1187,6 +1192,11 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
         state = stage_item<WPI, MaskT, LEARN>(P, c, it, sl, g);
         if (state == IT_NONE) break;
         if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
+    }
+    if (LEARN && P.learn && lane == 0) {
+        for (int x = 0; x < FC_N; ++x)
+            if (fc[x]) atomicAdd(&P.flt.st->cnt[x], (unsigned long long)fc[x]);
+        if (skipped_trials) atomicAdd((unsigned long long *)&P.st->cnt[3], (unsigned long long)skipped_trials);
     }
 }
 
