@@ -724,7 +724,7 @@ __device__ __forceinline__ void stage_draws(const GomParams &P, uint32_t *sl, ui
 // previous generation, and a constant.
 __device__ __forceinline__ float bf16_bits_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
-__device__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x)[kFilterIn])
+__device__ __forceinline__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x)[kFilterIn])
 {
     const int4 a = P.hdr[2 * q], b = P.hdr[2 * q + 1];
     const int s = a.w & 0xFF, n_in = a.w >> 8, n_out = b.x;
@@ -755,7 +755,7 @@ __device__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x
 // The MLP's output (logit): 64 ReLU units over the 16 features (rounded to
 // bf16, as logged), bf16 weights, fp32 accumulation, two units per lane and a
 // fixed-order warp sum -- the order of the training code's evaluation.
-__device__ float filter_logit(const GomParams &P, const float (&x0)[kFilterIn])
+__device__ __forceinline__ float filter_logit(const GomParams &P, const float (&x0)[kFilterIn])
 {
     const int lane = threadIdx.x & 31;
     float x[kFilterIn]; // the features as the training log holds them (bf16)
@@ -796,11 +796,10 @@ __device__ __forceinline__ bool filter_sample(int q, uint32_t g)
 // Slice validity states: no item, staged, skipped by the filter, staged for an audit.
 enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
 
-// The filter's decision on a decoded item (warp-wide; kept out of line, so
-// the mixing loop stays small when the filter is off): IT_STAGED, IT_SKIPPED
+// The filter's decision on a decoded item (warp-wide): IT_STAGED, IT_SKIPPED
 // (the element is marked skipped and counted) or IT_AUDIT; written to the
 // slice header.
-__device__ __noinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
+__device__ __forceinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
 {
     int state = IT_STAGED;
     if (P.flt.st->enabled) {
@@ -892,7 +891,7 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
 // sampled elements a training sample (the features as at the decision,
 // label: the item accepted a trial).  Returns the item's counter increments
 // (bits: run, useful, audited, audited and useful) for the caller to sum.
-__device__ __noinline__ unsigned item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
+__device__ __forceinline__ unsigned item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
                                             unsigned imp)
 {
     const int lane = threadIdx.x & 31;
