@@ -184,3 +184,27 @@ def test_batch_config4_full_size_sampled(oracle):
     for b, P in enumerate(pops):
         pop, fit, fe = P.population()
         assert np.array_equal(P.fitness().cpu().numpy(), fit.cpu().numpy()), b
+
+
+def test_batch_with_linkage_tree_instances(oracle):
+    """Instances whose FOS is the paper's bounded linkage tree (nested sets of
+    up to 32 and 64 variables) next to neighbourhood ones, in one launch."""
+    specs = [(I.random_regular(200, 4, seed=41), 40, 3, 32), (I.torus2d(12, seed=42), 70, 4, 64),
+             (I.random_regular(300, 3, seed=43), 33, 5, 0)]
+    pops, runs = [], []
+    for g, p, s, bound in specs:
+        fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound) if bound else None
+        pops.append(gom.Population(g, p, s, fos=fos))
+        if bound:
+            ep, ev = oracle.build_bflt(g, bound)
+        else:
+            ep, ev = oracle.build_fos(g)
+        k, co = oracle.color(g, ep, ev)
+        runs.append(oracle.Run(g, ep, ev, co, k, p, s))
+    batch = _batch(pops, (2, 3))
+    assert list(gom.gom_batch_generation(batch, 4)) == [4, 4, 4]
+    for b, (P, run) in enumerate(zip(pops, runs)):
+        ost = run.run(4)
+        for a, o in zip(gom.gom_batch_stats(batch, b, 4), ost):
+            _assert_same_stats(a, o)
+        _assert_same_state(_gpu_state(P), run.get(), f"instance {b}")

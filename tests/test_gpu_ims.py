@@ -86,3 +86,25 @@ def test_ims_first_reach_in_scheme_order(oracle):
     assert r["reached"] == 1
     assert (r["reached_step"], r["reached_population"]) == first
     assert r["best_fitness"] >= target
+
+
+def test_ims_on_the_linkage_tree(oracle):
+    """The scheme over the paper's bounded linkage tree FOS (Sec. 4.1 and 6.3 together)."""
+    g = I.torus2d(9, seed=8)
+    base, c, maxp, seed = 8, 2, 32, 4
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, 16)
+    gom.gom_color_fos(g, fos)
+    nb = gom.gom_ims_workspace_bytes(g, fos, base, maxp)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    ims = gom.gom_ims_create(g, fos, base, c, maxp, seed, ws)
+    gom.gom_ims_run(ims, 12)
+    ep, ev = oracle.build_bflt(g, 16)
+    k, co = oracle.color(g, ep, ev)
+    for i in range(gom.gom_ims_num_populations(ims)):
+        p = base << i
+        run = oracle.Run(g, ep, ev, co, k, p, seed + i)
+        run.run(12 // c ** i)
+        st = _ctx_state(gom.gom_ims_population(ims, i), g.n, p)
+        ref = run.get()
+        assert np.array_equal(st["pop"], ref["pop"]) and np.array_equal(st["f"], ref["f"]) and st["fe"] == ref["fe"]
