@@ -162,7 +162,7 @@ def test_batch_arguments():
     assert list(gom.gom_batch_generation(batch, 0)) == [0, 0]
 
 
-def test_batch_config4_full_size_sampled(oracle):
+def test_batch_256_instances_full_size_sampled(oracle):
     """The 256-instance batch of random d-regular graphs (n log-uniform in
     [1000, 65536], d in 3..8, p in {32, 64, 128, 256}): one batched
     generation, then the oracle replays it for a sample of instances

@@ -69,12 +69,12 @@ def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MA
     return Ps[0], run
 
 
-def test_config_torus10_p16_every_generation(oracle):
+def test_torus10_p16_every_generation(oracle):
     """2D torus 10x10, int32 weights U[1,100], p = 16, 20 generations, seed 1."""
     _parity(oracle, I.torus2d(10), 16, 1, 20)
 
 
-def test_config_torus100_p64(oracle):
+def test_torus100_p64(oracle):
     """2D torus 100x100, weights U[1,100], p = 64 (oracle-sized run length)."""
     _parity(oracle, I.torus2d(100), 64, 1, 30, check_every=5)
 
