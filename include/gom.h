@@ -84,7 +84,8 @@ extern "C" {
 
 /* Supported maxima of the library. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
-#define GOM_MAX_ELEMENT 64      /* variables in one FOS element */
+#define GOM_MAX_ELEMENT 128     /* variables in one FOS element (the paper's largest
+                                   linkage-tree bound, Sec. 6.1, is 100) */
 #define GOM_MAX_COLORS 28000    /* colour groups */
 
 /*
@@ -133,8 +134,8 @@ typedef struct gom_gen_stats {
  * variables is left out (Sec. 4.1), ties go to the pair of smaller creation
  * ids (singletons 0..n-1, then merges in order).  Elements: the n
  * singletons, then the merged sets in creation order, variables ascending.
- * The mixing kernels take elements of up to GOM_MAX_ELEMENT variables.
- * Validates the graph (GOM_E_GRAPH).  *out receives a handle to free with
+ * The mixing kernels take elements of up to GOM_MAX_ELEMENT variables (the
+ * paper's bounds of 10 and 100 both fit).  Validates the graph (GOM_E_GRAPH).  *out receives a handle to free with
  * gom_fos_destroy.
  */
 int gom_build_fos(const gom_graph_t *g, int32_t kind, int32_t param, gom_fos_t **out);
@@ -428,7 +429,9 @@ size_t gom_filter_workspace_bytes(gom_ctx_t *ctx, int64_t log_capacity);
 /* Attaches caller-owned device memory (256-byte aligned) as the filter state; mode 0. */
 int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_t log_capacity);
 
-/* Mode 0, 1 or 2 (above).  Waits for the stream. */
+/* Mode 0, 1 or 2 (above).  Waits for the stream.  GOM_E_LIMIT for modes 1
+ * and 2 when the FOS has an element of more than 64 variables (the filter's
+ * kernel instances take elements of up to 64). */
 int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode);
 
 /* Skip threshold (logit), the recall the threshold follows, and the recall

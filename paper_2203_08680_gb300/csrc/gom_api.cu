@@ -342,7 +342,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->k = fos->k;
 
     // kernel instance: words per item, mask and delta widths
-    const bool narrow = tabs.max_s <= 32 && tabs.max_abs_w < (int64_t(1) << 30);
+    const int32_t variant = kernel_variant(tabs.max_s, tabs.max_abs_w);
     int64_t max_group = 1;
     for (int32_t q = 0; q < fos->k; ++q) max_group = std::max(max_group, fos->cptr[q + 1] - fos->cptr[q]);
     int dev = 0;
@@ -351,11 +351,11 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     // Work split for the whole grid (~24 resident warps per SM).
     const int wv = (pop + 31) / 32;
     int wpi = 1, split = 0;
-    item_split(c->W, pop, max_group, static_cast<int64_t>(c->sms) * 24, &wpi, &split);
+    item_split(c->W, pop, max_group, static_cast<int64_t>(c->sms) * 24, variant, &wpi, &split);
     const int nwg = (wv + wpi - 1) / wpi;
     const int per = split ? nwg : 1;
-    c->mix_fn = gom_mix_kernel(wpi, narrow, false);
-    const SliceLayout SL = slice_layout(tabs.max_s, tabs.max_edges, c->W, wpi, narrow, split != 0, nwg);
+    c->mix_fn = gom_mix_kernel(wpi, variant, false);
+    const SliceLayout SL = slice_layout(tabs.max_s, tabs.max_edges, c->W, wpi, variant, split != 0, nwg);
     const int64_t off_fv = SL.off_fv, off_seg = SL.off_seg, off_wout = SL.off_wout, off_pr = SL.off_pr;
     const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_ds = SL.off_ds;
     const int64_t base_words = SL.base_words;
@@ -368,7 +368,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     const int64_t need_blocks = (max_group * per + warps_per_block - 1) / warps_per_block;
 
     // persistent path: one cooperative kernel, grid limited to co-resident blocks
-    c->run_fn = gom_run_kernel(wpi, narrow, false);
+    c->run_fn = gom_run_kernel(wpi, variant, false);
     const size_t keys_smem = sizeof(unsigned long long) * static_cast<size_t>(std::max(c->k, 1));
     int coop = 0;
     GOM_CUDA(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -421,7 +421,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     c->grid_mix = static_cast<int>(grid);
     c->persistent = c->can_persist;
     c->wpi = wpi;
-    c->narrow = narrow;
+    c->variant = variant;
     c->max_items = std::max<int64_t>(1, max_group * per);
     c->max_group = max_group;
     c->celems.assign(fos->celems.begin(), fos->celems.end());

@@ -70,7 +70,7 @@ bool valid_config(const gom_batch_config_t &c)
 int64_t max_split_items(const gom_ctx *c)
 {
     int wpi = 1, split = 0;
-    item_split(c->W, c->p, c->max_group, INT64_MAX / 8, &wpi, &split);
+    item_split(c->W, c->p, c->max_group, INT64_MAX / 8, c->variant, &wpi, &split);
     const int wv = (c->p + 31) / 32;
     return c->max_group * (split ? (wv + wpi - 1) / wpi : 1);
 }
@@ -153,9 +153,9 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         const int wv = (c->p + 31) / 32;
         for (int64_t warps : {int64_t(1), INT64_MAX / 8}) {
             int wpi = 1, split = 0;
-            item_split(c->W, c->p, c->max_group, warps, &wpi, &split);
+            item_split(c->W, c->p, c->max_group, warps, c->variant, &wpi, &split);
             const SliceLayout SL =
-                slice_layout(c->max_s, c->max_edges, c->W, wpi, c->narrow, split != 0, (wv + wpi - 1) / wpi);
+                slice_layout(c->max_s, c->max_edges, c->W, wpi, c->variant, split != 0, (wv + wpi - 1) / wpi);
             max_warp_words = std::max<int64_t>(max_warp_words, SL.base_words);
         }
     }
@@ -198,10 +198,10 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         const gom_ctx *c = cs[b];
         // the item split for this instance's warps, and its slice layout
         int wpi = 1, split = 0;
-        item_split(c->W, c->p, c->max_group, int64_t(nb[b]) * conf.warps_per_block, &wpi, &split);
+        item_split(c->W, c->p, c->max_group, int64_t(nb[b]) * conf.warps_per_block, c->variant, &wpi, &split);
         const int wv = (c->p + 31) / 32;
         const SliceLayout SL =
-            slice_layout(c->max_s, c->max_edges, c->W, wpi, c->narrow, split != 0, (wv + wpi - 1) / wpi);
+            slice_layout(c->max_s, c->max_edges, c->W, wpi, c->variant, split != 0, (wv + wpi - 1) / wpi);
         GomParams P = c->prm;
         P.stage_all = 0; // one staging slice per warp
         P.split = split;
@@ -224,7 +224,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         I.blk0 = blk;
         I.nblk = nb[b];
         I.wpi = wpi;
-        I.narrow = cs[b]->narrow ? 1 : 0;
+        I.variant = cs[b]->variant;
         I.target = INT64_MAX;
         blk += nb[b];
     }

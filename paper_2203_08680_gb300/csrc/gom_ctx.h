@@ -37,7 +37,7 @@ struct gom_ctx {
     int last_cuda = 0;
     // for batched launches (gom_batch_*)
     int wpi = 1;                 // words per mixing item
-    bool narrow = true;          // 32-bit masks and deltas
+    int32_t variant = kVarNarrow; // kernel variant (mask and delta widths)
     int64_t max_items = 1;       // mixing items of the largest colour group
     double sum_se = 0.0;         // sum over elements of (variables + edges)
     int64_t max_group = 1;       // elements of the largest colour group
@@ -61,7 +61,7 @@ inline int cuda_fail(gom_ctx *ctx, cudaError_t e)
 // of its layout; the kernels take these offsets (32-bit words): an 8-word
 // item header, the element's variables, their outside-edge starts (s+1),
 // their outside weight sums (int64), the rows of P on the element (W words
-// each), the pattern table (32 W masks of 4 or 8 bytes), its run starts (W
+// each), the pattern table (32 W masks of 4, 8 or 16 bytes), its run starts (W
 // words), each edge's {code, weight} (two words), each outside edge's parent
 // words (WPI words), and in stage-all mode the item's donor start positions
 // (one int per individual of its words).  Every offset is a multiple of 4
@@ -72,7 +72,7 @@ struct SliceLayout {
     int64_t all_words;  // with them (stage-all mode)
 };
 
-inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi, bool narrow, bool split,
+inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi, int32_t variant, bool split,
                                 int nwg)
 {
     auto round4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
@@ -82,7 +82,7 @@ inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi
     L.off_wout = L.off_seg + round4(max_s + 1);
     L.off_pr = L.off_wout + round4(2 * max_s);
     L.off_pat = L.off_pr + round4(max_s * W);
-    L.off_rs = L.off_pat + int64_t(32) * W * (narrow ? 1 : 2);
+    L.off_rs = L.off_pat + int64_t(32) * W * (variant == kVarNarrow ? 1 : variant == kVarWide ? 2 : 4);
     L.off_cw = L.off_rs + round4(W);
     L.off_xw = L.off_cw + round4(2 * max_edges);
     L.off_ds = L.off_xw + round4(max_edges * wpi);
@@ -96,11 +96,13 @@ inline SliceLayout slice_layout(int64_t max_s, int64_t max_edges, int W, int wpi
 // element walking all its words in groups of min(W, 4) words, or, with fewer
 // than about 4 elements per warp, one warp per (element, word group) so that
 // the warps stay busy (then single words if the population has only one
-// group of min(W, 4) words).
-inline void item_split(int W, int32_t p, int64_t max_group, int64_t warps, int *wpi, int *split)
+// group of min(W, 4) words).  The kernel variant for elements of more than
+// 64 variables has instances for groups of at most 2 words.
+inline void item_split(int W, int32_t p, int64_t max_group, int64_t warps, int32_t variant, int *wpi, int *split)
 {
     const int wv = (p + 31) / 32;
-    *wpi = W < 4 ? W : 4;
+    const int most = variant == kVarHuge ? 2 : 4;
+    *wpi = W < most ? W : most;
     *split = 0;
     if (max_group < 4 * warps && wv > 1) {
         *split = 1;

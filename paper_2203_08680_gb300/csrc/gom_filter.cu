@@ -237,8 +237,9 @@ int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode)
     if (mode == 2 && ctx->prm.stage_all && ctx->persistent) return GOM_E_STATE;
     // the kernel instances with (or without) the filter's bookkeeping, on the same grids
     const bool learn = mode > 0;
-    const void *mix = gom_mix_kernel(ctx->wpi, ctx->narrow, learn);
-    const void *run = gom_run_kernel(ctx->wpi, ctx->narrow, learn);
+    const void *mix = gom_mix_kernel(ctx->wpi, ctx->variant, learn);
+    const void *run = gom_run_kernel(ctx->wpi, ctx->variant, learn);
+    if (!mix || !run) return GOM_E_LIMIT; // no filter instances for elements of more than 64 variables
     GOM_CUDA(ctx, raise_smem_limit(mix, ctx->mix_smem));
     if (ctx->can_persist) {
         GOM_CUDA(ctx, raise_smem_limit(run, ctx->run_smem));

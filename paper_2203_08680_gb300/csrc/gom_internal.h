@@ -62,6 +62,18 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
 // ----------------------------------------------------------------------------
 // Device-side state and parameters.
 
+// Kernel variants by the largest element and the element weight sums:
+// narrow = elements of <= 32 variables with sums of |w| below 2^30 (32-bit
+// masks and deltas), wide = <= 64 variables (64-bit masks and deltas), huge =
+// 65 to GOM_MAX_ELEMENT variables (128-bit masks, 64-bit deltas; at most two
+// population words per item, no learned filter).
+enum : int32_t { kVarNarrow = 0, kVarWide = 1, kVarHuge = 2 };
+inline int32_t kernel_variant(int64_t max_s, int64_t max_abs_w)
+{
+    if (max_s <= 32 && max_abs_w < (int64_t(1) << 30)) return kVarNarrow;
+    return max_s <= 64 ? kVarWide : kVarHuge;
+}
+
 struct GomDevState {
     uint32_t g;        // generation counter
     int32_t done;      // a generation of the current call reached the target
@@ -85,7 +97,7 @@ struct GomBarrier { // grid barrier of the persistent kernel: monotonic arrival 
 struct GomBatchInst {
     int32_t blk0, nblk; // its blocks [blk0, blk0 + nblk) of the launch
     int32_t wpi;        // words per item of its mixing (1, 2, 4)
-    int32_t narrow;     // 1: elements of <= 32 variables and |w| sums < 2^30
+    int32_t variant;    // kernel variant (kVarNarrow, kVarWide, kVarHuge)
     int64_t target;     // target fitness of the current call
     int32_t gens;       // generations of the current call for this instance
     int32_t pad;

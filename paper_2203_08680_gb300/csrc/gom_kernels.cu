@@ -27,6 +27,10 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
+// Per-individual mask of an element's variables in the instances for elements
+// of 65 to 128 variables.
+using Mask128 = unsigned __int128;
+
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies with the published multipliers, the key bumped by the
 // published Weyl constants between rounds.
@@ -495,13 +499,20 @@ __device__ int scan_donor(const uint32_t *sP, int W, int Wv, int p, int s, MaskT
     return -1;
 }
 
-// Value held by lane (a mod 32) of lo (a < 32) or hi (a >= 32): per-variable
-// registers of elements with up to 64 variables.  Warp-uniform a.
-template <bool WIDE, typename T>
-__device__ __forceinline__ T lane_get(T lo, T hi, int a)
+// Value held by lane (a mod 32) of X[a / 32][r]: per-variable registers of
+// elements with up to 32 NQ variables, lane l holding variables l, l + 32,
+// ...  Warp-uniform a.
+template <int NQ, int WPI>
+__device__ __forceinline__ uint32_t lane_get(const uint32_t (&X)[NQ][WPI], int r, int a)
 {
-    if (WIDE && a >= 32) return __shfl_sync(kFull, hi, a - 32);
-    return __shfl_sync(kFull, lo, a);
+    if constexpr (NQ == 1) {
+        return __shfl_sync(kFull, X[0][r], a);
+    } else {
+        uint32_t v = X[0][r];
+#pragma unroll
+        for (int h = 1; h < NQ; ++h) v = (a >> 5) == h ? X[h][r] : v;
+        return __shfl_sync(kFull, v, a & 31);
+    }
 }
 
 // First position after d, in cyclic order over [0, p), whose bit is set in
@@ -946,7 +957,7 @@ template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
                                          unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
 {
-    constexpr bool WIDE = sizeof(MaskT) == 8;
+    constexpr int NQ = sizeof(MaskT) / 4; // 32-variable quarters of a mask: 1, 2 or 4
     const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p;
     const int *h = reinterpret_cast<const int *>(sl);
@@ -965,18 +976,21 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     const int ne_tot = n_out + n_in;
     const unsigned acc0 = n_acc, dl0 = n_dl, imp0 = n_imp; // this item's counts, for the learned filter
-    const int fl = lane < s ? fv[lane] : 0;
-    const int fl2 = (WIDE && lane + 32 < s) ? fv[lane + 32] : 0;
+    int fl[NQ]; // lane l: variables l, l + 32, ... of F_j
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) fl[q] = lane + 32 * q < s ? fv[lane + 32 * q] : 0;
 
     for (int wg = wg0; wg < wg1; ++wg) {
         const int w0 = wg * WPI;
         // global loads: the parent's rows on F_j (lane a loads row F_j[a]),
         // the elitist flags, the outside neighbours' words (to shared memory)
-        uint32_t Xa[WPI], Xa2[WPI], eqv[WPI];
+        uint32_t Xa[NQ][WPI], eqv[WPI];
 #pragma unroll
-        for (int r = 0; r < WPI; ++r) Xa[r] = Xa2[r] = 0;
-        if (lane < s) load_words<WPI>(P.O + fl * W + w0, Xa);
-        if (WIDE && lane + 32 < s) load_words<WPI>(P.O + fl2 * W + w0, Xa2);
+        for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) Xa[q][r] = 0;
+            if (lane + 32 * q < s) load_words<WPI>(P.O + fl[q] * W + w0, Xa[q]);
+        }
         load_words<WPI>(P.eqw + (g & 1) * W + w0, eqv);
         __syncwarp();
         for (int x = lane; x < n_out; x += 32) {
@@ -991,7 +1005,7 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
         for (int a = 0; a < s; ++a) {
 #pragma unroll
             for (int r = 0; r < WPI; ++r)
-                xf[r] |= (MaskT)((lane_get<WIDE>(Xa[r], Xa2[r], a) >> lane) & 1u) << a;
+                xf[r] |= (MaskT)((lane_get<NQ, WPI>(Xa, r, a) >> lane) & 1u) << a;
         }
         __syncwarp();
 
@@ -1087,28 +1101,27 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
             if (i < p && donor[r] < 0) ++n_dl;
         }
         if (__any_sync(kFull, anyacc)) {
-            uint32_t mine[WPI], mine2[WPI];
+            uint32_t mine[NQ][WPI]; // lane l: accepted flips of variables l, l + 32, ...
 #pragma unroll
-            for (int r = 0; r < WPI; ++r) mine[r] = mine2[r] = 0;
+            for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+                for (int r = 0; r < WPI; ++r) mine[q][r] = 0;
+            }
             for (int a = 0; a < s; ++a) {
-                const bool me = lane == a, me2 = WIDE && lane + 32 == a;
 #pragma unroll
                 for (int r = 0; r < WPI; ++r) {
-                    const uint32_t mk = __ballot_sync(kFull, (afm[r] >> a) & 1u);
-                    mine[r] = me ? mk : mine[r];
-                    if (WIDE) mine2[r] = me2 ? mk : mine2[r];
+                    const uint32_t mk = __ballot_sync(kFull, (unsigned)((afm[r] >> a) & 1u));
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) mine[q][r] = lane + 32 * q == a ? mk : mine[q][r];
                 }
             }
 #pragma unroll
-            for (int half = 0; half < (WIDE ? 2 : 1); ++half) {
-                const int f = half ? fl2 : fl;
-                if (lane + 32 * half < s) {
-                    uint32_t *row = P.O + f * W + w0;
+            for (int q = 0; q < NQ; ++q) {
+                if (lane + 32 * q < s) {
+                    uint32_t *row = P.O + fl[q] * W + w0;
 #pragma unroll
-                    for (int r = 0; r < WPI; ++r) {
-                        const uint32_t mk = half ? mine2[r] : mine[r];
-                        if (mk) row[r] ^= mk;
-                    }
+                    for (int r = 0; r < WPI; ++r)
+                        if (mine[q][r]) row[r] ^= mine[q][r];
                 }
             }
         }
@@ -1395,13 +1408,18 @@ __global__ void __launch_bounds__(kMixThreads, MINB)
     const RunShared S{s_dyn + f_words, reinterpret_cast<long long *>(s_dyn), s_cnt, nullptr, nullptr};
     GomBarrier *bar = bars + b;
     G = min(G, I.gens);
-    if (I.narrow) {
+    if (I.variant == kVarNarrow) {
         if (I.wpi == 4)
             batch_variant<4, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
         else if (I.wpi == 2)
             batch_variant<2, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
         else
             batch_variant<1, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
+    } else if (I.variant == kVarHuge) {
+        if (I.wpi == 2)
+            batch_variant<2, Mask128, long long>(sP, V, bar, G, I.target, S);
+        else
+            batch_variant<1, Mask128, long long>(sP, V, bar, G, I.target, S);
     } else {
         if (I.wpi == 4)
             batch_variant<4, uint64_t, long long>(sP, V, bar, G, I.target, S);
@@ -1439,37 +1457,45 @@ __global__ void k_barrier_selftest(GomBarrier *bar, int *err, int extra, unsigne
 }
 
 template <bool LEARN>
-const void *mix_kernel(int wpi, bool narrow)
+const void *mix_kernel(int wpi, int variant)
 {
-    if (narrow)
+    if (variant == kVarNarrow)
         return wpi == 4 ? (const void *)k_mix<4, uint32_t, int32_t, LEARN>
              : wpi == 2 ? (const void *)k_mix<2, uint32_t, int32_t, LEARN>
                         : (const void *)k_mix<1, uint32_t, int32_t, LEARN>;
+    if (variant == kVarHuge) // no filter instances, at most two words per item
+        return LEARN || wpi > 2 ? nullptr
+             : wpi == 2         ? (const void *)k_mix<2, Mask128, long long, false>
+                                : (const void *)k_mix<1, Mask128, long long, false>;
     return wpi == 4 ? (const void *)k_mix<4, uint64_t, long long, LEARN>
          : wpi == 2 ? (const void *)k_mix<2, uint64_t, long long, LEARN>
                     : (const void *)k_mix<1, uint64_t, long long, LEARN>;
 }
 
 template <bool LEARN>
-const void *run_kernel(int wpi, bool narrow)
+const void *run_kernel(int wpi, int variant)
 {
-    if (narrow)
+    if (variant == kVarNarrow)
         return wpi == 4 ? (const void *)k_run<4, uint32_t, int32_t, LEARN>
              : wpi == 2 ? (const void *)k_run<2, uint32_t, int32_t, LEARN>
                         : (const void *)k_run<1, uint32_t, int32_t, LEARN>;
+    if (variant == kVarHuge)
+        return LEARN || wpi > 2 ? nullptr
+             : wpi == 2         ? (const void *)k_run<2, Mask128, long long, false>
+                                : (const void *)k_run<1, Mask128, long long, false>;
     return wpi == 4 ? (const void *)k_run<4, uint64_t, long long, LEARN>
          : wpi == 2 ? (const void *)k_run<2, uint64_t, long long, LEARN>
                     : (const void *)k_run<1, uint64_t, long long, LEARN>;
 }
 
-const void *gom_mix_kernel(int wpi, bool narrow, bool learn)
+const void *gom_mix_kernel(int wpi, int variant, bool learn)
 {
-    return learn ? mix_kernel<true>(wpi, narrow) : mix_kernel<false>(wpi, narrow);
+    return learn ? mix_kernel<true>(wpi, variant) : mix_kernel<false>(wpi, variant);
 }
 
-const void *gom_run_kernel(int wpi, bool narrow, bool learn)
+const void *gom_run_kernel(int wpi, int variant, bool learn)
 {
-    return learn ? run_kernel<true>(wpi, narrow) : run_kernel<false>(wpi, narrow);
+    return learn ? run_kernel<true>(wpi, variant) : run_kernel<false>(wpi, variant);
 }
 
 // ----------------------------------------------------------------------------

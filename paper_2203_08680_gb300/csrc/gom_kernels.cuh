@@ -13,12 +13,16 @@ __global__ void k_set_state(GomParams P, int64_t fe, int64_t g);
 __global__ void k_begin_call(GomParams P, int64_t target);
 __global__ void k_gen_start(GomParams P);
 __global__ void k_order(GomParams P);
-// The mixing kernel instance for WPI words per warp item (1, 2 or 4), 32-bit
-// (narrow) or 64-bit masks and deltas, with or without the learned filter's
-// bookkeeping; a host-stub address usable as a graph-node function.
-const void *gom_mix_kernel(int wpi, bool narrow, bool learn);
-// The persistent generation kernel k_run<WPI, mask, delta, learn>(GomParams, int G, int64_t target).
-const void *gom_run_kernel(int wpi, bool narrow, bool learn);
+// The mixing kernel instance for WPI words per warp item (1, 2 or 4) and
+// variant (kVarNarrow: 32-bit masks and deltas; kVarWide: 64-bit masks and
+// deltas; kVarHuge: 128-bit masks and 64-bit deltas, WPI <= 2, no learned
+// filter), with or without the learned filter's bookkeeping; a host-stub
+// address usable as a graph-node function, or null for a combination that
+// has no instance.
+const void *gom_mix_kernel(int wpi, int variant, bool learn);
+// The persistent generation kernel k_run<WPI, mask, delta, learn>(GomParams,
+// int G, int64_t target), with the same instances (null where none).
+const void *gom_run_kernel(int wpi, int variant, bool learn);
 // Batched path: instances on block ranges of one cooperative launch.
 // k_batch<MINB>(const GomParams *Ps, const GomBatchInst *inst, GomBarrier *bars, int B, int G, int f_words),
 // registers cut for MINB (2 or 3) resident blocks of 256 threads.

@@ -20,7 +20,7 @@ GOM_FOS_NEIGHBOURHOOD = 0
 GOM_FOS_SINGLETON = 1
 GOM_FOS_BFLT = 2
 GOM_MAX_POPULATION = 1024
-GOM_MAX_ELEMENT = 64
+GOM_MAX_ELEMENT = 128
 GOM_OPT_PERSISTENT = 1
 GOM_OPT_PHASE_TRACE = 2
 GOM_OPT_DYNAMIC = 3

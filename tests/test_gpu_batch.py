@@ -186,11 +186,14 @@ def test_batch_256_instances_full_size_sampled(oracle):
         assert np.array_equal(P.fitness().cpu().numpy(), fit.cpu().numpy()), b
 
 
-def test_batch_with_linkage_tree_instances(oracle):
+@pytest.mark.parametrize("config", [(2, 3), (4, 2)])
+def test_batch_with_linkage_tree_instances(oracle, config):
     """Instances whose FOS is the paper's bounded linkage tree (nested sets of
-    up to 32 and 64 variables) next to neighbourhood ones, in one launch."""
+    up to 32, 64 and 100 variables: all three mask widths) next to
+    neighbourhood ones, in one launch."""
     specs = [(I.random_regular(200, 4, seed=41), 40, 3, 32), (I.torus2d(12, seed=42), 70, 4, 64),
-             (I.random_regular(300, 3, seed=43), 33, 5, 0)]
+             (I.random_regular(300, 3, seed=43), 33, 5, 0), (I.random_regular(400, 4, seed=52), 100, 6, 100),
+             (I.torus2d(20, seed=51), 50, 7, 100)]
     pops, runs = [], []
     for g, p, s, bound in specs:
         fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound) if bound else None
@@ -201,8 +204,8 @@ def test_batch_with_linkage_tree_instances(oracle):
             ep, ev = oracle.build_fos(g)
         k, co = oracle.color(g, ep, ev)
         runs.append(oracle.Run(g, ep, ev, co, k, p, s))
-    batch = _batch(pops, (2, 3))
-    assert list(gom.gom_batch_generation(batch, 4)) == [4, 4, 4]
+    batch = _batch(pops, config)
+    assert list(gom.gom_batch_generation(batch, 4)) == [4] * len(specs)
     for b, (P, run) in enumerate(zip(pops, runs)):
         ost = run.run(4)
         for a, o in zip(gom.gom_batch_stats(batch, b, 4), ost):

@@ -344,6 +344,25 @@ def test_runs_of_identical_individuals(oracle, p):
         _assert_same_state(_gpu_state(P), run.get())
 
 
+def _fos_parity(oracle, g, fos, ep, ev, p, seed, gens):
+    """A given FOS (library handle and the oracle's arrays of the same sets)
+    on both execution paths against the oracle, every generation."""
+    k, co = oracle.color(g, ep, ev)
+    run = oracle.Run(g, ep, ev, co, k, p, seed)
+    Ps = [gom.Population(g, p, seed, fos=fos, persistent=True), gom.Population(g, p, seed, fos=fos, persistent=False)]
+    for P in Ps:
+        assert P.k == k
+        _assert_same_state(_gpu_state(P), run.get(), "init")
+    for gen in range(gens):
+        ost = run.generation()
+        for P in Ps:
+            gst, _ = P.generation(1)
+            _assert_same_stats(gst[0], ost)
+            _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")
+    for P in Ps:
+        assert np.array_equal(P.fitness().cpu().numpy(), run.get()["f"])
+
+
 @pytest.mark.parametrize("name,bound,p", [("torus12", 10, 50), ("rreg300_d5", 20, 100), ("rreg200_d4", 64, 40)])
 def test_bflt_fos(oracle, name, bound, p):
     """The paper's own linkage model (Sec. 4.1): a bounded fixed linkage tree
@@ -353,15 +372,48 @@ def test_bflt_fos(oracle, name, bound, p):
          "rreg200_d4": lambda: I.random_regular(200, 4, seed=23)}[name]()
     fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
     ep, ev = oracle.build_bflt(g, bound)
-    k, co = oracle.color(g, ep, ev)
-    run = oracle.Run(g, ep, ev, co, k, p, 31)
-    Ps = [gom.Population(g, p, 31, fos=fos, persistent=True), gom.Population(g, p, 31, fos=fos, persistent=False)]
-    for P in Ps:
-        assert P.k == k
-        _assert_same_state(_gpu_state(P), run.get(), "init")
-    for gen in range(6):
-        ost = run.generation()
-        for P in Ps:
-            gst, _ = P.generation(1)
-            _assert_same_stats(gst[0], ost)
-            _assert_same_state(_gpu_state(P), run.get(), f"gen {gen}")
+    _fos_parity(oracle, g, fos, ep, ev, p, 31, 6)
+
+
+@pytest.mark.parametrize("name,bound,p", [("torus20", 100, 50), ("rreg400_d4", 100, 100), ("rreg300_d6", 128, 200)])
+def test_bflt_paper_bound_100_128bit_masks(oracle, name, bound, p):
+    """The paper's larger linkage-tree bound (100, Sec. 6.1) and the library's
+    maximum (128): sets of 65 to 128 variables take the kernel instance with
+    128-bit masks (at most two population words per item; p = 50, 100, 200
+    give 2, 4 and 8 words), on both execution paths, every generation."""
+    g = {"torus20": lambda: I.torus2d(20, seed=51), "rreg400_d4": lambda: I.random_regular(400, 4, seed=52),
+         "rreg300_d6": lambda: I.random_regular(300, 6, seed=53)}[name]()
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
+    ep, ev = oracle.build_bflt(g, bound)
+    assert np.diff(ep).max() > 64
+    _fos_parity(oracle, g, fos, ep, ev, p, 32, 6)
+
+
+@pytest.mark.parametrize("p", [33, 96])
+def test_elements_of_128_variables(oracle, p):
+    """Elements at the library's maximum of 128 variables, next to elements of
+    65 and 100 variables that overlap them, and the singletons: variables
+    0..127 of a random 5-regular graph in one element, so that lanes hold up
+    to four variables each and edges run inside and out of every quarter."""
+    g = I.random_regular(400, 5, seed=61)
+    sets = [[v] for v in range(g.n)]
+    sets += [list(range(0, 128)), list(range(128, 228)), list(range(300, 365)), list(range(100, 165)),
+             list(range(272, 400))]
+    ep = np.cumsum([0] + [len(x) for x in sets]).astype(np.int64)
+    ev = np.concatenate([np.array(x, dtype=np.int32) for x in sets])
+    fos = gom.gom_fos_create(g.n, ep, ev)
+    _fos_parity(oracle, g, fos, ep, ev, p, 62, 8)
+
+
+def test_no_learned_filter_for_elements_above_64_variables():
+    """The learned filter's kernel instances take elements of up to 64
+    variables: switching it on for a larger FOS is refused, plain GOM goes on."""
+    g = I.random_regular(300, 6, seed=53)
+    P = gom.Population(g, 64, 3, fos=gom.gom_build_fos(g, gom.GOM_FOS_BFLT, 100))
+    ws = torch.empty(gom.gom_filter_workspace_bytes(P.ctx, 1024) + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    gom.gom_filter_attach(P.ctx, ws, 1024)
+    with pytest.raises(gom.GomError) as ei:
+        gom.gom_filter_set_mode(P.ctx, 1)
+    assert ei.value.code == -8
+    P.generation(2)

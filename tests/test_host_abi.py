@@ -181,8 +181,8 @@ def test_incomplete_or_bad_custom_fos():
 
 
 def test_oversized_element_is_rejected_at_init():
-    # a star: the centre's neighbourhood element has 81 variables
-    n = 81
+    # a star: the centre's neighbourhood element has 129 variables, one above GOM_MAX_ELEMENT
+    n = 129
     g = I.from_edges(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n), np.ones(n - 1, dtype=np.int32))
     fos = gom.gom_build_fos(g)
     gom.gom_color_fos(g, fos)
