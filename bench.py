@@ -51,7 +51,14 @@ WORKLOADS = {
                    "random 12-regular n=1,000,000, int32 weights U[1,100], pop 512"),
     "torus1000": (lambda: I.torus2d(1000), 256,
                   "2D torus 1000x1000 (n=1,000,000), int32 weights U[1,100], pop 256"),
+    "torus100_lt128": (lambda: I.torus2d(100), 1024,
+                       "2D torus 100x100 (n=10,000, 20,000 edges), int32 weights U[1,100] seed 1, pop 1024, "
+                       "bounded linkage tree FOS (UPGMA on the weights, sets of up to 128 variables)"),
 }
+# workloads whose FOS is the bounded linkage tree (Sec. 4.1), by bound; the rest use the neighbourhood FOS
+WORKLOAD_BFLT = {"torus100_lt128": 128}
+BFLT_ORACLE_NOTE = ("the oracle states UPGMA plainly (every cluster pair rescanned per merge), which takes "
+                    "hours at n = 10,000; no CPU figure for linkage-tree workloads")
 BATCH_WORKLOADS = {
     "batch256": "256 independent Max-Cut instances in one persistent launch: random d-regular graphs, n "
                 "log-uniform in [1000, 65536] (even), d uniform in 3..8, int32 weights U[1,100], pop uniform "
@@ -262,6 +269,9 @@ def run_reference(args, wl, rank, world):
                 "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
+    if wl in WORKLOAD_BFLT:
+        print(json.dumps({"impl": "reference", "unavailable": BFLT_ORACLE_NOTE}), flush=True)
+        return
     # the learned workload's reference is the oracle on its graph (plain GOM, no filter)
     build, p, desc = WORKLOADS["torus1000" if wl in LEARNED_WORKLOADS else wl]
     g = build()
@@ -291,7 +301,10 @@ def run_gpu(args, wl, rank, world, local):
     g = build()
     seed = SEED + rank
     stream = torch.cuda.current_stream()
-    P = gom.Population(g, p, seed, stream=stream, persistent=None if args.path == "auto" else args.path == "persistent")
+    bflt = WORKLOAD_BFLT.get(wl, 0)
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bflt) if bflt else None
+    P = gom.Population(g, p, seed, fos=fos, stream=stream,
+                       persistent=None if args.path == "auto" else args.path == "persistent")
     m, k = P.m, P.k
     persistent = bool(gom.gom_get_option(P.ctx, gom.GOM_OPT_PERSISTENT))
     trials_per_step = p * m
@@ -353,17 +366,20 @@ def run_gpu(args, wl, rank, world, local):
     # (every edge cut on an even torus) or a generation cap
     ttt = None
     if not args.no_ttt:
-        ttt = time_to_target(args, g, p, seed, stream, wl)
-        if wl.startswith("torus"):
+        ttt = time_to_target(args, g, p, seed, stream, wl, fos)
+        if wl.startswith("torus") and not bflt:
             ttt["ims"] = ims_time_to_target(args, g, seed, stream)
+            ttt["linkage_tree"] = [linkage_tree_time_to_target(args, g, seed, stream, b) for b in (100, 128)]
 
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step)
+        e2e = end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step, bflt)
 
     # CPU baseline: the oracle, bounded sample, rank 0
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and bflt:
+        cpu = {"value": None, "kind": "oracle", "unavailable": BFLT_ORACLE_NOTE}
+    elif rank == 0 and not args.no_cpu:
         nth = oracle_threads()
         cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2, threads=nth)
         sval, sgens, sel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2)
@@ -593,13 +609,13 @@ def run_learned(args, wl, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def time_to_target(args, g, p, seed, stream, wl):
+def time_to_target(args, g, p, seed, stream, wl, fos=None):
     import torch
 
     from paper_2203_08680_gb300 import gom
     tw = g.total_weight()
     target = int(math.ceil(0.999 * tw))
-    P2 = gom.Population(g, p, seed, stream=stream)
+    P2 = gom.Population(g, p, seed, fos=fos, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -612,6 +628,34 @@ def time_to_target(args, g, p, seed, stream, wl):
            "max_generations": args.ttt_gens}
     del P2
     return ttt
+
+
+def linkage_tree_time_to_target(args, g, seed, stream, bound):
+    """Time to target with the paper's linkage model: the bounded fixed
+    linkage tree (UPGMA on the weights, Sec. 4.1) at `bound` variables, one
+    population of --lt-pop individuals, up to --lt-gens generations.  The
+    set-up (tree, colouring, initial population) is timed apart."""
+    import torch
+
+    from paper_2203_08680_gb300 import gom
+    tw = g.total_weight()
+    target = int(math.ceil(0.999 * tw))
+    t0 = time.perf_counter()
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
+    P = gom.Population(g, args.lt_pop, seed, fos=fos, stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats, nrun = P.generation(args.lt_gens, target)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"fos": f"bounded linkage tree, bound {bound}", "population": args.lt_pop, "colours": P.k,
+           "target": target, "reached": bool(stats and stats[-1]["reached_target"]), "generations": nrun,
+           "best": stats[-1]["best_fitness"] if stats else None, "ms": e0.elapsed_time(e1),
+           "setup_ms": setup_s * 1e3, "max_generations": args.lt_gens}
+    del P
+    return out
 
 
 def ims_time_to_target(args, g, seed, stream):
@@ -652,7 +696,7 @@ def ims_time_to_target(args, g, seed, stream):
     return out
 
 
-def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step):
+def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step, bflt=0):
     """End to end through the C ABI from host buffers: FOS, colouring, upload,
     generations with host statistics, population and fitness back to host."""
     import torch
@@ -661,7 +705,7 @@ def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     G = gom.Graph(g)
-    fos = gom.gom_build_fos(G)
+    fos = gom.gom_build_fos(G, gom.GOM_FOS_BFLT, bflt) if bflt else gom.gom_build_fos(G)
     gom.gom_color_fos(G, fos)
     nbytes = gom.gom_workspace_bytes(G, fos, p)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -727,6 +771,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-count", type=int, default=256,
                     help="batch workloads: the first N instances of the mix (a smaller case for profiling)")
+    ap.add_argument("--lt-pop", type=int, default=1024, help="linkage-tree time-to-target runs: population")
+    ap.add_argument("--lt-gens", type=int, default=400, help="linkage-tree time-to-target runs: generation cap")
     ap.add_argument("--ims-base", type=int, default=16, help="IMS base population (time-to-target run)")
     ap.add_argument("--ims-c", type=int, default=4, help="IMS generation ratio c")
     ap.add_argument("--ims-seconds", type=float, default=20.0, help="IMS time-to-target budget")
