@@ -352,6 +352,12 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     const int wv = (pop + 31) / 32;
     int wpi = 1, split = 0;
     item_split(c->W, pop, max_group, static_cast<int64_t>(c->sms) * 24, variant, &wpi, &split);
+    // Block mode (the 128-bit instances, 4 or more word groups per element):
+    // the warps of a block stage each element once, together, and share its
+    // word groups -- rather than every (element, word group) item staging the
+    // element's rows and pattern table (both grow with the population) on its own.
+    const bool blk = variant == kVarHuge && (wv + wpi - 1) / wpi >= 4;
+    if (blk) split = 0;
     const int nwg = (wv + wpi - 1) / wpi;
     const int per = split ? nwg : 1;
     c->mix_fn = gom_mix_kernel(wpi, variant, false);
@@ -360,12 +366,24 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     const int64_t off_pat = SL.off_pat, off_rs = SL.off_rs, off_ds = SL.off_ds;
     const int64_t base_words = SL.base_words;
     const int64_t all_words = SL.all_words;
+    const int64_t xw_words = SL.off_ds - SL.off_xw; // one warp's region of outside neighbours' words
     constexpr int64_t kSmemBudget = 200 * 1024;
-    const int warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (base_words * 4)));
+    int warps_per_block = 0;
+    if (blk) { // one slice per block plus a region of outside words per further warp
+        warps_per_block = std::min(kMixThreads / 32, nwg);
+        while (warps_per_block > 1 && (base_words + (warps_per_block - 1) * xw_words) * 4 > kSmemBudget)
+            --warps_per_block;
+        if (base_words * 4 > kSmemBudget) warps_per_block = 0;
+    } else {
+        warps_per_block = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (base_words * 4)));
+    }
     if (warps_per_block < 1) return GOM_E_LIMIT;
     c->mix_threads = 32 * warps_per_block;
-    // one warp per item of the largest group, at most a full wave
-    const int64_t need_blocks = (max_group * per + warps_per_block - 1) / warps_per_block;
+    // shared-memory words of a block's staging outside stage-all mode
+    const int64_t block_words =
+        blk ? base_words + (warps_per_block - 1) * xw_words : base_words * warps_per_block;
+    // one warp per item (a block per element in block mode) of the largest group, at most a full wave
+    const int64_t need_blocks = blk ? max_group : (max_group * per + warps_per_block - 1) / warps_per_block;
 
     // persistent path: one cooperative kernel, grid limited to co-resident blocks
     c->run_fn = gom_run_kernel(wpi, variant, false);
@@ -392,7 +410,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
         // for every block to hold the group order
         const size_t all_smem = static_cast<size_t>(c->k) * all_words * 4 * warps_per_block;
         int grid_all = 0;
-        if (c->k <= kStageAllMaxK) GOM_CUDA(c, run_grid(all_smem, &grid_all));
+        if (c->k <= kStageAllMaxK && !blk) GOM_CUDA(c, run_grid(all_smem, &grid_all));
         if (grid_all > 0 && max_group * per <= static_cast<int64_t>(grid_all) * warps_per_block) {
             c->run_smem = all_smem;
             c->grid_run = grid_all;
@@ -400,7 +418,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             c->can_persist = true;
             warp_words = all_words;
         } else {
-            const size_t one_smem = std::max(keys_smem, static_cast<size_t>(base_words * 4 * warps_per_block));
+            const size_t one_smem = std::max(keys_smem, static_cast<size_t>(block_words * 4));
             int grid_one = 0;
             GOM_CUDA(c, run_grid(one_smem, &grid_one));
             if (grid_one > 0) {
@@ -411,7 +429,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             }
         }
     }
-    c->mix_smem = static_cast<size_t>(warp_words * 4 * warps_per_block);
+    c->mix_smem = static_cast<size_t>(c->prm.stage_all ? all_words * 4 * warps_per_block : block_words * 4);
+    if (blk) warp_words = block_words; // the block's one slice
     GOM_CUDA(c, raise_smem_limit(c->mix_fn, c->mix_smem));
     int occ = 0;
     GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->mix_fn, c->mix_threads, c->mix_smem));
@@ -455,6 +474,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.k = fos->k;
     P.seed = seed;
     P.split = split;
+    P.blk = blk ? 1 : 0;
+    P.xw_words = static_cast<int32_t>(xw_words);
     P.warp_smem = static_cast<int32_t>(warp_words);
     P.off_fv = static_cast<int32_t>(off_fv);
     P.off_seg = static_cast<int32_t>(off_seg);

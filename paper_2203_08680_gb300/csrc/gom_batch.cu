@@ -204,6 +204,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
             slice_layout(c->max_s, c->max_edges, c->W, wpi, c->variant, split != 0, (wv + wpi - 1) / wpi);
         GomParams P = c->prm;
         P.stage_all = 0; // one staging slice per warp
+        P.blk = 0;
         P.split = split;
         P.warp_smem = static_cast<int32_t>(SL.base_words);
         P.off_fv = static_cast<int32_t>(SL.off_fv);

@@ -170,7 +170,11 @@ struct GomParams {
     int32_t off_cw;
     int32_t off_xw;
     int32_t off_ds;     //   [off_ds, ..) donor start positions (stage-all mode only)
-    int32_t dyn;        // 1: after its first item, a warp claims items from work[t]
+    int32_t dyn;        // 1: after its first item, a warp (a block in block mode) claims items from work[t]
+    int32_t blk;        // block mode (128-bit instances): a block stages one element at a time into one
+                        //   slice and its warps share the element's word groups
+    int32_t xw_words;   // block mode: words of one warp's region of outside neighbours' words, the
+                        //   regions of warps 0, 1, ... following each other from off_xw
     int32_t learn;      // learned filter: 0 off, 1 history and training log, 2 also skip elements
     GomFilter flt;
     uint64_t seed;

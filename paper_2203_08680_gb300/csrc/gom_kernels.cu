@@ -953,9 +953,12 @@ __device__ __forceinline__ unsigned item_record(const GomParams &P, const int *h
 //           XORs the accepted flips into row F_j[a]
 // Fitness deltas go to the block's shared accumulators s_f; counters to
 // per-lane counts.
+// In block mode the caller names the one word group to run (wg_only) and
+// gives the warp's own region for the outside neighbours' words (xw_own).
 template <int WPI, typename MaskT, typename AccT, bool LEARN>
 __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, uint32_t g, bool pre, long long *s_f,
-                                         unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
+                                         unsigned &n_dl, unsigned &n_acc, unsigned &n_imp, int wg_only = -1,
+                                         uint32_t *xw_own = nullptr)
 {
     constexpr int NQ = sizeof(MaskT) / 4; // 32-variable quarters of a mask: 1, 2 or 4
     const int lane = threadIdx.x & 31;
@@ -963,7 +966,8 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
     const int *h = reinterpret_cast<const int *>(sl);
     const int j = h[H_J], s = h[H_SN] & 0xFF, n_in = h[H_SN] >> 8, n_out = h[H_NOUT], sub = h[H_SUB];
     const int nwg = (Wv + WPI - 1) / WPI;
-    const int wg0 = P.split ? sub : 0, wg1 = P.split ? sub + 1 : nwg;
+    const int wg0 = wg_only >= 0 ? wg_only : P.split ? sub : 0;
+    const int wg1 = wg_only >= 0 ? wg_only + 1 : P.split ? sub + 1 : nwg;
     const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
     const uint32_t *sseg = sl + P.off_seg;
     const int64_t *swout = reinterpret_cast<const int64_t *>(sl + P.off_wout);
@@ -972,7 +976,7 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
     const uint32_t *rs = sl + P.off_rs;
     const int *sds = reinterpret_cast<const int *>(sl + P.off_ds);
     const int2 *cw = reinterpret_cast<const int2 *>(sl + P.off_cw);
-    uint32_t *xw = sl + P.off_xw;
+    uint32_t *xw = xw_own ? xw_own : sl + P.off_xw;
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
     const int ne_tot = n_out + n_in;
     const unsigned acc0 = n_acc, dl0 = n_dl, imp0 = n_imp; // this item's counts, for the learned filter
@@ -1212,6 +1216,82 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
     }
 }
 
+// Block mode (only in the 128-bit instances, for elements with 4 or more
+// word groups): the warps of a block stage one element together into the
+// block's one slice and share its word groups, so an element's rows and
+// pattern table are made once, not once per (element, word group) item.
+// Staging: the header and lists by warp 0, then P's rows, the pattern table
+// and its run starts split over the warps.  Called by every thread of the
+// block with the same `it`; it first waits until every warp has left the
+// slice's previous contents.  Returns the item's validity (block-uniform).
+template <typename MaskT>
+__device__ bool stage_item_block(const GomParams &P, int c, int it, uint32_t *sl)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    __syncthreads(); // every thread has read the previous header and runs no item any more
+    if (wib == 0 && decode_item(P, c, it, 1, sl)) { // P.split is 0: items are elements
+        __syncwarp();
+        stage_lists<1>(P, sl);
+        cp_wait_warp();
+    }
+    __syncthreads();
+    const int *h = reinterpret_cast<const int *>(sl);
+    if (!h[H_VALID]) return false;
+    const int s = h[H_SN] & 0xFF, W = P.W, Wv = P.Wv, p = P.p;
+    const int *fv = reinterpret_cast<const int *>(sl + P.off_fv);
+    uint32_t *sP = sl + P.off_pr;
+    if (W >= 4) {
+        const int n4 = (s * W) >> 2, lw4 = __ffs(W >> 2) - 1;
+        for (int x = threadIdx.x; x < n4; x += blockDim.x)
+            cp_async16(sP + 4 * x, P.P + fv[x >> lw4] * W + 4 * (x & ((W >> 2) - 1)));
+    } else {
+        const int lw = __ffs(W) - 1;
+        for (int x = threadIdx.x; x < (s << lw); x += blockDim.x) cp_async4(sP + x, P.P + fv[x >> lw] * W + (x & (W - 1)));
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    MaskT *patP = reinterpret_cast<MaskT *>(sl + P.off_pat);
+    uint32_t *rs = sl + P.off_rs;
+    for (int wc = wib; wc < Wv; wc += nwb) { // warp wib: the patterns of words wib, wib + nwb, ...
+        MaskT pat = 0;
+        for (int a = 0; a < s; ++a) pat |= (MaskT)((sP[a * W + wc] >> lane) & 1u) << a;
+        patP[32 * wc + lane] = pat;
+    }
+    __syncthreads();
+    for (int wc = wib; wc < Wv; wc += nwb) {
+        const int d = 32 * wc + lane;
+        const bool start = d < p && patP[d] != patP[d == 0 ? p - 1 : d - 1];
+        const uint32_t b = __ballot_sync(kFull, start);
+        if (lane == 0) rs[wc] = b;
+    }
+    __syncthreads();
+    return true;
+}
+
+// One colour group in block mode: block b of the (virtual) grid takes
+// element b first (already staged when `first_staged`), then elements
+// nblk + x for the claims x it draws from work[t] (P.dyn) or b + nblk,
+// b + 2 nblk, ...; warp w runs word groups w, w + nwarps, ... of each, with
+// its own region for the outside neighbours' words.
+template <int WPI, typename MaskT, typename AccT>
+__device__ void phase_mix_block(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *sl,
+                                bool first_staged, long long *s_f, unsigned &n_dl, unsigned &n_acc, unsigned &n_imp)
+{
+    __shared__ int s_next[1];
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const int nwg = (P.Wv + WPI - 1) / WPI;
+    uint32_t *xw = sl + P.off_xw + wib * P.xw_words;
+    bool valid = first_staged ? sl[H_VALID] != 0 : stage_item_block<MaskT>(P, c, V.blk, sl);
+    for (int next = V.blk + V.nblk; valid; next += V.nblk) {
+        if (threadIdx.x == 0) s_next[0] = P.dyn ? V.nblk + (int)atomicAdd(&P.work[t], 1u) : next;
+        for (int wg = wib; wg < nwg; wg += nwb)
+            run_item<WPI, MaskT, AccT, false>(P, sl, g, false, s_f, n_dl, n_acc, n_imp, wg, xw);
+        __syncthreads(); // the claim is visible (thread 0 writes the next one only after the staging's barriers)
+        const int it = s_next[0];
+        valid = stage_item_block<MaskT>(P, c, it, sl);
+    }
+}
+
 // Shared-memory words of one warp's staging: k slices in stage-all mode, else one.
 __device__ __forceinline__ int warp_words(const GomParams &P, bool all)
 {
@@ -1256,9 +1336,13 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
     unsigned n_dl = 0, n_acc = 0, n_imp = 0;
-    phase_mix<WPI, MaskT, AccT, LEARN>(P, whole_grid(), t, P.order[t], P.st->g,
-                                s_dyn + (threadIdx.x >> 5) * warp_words(P, false), false, false, s_f, n_dl, n_acc,
-                                n_imp);
+    if (sizeof(MaskT) == 16 && P.blk)
+        phase_mix_block<WPI, MaskT, AccT>(P, whole_grid(), t, P.order[t], P.st->g, s_dyn, false, s_f, n_dl, n_acc,
+                                          n_imp);
+    else
+        phase_mix<WPI, MaskT, AccT, LEARN>(P, whole_grid(), t, P.order[t], P.st->g,
+                                    s_dyn + (threadIdx.x >> 5) * warp_words(P, false), false, false, s_f, n_dl, n_acc,
+                                    n_imp);
     count_flush(s_cnt, n_dl, n_acc, n_imp);
     acc_flush(P, s_f, s_cnt);
 }
@@ -1301,8 +1385,10 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
     const int gwarp = (int)(V.thread() >> 5);
     const bool all = P.stage_all != 0;
     const bool lead = V.blk == 0;
+    // block mode: one slice for the whole block (the 128-bit instances only)
+    const bool blkm = sizeof(MaskT) == 16 && P.blk;
     // this warp's staging: one slice, or one per colour with stage_all
-    uint32_t *slices = S.dyn + (threadIdx.x >> 5) * warp_words(P, all);
+    uint32_t *slices = S.dyn + (blkm ? 0 : (threadIdx.x >> 5) * warp_words(P, all));
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
     unsigned long long bnext = 0; // next barrier epoch end (thread 0)
@@ -1333,10 +1419,16 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
             const int c = all ? S.order[t] : P.order[t];
             uint32_t *sl = all ? slices + c * P.warp_smem : slices;
             // without stage_all: stage the first item of group t before its barrier
-            if (!all) stage_item<WPI, MaskT, LEARN>(P, c, gwarp, sl, g);
+            if (blkm)
+                stage_item_block<MaskT>(P, c, V.blk, sl);
+            else if (!all)
+                stage_item<WPI, MaskT, LEARN>(P, c, gwarp, sl, g);
             if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
             if (tr) P.trace[4 + 2 * t] = global_ns();
-            phase_mix<WPI, MaskT, AccT, LEARN>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);
+            if (blkm)
+                phase_mix_block<WPI, MaskT, AccT>(P, V, t, c, g, sl, true, S.f, n_dl, n_acc, n_imp);
+            else
+                phase_mix<WPI, MaskT, AccT, LEARN>(P, V, t, c, g, sl, true, all, S.f, n_dl, n_acc, n_imp);
             if (tr) P.trace[5 + 2 * t] = global_ns();
         }
         count_flush(S.cnt, n_dl, n_acc, n_imp);

@@ -346,10 +346,12 @@ def test_runs_of_identical_individuals(oracle, p):
 
 def _fos_parity(oracle, g, fos, ep, ev, p, seed, gens):
     """A given FOS (library handle and the oracle's arrays of the same sets)
-    on both execution paths against the oracle, every generation."""
+    on both execution paths, the persistent one with either item schedule,
+    against the oracle, every generation."""
     k, co = oracle.color(g, ep, ev)
     run = oracle.Run(g, ep, ev, co, k, p, seed)
-    Ps = [gom.Population(g, p, seed, fos=fos, persistent=True), gom.Population(g, p, seed, fos=fos, persistent=False)]
+    Ps = [gom.Population(g, p, seed, fos=fos, persistent=True), gom.Population(g, p, seed, fos=fos, persistent=False),
+          gom.Population(g, p, seed, fos=fos, persistent=True, dynamic=False)]
     for P in Ps:
         assert P.k == k
         _assert_same_state(_gpu_state(P), run.get(), "init")
@@ -380,7 +382,8 @@ def test_bflt_paper_bound_100_128bit_masks(oracle, name, bound, p):
     """The paper's larger linkage-tree bound (100, Sec. 6.1) and the library's
     maximum (128): sets of 65 to 128 variables take the kernel instance with
     128-bit masks (at most two population words per item; p = 50, 100, 200
-    give 2, 4 and 8 words), on both execution paths, every generation."""
+    give 2, 4 and 8 words; p = 200 runs in block mode), on both execution
+    paths, every generation."""
     g = {"torus20": lambda: I.torus2d(20, seed=51), "rreg400_d4": lambda: I.random_regular(400, 4, seed=52),
          "rreg300_d6": lambda: I.random_regular(300, 6, seed=53)}[name]()
     fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
@@ -389,12 +392,14 @@ def test_bflt_paper_bound_100_128bit_masks(oracle, name, bound, p):
     _fos_parity(oracle, g, fos, ep, ev, p, 32, 6)
 
 
-@pytest.mark.parametrize("p", [33, 96])
+@pytest.mark.parametrize("p", [33, 96, 300, 1024])
 def test_elements_of_128_variables(oracle, p):
     """Elements at the library's maximum of 128 variables, next to elements of
     65 and 100 variables that overlap them, and the singletons: variables
     0..127 of a random 5-regular graph in one element, so that lanes hold up
-    to four variables each and edges run inside and out of every quarter."""
+    to four variables each and edges run inside and out of every quarter.
+    p = 300 and 1024 (5 and 16 two-word groups per element) run in block mode:
+    the warps of a block stage each element once and share its word groups."""
     g = I.random_regular(400, 5, seed=61)
     sets = [[v] for v in range(g.n)]
     sets += [list(range(0, 128)), list(range(128, 228)), list(range(300, 365)), list(range(100, 165)),
