@@ -200,11 +200,18 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         int wpi = 1, split = 0;
         item_split(c->W, c->p, c->max_group, int64_t(nb[b]) * conf.warps_per_block, c->variant, &wpi, &split);
         const int wv = (c->p + 31) / 32;
+        // block mode, as for a single context: 128-bit instances with 4 or
+        // more word groups per element, here when a block has several warps;
+        // its one slice and the further warps' outside-word regions fit in
+        // the warps' slices of the launch
+        const bool bm = c->variant == kVarHuge && (wv + wpi - 1) / wpi >= 4 && conf.warps_per_block >= 2;
+        if (bm) split = 0;
         const SliceLayout SL =
             slice_layout(c->max_s, c->max_edges, c->W, wpi, c->variant, split != 0, (wv + wpi - 1) / wpi);
         GomParams P = c->prm;
-        P.stage_all = 0; // one staging slice per warp
-        P.blk = 0;
+        P.stage_all = 0; // one staging slice per warp (per block in block mode)
+        P.blk = bm ? 1 : 0;
+        P.xw_words = static_cast<int32_t>(SL.off_ds - SL.off_xw);
         P.split = split;
         P.warp_smem = static_cast<int32_t>(SL.base_words);
         P.off_fv = static_cast<int32_t>(SL.off_fv);

@@ -189,11 +189,11 @@ def test_batch_256_instances_full_size_sampled(oracle):
 @pytest.mark.parametrize("config", [(2, 3), (4, 2)])
 def test_batch_with_linkage_tree_instances(oracle, config):
     """Instances whose FOS is the paper's bounded linkage tree (nested sets of
-    up to 32, 64 and 100 variables: all three mask widths) next to
-    neighbourhood ones, in one launch."""
+    up to 32, 64, 100 and 128 variables: all three mask widths, the last with
+    p = 300 in block mode) next to neighbourhood ones, in one launch."""
     specs = [(I.random_regular(200, 4, seed=41), 40, 3, 32), (I.torus2d(12, seed=42), 70, 4, 64),
              (I.random_regular(300, 3, seed=43), 33, 5, 0), (I.random_regular(400, 4, seed=52), 100, 6, 100),
-             (I.torus2d(20, seed=51), 50, 7, 100)]
+             (I.torus2d(20, seed=51), 50, 7, 100), (I.random_regular(300, 6, seed=53), 300, 8, 128)]
     pops, runs = [], []
     for g, p, s, bound in specs:
         fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound) if bound else None
