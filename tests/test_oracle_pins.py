@@ -144,6 +144,21 @@ def test_partial_delta_random_subsets(oracle):
         assert oracle.partial_delta(g, x, F, y) == oracle.cut_value(g, x2) - oracle.cut_value(g, x)
 
 
+@pytest.mark.parametrize("sz", [65, 100, 128])
+def test_partial_delta_large_elements(oracle, sz):
+    """Elements of 65 to 128 variables (the largest linkage sets the library
+    takes), with many edges inside them and across their border."""
+    g = I.random_regular(200, 5, seed=9, wmin=-50, wmax=100)
+    rng = np.random.default_rng(sz)
+    for _ in range(40):
+        F = np.sort(rng.choice(g.n, sz, replace=False)).astype(np.int32)
+        x = rng.integers(0, 2, g.n).astype(np.uint8)
+        y = rng.integers(0, 2, sz).astype(np.uint8)
+        x2 = x.copy()
+        x2[F] = y
+        assert oracle.partial_delta(g, x, F, y) == oracle.cut_value(g, x2) - oracle.cut_value(g, x)
+
+
 def test_singleton_delta_is_one_flip_gain(oracle):
     g = I.random_regular(30, 4, seed=6)
     rng = np.random.default_rng(3)
@@ -315,6 +330,28 @@ def test_gom_group_order_invariance(oracle, gname, p):
         assert sa == sb
     ga, gb = a.get(), b.get()
     assert np.array_equal(ga["pop"], gb["pop"]) and np.array_equal(ga["f"], gb["f"])
+
+
+def test_gom_linkage_tree_large_sets(oracle):
+    """GOM over the bounded linkage tree at 128 variables (sets of 65 and more
+    variables among the nested ones, Sec. 4.1): incremental fitness equals full
+    evaluation after every generation, fitness never drops, and each colour
+    group gives the same result in a shuffled trial order."""
+    g = I.random_regular(300, 6, seed=53)
+    eptr, evars = oracle.build_bflt(g, 128)
+    assert np.diff(eptr).max() > 64
+    k, colors = oracle.color(g, eptr, evars)
+    a = oracle.Run(g, eptr, evars, colors, k, 40, seed=4)
+    b = oracle.Run(g, eptr, evars, colors, k, 40, seed=4)
+    prev = a.get()["f"].copy()
+    for gen in range(5):
+        sa = a.generation()
+        assert sa == b.generation(shuffle=2000 + gen)
+        s = a.get()
+        assert all(s["f"][i] == oracle.cut_value(g, s["pop"][i]) for i in range(40))
+        assert np.all(s["f"] >= prev)
+        prev = s["f"].copy()
+    assert np.array_equal(a.get()["pop"], b.get()["pop"])
 
 
 def test_gom_wrong_coloring_breaks_invariance(oracle):
