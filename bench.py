@@ -370,6 +370,7 @@ def run_gpu(args, wl, rank, world, local):
         if wl.startswith("torus") and not bflt:
             ttt["ims"] = ims_time_to_target(args, g, seed, stream)
             ttt["linkage_tree"] = [linkage_tree_time_to_target(args, g, seed, stream, b) for b in (100, 128)]
+            ttt["linkage_tree"].append(ims_time_to_target(args, g, seed, stream, bflt=128, base=128, c=2, chunk=16))
 
     e2e = None
     if not args.no_e2e:
@@ -658,37 +659,41 @@ def linkage_tree_time_to_target(args, g, seed, stream, bound):
     return out
 
 
-def ims_time_to_target(args, g, seed, stream):
+def ims_time_to_target(args, g, seed, stream, bflt=0, base=None, c=None, chunk=1024):
     """Time to target of the Interleaved Multi-start Scheme (Sec. 6.3):
     populations of base_pop * 2^i individuals (up to 1024), P_i one generation
-    per c of P_{i-1}, advanced in batched calls of up to 1024 P_0 generations
-    until a population reaches the target or the time budget runs out."""
+    per c of P_{i-1}, advanced in batched calls of `chunk` P_0 generations
+    until a population reaches the target or the time budget runs out; the
+    neighbourhood FOS, or the bounded linkage tree with bound `bflt`."""
     import torch
 
     from paper_2203_08680_gb300 import gom
+    base = args.ims_base if base is None else base
+    c = args.ims_c if c is None else c
     tw = g.total_weight()
     target = int(math.ceil(0.999 * tw))
-    fos = gom.gom_build_fos(g)
+    fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bflt) if bflt else gom.gom_build_fos(g)
     gom.gom_color_fos(g, fos)
-    nb = gom.gom_ims_workspace_bytes(g, fos, args.ims_base, 1024)
+    nb = gom.gom_ims_workspace_bytes(g, fos, base, 1024)
     ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
     ws = ws[(-ws.data_ptr()) % 256:]
-    ims = gom.gom_ims_create(g, fos, args.ims_base, args.ims_c, 1024, seed, ws, stream)
+    ims = gom.gom_ims_create(g, fos, base, c, 1024, seed, ws, stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     t0 = time.perf_counter()
     best, res = None, None
     while True:
-        res = gom.gom_ims_run(ims, 1024, target)
+        res = gom.gom_ims_run(ims, chunk, target)
         best = res["best_fitness"] if best is None else max(best, res["best_fitness"])
         if res["reached"] or time.perf_counter() - t0 > args.ims_seconds:
             break
     e1.record(stream)
     torch.cuda.synchronize()
-    out = {"target": target, "closed_form_optimum": tw, "reached": bool(res["reached"]), "ms": e0.elapsed_time(e1),
-           "p0_generations": res["steps"], "best": best, "base_pop": args.ims_base, "c": args.ims_c,
-           "max_pop": 1024, "populations": gom.gom_ims_num_populations(ims)}
+    out = {"fos": f"bounded linkage tree, bound {bflt}" if bflt else "neighbourhood", "target": target,
+           "closed_form_optimum": tw, "reached": bool(res["reached"]), "ms": e0.elapsed_time(e1),
+           "p0_generations": res["steps"], "p0_generations_per_call": chunk, "best": best, "base_pop": base,
+           "c": c, "max_pop": 1024, "populations": gom.gom_ims_num_populations(ims)}
     if res["reached"]:
         out.update(reached_step=res["reached_step"], reached_population=res["reached_population"],
                    reached_generation=res["reached_generation"])
