@@ -6,9 +6,12 @@ trials per second (a trial is one (individual, FOS element) pair, donor-less
 trials included); time-to-target and the mixing kernel's HBM roofline
 fraction are reported beside it.
 
-Default workload: 2D torus 100x100 (n = 10,000, 20,000 edges), int32 weights
-uniform in [1,100] from seed 1, neighbourhood FOS, Welsh-Powell colouring,
-population 64, Philox seed 1.
+Default workload: 2D torus 1000x1000 (n = 1,000,000, 2,000,000 edges), int32
+weights uniform in [1,100] from seed 1, neighbourhood FOS, Welsh-Powell
+colouring, population 256, Philox seed 1.  The default line also carries, as
+`extras`, plain GOM on the 100x100 torus (trials/s, time to target with the
+IMS and the bounded linkage tree), batched against sequential plain GOM on
+the 256-instance mix, and the learned trial filter against plain GOM.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gom|reference]
                 [--workload NAME] [--pop P]
@@ -72,6 +75,8 @@ LEARNED_WORKLOADS = {
 }
 BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300)]
 SEED = 1
+# the largest single-GPU plain configuration: the 1000x1000 torus (the learned filter's graph), plain GOM
+DEFAULT_WORKLOAD = "torus1000"
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "GOM trials/sec (plain parallel GOM, weighted Max-Cut)"
 
@@ -225,26 +230,58 @@ def oracle_threads() -> int:
     return max(1, O.max_threads())
 
 
+class OracleSample:
+    """The CPU oracle as it stands on one workload, timed on bounded samples:
+    a step is one generation (its multi-threaded form for threads > 1) of the
+    whole population, or, when that would take longer than step_s, of an
+    evenly spread subset of the individuals sized from a probe generation
+    (trials of one group are independent, so a subset's trials are the
+    workload's own)."""
+
+    def __init__(self, g, p: int, seed: int, threads: int = 1, step_s: float = 0.5):
+        from oracle import oracle as O
+        ep, ev = O.build_fos(g)
+        k, co = O.color(g, ep, ev)
+        self.run = O.Run(g, ep, ev, co, k, p, seed)
+        self.p, self.m, self.threads = p, len(ep) - 1, threads
+        self.only = None
+        probe = self._subset(min(p, max(threads, 4)))
+        t0 = time.perf_counter()
+        self.step(probe)
+        rate = len(probe) * self.m / (time.perf_counter() - t0)
+        want = max(threads, int(rate * step_s / max(self.m, 1)))  # at least one individual per thread
+        if want < p:
+            self.only = self._subset(max(1, want))
+
+    def _subset(self, q: int):
+        return None if q >= self.p else [int(i) for i in np.linspace(0, self.p - 1, q).round()]
+
+    def step(self, only="default"):
+        only = self.only if isinstance(only, str) else only
+        self.run.generation(threads=self.threads, only=only)
+        return (self.p if only is None else len(only)) * self.m
+
+    def describe(self) -> str:
+        who = "the whole population" if self.only is None else f"{len(self.only)} of {self.p} individuals"
+        return f"generations of {who}, {self.threads} thread(s)"
+
+
 def oracle_trials_per_sec(g, p: int, seed: int, budget_s: float, warmup: int = 0, steps: int = None,
                           threads: int = 1):
-    """The CPU oracle as it stands, timed on a bounded sample (generations
-    until budget_s, or `steps` generations after `warmup`), on `threads`
-    threads (its multi-threaded generation for threads > 1)."""
-    from oracle import oracle as O
-    ep, ev = O.build_fos(g)
-    k, co = O.color(g, ep, ev)
-    run = O.Run(g, ep, ev, co, k, p, seed)
-    m = len(ep) - 1
+    """The CPU oracle timed on bounded samples (OracleSample): steps until
+    budget_s, or `steps` steps after `warmup`.  Returns (trials/s, steps,
+    seconds, sample description)."""
+    S = OracleSample(g, p, seed, threads)
     for _ in range(warmup):
-        run.generation(threads=threads)
-    gens, t0 = 0, time.perf_counter()
+        S.step()
+    gens, trials, t0 = 0, 0, time.perf_counter()
     while True:
-        run.generation(threads=threads)
+        trials += S.step()
         gens += 1
         el = time.perf_counter() - t0
         if (steps is not None and gens >= steps) or (steps is None and el >= budget_s):
             break
-    return p * m * gens / el, gens, el
+    return trials / el, gens, el, S.describe()
 
 
 def run_reference(args, wl, rank, world):
@@ -276,14 +313,15 @@ def run_reference(args, wl, rank, world):
     build, p, desc = WORKLOADS["torus1000" if wl in LEARNED_WORKLOADS else wl]
     g = build()
     nth = oracle_threads()
-    val, gens, el = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps, threads=nth)
+    val, gens, el, what = oracle_trials_per_sec(g, p, SEED, 0.0, warmup=args.warmup, steps=args.steps,
+                                                threads=nth)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "trials/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / gens,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": wl, "description": desc},
             "cpu_baseline": {"value": val, "unit": "trials/s", "cores": nth, "kind": "oracle",
-                             "sample": f"{gens} generations of the workload after {args.warmup} warm-up, "
-                                       f"{nth} threads"},
+                             "sample": f"{gens} steps after {args.warmup} warm-up; a step is one of the "
+                                       f"{what}"},
             "e2e": {"value": val, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -367,10 +405,8 @@ def run_gpu(args, wl, rank, world, local):
     ttt = None
     if not args.no_ttt:
         ttt = time_to_target(args, g, p, seed, stream, wl, fos)
-        if wl.startswith("torus") and not bflt:
-            ttt["ims"] = ims_time_to_target(args, g, seed, stream)
-            ttt["linkage_tree"] = [linkage_tree_time_to_target(args, g, seed, stream, b) for b in (100, 128)]
-            ttt["linkage_tree"].append(ims_time_to_target(args, g, seed, stream, bflt=128, base=128, c=2, chunk=16))
+        if wl == "torus100":
+            ttt.update(torus100_ttt_extras(args, g, seed, stream))
 
     e2e = None
     if not args.no_e2e:
@@ -382,14 +418,70 @@ def run_gpu(args, wl, rank, world, local):
         cpu = {"value": None, "kind": "oracle", "unavailable": BFLT_ORACLE_NOTE}
     elif rank == 0 and not args.no_cpu:
         nth = oracle_threads()
-        cval, cgens, cel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2, threads=nth)
-        sval, sgens, sel = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2)
+        cval, cgens, cel, cwhat = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2, threads=nth)
+        sval, sgens, sel, swhat = oracle_trials_per_sec(g, p, seed, args.cpu_seconds / 2)
         cpu = {"value": cval, "unit": "trials/s", "cores": nth, "kind": "oracle",
-               "sample": f"{cgens} generations from initialisation ({cel:.1f} s, {nth} threads)",
+               "sample": f"{cgens} {cwhat} from initialisation ({cel:.1f} s)",
                "single_thread": {"value": sval, "cores": 1,
-                                 "sample": f"{sgens} generations from initialisation ({sel:.1f} s)"}}
+                                 "sample": f"{sgens} {swhat} from initialisation ({sel:.1f} s)"}}
     return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e,
                   launches_per_step, clk, cpu, persistent)
+
+
+def torus100_ttt_extras(args, g, seed, stream):
+    """Time-to-target runs beside plain GOM on the 100x100 torus: the IMS over
+    the neighbourhood FOS, and the paper's bounded linkage tree (bounds 100
+    and 128, p = --lt-pop) alone and under the IMS."""
+    out = {"ims": ims_time_to_target(args, g, seed, stream)}
+    out["linkage_tree"] = [linkage_tree_time_to_target(args, g, seed, stream, b) for b in (100, 128)]
+    out["linkage_tree"].append(ims_time_to_target(args, g, seed, stream, bflt=128, base=128, c=2, chunk=16))
+    return out
+
+
+def extras(args, rank, world, local):
+    """The rest of the metric, measured in the same run as the headline line:
+    plain GOM on the 100x100 torus (trials/s and time to target, with the IMS
+    and linkage-tree runs), batched against sequential plain GOM on the
+    256-instance mix, and the learned trial filter against plain GOM on the
+    1000x1000 torus."""
+    import copy
+
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    t0 = time.perf_counter()
+    a = copy.copy(args)
+    a.no_cpu, a.no_e2e, a.mix_steps = True, True, 0
+    a.steps = min(args.steps, 200)
+    a.ims_seconds = min(args.ims_seconds, 5.0)
+    build, p, desc = WORKLOADS["torus100"]
+    g = build()
+    import contextlib
+    import io
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        line = run_gpu(a, "torus100", rank, world, local)
+    out["torus100"] = {"description": desc, "trials_per_sec": line["value"], "ms_per_generation": line["ms_per_step"],
+                       "roofline_frac": line["roofline"]["frac"], "time_to_target": line["time_to_target"],
+                       "seconds": time.perf_counter() - t0}
+    t0 = time.perf_counter()
+    b = copy.copy(args)
+    b.no_cpu, b.no_e2e = True, True
+    b.steps = min(args.steps, 20)
+    bl = run_batch(b, "batch256", rank, world, local)
+    out["batch256"] = {"description": BATCH_WORKLOADS["batch256"], "trials_per_sec": bl["value"],
+                       "ms_per_generation": bl["ms_per_step"], "plain_gpu": bl["plain_gpu"],
+                       "speedup_of_batch_over_plain": bl["plain_gpu"]["speedup_of_batch"],
+                       "roofline_frac": bl["roofline"]["frac"], "batch_config": bl["config"]["batch_config"],
+                       "seconds": time.perf_counter() - t0}
+    t0 = time.perf_counter()
+    ll = run_learned(args, "learned1000", rank, world, local)
+    out["learned1000"] = {"description": LEARNED_WORKLOADS["learned1000"], "plain_ms": ll["plain"]["ms"],
+                          "learned_ms": ll["value"], "reached": ll["learned"]["reached"],
+                          "speedup_vs_plain": ll["speedup_vs_plain"], "target": ll["config"]["target"],
+                          "generations_filtered": ll["learned"]["generations_filtered"],
+                          "seconds": time.perf_counter() - t0}
+    return out
 
 
 def oracle_batch_sample(graphs, mix, budget_s: float, threads: int, max_instances: int = None):
@@ -540,8 +632,7 @@ def run_batch(args, wl, rank, world, local):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_learned(args, wl, rank, world, local):
@@ -606,8 +697,7 @@ def run_learned(args, wl, rank, world, local):
         "speedup_vs_plain": tA / learned_s if reached else None,
         "gpu_launches": None,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def time_to_target(args, g, p, seed, stream, wl, fos=None):
@@ -708,14 +798,21 @@ def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step, bfl
 
     from paper_2203_08680_gb300 import gom
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    marks = [("start", time.perf_counter())]
     G = gom.Graph(g)
     fos = gom.gom_build_fos(G, gom.GOM_FOS_BFLT, bflt) if bflt else gom.gom_build_fos(G)
+    marks.append(("fos_ms", time.perf_counter()))
     gom.gom_color_fos(G, fos)
+    marks.append(("colouring_ms", time.perf_counter()))
     nbytes = gom.gom_workspace_bytes(G, fos, p)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    marks.append(("workspace_ms", time.perf_counter()))
+    # element tables built on the host, uploads, initial population, fitness, elitist (synchronous)
     ctx = gom.gom_init_population(G, fos, p, seed, ws, nbytes, stream)
+    marks.append(("tables_upload_init_ms", time.perf_counter()))
     est, _ = gom.gom_generation(ctx, args.steps, gom.INT64_MAX, True)
+    torch.cuda.synchronize()
+    marks.append(("generations_ms", time.perf_counter()))
     dpop = torch.empty((p, g.n), dtype=torch.uint8, device=dev)
     dfit = torch.empty(p, dtype=torch.int64, device=dev)
     gom.gom_get_population(ctx, dpop, dfit, True)
@@ -724,14 +821,17 @@ def end_to_end(args, g, p, seed, stream, dev, world, ex, m, trials_per_step, bfl
     hpop.copy_(dpop, non_blocking=True)
     hfit.copy_(dfit, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    marks.append(("export_download_ms", time.perf_counter()))
+    e2e_s = marks[-1][1] - marks[0][1]
+    breakdown = {name: 1e3 * (t - marks[i][1]) for i, (name, t) in enumerate(marks[1:])}
     e2e_s = dist_max(e2e_s, world)
     h2d = (G.row_ptr.nbytes + G.col.nbytes + G.weight.nbytes + ex["elem_ptr"].nbytes // 2 +
            ex["elem_vars"].nbytes + 8 * (m + 1) + 8 * int(np.diff(G.row_ptr).sum()) + 2 * (len(ex["elem_vars"]) + m))
     d2h = 64 * args.steps + p * g.n + 8 * p
     del ctx, ws
     return {"value": trials_per_step * args.steps * world / e2e_s, "unit": "trials/s",
-            "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+            "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+            "generations": args.steps, "total_ms": 1e3 * e2e_s, "breakdown": breakdown}
 
 
 def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e, launches_per_step, clk,
@@ -759,6 +859,7 @@ def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -767,7 +868,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gom", choices=["gom", "reference"])
-    ap.add_argument("--workload", default="torus100",
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the torus100, batch256 and learned1000 keys")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(LEARNED_WORKLOADS))
     ap.add_argument("--learn-recall", type=float, default=0.9, help="learned filter: recall target")
     ap.add_argument("--learn-min-recall", type=float, default=0.5, help="learned filter: self-disable recall")
@@ -794,11 +897,24 @@ def main():
     if args.impl == "reference":
         run_reference(args, args.workload, rank, world)
     elif args.workload in BATCH_WORKLOADS:
-        run_batch(args, args.workload, rank, world, local)
+        line = run_batch(args, args.workload, rank, world, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     elif args.workload in LEARNED_WORKLOADS:
-        run_learned(args, args.workload, rank, world, local)
+        line = run_learned(args, args.workload, rank, world, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     else:
-        run_gpu(args, args.workload, rank, world, local)
+        import contextlib
+        import io
+        want_extras = args.workload == DEFAULT_WORKLOAD and not args.no_extras
+        buf = io.StringIO()
+        with contextlib.redirect_stdout(buf) if want_extras else contextlib.nullcontext():
+            line = run_gpu(args, args.workload, rank, world, local)
+        if want_extras:
+            line["extras"] = extras(args, rank, world, local)
+            if rank == 0:
+                print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -309,12 +309,17 @@ int gom_selftest_barrier(void *d_scratch, int32_t blocks, int32_t extra, int64_t
  *   d_fitness_out[pop]: int64, device, overwritten.
  * Enqueued on cuda_stream (NULL = legacy default stream).  Returns
  * GOM_E_LIMIT if num_vertices * W > GOM_NOALLOC_MAX_WORDS or
- * pop > GOM_MAX_POPULATION, GOM_E_ARG on null pointers or non-positive sizes.
- * The first call on a device looks up the scratch array's device address (a
- * one-time set-up per device); make that first call before any stream
- * capture.  All calls share the one scratch array, which keeps the last
- * call's contents (every call rewrites the part it reads): calls that overlap
- * on the GPU, on different streams or threads, race.
+ * pop > GOM_MAX_POPULATION, GOM_E_ARG if any pointer is null (d_col and
+ * d_weight included, even for a graph without edges) or a size is not
+ * positive.  The first call in a CUDA context (once per device in the usual
+ * case of its primary context; again after cudaDeviceReset, or in a context
+ * the caller made current itself) looks up the scratch array's device
+ * address in that context; make that first call before any stream capture.
+ * With no context current on the calling thread, the current device's
+ * primary context is made current.  All calls share the one scratch array,
+ * which keeps the last call's contents (every call rewrites the part it
+ * reads): calls that overlap on the GPU, on different streams or threads,
+ * race.
  */
 int gom_fitness_noalloc(const int64_t *d_row_ptr, const int32_t *d_col, const int32_t *d_weight,
                         int32_t num_vertices, const uint8_t *d_pop, int32_t pop, int64_t *d_fitness_out,

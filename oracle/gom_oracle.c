@@ -854,10 +854,22 @@ int32_t orc_max_threads(void)
  * donors come from the frozen P, the elitist flags are fixed -- so any order,
  * and this parallel one, gives the single-threaded result (checked by the
  * test suite).  Each thread has its own scratch and counters. */
+int32_t orc_generation_par_ex(orc_state *s, int64_t target, int32_t threads, const int32_t *only, int32_t n_only,
+                              orc_stats *st);
+
 int32_t orc_generation_par(orc_state *s, int64_t target, int32_t threads, orc_stats *st)
 {
+    return orc_generation_par_ex(s, target, threads, NULL, 0, st);
+}
+
+/* The multi-threaded generation for the individuals only[0..n_only) (all if
+ * only is NULL); with a subset the elitist update is skipped, as in
+ * orc_generation_ex. */
+int32_t orc_generation_par_ex(orc_state *s, int64_t target, int32_t threads, const int32_t *only, int32_t n_only,
+                              orc_stats *st)
+{
     memset(st, 0, sizeof(*st));
-    const int32_t p = s->p;
+    const int32_t p = only ? n_only : s->p;
     if (threads < 1) threads = 1;
     generation_start(s);
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->k > 0 ? s->k : 1));
@@ -869,12 +881,13 @@ int32_t orc_generation_par(orc_state *s, int64_t target, int32_t threads, orc_st
         const int32_t c = order[t];
         const int64_t e0 = s->cptr[c], e1 = s->cptr[c + 1];
 #pragma omp parallel for num_threads(threads) schedule(static)
-        for (int32_t i = 0; i < p; ++i) {
+        for (int32_t ii = 0; ii < p; ++ii) {
 #ifdef _OPENMP
             const int th = omp_get_thread_num();
 #else
             const int th = 0;
 #endif
+            const int32_t i = only ? only[ii] : ii;
             for (int64_t q = e0; q < e1; ++q) gom_trial(s, &sc[th], i, s->celems[q], &ts[th]);
         }
     }
@@ -889,7 +902,7 @@ int32_t orc_generation_par(orc_state *s, int64_t target, int32_t threads, orc_st
     free(ts);
     free(order);
     st->generation = s->g;
-    generation_end(s, target, st);
+    if (!only) generation_end(s, target, st);
     s->g++;
     return 0;
 }

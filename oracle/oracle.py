@@ -77,6 +77,8 @@ def lib():
         L.orc_generation_skip.restype = i32
         L.orc_generation_par.argtypes = [P, i64, i32, P]
         L.orc_generation_par.restype = i32
+        L.orc_generation_par_ex.argtypes = [P, i64, i32, P, i32, P]
+        L.orc_generation_par_ex.restype = i32
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = i32
         _lib = L
@@ -226,8 +228,12 @@ class Run:
         """One generation; threads > 1 splits each group's individuals over
         that many threads (same result)."""
         st = Stats()
-        if threads > 1:
-            assert not shuffle and only is None
+        if threads > 1 and only is not None:
+            assert not shuffle
+            o = np.ascontiguousarray(only, dtype=np.int32)
+            lib().orc_generation_par_ex(self._h, target, threads, _p(o), len(o), C.byref(st))
+        elif threads > 1:
+            assert not shuffle
             lib().orc_generation_par(self._h, target, threads, C.byref(st))
         elif only is None:
             lib().orc_generation_ex(self._h, target, shuffle, None, 0, C.byref(st))

@@ -443,15 +443,34 @@ def test_gom_split_runs_and_resume(oracle):
 
 
 def test_gom_target_stop_and_optimum_bound(oracle):
-    g = I.torus2d(4, seed=6)
-    best, _ = oracle.brute_force_maxcut(g)
-    eptr, evars, k, colors = _setup(oracle, g)
-    run = oracle.Run(g, eptr, evars, colors, k, 16, seed=1)
-    stats = run.run(50, target=best)
-    assert all(s["best"] <= best for s in stats)
-    if stats[-1]["reached"]:
-        assert stats[-1]["best"] == best and len(stats) <= 50
-        assert not any(s["reached"] for s in stats[:-1])
+    """A run that reaches the brute-force optimum after a few generations
+    (random 3-regular graph on 20 vertices, singleton FOS, p = 8, seed 1:
+    best 1463, 1540, 1540, then the optimum 1547 at the fourth generation)
+    stops exactly there; fitness never exceeds the optimum; the stop does not
+    change the trajectory (a run without target has the same state after
+    four generations and goes past the optimum never)."""
+    g = I.random_regular(20, 3, seed=2)
+    best, xbest = oracle.brute_force_maxcut(g)
+    assert best == 1547 and oracle.cut_value(g, xbest) == best
+    eptr, evars = oracle.build_fos(g, oracle.SINGLETON)
+    k, colors = oracle.color(g, eptr, evars)
+    run = oracle.Run(g, eptr, evars, colors, k, 8, seed=1)
+    stats = run.run(60, target=best)
+    assert [s["best"] for s in stats] == [1463, 1540, 1540, 1547]
+    assert stats[-1]["reached"] and not any(s["reached"] for s in stats[:-1])
+    free = oracle.Run(g, eptr, evars, colors, k, 8, seed=1)
+    fst = free.run(10)
+    assert [s["best"] for s in fst[:4]] == [1463, 1540, 1540, 1547]
+    assert all(s["best"] <= best for s in fst)
+    a = run.get()
+    b = oracle.Run(g, eptr, evars, colors, k, 8, seed=1)
+    b.run(4)
+    for key in ("pop", "f", "xe"):
+        assert np.array_equal(a[key], b.get()[key])
+    # a target above the optimum is never reached
+    c = oracle.Run(g, eptr, evars, colors, k, 8, seed=1)
+    cst = c.run(30, target=best + 1)
+    assert len(cst) == 30 and not any(s["reached"] for s in cst)
 
 
 def test_gom_subset_replay_matches_full_generation(oracle):
@@ -473,6 +492,15 @@ def test_gom_subset_replay_matches_full_generation(oracle):
     for i in only:
         assert np.array_equal(part["pop"][i], full["pop"][i])
         assert part["f"][i] == full["f"][i]
+    # the same subset on the multi-threaded generation (the reference arm's timing sample)
+    c = oracle.Run(g, eptr, evars, colors, k, 20, seed=4)
+    c.load(snap["pop"], snap["f"], snap["xe"], snap["fe"], snap["g"])
+    sc = c.generation(only=only, threads=3)
+    part2 = c.get()
+    assert sc["trials"] == len(only) * (len(eptr) - 1)
+    for i in only:
+        assert np.array_equal(part2["pop"][i], full["pop"][i])
+        assert part2["f"][i] == full["f"][i]
 
 
 def test_multithreaded_generation_equals_single_threaded(oracle):

@@ -1,8 +1,17 @@
-"""The entry point that allocates no device memory (gom_fitness_noalloc):
-its output must equal the handle-based full evaluation gom_fitness on the
-same population, on consecutive calls whose populations differ.  It is for
-callers that must not allocate device memory; its scratch is a fixed array
-inside the library, shared by all calls."""
+"""The entry point that allocates no device memory (gom_fitness_noalloc).
+
+It is for callers that must not allocate device memory: cudaMalloc can
+synchronise the device and fail under memory pressure, and some host
+programs hand out all device memory through their own allocator.  Its
+scratch is a fixed array inside the library, shared by all calls.
+
+Each individual's output must equal the oracle's full evaluation of its cut
+weight (integer arithmetic: exact equality is the tolerance), on two calls in
+a row whose populations differ; the population sizes cover one word of 32
+individuals up to 32 words, and one graph has negative weights.  The same
+populations also go through the handle-based gom_fitness.
+"""
+import numpy as np
 import pytest
 
 from paper_2203_08680_gb300 import gom
@@ -21,32 +30,45 @@ def _device_csr(g):
             torch.from_numpy(g.weight).to(dev))
 
 
-@pytest.mark.parametrize("gname,p", [("rreg", 100), ("torus", 64)])
-def test_fitness_noalloc_equals_gom_fitness(gname, p):
-    g = I.random_regular(3000, 5, seed=4) if gname == "rreg" else I.torus2d(60, seed=2)
+GRAPHS = {
+    "rreg": lambda: I.random_regular(3000, 5, seed=4),
+    "torus": lambda: I.torus2d(60, seed=2),
+    "rreg_negative": lambda: I.random_regular(2000, 6, seed=7, wmin=-100, wmax=100),
+}
+
+
+@pytest.mark.parametrize("gname,p", [("torus", 20), ("torus", 64), ("rreg", 100), ("rreg", 300),
+                                     ("rreg_negative", 257), ("torus", 1024)])
+def test_fitness_noalloc_equals_oracle(oracle, gname, p):
+    g = GRAPHS[gname]()
     P = gom.Population(g, p, 3)
     rp, col, w = _device_csr(g)
     for call in range(2):
         pop, _, _ = P.population()            # device uint8 rows
-        ref = P.fitness()                     # gom_fitness on the handle's workspace
         out = torch.full((p,), -7, dtype=torch.int64, device="cuda")
         gom.gom_fitness_noalloc(rp, col, w, g.n, pop, p, out)
         torch.cuda.synchronize()
-        # integer cut weights: exact equality is the tolerance
-        assert torch.equal(out, ref), f"call {call}"
+        hpop = pop.cpu().numpy()
+        want = np.array([oracle.cut_value(g, hpop[i]) for i in range(p)], dtype=np.int64)
+        got = out.cpu().numpy()
+        assert np.array_equal(got, want), f"call {call}: first mismatch at {np.flatnonzero(got != want)[:5]}"
+        assert torch.equal(out, P.fitness()), f"call {call}"
         P.generation(3)                       # the next call sees another population
 
 
-def test_fitness_noalloc_rejects_sizes_beyond_its_scratch():
+GOM_E_ARG, GOM_E_LIMIT = -1, -8  # include/gom.h
+
+
+def test_fitness_noalloc_rejects_bad_arguments():
     L = gom.load()
     dummy = torch.zeros(16, dtype=torch.int64, device="cuda")
+    d = dummy.data_ptr()
     n_over = (4 * 1024 * 1024) // 2 + 1  # W = 2 words per variable for pop = 64
-    rc = L.gom_fitness_noalloc(dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), n_over,
-                               dummy.data_ptr(), 64, dummy.data_ptr(), None)
-    assert rc == -8
-    rc = L.gom_fitness_noalloc(dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(), 10, dummy.data_ptr(), 2000,
-                               dummy.data_ptr(), None)
-    assert rc == -8
-    rc = L.gom_fitness_noalloc(None, dummy.data_ptr(), dummy.data_ptr(), 10, dummy.data_ptr(), 4,
-                               dummy.data_ptr(), None)
-    assert rc == -1
+    assert L.gom_fitness_noalloc(d, d, d, n_over, d, 64, d, None) == GOM_E_LIMIT
+    assert L.gom_fitness_noalloc(d, d, d, 10, d, 2000, d, None) == GOM_E_LIMIT
+    for k in range(5):  # each pointer null in turn
+        ptrs = [d] * 5
+        ptrs[k] = None
+        rp, col, wt, pp, out = ptrs
+        assert L.gom_fitness_noalloc(rp, col, wt, 10, pp, 4, out, None) == GOM_E_ARG
+    assert L.gom_fitness_noalloc(d, d, d, 0, d, 4, d, None) == GOM_E_ARG
