@@ -341,10 +341,12 @@ def run_gpu(args, wl, rank, world, local):
     stream = torch.cuda.current_stream()
     bflt = WORKLOAD_BFLT.get(wl, 0)
     fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bflt) if bflt else None
+    bits = None if args.bitsliced == "auto" else args.bitsliced == "on"
     P = gom.Population(g, p, seed, fos=fos, stream=stream,
-                       persistent=None if args.path == "auto" else args.path == "persistent")
+                       persistent=None if args.path == "auto" else args.path == "persistent", bitsliced=bits)
     m, k = P.m, P.k
     persistent = bool(gom.gom_get_option(P.ctx, gom.GOM_OPT_PERSISTENT))
+    bitsliced = bool(gom.gom_get_option(P.ctx, gom.GOM_OPT_BITSLICED))
     trials_per_step = p * m
     ex = gom.gom_fos_export(P.fos)
     mix_bytes = mixing_bytes_per_generation(g, ex["elem_ptr"], ex["elem_vars"], p)
@@ -371,13 +373,14 @@ def run_gpu(args, wl, rank, world, local):
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     launches_per_step = gom.gom_launches_per_generation(P.ctx) + (0 if persistent else 1)
     if persistent:
-        dom = {"kernel": "k_run (persistent generation kernel)", "bytes_per_launch": gen_bytes,
+        dom = {"kernel": "k_run_bs (persistent generation kernel, bit-sliced mixing)" if bitsliced else
+               "k_run (persistent generation kernel)", "bytes_per_launch": gen_bytes,
                "avg_ms": sum(step_ms) / len(step_ms), "launches": args.steps}
     else:
         mix_ms, mix_launches = gom.gom_read_timing(P.ctx)
         gom.gom_set_timing(P.ctx, False)
-        dom = {"kernel": "k_mix", "bytes_per_launch": mix_bytes / k, "avg_ms": mix_ms / max(mix_launches, 1),
-               "launches": mix_launches}
+        dom = {"kernel": "k_mix_bs" if bitsliced else "k_mix", "bytes_per_launch": mix_bytes / k,
+               "avg_ms": mix_ms / max(mix_launches, 1), "launches": mix_launches}
     dist_barrier(world)
     total_ms = dist_max(sum(step_ms), world)
     value = world * trials_per_step * args.steps / (total_ms / 1e3)
@@ -385,7 +388,7 @@ def run_gpu(args, wl, rank, world, local):
     # the mixing kernel alone: per-launch events on the graph path
     mix = None
     if args.mix_steps > 0:
-        Q = gom.Population(g, p, seed, stream=stream, persistent=False, fos=P.fos)
+        Q = gom.Population(g, p, seed, stream=stream, persistent=False, fos=P.fos, bitsliced=bitsliced)
         Q.generation(args.warmup, want_stats=False)
         gom.gom_set_timing(Q.ctx, True)
         gom.gom_read_timing(Q.ctx)
@@ -396,7 +399,7 @@ def run_gpu(args, wl, rank, world, local):
         peak, peak_kind = peaks()
         avg = mix_ms / max(mix_launches, 1)
         ach = (mix_bytes / k) / (avg / 1e3) / 1e9
-        mix = {"kernel": "k_mix", "avg_launch_ms": avg, "launches": mix_launches,
+        mix = {"kernel": "k_mix_bs" if bitsliced else "k_mix", "avg_launch_ms": avg, "launches": mix_launches,
                "algorithmic_bytes_per_launch": mix_bytes / k, "achieved_gbs": ach, "frac": ach / peak}
         del Q
 
@@ -424,8 +427,10 @@ def run_gpu(args, wl, rank, world, local):
                "sample": f"{cgens} {cwhat} from initialisation ({cel:.1f} s)",
                "single_thread": {"value": sval, "cores": 1,
                                  "sample": f"{sgens} {swhat} from initialisation ({sel:.1f} s)"}}
-    return finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e,
+    line = finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt, e2e,
                   launches_per_step, clk, cpu, persistent)
+    line["config"]["mixing"] = "bit-sliced" if bitsliced else "per-lane"
+    return line
 
 
 def torus100_ttt_extras(args, g, seed, stream):
@@ -456,11 +461,7 @@ def extras(args, rank, world, local):
     a.ims_seconds = min(args.ims_seconds, 5.0)
     build, p, desc = WORKLOADS["torus100"]
     g = build()
-    import contextlib
-    import io
-    buf = io.StringIO()
-    with contextlib.redirect_stdout(buf):
-        line = run_gpu(a, "torus100", rank, world, local)
+    line = run_gpu(a, "torus100", rank, world, local)
     out["torus100"] = {"description": desc, "trials_per_sec": line["value"], "ms_per_generation": line["ms_per_step"],
                        "roofline_frac": line["roofline"]["frac"], "time_to_target": line["time_to_target"],
                        "seconds": time.perf_counter() - t0}
@@ -857,8 +858,6 @@ def finish(args, wl, rank, world, desc, p, m, k, value, total_ms, dom, mix, ttt,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     return line
 
 
@@ -888,6 +887,8 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run")
     ap.add_argument("--path", default="auto", choices=["auto", "persistent", "graph"])
+    ap.add_argument("--bitsliced", default="auto", choices=["auto", "on", "off"],
+                    help="mixing on bit-planes (GOM_OPT_BITSLICED) or per lane; auto = the library's default")
     ap.add_argument("--mix-steps", type=int, default=50,
                     help="generations timed per mixing launch on the graph path (0: skip)")
     args = ap.parse_args()
@@ -905,16 +906,11 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
     else:
-        import contextlib
-        import io
-        want_extras = args.workload == DEFAULT_WORKLOAD and not args.no_extras
-        buf = io.StringIO()
-        with contextlib.redirect_stdout(buf) if want_extras else contextlib.nullcontext():
-            line = run_gpu(args, args.workload, rank, world, local)
-        if want_extras:
+        line = run_gpu(args, args.workload, rank, world, local)
+        if args.workload == DEFAULT_WORKLOAD and not args.no_extras:
             line["extras"] = extras(args, rank, world, local)
-            if rank == 0:
-                print(json.dumps(line), flush=True)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -82,6 +82,16 @@ extern "C" {
                              then claims further items from a per-group counter (faster
                              warps take more; the default).  Same results either way */
 
+#define GOM_OPT_BITSLICED 4 /* mixing on bit-planes: each lane owns 32 individuals of one element and
+                               takes the partial evaluation, the acceptance and the fitness
+                               bookkeeping as bit-plane arithmetic on them (one logic instruction
+                               works on 32 trials); the donor search stays per individual.
+                               Available for elements of at most 32 variables, |w| <= 255 and
+                               element weight sums (of |w| over their edges) below 2^16; the
+                               default where available and the colour groups are large enough to
+                               fill the GPU (GOM_E_STATE when set to 1 where unavailable).  Same
+                               results either way.  Not used while the learned filter is on */
+
 /* Supported maxima of the library. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 128     /* variables in one FOS element (the paper's largest

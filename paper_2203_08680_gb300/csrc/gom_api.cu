@@ -2,6 +2,7 @@
 // layout, uploads, the per-generation CUDA graph and the exports.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -30,7 +31,7 @@ int words_for(int32_t p)
 // Byte offsets of every device array inside the workspace.
 struct Layout {
     size_t O, P, f, eqw, xe, st, bar, trace, stats, order, work;
-    size_t row_ptr, col, wgt, hdr, fv, wout, seg, dep, cptr;
+    size_t row_ptr, col, wgt, hdr, fv, wout, wabs, seg, dep, cptr;
     size_t total;
 };
 
@@ -62,6 +63,7 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.hdr = take(sizeof(int32_t) * 8 * m);
     L.fv = take(sizeof(int32_t) * total_vars);
     L.wout = take(sizeof(int64_t) * total_vars);
+    L.wabs = take(sizeof(int32_t) * total_vars);
     L.seg = take(sizeof(uint32_t) * (total_vars + m));
     L.dep = take(sizeof(int32_t) * 2 * ndeps);
     L.cptr = take(sizeof(int32_t) * (std::max<int32_t>(k, 0) + 1));
@@ -120,7 +122,10 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         }
         ts[t] = t;
         void *args2[] = {&prm, &ts[t]};
-        e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, ctx->mix_threads, ctx->mix_smem, args2);
+        if (use_bs(ctx))
+            e = add_kernel(g, &node, last, ctx->mix_bs_fn, ctx->bs_grid_mix, ctx->bs_threads, ctx->bs_smem, args2);
+        else
+            e = add_kernel(g, &node, last, ctx->mix_fn, ctx->grid_mix, ctx->mix_threads, ctx->mix_smem, args2);
         if (e == cudaSuccess && timed) {
             last = node;
             e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
@@ -450,6 +455,44 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
         const int32_t *h = tabs.hdr.data() + 8 * q;
         c->sum_se += (h[3] & 0xFF) + (h[3] >> 8) + h[4];
     }
+    // the bit-sliced path: elements of <= 32 variables, |w| <= 255, element
+    // sums of |w| below 2^16 (R-bit plane accumulators, R = 12 or 16); an item
+    // is E = 32 / W elements, one pair (element, word) per lane
+    {
+        int64_t max_w = 0;
+        for (int64_t x = 0; x < g->num_adj; ++x) max_w = std::max<int64_t>(max_w, std::llabs(g->weight[x]));
+        const int R = tabs.max_abs_w < (int64_t(1) << 12) ? 12 : 16;
+        if (coop && variant == kVarNarrow && max_w <= 255 && tabs.max_abs_w < (int64_t(1) << 16)) {
+            const int sm = static_cast<int>((std::max<int64_t>(tabs.max_s, 1) + 3) & ~int64_t(3));
+            const int64_t ww = gom_bs_warp_words(sm);
+            const int wpb = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (ww * 4)));
+            const size_t smem = std::max(static_cast<size_t>(ww * 4 * wpb), keys_smem);
+            const void *rf = gom_run_bs_kernel(R), *mf = gom_mix_bs_kernel(R);
+            if (wpb >= 1 && smem <= static_cast<size_t>(kSmemBudget) && rf && mf) {
+                const int E = 32 / c->W;
+                const int64_t items = (max_group + E - 1) / E;
+                const int64_t need = std::max<int64_t>(1, (items + wpb - 1) / wpb);
+                GOM_CUDA(c, raise_smem_limit(rf, smem));
+                GOM_CUDA(c, raise_smem_limit(mf, smem));
+                int occ_r = 0, occ_m = 0;
+                GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, rf, 32 * wpb, smem));
+                GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_m, mf, 32 * wpb, smem));
+                if (occ_r > 0 && occ_m > 0) {
+                    c->bs_ok = true;
+                    c->run_bs_fn = rf;
+                    c->mix_bs_fn = mf;
+                    c->bs_smem = smem;
+                    c->bs_threads = 32 * wpb;
+                    c->bs_grid_run = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_r, need));
+                    c->bs_grid_mix = static_cast<int>(std::min<int64_t>(
+                        std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_m, need), kMaxMixBlocks));
+                    c->prm.bs_sm = sm;
+                    // the default where every resident warp gets an item of the largest group
+                    c->bs_on = items >= static_cast<int64_t>(c->sms) * occ_r * wpb;
+                }
+            }
+        }
+    }
     // dynamic item claims: faster warps take more items (in stage-all mode
     // every warp has at most one item per group and the schedule is moot)
     c->prm.dyn = 1;
@@ -504,6 +547,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.hdr = reinterpret_cast<const int4 *>(base + L.hdr);
     P.fv = reinterpret_cast<const int32_t *>(base + L.fv);
     P.wout = reinterpret_cast<const int64_t *>(base + L.wout);
+    P.wabs = reinterpret_cast<const int32_t *>(base + L.wabs);
     P.seg = reinterpret_cast<const uint32_t *>(base + L.seg);
     P.dep = reinterpret_cast<const int2 *>(base + L.dep);
     P.cptr = reinterpret_cast<const int32_t *>(base + L.cptr);
@@ -518,6 +562,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     GOM_CUDA(c, upload(base, L.hdr, tabs.hdr, s));
     GOM_CUDA(c, upload(base, L.fv, tabs.fv, s));
     GOM_CUDA(c, upload(base, L.wout, tabs.wout, s));
+    GOM_CUDA(c, upload(base, L.wabs, tabs.wabs, s));
     GOM_CUDA(c, upload(base, L.seg, tabs.seg, s));
     GOM_CUDA(c, upload(base, L.dep, tabs.dep, s));
     GOM_CUDA(c, upload(base, L.cptr, cptr32, s));
@@ -557,8 +602,12 @@ int gom_generation(gom_ctx_t *ctx, int32_t num_generations, int64_t target_fitne
             int gens = chunk;
             int64_t target = target_fitness;
             void *args[] = {&prm, &gens, &target};
-            GOM_CUDA(ctx, cudaLaunchCooperativeKernel(ctx->run_fn, dim3(ctx->grid_run), dim3(ctx->mix_threads), args,
-                                                      ctx->run_smem, ctx->stream));
+            if (use_bs(ctx))
+                GOM_CUDA(ctx, cudaLaunchCooperativeKernel(ctx->run_bs_fn, dim3(ctx->bs_grid_run), dim3(ctx->bs_threads),
+                                                          args, ctx->bs_smem, ctx->stream));
+            else
+                GOM_CUDA(ctx, cudaLaunchCooperativeKernel(ctx->run_fn, dim3(ctx->grid_run), dim3(ctx->mix_threads),
+                                                          args, ctx->run_smem, ctx->stream));
         } else {
             k_begin_call<<<1, 1, 0, ctx->stream>>>(ctx->prm, target_fitness);
             GOM_CUDA(ctx, cudaGetLastError());
@@ -712,6 +761,13 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
         ctx->prm.dyn = static_cast<int32_t>(value);
         return rebuild_graphs(ctx); // the graphs hold a copy of the parameters
     }
+    if (option == GOM_OPT_BITSLICED) {
+        if (value != 0 && value != 1) return GOM_E_ARG;
+        if (value && !ctx->bs_ok) return GOM_E_STATE;
+        if (ctx->bs_on == (value != 0)) return GOM_OK;
+        ctx->bs_on = value != 0;
+        return rebuild_graphs(ctx); // the graphs hold the mixing kernel
+    }
     return GOM_E_ARG;
 }
 
@@ -728,6 +784,10 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
     }
     if (option == GOM_OPT_DYNAMIC) {
         *value = ctx->prm.dyn;
+        return GOM_OK;
+    }
+    if (option == GOM_OPT_BITSLICED) {
+        *value = ctx->bs_on ? 1 : 0;
         return GOM_OK;
     }
     return GOM_E_ARG;

@@ -1,0 +1,518 @@
+// gom_bs.cu -- the bit-sliced mixing path of parallel GOM for weighted Max-Cut.
+//
+// Same generations as the per-lane path of gom_kernels.cu (Alg. 3; every
+// trial of Alg. 2 decided by the exact integer delta), with the partial
+// evaluation, the acceptance and the fitness bookkeeping done on bit-planes:
+// one 32-bit register holds one bit of 32 individuals, so one logic
+// instruction works on 32 trials at once.
+//
+// A warp takes an item of E = 32 / W elements of the colour group (W = words
+// per variable row); lane k owns the pair (element slot k / W, word k mod W),
+// i.e. 32 individuals of one element.  Per item:
+//   phase 0  (lane = pair) the parent's current rows on F_j and the
+//            generation-start rows of P on F_j into shared memory, the run
+//            starts of P's patterns on F_j, and the Philox donor starts of
+//            all 1024 trials (one Philox call per 4 individuals)
+//   phase 1  (lane = individual, one pair after the other) the donor search
+//            of Sec. 4.2 with the run starts and the word-parallel scan; one
+//            ballot per variable turns the accepted candidates' flips into
+//            flip planes F_a (bit b: individual b flips variable a)
+//   phase 2  (lane = pair) the partial evaluation (Sec. 2.2, Alg. 4) as
+//            bit-plane arithmetic: with t_e the toggle plane of edge e (F_a
+//            for an edge leaving F_j, F_a ^ F_b inside), c_e its cut plane
+//            before the trial and S_e all ones for a negative weight,
+//              T = sum_e |w_e| t_e,   N = sum_e |w_e| (t_e & (c_e ^ S_e)),
+//              delta = T - 2 N        (each edge counted once),
+//            summed with ripple-carry bit-plane adders (T's outside-edge part
+//            is sum_a A_a F_a, A_a = sum of |w| over a's outside edges);
+//            then the accept plane (Alg. 2: delta > 0, or delta = 0 and not
+//            the elitist), counters by popcount, the accepted flips XORed
+//            into the rows, and the accepted deltas into a bit-sliced
+//            per-lane fitness accumulator, flushed into the block's
+//            accumulators once per generation (or before it could overflow).
+// Elements of one colour group share no variable and no edge (LMIG
+// colouring), so the rows a pair reads and writes belong to it alone during
+// the group.
+//
+// The path takes elements of at most 32 variables, |w| <= 255, and elements
+// whose sum of |w| over their edges is below 2^R (R = 12 or 16, the width of
+// the bit-plane accumulators); the host selects it only then.
+#include <climits>
+#include <cuda_runtime.h>
+
+#include "gom_device.cuh"
+#include "gom_internal.h"
+#include "gom_kernels.cuh"
+
+namespace {
+
+constexpr int kFitPlanes = 24;  // bits of the per-lane bit-sliced fitness accumulator
+constexpr int kWeightBits = 8;  // |w| < 2^8 on this path
+
+// x & (bit t of u ? ~0 : 0), for a per-lane weight u.
+__device__ __forceinline__ uint32_t bit_mask(uint32_t x, uint32_t u, int t) { return ((u >> t) & 1u) ? x : 0u; }
+
+// acc += u * x over R bit-planes (ripple carry; u < 2^UB; the sum stays below
+// 2^R by the caller's bound, so the last carry is always zero).
+template <int R, int UB, int NA>
+__device__ __forceinline__ void add_weighted(uint32_t (&acc)[NA], uint32_t x, uint32_t u)
+{
+    static_assert(NA >= R, "accumulator narrower than R");
+    uint32_t carry = 0;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        if (t < UB) {
+            const uint32_t in = bit_mask(x, u, t);
+            const uint32_t a = acc[t];
+            acc[t] = a ^ in ^ carry;
+            carry = (a & in) | (a & carry) | (in & carry);
+        } else {
+            const uint32_t a = acc[t];
+            acc[t] = a ^ carry;
+            carry = a & carry;
+        }
+    }
+}
+
+// Per-lane state of the bit-sliced path across the groups of a generation.
+struct BsLane {
+    uint32_t fit[kFitPlanes]; // accepted deltas of this lane's 32 individuals (word lane mod W), bit-sliced
+    int since_flush;          // items added since the last flush (warp-uniform)
+    unsigned n_dl, n_acc, n_imp;
+};
+
+__device__ __forceinline__ void bs_lane_zero(BsLane &L)
+{
+#pragma unroll
+    for (int t = 0; t < kFitPlanes; ++t) L.fit[t] = 0;
+    L.since_flush = 0;
+    L.n_dl = L.n_acc = L.n_imp = 0;
+}
+
+// Adds the lane's accumulated deltas into the block's fitness accumulators
+// s_f[32 w + b] (one shared atomic per individual with a non-zero sum) and
+// clears them.  Warp-wide call.
+__device__ __forceinline__ void bs_flush(const GomParams &P, BsLane &L, long long *s_f)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = lane & (P.W - 1);
+    uint32_t any = 0;
+#pragma unroll
+    for (int t = 0; t < kFitPlanes; ++t) any |= L.fit[t];
+    if (any) {
+        for (int b = 0; b < 32; ++b) {
+            if (!((any >> b) & 1u)) continue;
+            unsigned v = 0;
+#pragma unroll
+            for (int t = 0; t < kFitPlanes; ++t) v |= ((L.fit[t] >> b) & 1u) << t;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&s_f[32 * w + b]), (unsigned long long)v);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kFitPlanes; ++t) L.fit[t] = 0;
+    L.since_flush = 0;
+}
+
+// The bits on F_j (variables 0 .. s-1 of the element in slot e) of individual
+// d of the generation-start population, from the staged rows
+// sP[(e W + word) SM + a].
+__device__ __forceinline__ uint32_t pattern_of(const uint32_t *sP, int SM, int e, int W, int s, int d)
+{
+    const uint32_t *row = sP + (e * W + (d >> 5)) * SM;
+    const int bd = d & 31;
+    uint32_t pat = 0;
+    for (int a4 = 0; a4 < s; a4 += 4) {
+        const uint4 r = *reinterpret_cast<const uint4 *>(row + a4);
+        pat |= ((r.x >> bd) & 1u) << a4;
+        pat |= ((r.y >> bd) & 1u) << (a4 + 1);
+        pat |= ((r.z >> bd) & 1u) << (a4 + 2);
+        pat |= ((r.w >> bd) & 1u) << (a4 + 3);
+    }
+    return pat;
+}
+
+// Word-parallel donor scan over the staged rows (32 candidates per step):
+// the first individual in cyclic order from `start`, skipping `self`, whose
+// generation-start bits on F_j differ from the parent's bits xf; -1 if none.
+__device__ int scan_rows(const uint32_t *sP, int SM, int e, int W, int Wv, int p, int s, uint32_t xf, int start,
+                         int self)
+{
+    const int ws = start >> 5, bs = start & 31;
+    for (int step = 0; step <= Wv; ++step) {
+        int wc = ws + step;
+        if (wc >= Wv) wc -= Wv;
+        const uint32_t *row = sP + (e * W + wc) * SM;
+        uint32_t diff = 0;
+        for (int a = 0; a < s; ++a) diff |= row[a] ^ (0u - ((xf >> a) & 1u));
+        const int lim = p - 32 * wc;
+        uint32_t mk = diff & (lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u));
+        if (wc == (self >> 5)) mk &= ~(1u << (self & 31));
+        if (step == 0)
+            mk &= 0xFFFFFFFFu << bs;
+        else if (step == Wv)
+            mk &= ~(0xFFFFFFFFu << bs);
+        if (mk) return 32 * wc + __ffs(mk) - 1;
+    }
+    return -1;
+}
+
+// The donor of individual `self` (Sec. 4.2): the first candidate in cyclic
+// order from `start`, skipping self, whose generation-start bits on F_j
+// differ from the parent's current bits xf, or -1.  rs are the run starts of
+// the element's patterns (bit d: pattern d differs from pattern d - 1,
+// cyclically): candidates strictly inside a run equal to the parent are
+// passed in one step.  *pd receives the donor's pattern.  Divergent code.
+__device__ int find_donor_rows(const uint32_t *sP, const uint32_t *rs, int SM, int e, int W, int Wv, int p, int s,
+                               uint32_t xf, int start, int self, uint32_t *pd)
+{
+    uint32_t pat = pattern_of(sP, SM, e, W, s, start);
+    if (pat != xf) {
+        *pd = pat;
+        return start;
+    }
+    int d = start; // pattern d == xf here
+    for (int it = 0; it < 4; ++it) {
+        const int d2 = next_set_cyclic(rs, Wv, p, d);
+        if (d2 < 0) return -1; // one run: every candidate equals the parent
+        const int dist_d = d - start + (d < start ? p : 0);
+        const int dist_2 = d2 - start + (d2 < start ? p : 0);
+        if (dist_2 <= dist_d) return -1; // the jump passed the start
+        if (d2 != self) {                // a run start after a run equal to xf differs from xf
+            *pd = pattern_of(sP, SM, e, W, s, d2);
+            return d2;
+        }
+        d = d2 + 1 == p ? 0 : d2 + 1; // skip the parent's own column
+        if (d == start) return -1;
+        pat = pattern_of(sP, SM, e, W, s, d);
+        if (pat != xf) {
+            *pd = pat;
+            return d;
+        }
+    }
+    const int d3 = d + 1 == p ? 0 : d + 1;
+    if (d3 == start) return -1;
+    const int r = scan_rows(sP, SM, e, W, Wv, p, s, xf, d3, self);
+    if (r >= 0) *pd = pattern_of(sP, SM, e, W, s, r);
+    return r;
+}
+
+// Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4):
+// rows of O on F_j [32 pairs][SM], rows of P [32][SM], flip planes [32][SM],
+// donor starts [32 pairs][32 individuals], run starts [32 pairs].
+__host__ __device__ __forceinline__ int bs_warp_words(int SM) { return 96 * SM + 32 * 32 + 32; }
+
+// One item of colour group c at position t: elements [q0, q1) (at most E)
+// with every word, all trials of Alg. 2.
+template <int R>
+__device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint32_t g, uint32_t *wsm, BsLane &L,
+                                        long long *s_f)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = P.W, Wv = P.Wv, p = P.p, SM = P.bs_sm;
+    const int lw = __ffs(W) - 1;
+    const int e = lane >> lw, w = lane & (W - 1);
+    const int q = q0 + e;
+    const bool kv = q < q1 && w < Wv; // this lane's pair exists
+    uint32_t *sO = wsm, *sP = wsm + 32 * SM, *sD = wsm + 64 * SM;
+    int *sStart = reinterpret_cast<int *>(wsm + 96 * SM);
+    uint32_t *sRS = wsm + 96 * SM + 32 * 32;
+
+    // ---- phase 0: the pair's rows, run starts, donor starts
+    int j = 0, s = 0, f0 = 0, d0 = 0, n_in = 0, n_out = 0;
+    if (q < q1) {
+        const int4 a = __ldg(P.hdr + 2 * q), b = __ldg(P.hdr + 2 * q + 1);
+        j = a.x;
+        f0 = a.y;
+        d0 = a.z;
+        s = a.w & 0xFF;
+        n_in = a.w >> 8;
+        n_out = b.x;
+    }
+    for (int a4 = 0; a4 < SM; a4 += 4) {
+        uint32_t xo[4], xp[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            xo[c] = xp[c] = 0;
+            if (kv && a4 + c < s) {
+                const int64_t v = __ldg(P.fv + f0 + a4 + c);
+                xo[c] = P.O[v * W + w];
+                xp[c] = P.P[v * W + w];
+            }
+        }
+        *reinterpret_cast<uint4 *>(sO + lane * SM + a4) = make_uint4(xo[0], xo[1], xo[2], xo[3]);
+        *reinterpret_cast<uint4 *>(sP + lane * SM + a4) = make_uint4(xp[0], xp[1], xp[2], xp[3]);
+    }
+    __syncwarp();
+    {   // run starts of the element's patterns in word w: bit b set iff the
+        // pattern of individual 32 w + b differs from the one before it (cyclically)
+        uint32_t rsw = 0;
+        if (kv) {
+            const uint32_t *cur = sP + lane * SM;
+            const uint32_t *prev = sP + (e * W + (w == 0 ? Wv - 1 : w - 1)) * SM;
+            const int pb = w == 0 ? (p - 1) & 31 : 31;
+            for (int a = 0; a < s; ++a) {
+                const uint32_t x = cur[a];
+                rsw |= x ^ ((x << 1) | ((prev[a] >> pb) & 1u));
+            }
+            const int lim = p - 32 * w;
+            rsw &= lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
+        }
+        sRS[lane] = rsw;
+    }
+    {   // donor starts: call (pair k2, c) covers individuals 32 w2 + 4c .. + 3
+        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int k2 = 4 * r + (lane >> 3), c = lane & 7;
+            const int w2 = k2 & (W - 1);
+            const int j2 = __shfl_sync(0xFFFFFFFFu, j, k2);
+            const bool v2 = __shfl_sync(0xFFFFFFFFu, kv ? 1 : 0, k2) && 32 * w2 + 4 * c < p;
+            if (v2) {
+                const uint4 r4 = philox10(make_uint4((uint32_t)j2, (uint32_t)(8 * w2 + c), g, kTagDonor), k0, k1);
+                const int i0 = 32 * w2 + 4 * c;
+                int st[4];
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int d = i0 + cc + 1 + (int)__umulhi(pick(r4, cc), (uint32_t)(p - 1));
+                    st[cc] = d >= p ? d - p : d;
+                }
+                *reinterpret_cast<int4 *>(sStart + k2 * 32 + 4 * c) = make_int4(st[0], st[1], st[2], st[3]);
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---- phase 1: donors, lane = individual, pair after pair
+    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, kv); todo; todo &= todo - 1) {
+        const int k2 = __ffs(todo) - 1;
+        const int e2 = k2 >> lw, w2 = k2 & (W - 1);
+        const int s2 = __shfl_sync(0xFFFFFFFFu, s, k2);
+        const int i = 32 * w2 + lane;
+        uint32_t fm = 0;
+        if (i < p) {
+            // the parent's current bits on F_j
+            const uint32_t *ro = sO + k2 * SM;
+            uint32_t xf = 0;
+            for (int a4 = 0; a4 < s2; a4 += 4) {
+                const uint4 r = *reinterpret_cast<const uint4 *>(ro + a4);
+                xf |= ((r.x >> lane) & 1u) << a4;
+                xf |= ((r.y >> lane) & 1u) << (a4 + 1);
+                xf |= ((r.z >> lane) & 1u) << (a4 + 2);
+                xf |= ((r.w >> lane) & 1u) << (a4 + 3);
+            }
+            uint32_t pd = 0;
+            const int d = find_donor_rows(sP, sRS + e2 * W, SM, e2, W, Wv, p, s2, xf, sStart[k2 * 32 + lane], i, &pd);
+            if (d >= 0) fm = pd ^ xf;
+        }
+        for (int a4 = 0; a4 < s2; a4 += 4) {
+            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, (fm >> a4) & 1u);
+            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 1)) & 1u);
+            const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 2)) & 1u);
+            const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 3)) & 1u);
+            if (lane == 0) *reinterpret_cast<uint4 *>(sD + k2 * SM + a4) = make_uint4(b0, b1, b2, b3);
+        }
+    }
+    __syncwarp();
+
+    // ---- phase 2: bit-plane partial evaluation, acceptance, write, lane = pair
+    // each item adds less than 2^R to an individual's sum: flush before it could pass 2^kFitPlanes
+    if (L.since_flush >= (1 << (kFitPlanes - R))) bs_flush(P, L, s_f);
+    if (kv) {
+        const uint32_t *myD = sD + lane * SM, *myO = sO + lane * SM;
+        uint32_t T[R + 2], N[R];
+#pragma unroll
+        for (int t = 0; t < R + 2; ++t) T[t] = 0;
+#pragma unroll
+        for (int t = 0; t < R; ++t) N[t] = 0;
+        uint32_t hd = 0;
+        for (int a = 0; a < s; ++a) {
+            const uint32_t Fa = myD[a];
+            hd |= Fa;
+            if (!Fa) continue; // no trial flips variable a: none of its edges changes
+            const uint32_t Xa = myO[a];
+            add_weighted<R, R>(T, Fa, (uint32_t)__ldg(P.wabs + f0 + a));
+            const int xb = (int)__ldg(P.seg + f0 + q + a), xe = (int)__ldg(P.seg + f0 + q + a + 1);
+            for (int x = xb; x < xe; ++x) {
+                const int2 ed = __ldg(P.dep + d0 + x);
+                const uint32_t Xv = P.O[(int64_t)ed.x * W + w];
+                const uint32_t S = (uint32_t)(ed.y >> 31);
+                add_weighted<R, kWeightBits>(N, Fa & (Xa ^ Xv ^ S), (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
+            }
+        }
+        for (int x = n_out; x < n_out + n_in; ++x) {
+            const int2 ed = __ldg(P.dep + d0 + x);
+            const int a = ed.x & 0xFF, b = ed.x >> 8;
+            const uint32_t tg = myD[a] ^ myD[b];
+            if (!tg) continue; // the edge toggles for no individual
+            const uint32_t c = myO[a] ^ myO[b] ^ (uint32_t)(ed.y >> 31);
+            const uint32_t u = (uint32_t)(ed.y < 0 ? -ed.y : ed.y);
+            add_weighted<R, kWeightBits>(T, tg, u);
+            add_weighted<R, kWeightBits>(N, tg & c, u);
+        }
+        // delta = T - 2N in R + 2 bits (two's complement), in place in T
+        {
+            uint32_t carry = 0xFFFFFFFFu; // + 1 of the negation
+#pragma unroll
+            for (int t = 0; t < R + 2; ++t) {
+                const uint32_t a = T[t];
+                const uint32_t b = ~((t >= 1 && t - 1 < R) ? N[t - 1] : 0u);
+                T[t] = a ^ b ^ carry;
+                carry = (a & b) | (a & carry) | (b & carry);
+            }
+        }
+        uint32_t nz = 0;
+#pragma unroll
+        for (int t = 0; t < R + 2; ++t) nz |= T[t];
+        const uint32_t neg = T[R + 1];
+        const uint32_t pos = nz & ~neg;
+        const int lim = p - 32 * w;
+        const uint32_t vm = lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
+        const uint32_t eqv = P.eqw[(g & 1) * W + w];
+        const uint32_t acc = hd & vm & (pos | (~nz & ~eqv));
+        L.n_acc += __popc(acc);
+        L.n_imp += __popc(acc & pos);
+        L.n_dl += __popc(vm & ~hd);
+        if (acc) {
+            for (int a = 0; a < s; ++a) {
+                const uint32_t m = myD[a] & acc;
+                if (m) {
+                    const int64_t v = __ldg(P.fv + f0 + a);
+                    P.O[v * W + w] = myO[a] ^ m;
+                }
+            }
+            // the accepted deltas (>= 0: their sign plane is clear) into the fitness accumulator
+            uint32_t carry = 0;
+#pragma unroll
+            for (int t = 0; t < kFitPlanes; ++t) {
+                const uint32_t in = t <= R ? (T[t] & acc) : 0u;
+                const uint32_t a = L.fit[t];
+                L.fit[t] = a ^ in ^ carry;
+                carry = (a & in) | (a & carry) | (in & carry);
+            }
+        }
+    }
+    ++L.since_flush;
+    __syncwarp();
+}
+
+// One colour group (position t, colour c) on the bit-sliced path: items of
+// E = 32 / W consecutive elements of the group; warp x takes item x, then
+// items nwarps + the claims it draws from work[t] (P.dyn), one ahead, or
+// x + nwarps, x + 2 nwarps, ... (static stride).
+template <int R>
+__device__ void phase_mix_bs(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *wsm, BsLane &L,
+                             long long *s_f)
+{
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
+    const int E = 32 / P.W;
+    const int qa = P.cptr[c], qz = P.cptr[c + 1];
+    const int items = (qz - qa + E - 1) / E;
+    unsigned claim = 0;
+    if (P.dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
+    for (int it = gwarp, next = gwarp + nwarps; it < items;) {
+        const int q0 = qa + it * E;
+        bs_item<R>(P, q0, min(q0 + E, qz), g, wsm, L, s_f);
+        if (P.dyn) {
+            it = nwarps + (int)__shfl_sync(0xFFFFFFFFu, claim, 0);
+            if (it < items && lane == 0) claim = atomicAdd(&P.work[t], 1u);
+        } else {
+            it = next;
+            next += nwarps;
+        }
+    }
+}
+
+// Adds the warp's counters and the lanes' fitness sums into the block's
+// accumulators.
+__device__ __forceinline__ void bs_finish_generation(const GomParams &P, BsLane &L, long long *s_f,
+                                                     unsigned long long *s_cnt)
+{
+    bs_flush(P, L, s_f);
+    count_flush(s_cnt, L.n_dl, L.n_acc, L.n_imp);
+    L.n_dl = L.n_acc = L.n_imp = 0;
+}
+
+// Persistent path on the bit-sliced phase: up to G generations in one
+// cooperative launch, the phases separated by grid barriers: [generation
+// start + group order] | group 0 | ... | group k-1 | and again; every block
+// computes a generation's end from the fitness array after the barrier that
+// closes its last group (block 0 records it).  The dynamic shared memory
+// holds the warps' regions (the k group keys of the order phase overlay them).
+template <int R>
+__global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, int64_t target)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ long long s_f[1024];
+    __shared__ unsigned long long s_cnt[4];
+    const VGrid V = whole_grid();
+    const unsigned nblk = (unsigned)V.nblk;
+    const bool lead = V.blk == 0;
+    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * bs_warp_words(P.bs_sm);
+    GomBarrier *bar = P.bar;
+    uint32_t g = P.st->g;
+    GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
+    unsigned long long bnext = 0;
+    if (threadIdx.x == 0) bnext = barrier_first(&bar->count, nblk);
+    if (lead && threadIdx.x == 0) {
+        P.st->call_g0 = g;
+        P.st->target = target;
+    }
+    const bool tr = P.trace != nullptr && lead && threadIdx.x == 0;
+    BsLane L;
+    bs_lane_zero(L);
+    for (int qg = 0; qg < G; ++qg) {
+        if (qg > 0 && phase_gen_end(P, target, g - 1, e, lead)) return;
+        if (tr) P.trace[0] = global_ns();
+        phase_gen_start(P, V, e.improved, e.argmax, g, true);
+        phase_order(P, V, reinterpret_cast<unsigned long long *>(s_dyn), g);
+        acc_zero(P, s_f, s_cnt);
+        if (tr) P.trace[1] = P.trace[2] = global_ns();
+        if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (tr) P.trace[3] = global_ns();
+        for (int t = 0; t < P.k; ++t) {
+            if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+            if (tr) P.trace[4 + 2 * t] = global_ns();
+            phase_mix_bs<R>(P, V, t, P.order[t], g, wsm, L, s_f);
+            if (tr) P.trace[5 + 2 * t] = global_ns();
+        }
+        bs_finish_generation(P, L, s_f, s_cnt);
+        acc_flush(P, s_f, s_cnt);
+        if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (tr) P.trace[4 + 2 * P.k] = global_ns();
+        ++g;
+    }
+    if (G > 0 && lead) phase_gen_end(P, target, g - 1, e, true);
+}
+
+// Per-launch path: the mixing of the group at position t (one launch per
+// group in the per-generation CUDA graph).
+template <int R>
+__global__ void __launch_bounds__(kMixThreads, 2) k_mix_bs(GomParams P, int t)
+{
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    __shared__ long long s_f[1024];
+    __shared__ unsigned long long s_cnt[4];
+    if (P.st->done) return;
+    acc_zero(P, s_f, s_cnt);
+    BsLane L;
+    bs_lane_zero(L);
+    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * bs_warp_words(P.bs_sm);
+    phase_mix_bs<R>(P, whole_grid(), t, P.order[t], P.st->g, wsm, L, s_f);
+    bs_finish_generation(P, L, s_f, s_cnt);
+    acc_flush(P, s_f, s_cnt);
+}
+
+} // namespace
+
+int gom_bs_warp_words(int sm) { return bs_warp_words(sm); }
+
+const void *gom_run_bs_kernel(int r)
+{
+    return r <= 12 ? (const void *)k_run_bs<12> : r <= 16 ? (const void *)k_run_bs<16> : nullptr;
+}
+
+const void *gom_mix_bs_kernel(int r)
+{
+    return r <= 12 ? (const void *)k_mix_bs<12> : r <= 16 ? (const void *)k_mix_bs<16> : nullptr;
+}

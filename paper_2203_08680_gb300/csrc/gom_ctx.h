@@ -23,6 +23,13 @@ struct gom_ctx {
     int grid_run = 0;             // its grid: co-resident blocks only
     bool can_persist = false;     // cooperative launch available and the sizes fit
     bool persistent = false;      // current path: k_run (true) or the per-generation graph
+    // the bit-sliced mixing path (gom_bs.cu), where the FOS and weights allow it
+    bool bs_ok = false;           // available for this context
+    bool bs_on = false;           // selected (GOM_OPT_BITSLICED); used while the learned filter is off
+    const void *run_bs_fn = nullptr, *mix_bs_fn = nullptr;
+    size_t bs_smem = 0;           // dynamic shared memory of both (warp regions, group keys)
+    int bs_threads = 0;           // their block size
+    int bs_grid_run = 0, bs_grid_mix = 0;
     unsigned long long *trace_buf = nullptr; // workspace slot of the phase trace
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;
@@ -50,6 +57,10 @@ struct gom_ctx {
     size_t state_bytes = 0;      // its state arrays: [0, state_bytes) (population, fitness, elitist, ...)
 };
 
+
+// The bit-sliced path runs the context's generations (selected, and the
+// learned filter's kernel instances not in use).
+inline bool use_bs(const gom_ctx *ctx) { return ctx->bs_on && ctx->prm.learn == 0; }
 
 inline int cuda_fail(gom_ctx *ctx, cudaError_t e)
 {

@@ -341,6 +341,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
     out->hdr.assign(8 * static_cast<size_t>(m), 0);
     out->fv.assign(total, 0);
     out->wout.assign(total, 0);
+    out->wabs.assign(total, 0);
     out->seg.assign(total + static_cast<size_t>(m), 0);
     std::vector<int64_t> d0(m + 1, 0);
     std::atomic<int> too_big{0};
@@ -361,13 +362,14 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
                 const int32_t u = fos.evars[e0 + a];
                 out->fv[f0[q] + a] = u;
                 seg[a] = static_cast<uint32_t>(n_out);
-                int64_t wsum = 0;
+                int64_t wsum = 0, wab = 0;
                 for (int64_t x = g->row_ptr[u]; x < g->row_ptr[u + 1]; ++x) {
                     const int32_t bb = pos[g->col[x]];
                     const int64_t w = g->weight[x];
                     if (bb < 0) {
                         ++n_out;
                         wsum += w;
+                        wab += w < 0 ? -w : w;
                         sum_abs += w < 0 ? -w : w;
                     } else if (bb > a) {
                         ++n_in;
@@ -375,6 +377,7 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
                     }
                 }
                 out->wout[f0[q] + a] = wsum;
+                out->wabs[f0[q] + a] = static_cast<int32_t>(std::min<int64_t>(wab, INT32_MAX));
                 if (n_out > 65535) too_big = 1;
             }
             seg[s] = static_cast<uint32_t>(n_out);

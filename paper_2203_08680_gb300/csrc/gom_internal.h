@@ -39,6 +39,7 @@ int color_fos(const gom_graph_t *g, gom_fos *fos);
 //   fv[f0 + a]       = a-th variable of F_j (ascending)
 //   wout[f0 + a]     = sum of the weights of the edges from F_j[a] to
 //                      variables outside F_j
+//   wabs[f0 + a]     = the same sum of their absolute values
 //   seg[f0 + q + a]  = start of F_j[a]'s outside edges in dep[d0 ..], a = 0..s
 //                      (seg[f0 + q + s] = n_out)
 //   dep[d0 + x]      = {v, w} for the n_out outside edges grouped by a, then
@@ -48,6 +49,7 @@ struct ElemTables {
     std::vector<int32_t> hdr;     // 8 ints per element (32 bytes)
     std::vector<int32_t> fv;      // [total_vars]
     std::vector<int64_t> wout;    // [total_vars]
+    std::vector<int32_t> wabs;    // [total_vars] sum of |w| over F_j[a]'s outside edges (saturated at INT32_MAX)
     std::vector<uint32_t> seg;    // [total_vars + m]
     std::vector<int32_t> dep;     // 2 ints per entry
     int32_t max_s = 0;            // largest element
@@ -176,6 +178,8 @@ struct GomParams {
     int32_t xw_words;   // block mode: words of one warp's region of outside neighbours' words, the
                         //   regions of warps 0, 1, ... following each other from off_xw
     int32_t learn;      // learned filter: 0 off, 1 history and training log, 2 also skip elements
+    int32_t bs_sm;      // bit-sliced path: words per staged row block of one pair (>= the largest
+                        //   element, a multiple of 4)
     GomFilter flt;
     uint64_t seed;
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
@@ -195,6 +199,7 @@ struct GomParams {
     const int4 *hdr;         // [2m] element headers in colour order: {j, f0, d0, s | n_in << 8}, {n_out, 0, 0, 0}
     const int32_t *fv;       // [total_vars]
     const int64_t *wout;     // [total_vars]
+    const int32_t *wabs;     // [total_vars] sum of |w| over each variable's outside edges
     const uint32_t *seg;     // [total_vars + m]
     const int2 *dep;         // outside edges {v, w}, then inside edges {a | b << 8, w}
     const int32_t *cptr;     // [k+1] colour -> positions

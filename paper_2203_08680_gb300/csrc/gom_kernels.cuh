@@ -23,6 +23,14 @@ const void *gom_mix_kernel(int wpi, int variant, bool learn);
 // The persistent generation kernel k_run<WPI, mask, delta, learn>(GomParams,
 // int G, int64_t target), with the same instances (null where none).
 const void *gom_run_kernel(int wpi, int variant, bool learn);
+// The bit-sliced path (gom_bs.cu): the persistent generation kernel
+// k_run_bs<R>(GomParams, int G, int64_t target) and the per-group mixing
+// kernel k_mix_bs<R>(GomParams, int t) for bit-plane accumulators of R bits
+// (12 or 16; null beyond), and the shared-memory words of one warp's region
+// for staged row blocks of `sm` words.
+const void *gom_run_bs_kernel(int r);
+const void *gom_mix_bs_kernel(int r);
+int gom_bs_warp_words(int sm);
 // Batched path: instances on block ranges of one cooperative launch.
 // k_batch<MINB>(const GomParams *Ps, const GomBatchInst *inst, GomBarrier *bars, int B, int G, int f_words),
 // registers cut for MINB (2 or 3) resident blocks of 256 threads.

@@ -24,6 +24,7 @@ GOM_MAX_ELEMENT = 128
 GOM_OPT_PERSISTENT = 1
 GOM_OPT_PHASE_TRACE = 2
 GOM_OPT_DYNAMIC = 3
+GOM_OPT_BITSLICED = 4
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
@@ -602,7 +603,8 @@ class Population:
     workspace with torch and drives the C ABI above."""
 
     def __init__(self, graph, pop: int, seed: int, kind: int = GOM_FOS_NEIGHBOURHOOD, fos: Fos = None,
-                 stream=None, device=None, persistent: bool = None, dynamic: bool = None):
+                 stream=None, device=None, persistent: bool = None, dynamic: bool = None,
+                 bitsliced: bool = None):
         import torch
         self.torch = torch
         self.graph = _graph(graph)
@@ -630,6 +632,8 @@ class Population:
             gom_set_option(self.ctx, GOM_OPT_PERSISTENT, 1 if persistent else 0)
         if dynamic is not None:
             gom_set_option(self.ctx, GOM_OPT_DYNAMIC, 1 if dynamic else 0)
+        if bitsliced is not None:
+            gom_set_option(self.ctx, GOM_OPT_BITSLICED, 1 if bitsliced else 0)
 
     def generation(self, num: int = 1, target: int = INT64_MAX, want_stats: bool = True):
         return gom_generation(self.ctx, num, target, want_stats)

@@ -44,13 +44,32 @@ def _assert_same_stats(gst, ost):
         assert gst[gk] == ost[ok], (gk, gst, ost)
 
 
-def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MAX):
-    """Both execution paths (persistent kernel, per-generation graph) against
-    the oracle after every generation; the graph path with the other item
-    schedule (static stride / dynamic claims) than the persistent default."""
-    A = gom.Population(g, p, seed, kind, persistent=True)
+def _bitsliced_available(P) -> bool:
+    try:
+        gom.gom_set_option(P.ctx, gom.GOM_OPT_BITSLICED, 1)
+        return True
+    except gom.GomError:
+        return False
+
+
+def _populations(g, p, seed, kind=0):
+    """Every execution path: the per-lane mixing and, where the FOS and the
+    weights allow it, the bit-sliced mixing, each on the persistent kernel and
+    on the per-generation graph (the graph with the other item schedule,
+    static stride / dynamic claims, than the persistent default)."""
+    A = gom.Population(g, p, seed, kind, persistent=True, bitsliced=False)
     dyn = gom.gom_get_option(A.ctx, gom.GOM_OPT_DYNAMIC)
-    Ps = [A, gom.Population(g, p, seed, kind, persistent=False, dynamic=not dyn)]
+    Ps = [A, gom.Population(g, p, seed, kind, persistent=False, dynamic=not dyn, bitsliced=False)]
+    B = gom.Population(g, p, seed, kind, persistent=True)
+    if _bitsliced_available(B):
+        Ps += [B, gom.Population(g, p, seed, kind, persistent=False, dynamic=not dyn, bitsliced=True)]
+    return Ps
+
+
+def _parity(oracle, g, p, seed, gens, kind=0, check_every=1, target=gom.INT64_MAX):
+    """Every execution path (_populations) against the oracle after every
+    generation."""
+    Ps = _populations(g, p, seed, kind)
     run, k = _oracle_run(oracle, g, p, seed, kind)
     for P in Ps:
         assert P.k == k
@@ -109,12 +128,24 @@ def test_empty_graph_all_neutral(oracle):
     _parity(oracle, I.empty_graph(70), 40, 5, 3, kind=gom.GOM_FOS_SINGLETON)
 
 
-def test_unit_weight_torus_reaches_closed_form(oracle):
+def _pop(g, p, seed, bitsliced, **kw):
+    """A population on the per-lane (bitsliced=False) or the bit-sliced mixing
+    path; skips the test where the bit-sliced path is unavailable."""
+    P = gom.Population(g, p, seed, **kw)
+    if bitsliced and not _bitsliced_available(P):
+        pytest.skip("bit-sliced path unavailable for this FOS")
+    if not bitsliced:
+        gom.gom_set_option(P.ctx, gom.GOM_OPT_BITSLICED, 0)
+    return P
+
+
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_unit_weight_torus_reaches_closed_form(oracle, bitsliced):
     """Even torus, unit weights: the optimum is every edge cut (2 L^2); the
     target stop must match the oracle generation by generation."""
     g = I.torus2d(8, unit=True)
     target = 2 * 8 * 8
-    P = gom.Population(g, 32, 3)
+    P = _pop(g, 32, 3, bitsliced)
     run, _ = _oracle_run(oracle, g, 32, 3)
     gst, nrun = P.generation(200, target)
     ost = run.run(200, target)
@@ -126,12 +157,13 @@ def test_unit_weight_torus_reaches_closed_form(oracle):
         assert gst[-1]["best_fitness"] == target
 
 
-def test_target_stop_midway(oracle):
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_target_stop_midway(oracle, bitsliced):
     g = I.torus2d(20, seed=3)
     run, _ = _oracle_run(oracle, g, 24, 4)
     probe = run.run(6)
     target = probe[3]["best"]  # reached at or before generation 3
-    P = gom.Population(g, 24, 4)
+    P = _pop(g, 24, 4, bitsliced)
     run2, _ = _oracle_run(oracle, g, 24, 4)
     gst, nrun = P.generation(10, target)
     ost = run2.run(10, target)
@@ -171,7 +203,8 @@ def test_async_calls_equal_sync_calls():
     assert np.array_equal(sa["pop"], sb["pop"]) and np.array_equal(sa["f"], sb["f"])
 
 
-def test_resume_from_oracle_state(oracle):
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_resume_from_oracle_state(oracle, bitsliced):
     """Checkpoint/resume: a state written into the GPU continues exactly as the
     oracle continues from the same state."""
     g = I.random_regular(600, 5, seed=4)
@@ -179,7 +212,7 @@ def test_resume_from_oracle_state(oracle):
     for _ in range(3):
         run.generation()
     s = run.get()
-    P = gom.Population(g, 40, 7)
+    P = _pop(g, 40, 7, bitsliced)
     dev = torch.device("cuda")
     P.set_population(torch.from_numpy(s["pop"]).to(dev), torch.from_numpy(s["xe"]).to(dev), s["fe"], s["g"])
     assert np.array_equal(P.fitness().cpu().numpy(), s["f"])
@@ -189,13 +222,14 @@ def test_resume_from_oracle_state(oracle):
     _assert_same_state(_gpu_state(P), run.get())
 
 
-def test_identical_population_is_all_donorless(oracle):
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_identical_population_is_all_donorless(oracle, bitsliced):
     g = I.torus2d(12, seed=6)
     run, _ = _oracle_run(oracle, g, 36, 2)
     x = run.get()["pop"][5]
     pop = np.tile(x, (36, 1))
     fx = oracle.cut_value(g, x)
-    P = gom.Population(g, 36, 2)
+    P = _pop(g, 36, 2, bitsliced)
     dev = torch.device("cuda")
     P.set_population(torch.from_numpy(pop).to(dev), torch.from_numpy(x).to(dev), fx, 0)
     gst, _ = P.generation(1)
@@ -255,12 +289,13 @@ def _overlapping_fos(n, seed):
     return ep, ev
 
 
+@pytest.mark.parametrize("bitsliced", [False, True])
 @pytest.mark.parametrize("p", [16, 100])
-def test_custom_overlapping_fos(oracle, p):
+def test_custom_overlapping_fos(oracle, p, bitsliced):
     g = I.torus2d(8, seed=12)
     ep, ev = _overlapping_fos(g.n, 1)
     fos = gom.gom_fos_create(g.n, ep, ev)
-    P = gom.Population(g, p, 13, fos=fos)
+    P = _pop(g, p, 13, bitsliced, fos=fos)
     k, co = oracle.color(g, ep, ev)
     assert P.k == k
     run = oracle.Run(g, ep, ev, co, k, p, 13)
@@ -301,13 +336,15 @@ def test_grid_barrier_bounded_wait():
     P.generation(2)
 
 
+@pytest.mark.parametrize("bitsliced", [False, True])
 @pytest.mark.parametrize("dynamic", [False, True])
-def test_large_groups_one_warp_per_element(oracle, dynamic):
-    """Colour groups of ~20,000 elements: one warp per element walking all its
-    word groups (smaller groups give each word group its own warp), several
-    items per warp, with either item schedule on the persistent path."""
+def test_large_groups_one_warp_per_element(oracle, dynamic, bitsliced):
+    """Colour groups of ~20,000 elements: several items per warp, with either
+    item schedule on the persistent path; per-lane mixing (one warp per
+    element walking all its word groups) and bit-sliced mixing (an item of 8
+    elements, one (element, word) pair per lane)."""
     g = I.torus2d(400, seed=12)
-    P = gom.Population(g, 96, 6, persistent=True, dynamic=dynamic)
+    P = _pop(g, 96, 6, bitsliced, persistent=True, dynamic=dynamic)
     run, _ = _oracle_run(oracle, g, 96, 6)
     for gen in range(3):
         ost = run.generation()
@@ -332,9 +369,10 @@ def test_runs_of_identical_individuals(oracle, p):
     run.load(pop, f, xe, int(f.max()), 0)
     Ps = []
     for persistent in (True, False):
-        P = gom.Population(g, p, 3, persistent=persistent)
-        P.set_population(torch.from_numpy(pop).to(dev), torch.from_numpy(xe).to(dev), int(f.max()), 0)
-        Ps.append(P)
+        for bitsliced in (False, True):
+            P = gom.Population(g, p, 3, persistent=persistent, bitsliced=bitsliced)
+            P.set_population(torch.from_numpy(pop).to(dev), torch.from_numpy(xe).to(dev), int(f.max()), 0)
+            Ps.append(P)
     for _ in range(6):
         ost = run.generation()
         for P in Ps:
@@ -350,8 +388,12 @@ def _fos_parity(oracle, g, fos, ep, ev, p, seed, gens):
     against the oracle, every generation."""
     k, co = oracle.color(g, ep, ev)
     run = oracle.Run(g, ep, ev, co, k, p, seed)
-    Ps = [gom.Population(g, p, seed, fos=fos, persistent=True), gom.Population(g, p, seed, fos=fos, persistent=False),
-          gom.Population(g, p, seed, fos=fos, persistent=True, dynamic=False)]
+    Ps = [gom.Population(g, p, seed, fos=fos, persistent=True, bitsliced=False),
+          gom.Population(g, p, seed, fos=fos, persistent=False, bitsliced=False),
+          gom.Population(g, p, seed, fos=fos, persistent=True, dynamic=False, bitsliced=False)]
+    B = gom.Population(g, p, seed, fos=fos, persistent=True, dynamic=False)
+    if _bitsliced_available(B):  # sets of at most 32 variables
+        Ps += [B, gom.Population(g, p, seed, fos=fos, persistent=False, bitsliced=True)]
     for P in Ps:
         assert P.k == k
         _assert_same_state(_gpu_state(P), run.get(), "init")
