@@ -43,6 +43,19 @@
  *  R11 bounded fixed linkage tree (Sec. 4.1): UPGMA on the edge weights, linked
  *     pairs only, merges above the bound never made, ties by creation ids
  *     (orc_build_bflt).
+ *  R12 Forced Improvement (Sec. 4, Alg. 1; off unless orc_set_fi switches it
+ *     on -- the paper's parallel GOMEA runs without it, Sec. 5.4, and names a
+ *     parallel-friendly variant as future work).  After the generation's
+ *     mixing the elitist is updated as in R9; FI then applies to every
+ *     individual with no accepted GOM step in the generation (or, with a
+ *     threshold nis > 0, whose fitness has not improved for nis generations,
+ *     this one included).  Such an individual takes GOM steps with the
+ *     elitist as donor on the elements of each colour group, the groups in
+ *     this generation's order; a step is accepted as in R8 with the flag
+ *     "equal to the elitist" taken at the start of FI; FI stops after the
+ *     first group in which a step improved its fitness (the elements of one
+ *     group are independent of each other, so their order does not matter);
+ *     if no step improved it, the individual becomes a copy of the elitist.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -509,6 +522,11 @@ typedef struct {
     int64_t accepted;
     int64_t improving;
     int64_t reached;      /* 1 if best >= target */
+    int64_t fi_individuals; /* R12: individuals that entered FI */
+    int64_t fi_trials;    /* their (individual, element) steps, those without variation included */
+    int64_t fi_accepted;
+    int64_t fi_improving;
+    int64_t fi_replaced;  /* individuals replaced by a copy of the elitist */
 } orc_stats;
 
 /* Scratch of one trial: the element's membership stamps and donor bits. */
@@ -537,6 +555,11 @@ typedef struct {
     int64_t fe;
     uint32_t g;
     uint8_t *eq;     /* [p] P[i] == x_e at generation start */
+    int32_t fi_on;   /* R12 */
+    int32_t fi_nis;  /* R12 threshold, 0 = condition off */
+    uint8_t *acc_any;/* [p] an accepted GOM step in this generation */
+    int32_t *nis;    /* [p] generations in a row without improvement */
+    int64_t *f_start;/* [p] fitness at generation start */
     int64_t max_s;   /* largest element */
     orc_scratch sc;  /* scratch of the single-threaded path */
 } orc_state;
@@ -614,6 +637,11 @@ orc_state *orc_new_ex(int32_t n, const int64_t *rp, const int32_t *col, const in
     s->f = (int64_t *)malloc(sizeof(int64_t) * (size_t)p);
     s->xe = (uint8_t *)malloc((size_t)n + 1);
     s->eq = (uint8_t *)malloc((size_t)p);
+    s->acc_any = (uint8_t *)calloc((size_t)p, 1);
+    s->nis = (int32_t *)calloc((size_t)p, sizeof(int32_t));
+    s->f_start = (int64_t *)calloc((size_t)p, sizeof(int64_t));
+    s->fi_on = 0;
+    s->fi_nis = 0;
     s->g = 0;
     if (!init) {
         memset(s->O, 0, (size_t)p * (size_t)n);
@@ -645,6 +673,9 @@ void orc_free(orc_state *s)
     free(s->rp); free(s->col); free(s->w); free(s->eptr); free(s->evars);
     free(s->cptr); free(s->celems); free(s->O); free(s->P); free(s->f); free(s->xe);
     free(s->eq);
+    free(s->acc_any);
+    free(s->nis);
+    free(s->f_start);
     scratch_free(&s->sc);
     free(s);
 }
@@ -735,7 +766,85 @@ static void gom_trial(orc_state *s, orc_scratch *sc, int32_t i, int32_t j, orc_s
         s->f[i] += d;
         st->accepted++;
         if (d > 0) st->improving++;
+        s->acc_any[i] = 1;
     }
+}
+
+/* R12: switches Forced Improvement on or off, with its no-improvement
+ * threshold (0: only individuals without an accepted step enter FI). */
+void orc_set_fi(orc_state *s, int32_t on, int32_t nis)
+{
+    s->fi_on = on ? 1 : 0;
+    s->fi_nis = nis > 0 ? nis : 0;
+}
+
+/* One FI step (R12) of individual i on element j: the elitist as donor,
+ * accepted as in R8 with the flag eq_fi.  Returns 1 if it improved f[i]. */
+static int fi_trial(orc_state *s, orc_scratch *sc, int32_t i, int32_t j, uint8_t eq_fi, orc_stats *st)
+{
+    const int32_t n = s->n;
+    const int32_t *F = s->evars + s->eptr[j];
+    const int32_t sz = (int32_t)(s->eptr[j + 1] - s->eptr[j]);
+    uint8_t *o = s->O + (size_t)i * n;
+    st->fi_trials++;
+    int differs = 0;
+    for (int32_t q = 0; q < sz; ++q)
+        if (s->xe[F[q]] != o[F[q]]) differs = 1;
+    if (!differs) return 0; /* no variation: GOM is not performed */
+    uint8_t *y = sc->ybuf;
+    sc->stamp++;
+    for (int32_t q = 0; q < sz; ++q) {
+        y[q] = s->xe[F[q]];
+        sc->in_f[F[q]] = sc->stamp;
+        sc->pos_in_f[F[q]] = q;
+    }
+    int64_t d = partial_delta(s->rp, s->col, s->w, o, F, sz, y, sc->pos_in_f, sc->in_f, sc->stamp);
+    if (d > 0 || (d == 0 && !eq_fi)) {
+        for (int32_t q = 0; q < sz; ++q) o[F[q]] = y[q];
+        s->f[i] += d;
+        st->fi_accepted++;
+        if (d > 0) st->fi_improving++;
+        return d > 0;
+    }
+    return 0;
+}
+
+/* R12: Forced Improvement after the generation's mixing, groups in `order`. */
+static void forced_improvement(orc_state *s, const int32_t *order, orc_stats *st)
+{
+    const int32_t n = s->n, p = s->p;
+    /* the elitist of the population as it is now (R9's rule) */
+    int64_t best = INT64_MIN;
+    int32_t arg = 0;
+    for (int32_t i = 0; i < p; ++i)
+        if (s->f[i] > best) { best = s->f[i]; arg = i; }
+    if (best > s->fe) {
+        s->fe = best;
+        memcpy(s->xe, s->O + (size_t)arg * n, (size_t)n);
+    }
+    for (int32_t i = 0; i < p; ++i) {
+        const int stale = s->fi_nis > 0 && (s->f[i] > s->f_start[i] ? 0 : s->nis[i] + 1) >= s->fi_nis;
+        if (s->acc_any[i] && !stale) continue;
+        st->fi_individuals++;
+        const uint8_t eq_fi = memcmp(s->O + (size_t)i * n, s->xe, (size_t)n) == 0;
+        int improved = 0;
+        for (int32_t t = 0; t < s->k && !improved; ++t) {
+            const int32_t c = order[t];
+            for (int64_t q = s->cptr[c]; q < s->cptr[c + 1]; ++q)
+                improved |= fi_trial(s, &s->sc, i, s->celems[q], eq_fi, st);
+        }
+        if (!improved) {
+            memcpy(s->O + (size_t)i * n, s->xe, (size_t)n);
+            s->f[i] = s->fe;
+            st->fi_replaced++;
+        }
+    }
+}
+
+/* R12 bookkeeping at generation end: generations without improvement. */
+static void fi_count_stale(orc_state *s)
+{
+    for (int32_t i = 0; i < s->p; ++i) s->nis[i] = s->f[i] > s->f_start[i] ? 0 : s->nis[i] + 1;
 }
 
 /* Small deterministic generator used only to permute the trials of one group
@@ -755,6 +864,8 @@ static void generation_start(orc_state *s)
     memcpy(s->P, s->O, (size_t)p * n);
     /* R8: the elitist flag of each individual is fixed at generation start */
     for (int32_t i = 0; i < p; ++i) s->eq[i] = memcmp(s->P + (size_t)i * n, s->xe, (size_t)n) == 0;
+    memset(s->acc_any, 0, (size_t)p);
+    memcpy(s->f_start, s->f, sizeof(int64_t) * (size_t)p);
 }
 
 /* Generation end: R9 elitist update, the target check, g += 1. */
@@ -830,6 +941,10 @@ static int32_t generation_impl(orc_state *s, int64_t target, uint64_t shuffle, c
         }
         free(perm);
     }
+    if (s->fi_on && !only) {
+        forced_improvement(s, order, st);
+        fi_count_stale(s);
+    }
     free(order);
 
     st->generation = s->g;
@@ -900,6 +1015,10 @@ int32_t orc_generation_par_ex(orc_state *s, int64_t target, int32_t threads, con
     }
     free(sc);
     free(ts);
+    if (s->fi_on && !only) {
+        forced_improvement(s, order, st);
+        fi_count_stale(s);
+    }
     free(order);
     st->generation = s->g;
     if (!only) generation_end(s, target, st);

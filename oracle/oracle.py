@@ -79,6 +79,7 @@ def lib():
         L.orc_generation_par.restype = i32
         L.orc_generation_par_ex.argtypes = [P, i64, i32, P, i32, P]
         L.orc_generation_par_ex.restype = i32
+        L.orc_set_fi.argtypes = [P, i32, i32]
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = i32
         _lib = L
@@ -102,7 +103,7 @@ def _csr(g):
 class Stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("generation", "best", "elite", "trials", "donorless", "accepted", "improving",
-                 "reached")]
+                 "reached", "fi_individuals", "fi_trials", "fi_accepted", "fi_improving", "fi_replaced")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -241,6 +242,10 @@ class Run:
             o = np.ascontiguousarray(only, dtype=np.int32)
             lib().orc_generation_ex(self._h, target, shuffle, _p(o), len(o), C.byref(st))
         return st.as_dict()
+
+    def set_fi(self, on: bool, nis: int = 0):
+        """Forced Improvement after each generation's mixing (reading R12)."""
+        lib().orc_set_fi(self._h, 1 if on else 0, nis)
 
     def generation_skip(self, skip_elem, target: int = 2 ** 63 - 1) -> dict:
         """One generation without the trials of the elements marked in skip_elem[j]."""

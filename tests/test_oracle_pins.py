@@ -632,3 +632,116 @@ def test_generation_skip_mask(oracle):
     after = b.get()
     assert st["trials"] == 0 and st["accepted"] == 0
     assert np.array_equal(before["pop"], after["pop"]) and after["g"] == before["g"] + 1
+
+
+# ---------------------------------------------------------------------------
+# Forced Improvement (Sec. 4, Alg. 1), in its parallel reading (R12 of the oracle)
+
+def _fi_path_case(oracle):
+    """Path 0-1-2-3-4-5 with weights 7, 5, 9, 9, 8, singleton FOS.  Welsh-Powell
+    on the path-shaped LMIG gives the groups {1,3,5} (colour 0) and {0,2,4}."""
+    g = I.from_edges(6, np.arange(5), np.arange(1, 6), np.array([7, 5, 9, 9, 8]))
+    ep, ev = oracle.build_fos(g, oracle.SINGLETON)
+    k, co = oracle.color(g, ep, ev)
+    assert k == 2 and list(np.flatnonzero(co == 0)) == [1, 3, 5] and list(np.flatnonzero(co == 1)) == [0, 2, 4]
+    return g, ep, ev, k, co
+
+
+def test_fi_hand_example_stops_after_first_improving_group(oracle):
+    """Both individuals are y = 111011 (cut 18) and the elitist is 010100
+    (cut 30), not in the population.  Mixing has no donor (the two
+    individuals are equal), so both enter FI with the elitist as donor.
+    Worked by hand: with group {1,3,5} first, {1} needs no change, {3} would
+    lose 18 (rejected), {5} gains 8 (accepted, f = 26) -- an improvement, so
+    FI stops there: 111010, although group {0,2,4} would gain 7 more.  With
+    group {0,2,4} first, {0} gains 7 (f = 25), {2} would lose 4 and {4}
+    would lose 1 (rejected): FI stops with 011011."""
+    g, ep, ev, k, co = _fi_path_case(oracle)
+    y = np.array([1, 1, 1, 0, 1, 1], dtype=np.uint8)
+    xe = np.array([0, 1, 0, 1, 0, 0], dtype=np.uint8)
+    assert oracle.cut_value(g, y) == 18 and oracle.cut_value(g, xe) == 30
+    seen = set()
+    for seed in range(1, 40):
+        order = list(oracle.group_order(seed, k, 0))
+        run = oracle.Run(g, ep, ev, co, k, 2, seed)
+        run.load(np.stack([y, y]), np.array([18, 18]), xe, 30, 0)
+        run.set_fi(True)
+        st = run.generation()
+        s = run.get()
+        want, fw = ([1, 1, 1, 0, 1, 0], 26) if order[0] == 0 else ([0, 1, 1, 0, 1, 1], 25)
+        for i in range(2):
+            assert list(s["pop"][i]) == want and s["f"][i] == fw, (seed, order)
+        assert s["fe"] == 30 and list(s["xe"]) == list(xe)
+        assert st["trials"] == 12 and st["donorless"] == 12 and st["accepted"] == 0
+        assert (st["fi_individuals"], st["fi_trials"], st["fi_accepted"], st["fi_improving"], st["fi_replaced"]) \
+            == (2, 6, 2, 2, 0)
+        seen.add(order[0])
+    assert seen == {0, 1}  # both group orders were exercised
+
+
+def test_fi_replaces_with_elitist_when_nothing_improves(oracle):
+    """An individual that no elitist step can improve becomes a copy of the
+    elitist.  y = 100100 (cut 25) differs from the elitist 010100 (cut 30) on
+    vertices 0 and 1 only; by hand, moving vertex 0 to the elitist's value
+    uncuts edge (0,1) (-7) and moving vertex 1 uncuts (0,1) and cuts (1,2)
+    (-7 + 5 = -2): FI improves nothing, and y is replaced (f 25 -> 30)."""
+    g, ep, ev, k, co = _fi_path_case(oracle)
+    xe = np.array([0, 1, 0, 1, 0, 0], dtype=np.uint8)
+    y = np.array([1, 0, 0, 1, 0, 0], dtype=np.uint8)
+    assert oracle.cut_value(g, y) == 25
+    run = oracle.Run(g, ep, ev, co, k, 2, 3)
+    run.load(np.stack([y, y]), np.array([25, 25]), xe, 30, 0)
+    run.set_fi(True)
+    st = run.generation()
+    s = run.get()
+    for i in range(2):
+        assert np.array_equal(s["pop"][i], xe) and s["f"][i] == 30
+    assert st["fi_individuals"] == 2 and st["fi_replaced"] == 2 and st["fi_improving"] == 0
+
+
+def test_fi_identical_population_equal_to_elitist_is_unchanged(oracle):
+    """Every individual equals the elitist: mixing has no donor, every
+    individual enters FI, no step varies anything, each is 'replaced' by the
+    elitist it already equals -- the state does not change."""
+    g = I.torus2d(6, seed=3)
+    eptr, evars, k, colors = _setup(oracle, g)
+    run = oracle.Run(g, eptr, evars, colors, k, 5, 2)
+    x = run.get()["xe"].copy()
+    fx = oracle.cut_value(g, x)
+    run.load(np.tile(x, (5, 1)), np.full(5, fx), x, fx, 0)
+    run.set_fi(True)
+    st = run.generation()
+    s = run.get()
+    assert np.array_equal(s["pop"], np.tile(x, (5, 1))) and (s["f"] == fx).all()
+    assert st["fi_individuals"] == 5 and st["fi_replaced"] == 5 and st["fi_accepted"] == 0
+    assert st["fi_trials"] == 5 * (len(eptr) - 1)  # no improvement: every group is visited
+
+
+@pytest.mark.parametrize("nis", [0, 2])
+def test_fi_against_the_same_generation_without_it(oracle, nis):
+    """From the same state, one generation with FI and one without: mixing is
+    identical (FI comes after it), so every individual FI left alone has the
+    same row and fitness, and every one it touched either improved on its
+    FI-less fitness or became a copy of the elitist.  FI never lowers a
+    fitness; incremental fitness equals full evaluation; each individual that
+    entered FI and was not replaced took at least one improving step."""
+    g = I.random_regular(120, 4, seed=9)
+    eptr, evars, k, colors = _setup(oracle, g)
+    base = oracle.Run(g, eptr, evars, colors, k, 24, 5)
+    for gen in range(12):
+        snap = base.get()
+        off = oracle.Run(g, eptr, evars, colors, k, 24, 5, init=False)
+        off.load(snap["pop"], snap["f"], snap["xe"], snap["fe"], snap["g"])
+        so = off.generation()
+        base.set_fi(True, nis)
+        sb = base.generation()
+        a, b = base.get(), off.get()
+        assert so["accepted"] == sb["accepted"] and so["donorless"] == sb["donorless"]
+        assert (a["f"] >= b["f"]).all() and (a["f"] >= snap["f"]).all()
+        assert a["fe"] >= b["fe"]
+        for i in range(24):
+            if not np.array_equal(a["pop"][i], b["pop"][i]):
+                assert a["f"][i] > b["f"][i] or (np.array_equal(a["pop"][i], a["xe"]) and a["f"][i] == a["fe"])
+            assert oracle.cut_value(g, a["pop"][i]) == a["f"][i]
+        assert sb["fi_improving"] >= sb["fi_individuals"] - sb["fi_replaced"] >= 0
+        assert sum(np.array_equal(a["pop"][i], a["xe"]) for i in range(24)) >= sb["fi_replaced"]
