@@ -386,6 +386,9 @@ def test_gom_identical_population_is_all_donorless(oracle):
     assert np.array_equal(run.get()["pop"], pop)
 
 
+FI_OFF = {"fi_individuals": 0, "fi_trials": 0, "fi_accepted": 0, "fi_improving": 0, "fi_replaced": 0}
+
+
 def test_gom_tie_rule_uses_generation_start_genotype(oracle):
     """Empty graph, singleton FOS: every move is neutral (delta = 0), so a
     move is accepted exactly when P[i] differs from the elitist (Alg. 2 with
@@ -400,7 +403,7 @@ def test_gom_tie_rule_uses_generation_start_genotype(oracle):
     run.load(pop, np.zeros(p, dtype=np.int64), pop[0], 0, 0)
     st = run.generation()
     assert st == {"generation": 0, "best": 0, "elite": 0, "trials": p * g.n, "donorless": 0,
-                  "accepted": g.n, "improving": 0, "reached": 0}
+                  "accepted": g.n, "improving": 0, "reached": 0, **FI_OFF}
     assert np.array_equal(run.get()["pop"], np.zeros((p, g.n), dtype=np.uint8))
     st = run.generation()
     assert st["donorless"] == st["trials"] and st["accepted"] == 0
