@@ -128,6 +128,12 @@ typedef struct gom_gen_stats {
     int64_t accepted;       /* trials whose change was kept */
     int64_t improving;      /* accepted trials with a positive delta */
     int64_t reached_target; /* 1 if best_fitness >= the call's target */
+    /* Forced Improvement (GOM_OPT_FORCED_IMPROVEMENT; zero while off): */
+    int64_t fi_individuals; /* individuals that entered FI */
+    int64_t fi_trials;      /* their (individual, element) steps, those without variation included */
+    int64_t fi_accepted;    /* FI steps whose change was kept */
+    int64_t fi_improving;   /* accepted FI steps with a positive delta */
+    int64_t fi_replaced;    /* individuals FI did not improve, replaced by a copy of the elitist */
 } gom_gen_stats_t;
 
 /*

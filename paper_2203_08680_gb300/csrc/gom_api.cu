@@ -207,6 +207,11 @@ int ctx_read_stats(gom_ctx *ctx, int32_t num, gom_gen_stats_t *host_stats, int32
             H.accepted = S.accepted;
             H.improving = S.improving;
             H.reached_target = S.reached;
+            H.fi_individuals = S.fi_individuals;
+            H.fi_trials = S.fi_trials;
+            H.fi_accepted = S.fi_accepted;
+            H.fi_improving = S.fi_improving;
+            H.fi_replaced = S.fi_replaced;
         }
     }
     return GOM_OK;
@@ -464,7 +469,10 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
         const int R = tabs.max_abs_w < (int64_t(1) << 12) ? 12 : 16;
         if (coop && variant == kVarNarrow && max_w <= 255 && tabs.max_abs_w < (int64_t(1) << 16)) {
             const int sm = static_cast<int>((std::max<int64_t>(tabs.max_s, 1) + 3) & ~int64_t(3));
-            const int64_t ww = gom_bs_warp_words(sm);
+            const int S = static_cast<int>(std::max<int64_t>(tabs.max_s, 1));
+            const int epw = 32 / S, E0 = 32 / c->W;
+            const int nc = (E0 + epw - 1) / epw;
+            const int64_t ww = gom_bs_warp_words(sm, nc, c->W);
             const int wpb = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (ww * 4)));
             const size_t smem = std::max(static_cast<size_t>(ww * 4 * wpb), keys_smem);
             const void *rf = gom_run_bs_kernel(R), *mf = gom_mix_bs_kernel(R);
@@ -487,6 +495,10 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
                     c->bs_grid_mix = static_cast<int>(std::min<int64_t>(
                         std::min<int64_t>(static_cast<int64_t>(c->sms) * occ_m, need), kMaxMixBlocks));
                     c->prm.bs_sm = sm;
+                    c->prm.bs_S = S;
+                    c->prm.bs_epw = epw;
+                    c->prm.bs_nc = nc;
+                    c->prm.bs_words = static_cast<int32_t>(ww);
                     // the default where every resident warp gets an item of the largest group
                     c->bs_on = items >= static_cast<int64_t>(c->sms) * occ_r * wpb;
                 }
@@ -516,6 +528,10 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.m = static_cast<int32_t>(fos->m);
     P.k = fos->k;
     P.seed = seed;
+    for (int r = 0; r < 10; ++r) { // Philox4x32-10 round keys (the published Weyl increments)
+        P.rk[2 * r] = static_cast<uint32_t>(seed) + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        P.rk[2 * r + 1] = static_cast<uint32_t>(seed >> 32) + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
     P.split = split;
     P.blk = blk ? 1 : 0;
     P.xw_words = static_cast<int32_t>(xw_words);

@@ -134,6 +134,8 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
     }
     for (gom_ctx *c : cs)
         if (!c || c->stream != s) return GOM_E_ARG;
+    for (gom_ctx *c : cs)
+        if (c->prm.fi.on) return GOM_E_STATE; // Forced Improvement runs on single-instance launches only
 
     int dev = 0, sms = 0, coop = 0;
     GOM_CUDA(nullptr, cudaGetDevice(&dev));
@@ -225,6 +227,7 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         P.off_ds = static_cast<int32_t>(SL.off_ds);
         P.dyn = 1;
         P.learn = 0; // the learned filter is not active inside batched launches
+        P.fi.on = 0; // nor Forced Improvement (refused above)
         P.bar = B->d_bars + b; // (P.trace: the context's phase trace, when switched on)
         B->params[b] = P;
         GomBatchInst &I = B->inst[b];

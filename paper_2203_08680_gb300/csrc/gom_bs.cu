@@ -40,95 +40,40 @@
 #include <climits>
 #include <cuda_runtime.h>
 
+#include "gom_bitplane.cuh"
 #include "gom_device.cuh"
+#include "gom_fi.cuh"
 #include "gom_internal.h"
 #include "gom_kernels.cuh"
 
 namespace {
 
-constexpr int kFitPlanes = 24;  // bits of the per-lane bit-sliced fitness accumulator
-constexpr int kWeightBits = 8;  // |w| < 2^8 on this path
-
-// x & (bit t of u ? ~0 : 0), for a per-lane weight u.
-__device__ __forceinline__ uint32_t bit_mask(uint32_t x, uint32_t u, int t) { return ((u >> t) & 1u) ? x : 0u; }
-
-// acc += u * x over R bit-planes (ripple carry; u < 2^UB; the sum stays below
-// 2^R by the caller's bound, so the last carry is always zero).
-template <int R, int UB, int NA>
-__device__ __forceinline__ void add_weighted(uint32_t (&acc)[NA], uint32_t x, uint32_t u)
-{
-    static_assert(NA >= R, "accumulator narrower than R");
-    uint32_t carry = 0;
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-        if (t < UB) {
-            const uint32_t in = bit_mask(x, u, t);
-            const uint32_t a = acc[t];
-            acc[t] = a ^ in ^ carry;
-            carry = (a & in) | (a & carry) | (in & carry);
-        } else {
-            const uint32_t a = acc[t];
-            acc[t] = a ^ carry;
-            carry = a & carry;
-        }
-    }
-}
-
-// Per-lane state of the bit-sliced path across the groups of a generation.
-struct BsLane {
-    uint32_t fit[kFitPlanes]; // accepted deltas of this lane's 32 individuals (word lane mod W), bit-sliced
-    int since_flush;          // items added since the last flush (warp-uniform)
-    unsigned n_dl, n_acc, n_imp;
-};
-
-__device__ __forceinline__ void bs_lane_zero(BsLane &L)
-{
-#pragma unroll
-    for (int t = 0; t < kFitPlanes; ++t) L.fit[t] = 0;
-    L.since_flush = 0;
-    L.n_dl = L.n_acc = L.n_imp = 0;
-}
-
-// Adds the lane's accumulated deltas into the block's fitness accumulators
-// s_f[32 w + b] (one shared atomic per individual with a non-zero sum) and
-// clears them.  Warp-wide call.
-__device__ __forceinline__ void bs_flush(const GomParams &P, BsLane &L, long long *s_f)
+// 32 x 32 bit-matrix transpose across the warp: lane r holds row r (bit c =
+// entry (r, c)) on entry and column r (bit c = entry (c, r)) on return.  Five
+// steps; step j swaps the off-diagonal j x j blocks of each 2j x 2j block
+// between lanes l and l ^ j.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x)
 {
     const int lane = threadIdx.x & 31;
-    const int w = lane & (P.W - 1);
-    uint32_t any = 0;
 #pragma unroll
-    for (int t = 0; t < kFitPlanes; ++t) any |= L.fit[t];
-    if (any) {
-        for (int b = 0; b < 32; ++b) {
-            if (!((any >> b) & 1u)) continue;
-            unsigned v = 0;
-#pragma unroll
-            for (int t = 0; t < kFitPlanes; ++t) v |= ((L.fit[t] >> b) & 1u) << t;
-            atomicAdd(reinterpret_cast<unsigned long long *>(&s_f[32 * w + b]), (unsigned long long)v);
-        }
+    for (int j = 16; j; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u
+                                                                                                  : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+        if (lane & j)
+            x = (x & ~m) | ((y >> j) & m);
+        else
+            x = (x & m) | ((y << j) & ~m);
     }
-#pragma unroll
-    for (int t = 0; t < kFitPlanes; ++t) L.fit[t] = 0;
-    L.since_flush = 0;
+    return x;
 }
 
-// The bits on F_j (variables 0 .. s-1 of the element in slot e) of individual
-// d of the generation-start population, from the staged rows
-// sP[(e W + word) SM + a].
-__device__ __forceinline__ uint32_t pattern_of(const uint32_t *sP, int SM, int e, int W, int s, int d)
+// The pattern (bits on F_j) of individual d from a packed table: tab[(c W +
+// d / 32) 32 + d mod 32] holds the patterns of the elements of chunk c side
+// by side, the element's at bit offset `off`.
+__device__ __forceinline__ uint32_t packed_pattern(const uint32_t *tab, int c, int W, int d, int off, uint32_t fmask)
 {
-    const uint32_t *row = sP + (e * W + (d >> 5)) * SM;
-    const int bd = d & 31;
-    uint32_t pat = 0;
-    for (int a4 = 0; a4 < s; a4 += 4) {
-        const uint4 r = *reinterpret_cast<const uint4 *>(row + a4);
-        pat |= ((r.x >> bd) & 1u) << a4;
-        pat |= ((r.y >> bd) & 1u) << (a4 + 1);
-        pat |= ((r.z >> bd) & 1u) << (a4 + 2);
-        pat |= ((r.w >> bd) & 1u) << (a4 + 3);
-    }
-    return pat;
+    return (tab[(c * W + (d >> 5)) * 32 + (d & 31)] >> off) & fmask;
 }
 
 // Word-parallel donor scan over the staged rows (32 candidates per step):
@@ -158,14 +103,18 @@ __device__ int scan_rows(const uint32_t *sP, int SM, int e, int W, int Wv, int p
 
 // The donor of individual `self` (Sec. 4.2): the first candidate in cyclic
 // order from `start`, skipping self, whose generation-start bits on F_j
-// differ from the parent's current bits xf, or -1.  rs are the run starts of
-// the element's patterns (bit d: pattern d differs from pattern d - 1,
-// cyclically): candidates strictly inside a run equal to the parent are
-// passed in one step.  *pd receives the donor's pattern.  Divergent code.
-__device__ int find_donor_rows(const uint32_t *sP, const uint32_t *rs, int SM, int e, int W, int Wv, int p, int s,
-                               uint32_t xf, int start, int self, uint32_t *pd)
+// differ from the parent's current bits xf, or -1.  Candidates' patterns come
+// from the packed table of P (chunk c, field offset off); rs are the run
+// starts of the element's patterns (bit d: pattern d differs from pattern
+// d - 1, cyclically), so candidates strictly inside a run equal to the parent
+// are passed in one step (a run start after such a run differs from xf);
+// after a few steps the word-parallel scan over the staged rows finishes the
+// search.  *pd receives the donor's pattern.  Divergent code.
+__device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t fmask, const uint32_t *sP,
+                                 const uint32_t *rs, int SM, int e, int W, int Wv, int p, int s, uint32_t xf,
+                                 int start, int self, uint32_t *pd)
 {
-    uint32_t pat = pattern_of(sP, SM, e, W, s, start);
+    uint32_t pat = packed_pattern(tabP, c, W, start, off, fmask);
     if (pat != xf) {
         *pd = pat;
         return start;
@@ -173,17 +122,17 @@ __device__ int find_donor_rows(const uint32_t *sP, const uint32_t *rs, int SM, i
     int d = start; // pattern d == xf here
     for (int it = 0; it < 4; ++it) {
         const int d2 = next_set_cyclic(rs, Wv, p, d);
-        if (d2 < 0) return -1; // one run: every candidate equals the parent
+        if (d2 < 0) return -1;
         const int dist_d = d - start + (d < start ? p : 0);
         const int dist_2 = d2 - start + (d2 < start ? p : 0);
-        if (dist_2 <= dist_d) return -1; // the jump passed the start
-        if (d2 != self) {                // a run start after a run equal to xf differs from xf
-            *pd = pattern_of(sP, SM, e, W, s, d2);
+        if (dist_2 <= dist_d) return -1;
+        if (d2 != self) {
+            *pd = packed_pattern(tabP, c, W, d2, off, fmask);
             return d2;
         }
-        d = d2 + 1 == p ? 0 : d2 + 1; // skip the parent's own column
+        d = d2 + 1 == p ? 0 : d2 + 1;
         if (d == start) return -1;
-        pat = pattern_of(sP, SM, e, W, s, d);
+        pat = packed_pattern(tabP, c, W, d, off, fmask);
         if (pat != xf) {
             *pd = pat;
             return d;
@@ -192,14 +141,15 @@ __device__ int find_donor_rows(const uint32_t *sP, const uint32_t *rs, int SM, i
     const int d3 = d + 1 == p ? 0 : d + 1;
     if (d3 == start) return -1;
     const int r = scan_rows(sP, SM, e, W, Wv, p, s, xf, d3, self);
-    if (r >= 0) *pd = pattern_of(sP, SM, e, W, s, r);
+    if (r >= 0) *pd = packed_pattern(tabP, c, W, r, off, fmask);
     return r;
 }
 
-// Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4):
-// rows of O on F_j [32 pairs][SM], rows of P [32][SM], flip planes [32][SM],
-// donor starts [32 pairs][32 individuals], run starts [32 pairs].
-__host__ __device__ __forceinline__ int bs_warp_words(int SM) { return 96 * SM + 32 * 32 + 32; }
+// Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4;
+// NC chunks of packed patterns): rows of O on F_j [32 pairs][SM], rows of P
+// [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals], run
+// starts [32 pairs], packed patterns of P and of O [NC][W][32] each.
+__host__ __device__ __forceinline__ int bs_warp_words(int SM, int NC, int W) { return 96 * SM + 32 * 32 + 32 + 64 * NC * W; }
 
 // One item of colour group c at position t: elements [q0, q1) (at most E)
 // with every word, all trials of Alg. 2.
@@ -260,7 +210,6 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         sRS[lane] = rsw;
     }
     {   // donor starts: call (pair k2, c) covers individuals 32 w2 + 4c .. + 3
-        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
 #pragma unroll 1
         for (int r = 0; r < 8; ++r) {
             const int k2 = 4 * r + (lane >> 3), c = lane & 7;
@@ -268,7 +217,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             const int j2 = __shfl_sync(0xFFFFFFFFu, j, k2);
             const bool v2 = __shfl_sync(0xFFFFFFFFu, kv ? 1 : 0, k2) && 32 * w2 + 4 * c < p;
             if (v2) {
-                const uint4 r4 = philox10(make_uint4((uint32_t)j2, (uint32_t)(8 * w2 + c), g, kTagDonor), k0, k1);
+                const uint4 r4 = philox10_rk(make_uint4((uint32_t)j2, (uint32_t)(8 * w2 + c), g, kTagDonor), P.rk);
                 const int i0 = 32 * w2 + 4 * c;
                 int st[4];
 #pragma unroll
@@ -280,36 +229,56 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             }
         }
     }
+    // packed patterns: for chunk c (elements c EPW .. c EPW + EPW - 1 of the
+    // item) and word w2, lane b receives the bits of individual 32 w2 + b on
+    // the chunk's elements side by side (element e_c at bit offset e_c S), by
+    // one transpose of the rows (row r = variable r mod S of element r / S)
+    const int S = P.bs_S, EPW = P.bs_epw, NC = P.bs_nc;
+    const int E = 32 >> lw;
+    uint32_t *tabP = wsm + 96 * SM + 32 * 32 + 32, *tabO = tabP + 32 * NC * W;
+    const uint32_t fmask = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
+    {
+        const int er = lane / S, ar = lane - er * S; // this lane's row: element er of the chunk, variable ar
+        for (int c = 0; c < NC; ++c) {
+            const int e3 = c * EPW + er;
+            const bool row = er < EPW && e3 < E;
+            for (int w2 = 0; w2 < Wv; ++w2) {
+                const int at = (e3 * W + w2) * SM + ar;
+                const uint32_t tp = transpose32(row ? sP[at] : 0u);
+                const uint32_t to = transpose32(row ? sO[at] : 0u);
+                tabP[(c * W + w2) * 32 + lane] = tp;
+                tabO[(c * W + w2) * 32 + lane] = to;
+            }
+        }
+    }
     __syncwarp();
 
-    // ---- phase 1: donors, lane = individual, pair after pair
-    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, kv); todo; todo &= todo - 1) {
-        const int k2 = __ffs(todo) - 1;
-        const int e2 = k2 >> lw, w2 = k2 & (W - 1);
-        const int s2 = __shfl_sync(0xFFFFFFFFu, s, k2);
+    // ---- phase 1: donors, lane = individual, word after word and chunk
+    // after chunk; each word's flips of a chunk are packed like the patterns
+    // and turned into flip planes by one transpose
+    for (int w2 = 0; w2 < Wv; ++w2) {
         const int i = 32 * w2 + lane;
-        uint32_t fm = 0;
-        if (i < p) {
-            // the parent's current bits on F_j
-            const uint32_t *ro = sO + k2 * SM;
-            uint32_t xf = 0;
-            for (int a4 = 0; a4 < s2; a4 += 4) {
-                const uint4 r = *reinterpret_cast<const uint4 *>(ro + a4);
-                xf |= ((r.x >> lane) & 1u) << a4;
-                xf |= ((r.y >> lane) & 1u) << (a4 + 1);
-                xf |= ((r.z >> lane) & 1u) << (a4 + 2);
-                xf |= ((r.w >> lane) & 1u) << (a4 + 3);
+        for (int c = 0; c < NC; ++c) {
+            const uint32_t xo = tabO[(c * W + w2) * 32 + lane]; // the parents' current patterns
+            uint32_t fmw = 0;
+            const int e_end = min(E, (c + 1) * EPW);
+            for (int e2 = c * EPW; e2 < e_end && q0 + e2 < q1; ++e2) {
+                const int s2 = __shfl_sync(0xFFFFFFFFu, s, e2 * W); // the element's size
+                const int k2 = e2 * W + w2;
+                const int off = (e2 - c * EPW) * S;
+                if (i < p) {
+                    const uint32_t xf = (xo >> off) & fmask;
+                    uint32_t pd = 0;
+                    const int d = find_donor_packed(tabP, c, off, fmask, sP, sRS + e2 * W, SM, e2, W, Wv, p, s2, xf,
+                                                    sStart[k2 * 32 + lane], i, &pd);
+                    if (d >= 0) fmw |= (pd ^ xf) << off;
+                }
             }
-            uint32_t pd = 0;
-            const int d = find_donor_rows(sP, sRS + e2 * W, SM, e2, W, Wv, p, s2, xf, sStart[k2 * 32 + lane], i, &pd);
-            if (d >= 0) fm = pd ^ xf;
-        }
-        for (int a4 = 0; a4 < s2; a4 += 4) {
-            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, (fm >> a4) & 1u);
-            const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 1)) & 1u);
-            const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 2)) & 1u);
-            const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, (fm >> (a4 + 3)) & 1u);
-            if (lane == 0) *reinterpret_cast<uint4 *>(sD + k2 * SM + a4) = make_uint4(b0, b1, b2, b3);
+            // the flip planes of the chunk's elements in word w2: lane r gets
+            // variable r mod S of element r / S (bit b: individual 32 w2 + b flips it)
+            const uint32_t tf = transpose32(fmw);
+            const int er = lane / S, ar = lane - er * S, e3 = c * EPW + er;
+            if (er < EPW && e3 < E) sD[(e3 * W + w2) * SM + ar] = tf;
         }
     }
     __syncwarp();
@@ -372,6 +341,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         L.n_acc += __popc(acc);
         L.n_imp += __popc(acc & pos);
         L.n_dl += __popc(vm & ~hd);
+        if (P.fi.on && acc) atomicOr(&P.fi.accw[w], acc); // Forced Improvement: who had an accepted step
         if (acc) {
             for (int a = 0; a < s; ++a) {
                 const uint32_t m = myD[a] & acc;
@@ -448,7 +418,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, i
     const VGrid V = whole_grid();
     const unsigned nblk = (unsigned)V.nblk;
     const bool lead = V.blk == 0;
-    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * bs_warp_words(P.bs_sm);
+    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * P.bs_words;
     GomBarrier *bar = P.bar;
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
@@ -479,6 +449,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, i
         bs_finish_generation(P, L, s_f, s_cnt);
         acc_flush(P, s_f, s_cnt);
         if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (P.fi.on && !fi_generation<R>(P, V, &bar->count, nblk, bnext, e, P.order, s_f, s_cnt)) return;
         if (tr) P.trace[4 + 2 * P.k] = global_ns();
         ++g;
     }
@@ -497,15 +468,88 @@ __global__ void __launch_bounds__(kMixThreads, 2) k_mix_bs(GomParams P, int t)
     acc_zero(P, s_f, s_cnt);
     BsLane L;
     bs_lane_zero(L);
-    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * bs_warp_words(P.bs_sm);
+    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * P.bs_words;
     phase_mix_bs<R>(P, whole_grid(), t, P.order[t], P.st->g, wsm, L, s_f);
     bs_finish_generation(P, L, s_f, s_cnt);
     acc_flush(P, s_f, s_cnt);
 }
 
+// Forced Improvement on the per-launch path (one CUDA graph per
+// generation): the elitist update of its start (one block), the start
+// (flags, x_e, the set of individuals in FI), one launch per group, the end.
+__global__ void __launch_bounds__(1024) k_fi_elite(GomParams P)
+{
+    if (P.st->done) return;
+    int64_t best;
+    int arg;
+    block_argmax(P.f, P.p, &best, &arg);
+    if (threadIdx.x == 0) {
+        const bool newel = best > P.st->fe;
+        if (newel) {
+            P.st->fe = best;
+            P.st->argmax = arg;
+            P.st->improved = 1;
+        }
+        P.st->fi_newel = newel ? 1 : 0;
+    }
+}
+
+__global__ void k_fi_start(GomParams P)
+{
+    if (P.st->done) return;
+    fi_start(P, whole_grid(), P.st->fi_newel != 0, P.st->argmax >> 5, P.st->argmax & 31, blockIdx.x == 0);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kMixThreads, 2) k_fi_group(GomParams P, int t)
+{
+    __shared__ long long s_f[1024];
+    __shared__ unsigned long long s_cnt[4];
+    __shared__ uint32_t s_act[32];
+    if (P.st->done) return;
+    if (threadIdx.x < 32) {
+        uint32_t done = 0;
+        if ((int)threadIdx.x < P.W)
+            for (int t2 = 0; t2 < t; ++t2) done |= P.fi.imp[(int64_t)t2 * P.W + threadIdx.x];
+        s_act[threadIdx.x] = (int)threadIdx.x < P.W ? P.fi.act0[threadIdx.x] & ~done : 0u;
+    }
+    acc_zero(P, s_f, s_cnt);
+    BsLane L;
+    bs_lane_zero(L);
+    unsigned cnt[3] = {0, 0, 0};
+    fi_group<R>(P, whole_grid(), t, P.order[t], s_act, L, cnt, s_f);
+    bs_flush(P, L, s_f);
+    fi_count_flush(P, cnt);
+    acc_flush(P, s_f, s_cnt);
+}
+
+__global__ void k_fi_finish(GomParams P)
+{
+    __shared__ uint32_t s_rep[32];
+    if (P.st->done) return;
+    if (threadIdx.x < 32) {
+        uint32_t done = 0;
+        if ((int)threadIdx.x < P.W)
+            for (int t2 = 0; t2 < P.k; ++t2) done |= P.fi.imp[(int64_t)t2 * P.W + threadIdx.x];
+        s_rep[threadIdx.x] = (int)threadIdx.x < P.W ? P.fi.act0[threadIdx.x] & ~done : 0u;
+    }
+    __syncthreads();
+    fi_finish(P, whole_grid(), s_rep, P.st->fe, blockIdx.x == 0);
+}
+
 } // namespace
 
-int gom_bs_warp_words(int sm) { return bs_warp_words(sm); }
+const void *gom_fi_kernel(int which, int r)
+{
+    switch (which) {
+    case 0: return (const void *)k_fi_elite;
+    case 1: return (const void *)k_fi_start;
+    case 2: return r <= 12 ? (const void *)k_fi_group<12> : (const void *)k_fi_group<16>;
+    default: return (const void *)k_fi_finish;
+    }
+}
+
+int gom_bs_warp_words(int sm, int nc, int w) { return bs_warp_words(sm, nc, w); }
 
 const void *gom_run_bs_kernel(int r)
 {

@@ -39,6 +39,19 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The same generator with the ten round keys precomputed (rk[2r], rk[2r+1]:
+// the key after r bumps), e.g. from the kernel parameters.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint32_t pick(uint4 r, int q)
 {
     return (q & 2) ? ((q & 1) ? r.w : r.z) : ((q & 1) ? r.y : r.x);
@@ -191,6 +204,13 @@ __device__ void phase_gen_start(const GomParams &P, const VGrid &V, int improved
     uint32_t *eqw = P.eqw + (g & 1) * W;
     if (tid < W) P.eqw[((g + 1) & 1) * W + tid] = kFull;
     for (int64_t t = tid; t < P.k; t += nth) P.work[t] = 0;
+    if (P.fi.on) { // Forced Improvement: the generation's accepted steps, FI's elitist flags, the fitness at its start
+        if (tid < W) {
+            P.fi.accw[tid] = 0;
+            P.fi.eq[tid] = kFull;
+        }
+        for (int64_t i = tid; i < 32 * W; i += nth) P.fi.f0[i] = P.f[i];
+    }
     if (P.learn) { // the learned filter's history and skip marks of generation g, and its counters
         uint32_t *cur = P.flt.hist + (size_t)(g & 1) * 3 * (size_t)P.m;
         for (int64_t x = tid; x < 3 * (int64_t)P.m; x += nth) cur[x] = 0;
@@ -330,7 +350,13 @@ __device__ bool phase_gen_end(const GomParams &P, int64_t target, uint32_t g, Ge
         S.accepted = st->cnt[1];
         S.improving = st->cnt[2];
         S.reached = reached;
+        S.fi_individuals = st->fi_cnt[0];
+        S.fi_trials = st->fi_cnt[1];
+        S.fi_accepted = st->fi_cnt[2];
+        S.fi_improving = st->fi_cnt[3];
+        S.fi_replaced = st->fi_cnt[4];
         st->cnt[0] = st->cnt[1] = st->cnt[2] = st->cnt[3] = 0;
+        st->fi_cnt[0] = st->fi_cnt[1] = st->fi_cnt[2] = st->fi_cnt[3] = st->fi_cnt[4] = 0;
         st->done = reached;
         st->g = g + 1;
         if (P.learn) filter_generation_end(P, g);

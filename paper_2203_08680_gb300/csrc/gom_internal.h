@@ -87,6 +87,10 @@ struct GomDevState {
     int32_t err;       // device-side error word (0 = none)
     uint32_t call_g0;  // generation counter at the start of the current call
     int64_t cnt[4];    // counters of the running generation: donorless, accepted, improving, trials skipped
+    int64_t fi_cnt[5]; // Forced Improvement counters of the running generation: individuals, trials,
+                       //   accepted, improving, replaced
+    int32_t fi_newel;  // per-launch path: the elitist changed at the start of FI
+    int32_t pad_;
 };
 
 struct GomBarrier { // grid barrier of the persistent kernel: monotonic arrival count
@@ -144,6 +148,20 @@ struct GomFilter {
 
 struct GomDevStats { // mirrors gom_gen_stats_t
     int64_t generation, best, elite, trials, donorless, accepted, improving, reached;
+    int64_t fi_individuals, fi_trials, fi_accepted, fi_improving, fi_replaced;
+};
+
+// Forced Improvement (Sec. 4, Alg. 1) after each generation's mixing, in the
+// parallel reading of the library (gom_fi.cuh); arrays in the workspace.
+struct GomFI {
+    int32_t on;        // 1: FI after each generation's mixing
+    int32_t nis;       // also individuals not improved for nis generations (0: that condition off)
+    uint32_t *accw;    // [W] individuals with an accepted GOM step in the generation
+    uint32_t *eq;      // [W] individuals equal to the elitist at the start of FI
+    uint32_t *act0;    // [W] individuals in FI
+    uint32_t *imp;     // [k][W] individuals FI improved in the group at position t
+    int32_t *stale;    // [32W] generations in a row without improvement
+    int64_t *f0;       // [32W] fitness at generation start
 };
 
 constexpr int kStatsCap = 1024;    // per-generation counters kept on the device
@@ -178,10 +196,16 @@ struct GomParams {
     int32_t xw_words;   // block mode: words of one warp's region of outside neighbours' words, the
                         //   regions of warps 0, 1, ... following each other from off_xw
     int32_t learn;      // learned filter: 0 off, 1 history and training log, 2 also skip elements
+    GomFI fi;
     int32_t bs_sm;      // bit-sliced path: words per staged row block of one pair (>= the largest
                         //   element, a multiple of 4)
+    int32_t bs_S;       //   field width of one element in a packed pattern (the largest element)
+    int32_t bs_epw;     //   elements per packed pattern word (32 / bs_S)
+    int32_t bs_nc;      //   packed words per individual for one item (ceil(E / bs_epw), E = 32 / W)
+    int32_t bs_words;   //   shared-memory words of one warp's region
     GomFilter flt;
     uint64_t seed;
+    uint32_t rk[20];   // Philox round keys of the seed: rk[2r], rk[2r+1] = the key after r bumps
     uint32_t *O;       // [n][W] offspring, bit-sliced: bit b of O[v][w] = x_v of 32w+b
     uint32_t *P;       // [n][W] generation-start population
     int64_t *f;        // [32W] fitness

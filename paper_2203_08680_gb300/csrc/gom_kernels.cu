@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "gom_device.cuh"
+#include "gom_fi.cuh"
 #include "gom_internal.h"
 #include "gom_kernels.cuh"
 
@@ -742,6 +743,13 @@ __device__ __forceinline__ unsigned run_item(const GomParams &P, uint32_t *sl, u
             }
             if (i < p && donor[r] < 0) ++n_dl;
         }
+        if (P.fi.on) { // Forced Improvement: the individuals with an accepted step in the generation
+#pragma unroll
+            for (int r = 0; r < WPI; ++r) {
+                const uint32_t mk = __ballot_sync(kFull, afm[r] != (MaskT)0);
+                if (lane == 0 && mk) atomicOr(&P.fi.accw[w0 + r], mk);
+            }
+        }
         if (__any_sync(kFull, anyacc)) {
             uint32_t mine[NQ][WPI]; // lane l: accepted flips of variables l, l + 32, ...
 #pragma unroll
@@ -1038,6 +1046,8 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
         count_flush(S.cnt, n_dl, n_acc, n_imp);
         acc_flush(P, S.f, S.cnt);
         if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (P.fi.on && !fi_generation<16>(P, V, &bar->count, nblk, bnext, e, all ? S.order : P.order, S.f, S.cnt))
+            return;
         if (tr) P.trace[4 + 2 * P.k] = global_ns();
         ++g;
     }

@@ -27,10 +27,15 @@ const void *gom_run_kernel(int wpi, int variant, bool learn);
 // k_run_bs<R>(GomParams, int G, int64_t target) and the per-group mixing
 // kernel k_mix_bs<R>(GomParams, int t) for bit-plane accumulators of R bits
 // (12 or 16; null beyond), and the shared-memory words of one warp's region
-// for staged row blocks of `sm` words.
+// for staged row blocks of `sm` words, `nc` packed pattern words per
+// individual and `w` population words per variable row.
 const void *gom_run_bs_kernel(int r);
 const void *gom_mix_bs_kernel(int r);
-int gom_bs_warp_words(int sm);
+int gom_bs_warp_words(int sm, int nc, int w);
+// Forced Improvement on the per-launch path: which = 0 k_fi_elite(GomParams)
+// (one block of 1024), 1 k_fi_start(GomParams), 2 k_fi_group<R>(GomParams,
+// int t) (256 threads), 3 k_fi_finish(GomParams).
+const void *gom_fi_kernel(int which, int r);
 // Batched path: instances on block ranges of one cooperative launch.
 // k_batch<MINB>(const GomParams *Ps, const GomBatchInst *inst, GomBarrier *bars, int B, int G, int f_words),
 // registers cut for MINB (2 or 3) resident blocks of 256 threads.

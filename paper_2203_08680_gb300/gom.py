@@ -46,7 +46,8 @@ class GraphT(C.Structure):
 class GenStats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("generation", "best_fitness", "elite_fitness", "trials", "donorless", "accepted",
-                 "improving", "reached_target")]
+                 "improving", "reached_target", "fi_individuals", "fi_trials", "fi_accepted", "fi_improving",
+                 "fi_replaced")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
