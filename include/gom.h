@@ -92,6 +92,24 @@ extern "C" {
                                fill the GPU (GOM_E_STATE when set to 1 where unavailable).  Same
                                results either way.  Not used while the learned filter is on */
 
+#define GOM_OPT_FORCED_IMPROVEMENT 5 /* 1: Forced Improvement (Sec. 4, Alg. 1) after each generation's
+                                        mixing, in this library's parallel reading (the paper's
+                                        parallel GOMEA runs without it, Sec. 5.4): the elitist is
+                                        first updated from the population; every individual without
+                                        an accepted GOM step in the generation (see GOM_OPT_FI_NIS)
+                                        then takes GOM steps with the elitist as donor on the
+                                        elements of each colour group, groups in the generation's
+                                        order, accepted as in Alg. 2 with "equal to the elitist"
+                                        taken at the start of FI; it leaves FI after the first group
+                                        in which a step improved its fitness, and one that no step
+                                        improved becomes a copy of the elitist.  0 (default): off.
+                                        GOM_E_LIMIT where |w| > 255 or an element's sum of |w| over
+                                        its edges reaches 2^16; not available in batched launches */
+
+#define GOM_OPT_FI_NIS 6 /* Forced Improvement also for individuals whose fitness has not improved
+                            for this many generations, the current one included (0, the default:
+                            only individuals without an accepted step) */
+
 /* Supported maxima of the library. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 128     /* variables in one FOS element (the paper's largest

@@ -31,6 +31,7 @@ int words_for(int32_t p)
 // Byte offsets of every device array inside the workspace.
 struct Layout {
     size_t O, P, f, eqw, xe, st, bar, trace, stats, order, work;
+    size_t fi_accw, fi_eq, fi_act0, fi_imp, fi_stale, fi_f0;
     size_t row_ptr, col, wgt, hdr, fv, wout, wabs, seg, dep, cptr;
     size_t total;
 };
@@ -57,6 +58,12 @@ Layout make_layout(int64_t n, int32_t p, int64_t nadj, int64_t m, int64_t total_
     L.stats = take(sizeof(GomDevStats) * kStatsCap);
     L.order = take(sizeof(int32_t) * std::max<int32_t>(k, 1));
     L.work = take(sizeof(uint32_t) * std::max<int32_t>(k, 1));
+    L.fi_accw = take(sizeof(uint32_t) * W);
+    L.fi_eq = take(sizeof(uint32_t) * W);
+    L.fi_act0 = take(sizeof(uint32_t) * W);
+    L.fi_imp = take(sizeof(uint32_t) * W * std::max<int32_t>(k, 1));
+    L.fi_stale = take(sizeof(int32_t) * 32 * W);
+    L.fi_f0 = take(sizeof(int64_t) * 32 * W);
     L.row_ptr = take(sizeof(int64_t) * (n + 1));
     L.col = take(sizeof(int32_t) * nadj);
     L.wgt = take(sizeof(int32_t) * nadj);
@@ -129,6 +136,25 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         if (e == cudaSuccess && timed) {
             last = node;
             e = cudaGraphAddEventRecordNode(&node, g, &last, 1, ctx->events[2 * t + 1]);
+        }
+    }
+    std::vector<int> fts(ctx->prm.fi.on ? ctx->k : 0);
+    if (e == cudaSuccess && ctx->prm.fi.on) { // Forced Improvement after the mixing
+        last = node;
+        e = add_kernel(g, &node, last, gom_fi_kernel(0, ctx->fi_r), 1, 1024, 0, args1);
+        if (e == cudaSuccess) {
+            last = node;
+            e = add_kernel(g, &node, last, gom_fi_kernel(1, ctx->fi_r), ctx->grid_start, 256, 0, args1);
+        }
+        for (int t = 0; t < ctx->k && e == cudaSuccess; ++t) {
+            last = node;
+            fts[t] = t;
+            void *args3[] = {&prm, &fts[t]};
+            e = add_kernel(g, &node, last, gom_fi_kernel(2, ctx->fi_r), ctx->fi_grid, 256, 0, args3);
+        }
+        if (e == cudaSuccess) {
+            last = node;
+            e = add_kernel(g, &node, last, gom_fi_kernel(3, ctx->fi_r), ctx->grid_start, 256, 0, args1);
         }
     }
     if (e == cudaSuccess) {
@@ -463,9 +489,17 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     // the bit-sliced path: elements of <= 32 variables, |w| <= 255, element
     // sums of |w| below 2^16 (R-bit plane accumulators, R = 12 or 16); an item
     // is E = 32 / W elements, one pair (element, word) per lane
+    int64_t max_w = 0;
+    for (int64_t x = 0; x < g->num_adj; ++x) max_w = std::max<int64_t>(max_w, std::llabs(g->weight[x]));
+    // Forced Improvement works on bit-planes too: |w| <= 255 and element sums of |w| below 2^16
+    c->fi_ok = max_w <= 255 && tabs.max_abs_w < (int64_t(1) << 16);
+    c->fi_r = tabs.max_abs_w < (int64_t(1) << 12) ? 12 : 16;
+    if (c->fi_ok) {
+        int occ_f = 0;
+        GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, gom_fi_kernel(2, c->fi_r), 256, 0));
+        c->fi_grid = std::max(1, c->sms * std::max(occ_f, 1));
+    }
     {
-        int64_t max_w = 0;
-        for (int64_t x = 0; x < g->num_adj; ++x) max_w = std::max<int64_t>(max_w, std::llabs(g->weight[x]));
         const int R = tabs.max_abs_w < (int64_t(1) << 12) ? 12 : 16;
         if (coop && variant == kVarNarrow && max_w <= 255 && tabs.max_abs_w < (int64_t(1) << 16)) {
             const int sm = static_cast<int>((std::max<int64_t>(tabs.max_s, 1) + 3) & ~int64_t(3));
@@ -557,6 +591,14 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     P.stats = reinterpret_cast<GomDevStats *>(base + L.stats);
     P.order = reinterpret_cast<int32_t *>(base + L.order);
     P.work = reinterpret_cast<uint32_t *>(base + L.work);
+    P.fi.on = 0;
+    P.fi.nis = 0;
+    P.fi.accw = reinterpret_cast<uint32_t *>(base + L.fi_accw);
+    P.fi.eq = reinterpret_cast<uint32_t *>(base + L.fi_eq);
+    P.fi.act0 = reinterpret_cast<uint32_t *>(base + L.fi_act0);
+    P.fi.imp = reinterpret_cast<uint32_t *>(base + L.fi_imp);
+    P.fi.stale = reinterpret_cast<int32_t *>(base + L.fi_stale);
+    P.fi.f0 = reinterpret_cast<int64_t *>(base + L.fi_f0);
     P.row_ptr = reinterpret_cast<const int64_t *>(base + L.row_ptr);
     P.col = reinterpret_cast<const int32_t *>(base + L.col);
     P.wgt = reinterpret_cast<const int32_t *>(base + L.wgt);
@@ -755,7 +797,9 @@ int gom_read_timing(gom_ctx_t *ctx, double *mix_ms, int64_t *mix_launches)
 int gom_launches_per_generation(gom_ctx_t *ctx, int64_t *launches)
 {
     if (!ctx || !launches) return GOM_E_ARG;
-    *launches = (ctx->persistent && !ctx->timing) ? 1 : 3 + static_cast<int64_t>(ctx->k);
+    *launches = (ctx->persistent && !ctx->timing)
+                    ? 1
+                    : 3 + static_cast<int64_t>(ctx->k) + (ctx->prm.fi.on ? 3 + static_cast<int64_t>(ctx->k) : 0);
     return GOM_OK;
 }
 
@@ -784,6 +828,20 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
         ctx->bs_on = value != 0;
         return rebuild_graphs(ctx); // the graphs hold the mixing kernel
     }
+    if (option == GOM_OPT_FORCED_IMPROVEMENT) {
+        if (value != 0 && value != 1) return GOM_E_ARG;
+        if (value && !ctx->fi_ok) return GOM_E_LIMIT;
+        if (ctx->prm.fi.on == value) return GOM_OK;
+        if (value) // no generation without improvement counted yet
+            GOM_CUDA(ctx, cudaMemsetAsync(ctx->prm.fi.stale, 0, sizeof(int32_t) * 32 * ctx->W, ctx->stream));
+        ctx->prm.fi.on = static_cast<int32_t>(value);
+        return rebuild_graphs(ctx); // the graphs hold the parameters and the FI nodes
+    }
+    if (option == GOM_OPT_FI_NIS) {
+        if (value < 0 || value > INT32_MAX) return GOM_E_ARG;
+        ctx->prm.fi.nis = static_cast<int32_t>(value);
+        return rebuild_graphs(ctx);
+    }
     return GOM_E_ARG;
 }
 
@@ -804,6 +862,14 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
     }
     if (option == GOM_OPT_BITSLICED) {
         *value = ctx->bs_on ? 1 : 0;
+        return GOM_OK;
+    }
+    if (option == GOM_OPT_FORCED_IMPROVEMENT) {
+        *value = ctx->prm.fi.on;
+        return GOM_OK;
+    }
+    if (option == GOM_OPT_FI_NIS) {
+        *value = ctx->prm.fi.nis;
         return GOM_OK;
     }
     return GOM_E_ARG;

@@ -52,6 +52,9 @@ namespace {
 // entry (r, c)) on entry and column r (bit c = entry (c, r)) on return.  Five
 // steps; step j swaps the off-diagonal j x j blocks of each 2j x 2j block
 // between lanes l and l ^ j.
+// Branch-free: the lane keeps its own half of each block (mask `keep`) and
+// takes the partner's other half rotated into place (left by j for the lower
+// lane of a pair, right by j for the upper one).
 __device__ __forceinline__ uint32_t transpose32(uint32_t x)
 {
     const int lane = threadIdx.x & 31;
@@ -59,11 +62,11 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x)
     for (int j = 16; j; j >>= 1) {
         const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u
                                                                                                   : 0x55555555u;
+        const uint32_t up = 0u - (uint32_t)((lane >> (31 - __clz(j))) & 1); // all ones in the upper lane
+        const uint32_t keep = m ^ up;
         const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-        if (lane & j)
-            x = (x & ~m) | ((y >> j) & m);
-        else
-            x = (x & m) | ((y << j) & ~m);
+        const uint32_t ys = __funnelshift_l(y, y, up ? 32 - j : j);
+        x = (x & keep) | (ys & ~keep);
     }
     return x;
 }

@@ -30,6 +30,10 @@ struct gom_ctx {
     size_t bs_smem = 0;           // dynamic shared memory of both (warp regions, group keys)
     int bs_threads = 0;           // their block size
     int bs_grid_run = 0, bs_grid_mix = 0;
+    // Forced Improvement (GOM_OPT_FORCED_IMPROVEMENT)
+    bool fi_ok = false;           // available: |w| <= 255, element sums of |w| below 2^16
+    int fi_r = 16;                // bit-plane width of its accumulators
+    int fi_grid = 0;              // grid of its per-group kernel on the per-launch path
     unsigned long long *trace_buf = nullptr; // workspace slot of the phase trace
     size_t order_smem = 0;
     cudaGraph_t graph = nullptr;

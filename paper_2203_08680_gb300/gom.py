@@ -25,6 +25,8 @@ GOM_OPT_PERSISTENT = 1
 GOM_OPT_PHASE_TRACE = 2
 GOM_OPT_DYNAMIC = 3
 GOM_OPT_BITSLICED = 4
+GOM_OPT_FORCED_IMPROVEMENT = 5
+GOM_OPT_FI_NIS = 6
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",
@@ -605,7 +607,7 @@ class Population:
 
     def __init__(self, graph, pop: int, seed: int, kind: int = GOM_FOS_NEIGHBOURHOOD, fos: Fos = None,
                  stream=None, device=None, persistent: bool = None, dynamic: bool = None,
-                 bitsliced: bool = None):
+                 bitsliced: bool = None, forced_improvement: bool = None, fi_nis: int = None):
         import torch
         self.torch = torch
         self.graph = _graph(graph)
@@ -635,6 +637,10 @@ class Population:
             gom_set_option(self.ctx, GOM_OPT_DYNAMIC, 1 if dynamic else 0)
         if bitsliced is not None:
             gom_set_option(self.ctx, GOM_OPT_BITSLICED, 1 if bitsliced else 0)
+        if fi_nis is not None:
+            gom_set_option(self.ctx, GOM_OPT_FI_NIS, fi_nis)
+        if forced_improvement is not None:
+            gom_set_option(self.ctx, GOM_OPT_FORCED_IMPROVEMENT, 1 if forced_improvement else 0)
 
     def generation(self, num: int = 1, target: int = INT64_MAX, want_stats: bool = True):
         return gom_generation(self.ctx, num, target, want_stats)
