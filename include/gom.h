@@ -492,6 +492,39 @@ int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float 
 
 int gom_filter_stats(gom_ctx_t *ctx, gom_filter_stats_t *out);
 
+/* ---- Inspection and stepwise training of the filter's MLP.
+ * Parameters, as one fp32 vector theta of GOM_FILTER_PARAMS values: W1 [64][16]
+ * (unit h, feature k at 16 h + k), b1 [64], W2 [64], b2 [1], in that order.
+ * The mixing kernels and the logits read W1 and W2 rounded to bf16. */
+#define GOM_FILTER_PARAMS 1153
+
+/* Copies theta, the Adam moments and the gradient of the last training step
+ * (each GOM_FILTER_PARAMS floats, host; any may be NULL).  Waits. */
+int gom_filter_get_params(gom_ctx_t *ctx, float *theta, float *adam_m, float *adam_v, float *grad);
+
+/* Sets theta (and the Adam moments; NULL = zero) from host arrays, and the
+ * bf16 copies of W1 and W2 the kernels read.  Waits. */
+int gom_filter_set_params(gom_ctx_t *ctx, const float *theta, const float *adam_m, const float *adam_v);
+
+/* One training step on the logged samples: the full-batch gradient of the
+ * mean weighted logistic loss (the forward pass with bf16-rounded W1 and
+ * W2, fp32 sums; positive samples weighted pos_weight), then one Adam step
+ * (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias correction of
+ * step `step` >= 1, learning rate lr).  *loss (may be NULL) receives the mean
+ * loss at the parameters before the step.  GOM_E_STATE with an empty log.
+ * Waits. */
+int gom_filter_epoch(gom_ctx_t *ctx, float learning_rate, float pos_weight, int32_t step, double *loss);
+
+/* The training log: *n = samples held (the latest min(offered, capacity));
+ * copies the first min(*n, max) of them, features as bf16 bits [.][16] (x) and
+ * labels [.] (y), into host arrays (either may be NULL).  Waits. */
+int gom_filter_log(gom_ctx_t *ctx, int64_t max, uint16_t *x, uint8_t *y, int64_t *n);
+
+/* Logits of the first n logged samples with the current parameters, as the
+ * mixing kernels compute them (bf16 W1 and W2, fp32 sums: two units per lane,
+ * a fixed-order warp sum), into host logits[n].  Waits. */
+int gom_filter_logits(gom_ctx_t *ctx, int64_t n, float *logits);
+
 /* The elements skipped in the last generation: host_mask[j] = 1 (host, [m]). */
 int gom_filter_skipped(gom_ctx_t *ctx, uint8_t *host_mask);
 

@@ -560,6 +560,8 @@ typedef struct {
     uint8_t *acc_any;/* [p] an accepted GOM step in this generation */
     int32_t *nis;    /* [p] generations in a row without improvement */
     int64_t *f_start;/* [p] fitness at generation start */
+    int32_t *ecnt;   /* [3][m] per element: accepted, donor-less and improving trials of the last
+                        generation (NULL: not kept; single-threaded generations only) */
     int64_t max_s;   /* largest element */
     orc_scratch sc;  /* scratch of the single-threaded path */
 } orc_state;
@@ -676,6 +678,7 @@ void orc_free(orc_state *s)
     free(s->acc_any);
     free(s->nis);
     free(s->f_start);
+    free(s->ecnt);
     scratch_free(&s->sc);
     free(s);
 }
@@ -747,7 +750,11 @@ static void gom_trial(orc_state *s, orc_scratch *sc, int32_t i, int32_t j, orc_s
             if (pd[F[q]] != o[F[q]]) { donor = d; break; }
     }
     st->trials++;
-    if (donor < 0) { st->donorless++; return; }
+    if (donor < 0) {
+        st->donorless++;
+        if (s->ecnt) s->ecnt[s->m + j]++;
+        return;
+    }
 
     /* PartialEvaluation, R7 */
     const uint8_t *pd = s->P + (size_t)donor * n;
@@ -767,7 +774,28 @@ static void gom_trial(orc_state *s, orc_scratch *sc, int32_t i, int32_t j, orc_s
         st->accepted++;
         if (d > 0) st->improving++;
         s->acc_any[i] = 1;
+        if (s->ecnt) {
+            s->ecnt[j]++;
+            if (d > 0) s->ecnt[2 * s->m + j]++;
+        }
     }
+}
+
+/* Keeps (on != 0) or stops keeping the per-element counters of each
+ * generation: accepted, donor-less and improving trials of element j. */
+void orc_keep_element_counts(orc_state *s, int32_t on)
+{
+    free(s->ecnt);
+    s->ecnt = on ? (int32_t *)calloc(3 * (size_t)(s->m > 0 ? s->m : 1), sizeof(int32_t)) : NULL;
+}
+
+/* The per-element counters of the last generation (each [m], may be NULL). */
+void orc_element_counts(const orc_state *s, int32_t *acc, int32_t *dl, int32_t *imp)
+{
+    if (!s->ecnt) return;
+    if (acc) memcpy(acc, s->ecnt, sizeof(int32_t) * (size_t)s->m);
+    if (dl) memcpy(dl, s->ecnt + s->m, sizeof(int32_t) * (size_t)s->m);
+    if (imp) memcpy(imp, s->ecnt + 2 * s->m, sizeof(int32_t) * (size_t)s->m);
 }
 
 /* R12: switches Forced Improvement on or off, with its no-improvement
@@ -866,6 +894,7 @@ static void generation_start(orc_state *s)
     for (int32_t i = 0; i < p; ++i) s->eq[i] = memcmp(s->P + (size_t)i * n, s->xe, (size_t)n) == 0;
     memset(s->acc_any, 0, (size_t)p);
     memcpy(s->f_start, s->f, sizeof(int64_t) * (size_t)p);
+    if (s->ecnt) memset(s->ecnt, 0, sizeof(int32_t) * 3 * (size_t)s->m);
 }
 
 /* Generation end: R9 elitist update, the target check, g += 1. */
@@ -984,6 +1013,7 @@ int32_t orc_generation_par_ex(orc_state *s, int64_t target, int32_t threads, con
                               orc_stats *st)
 {
     memset(st, 0, sizeof(*st));
+    if (s->ecnt) return -1; /* per-element counters: single-threaded generations only */
     const int32_t p = only ? n_only : s->p;
     if (threads < 1) threads = 1;
     generation_start(s);

@@ -80,6 +80,8 @@ def lib():
         L.orc_generation_par_ex.argtypes = [P, i64, i32, P, i32, P]
         L.orc_generation_par_ex.restype = i32
         L.orc_set_fi.argtypes = [P, i32, i32]
+        L.orc_keep_element_counts.argtypes = [P, i32]
+        L.orc_element_counts.argtypes = [P, P, P, P]
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = i32
         _lib = L
@@ -242,6 +244,16 @@ class Run:
             o = np.ascontiguousarray(only, dtype=np.int32)
             lib().orc_generation_ex(self._h, target, shuffle, _p(o), len(o), C.byref(st))
         return st.as_dict()
+
+    def keep_element_counts(self, on: bool = True):
+        """Per-element counters of each generation (single-threaded generations only)."""
+        lib().orc_keep_element_counts(self._h, 1 if on else 0)
+
+    def element_counts(self):
+        """Accepted, donor-less and improving trials per element of the last generation."""
+        out = [np.zeros(max(self.m, 1), dtype=np.int32) for _ in range(3)]
+        lib().orc_element_counts(self._h, *(_p(a) for a in out))
+        return tuple(a[: self.m] for a in out)
 
     def set_fi(self, on: bool, nis: int = 0):
         """Forced Improvement after each generation's mixing (reading R12)."""

@@ -48,27 +48,30 @@
 
 namespace {
 
-// 32 x 32 bit-matrix transpose across the warp: lane r holds row r (bit c =
-// entry (r, c)) on entry and column r (bit c = entry (c, r)) on return.  Five
-// steps; step j swaps the off-diagonal j x j blocks of each 2j x 2j block
-// between lanes l and l ^ j.
-// Branch-free: the lane keeps its own half of each block (mask `keep`) and
-// takes the partner's other half rotated into place (left by j for the lower
-// lane of a pair, right by j for the upper one).
-__device__ __forceinline__ uint32_t transpose32(uint32_t x)
+// Four independent 32 x 32 bit-matrix transposes across the warp, interleaved
+// step by step (their shuffles and logic overlap instead of waiting on one
+// another): lane r holds row r of each matrix (bit c = entry (r, c)) on entry
+// and column r (bit c = entry (c, r)) on return.  Five steps; step j swaps
+// the off-diagonal j x j blocks of each 2j x 2j block between lanes l and
+// l ^ j, branch-free: a lane keeps its own half of each block (mask `keep`)
+// and takes the partner's other half rotated into place (left by j for the
+// lower lane of a pair, right by j for the upper one).
+__device__ __forceinline__ void transpose32x4(uint32_t (&x)[4])
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 16; j; j >>= 1) {
         const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu : j == 2 ? 0x33333333u
                                                                                                   : 0x55555555u;
-        const uint32_t up = 0u - (uint32_t)((lane >> (31 - __clz(j))) & 1); // all ones in the upper lane
+        const uint32_t up = 0u - (uint32_t)((lane >> (31 - __clz(j))) & 1);
         const uint32_t keep = m ^ up;
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-        const uint32_t ys = __funnelshift_l(y, y, up ? 32 - j : j);
-        x = (x & keep) | (ys & ~keep);
+        const int sh = up ? 32 - j : j;
+        uint32_t y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = __shfl_xor_sync(0xFFFFFFFFu, x[q], j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = (x[q] & keep) | (__funnelshift_l(y[q], y[q], sh) & ~keep);
     }
-    return x;
 }
 
 // The pattern (bits on F_j) of individual d from a packed table: tab[(c W +
@@ -151,8 +154,12 @@ __device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t 
 // Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4;
 // NC chunks of packed patterns): rows of O on F_j [32 pairs][SM], rows of P
 // [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals], run
-// starts [32 pairs], packed patterns of P and of O [NC][W][32] each.
-__host__ __device__ __forceinline__ int bs_warp_words(int SM, int NC, int W) { return 96 * SM + 32 * 32 + 32 + 64 * NC * W; }
+// starts [32 pairs], packed patterns of P and of O and packed flips
+// [NC][W][32] each, the item's element sizes [32].
+__host__ __device__ __forceinline__ int bs_warp_words(int SM, int NC, int W)
+{
+    return 96 * SM + 32 * 32 + 32 + 96 * NC * W + 32;
+}
 
 // One item of colour group c at position t: elements [q0, q1) (at most E)
 // with every word, all trials of Alg. 2.
@@ -235,53 +242,90 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     // packed patterns: for chunk c (elements c EPW .. c EPW + EPW - 1 of the
     // item) and word w2, lane b receives the bits of individual 32 w2 + b on
     // the chunk's elements side by side (element e_c at bit offset e_c S), by
-    // one transpose of the rows (row r = variable r mod S of element r / S)
+    // one transpose of the rows (row r = variable r mod S of element r / S);
+    // four words at a time, interleaved
     const int S = P.bs_S, EPW = P.bs_epw, NC = P.bs_nc;
     const int E = 32 >> lw;
-    uint32_t *tabP = wsm + 96 * SM + 32 * 32 + 32, *tabO = tabP + 32 * NC * W;
+    uint32_t *tabP = wsm + 96 * SM + 32 * 32 + 32, *tabO = tabP + 32 * NC * W, *sFM = tabO + 32 * NC * W;
+    int *sS = reinterpret_cast<int *>(sFM + 32 * NC * W);
     const uint32_t fmask = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
-    {
-        const int er = lane / S, ar = lane - er * S; // this lane's row: element er of the chunk, variable ar
-        for (int c = 0; c < NC; ++c) {
-            const int e3 = c * EPW + er;
-            const bool row = er < EPW && e3 < E;
-            for (int w2 = 0; w2 < Wv; ++w2) {
-                const int at = (e3 * W + w2) * SM + ar;
-                const uint32_t tp = transpose32(row ? sP[at] : 0u);
-                const uint32_t to = transpose32(row ? sO[at] : 0u);
-                tabP[(c * W + w2) * 32 + lane] = tp;
-                tabO[(c * W + w2) * 32 + lane] = to;
+    if (w == 0) sS[e] = s; // the item's element sizes, by slot
+    const int er = lane / S, ar = lane - er * S; // this lane's row in a transpose: element er of a chunk, variable ar
+    for (int c = 0; c < NC; ++c) {
+        const int e3 = c * EPW + er;
+        const bool row = er < EPW && e3 < E;
+        for (int w2 = 0; w2 < Wv; w2 += 4) {
+            uint32_t tp[4], to[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int at = (e3 * W + w2 + j) * SM + ar;
+                const bool ok = row && w2 + j < Wv;
+                tp[j] = ok ? sP[at] : 0u;
+                to[j] = ok ? sO[at] : 0u;
             }
+            transpose32x4(tp);
+            transpose32x4(to);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (w2 + j < Wv) {
+                    tabP[(c * W + w2 + j) * 32 + lane] = tp[j];
+                    tabO[(c * W + w2 + j) * 32 + lane] = to[j];
+                }
         }
     }
     __syncwarp();
 
-    // ---- phase 1: donors, lane = individual, word after word and chunk
-    // after chunk; each word's flips of a chunk are packed like the patterns
-    // and turned into flip planes by one transpose
+    // ---- phase 1: donors, lane = individual.  Pass A checks every pair's
+    // first candidate (straight-line: one table lookup each); pass B
+    // continues the search for the individuals whose first candidate equals
+    // them on F_j (run starts, then the word-parallel scan).  Each word's
+    // flips of a chunk are packed like the patterns into sFM.
     for (int w2 = 0; w2 < Wv; ++w2) {
         const int i = 32 * w2 + lane;
+        const bool vi = i < p;
         for (int c = 0; c < NC; ++c) {
             const uint32_t xo = tabO[(c * W + w2) * 32 + lane]; // the parents' current patterns
-            uint32_t fmw = 0;
-            const int e_end = min(E, (c + 1) * EPW);
-            for (int e2 = c * EPW; e2 < e_end && q0 + e2 < q1; ++e2) {
-                const int s2 = __shfl_sync(0xFFFFFFFFu, s, e2 * W); // the element's size
-                const int k2 = e2 * W + w2;
-                const int off = (e2 - c * EPW) * S;
-                if (i < p) {
-                    const uint32_t xf = (xo >> off) & fmask;
-                    uint32_t pd = 0;
-                    const int d = find_donor_packed(tabP, c, off, fmask, sP, sRS + e2 * W, SM, e2, W, Wv, p, s2, xf,
-                                                    sStart[k2 * 32 + lane], i, &pd);
-                    if (d >= 0) fmw |= (pd ^ xf) << off;
-                }
+            const int ne = min(EPW, min(E, q1 - q0) - c * EPW); // elements of this chunk in the item
+            uint32_t fmw = 0, fails = 0;
+#pragma unroll 4
+            for (int el = 0; el < ne; ++el) {
+                const int off = el * S, e2 = c * EPW + el;
+                const uint32_t xf = (xo >> off) & fmask;
+                // starts exist for individuals < p only (others read candidate 0, and are dropped below)
+                const int st = vi ? sStart[(e2 * W + w2) * 32 + lane] : 0;
+                const uint32_t pd = packed_pattern(tabP, c, W, st, off, fmask);
+                if (pd != xf)
+                    fmw |= (pd ^ xf) << off;
+                else
+                    fails |= 1u << el;
             }
-            // the flip planes of the chunk's elements in word w2: lane r gets
-            // variable r mod S of element r / S (bit b: individual 32 w2 + b flips it)
-            const uint32_t tf = transpose32(fmw);
-            const int er = lane / S, ar = lane - er * S, e3 = c * EPW + er;
-            if (er < EPW && e3 < E) sD[(e3 * W + w2) * SM + ar] = tf;
+            if (!vi) fmw = fails = 0;
+            for (uint32_t f = fails; f; f &= f - 1) { // pass B, divergent
+                const int el = __ffs(f) - 1, off = el * S, e2 = c * EPW + el;
+                const uint32_t xf = (xo >> off) & fmask;
+                uint32_t pd = 0;
+                const int d = find_donor_packed(tabP, c, off, fmask, sP, sRS + e2 * W, SM, e2, W, Wv, p, sS[e2], xf,
+                                                sStart[(e2 * W + w2) * 32 + lane], i, &pd);
+                if (d >= 0) fmw |= (pd ^ xf) << off;
+            }
+            sFM[(c * W + w2) * 32 + lane] = fmw;
+        }
+    }
+    __syncwarp();
+    // the flip planes: lane r of the transpose of a word's packed flips gets
+    // variable r mod S of element r / S of the chunk (bit b: individual 32 w2 + b
+    // flips it); four words at a time
+    for (int c = 0; c < NC; ++c) {
+        const int e3 = c * EPW + er;
+        const bool row = er < EPW && e3 < E;
+        for (int w2 = 0; w2 < Wv; w2 += 4) {
+            uint32_t tf[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tf[j] = w2 + j < Wv ? sFM[(c * W + w2 + j) * 32 + lane] : 0u;
+            transpose32x4(tf);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (row && w2 + j < Wv) sD[(e3 * W + w2 + j) * SM + ar] = tf[j];
         }
     }
     __syncwarp();

@@ -143,6 +143,15 @@ __global__ void k_filter_step(float *theta, float *m, float *v, const float *gra
         w2[i - kNW1 - kFilterHidden] = __bfloat16_as_ushort(__float2bfloat16_rn(theta[i]));
 }
 
+// The bf16 copies of W1 and W2 from the fp32 parameters (round to nearest even).
+__global__ void k_filter_bf16(const float *theta, uint16_t *w1, uint16_t *w2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNW1) w1[i] = __bfloat16_as_ushort(__float2bfloat16_rn(theta[i]));
+    else if (i >= kNW1 + kFilterHidden && i < kNW1 + 2 * kFilterHidden)
+        w2[i - kNW1 - kFilterHidden] = __bfloat16_as_ushort(__float2bfloat16_rn(theta[i]));
+}
+
 // Logit of every logged sample, with the bf16 weights the mixing kernels use
 // and the same summation order (two units per lane, fixed-order warp sum).
 __global__ void k_filter_eval(const uint16_t *X, int64_t N, const uint16_t *w1, const float *theta,
@@ -379,6 +388,109 @@ int gom_filter_stats(gom_ctx_t *ctx, gom_filter_stats_t *out)
         out->last[x] = static_cast<int64_t>(st.last[x]);
         out->total[x] = static_cast<int64_t>(st.total[x]);
     }
+    return GOM_OK;
+}
+
+int gom_filter_get_params(gom_ctx_t *ctx, float *theta, float *adam_m, float *adam_v, float *grad)
+{
+    if (!ctx || !ctx->filter_base) return GOM_E_ARG;
+    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    char *base = ctx->filter_base;
+    const size_t bytes = sizeof(float) * kNTheta;
+    if (theta) GOM_CUDA(ctx, cudaMemcpyAsync(theta, base + L.theta, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (adam_m) GOM_CUDA(ctx, cudaMemcpyAsync(adam_m, base + L.adam_m, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (adam_v) GOM_CUDA(ctx, cudaMemcpyAsync(adam_v, base + L.adam_v, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (grad) GOM_CUDA(ctx, cudaMemcpyAsync(grad, base + L.grad, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GOM_OK;
+}
+
+int gom_filter_set_params(gom_ctx_t *ctx, const float *theta, const float *adam_m, const float *adam_v)
+{
+    if (!ctx || !ctx->filter_base || !theta) return GOM_E_ARG;
+    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    char *base = ctx->filter_base;
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = sizeof(float) * kNTheta;
+    GOM_CUDA(ctx, cudaMemcpyAsync(base + L.theta, theta, bytes, cudaMemcpyHostToDevice, s));
+    if (adam_m) GOM_CUDA(ctx, cudaMemcpyAsync(base + L.adam_m, adam_m, bytes, cudaMemcpyHostToDevice, s));
+    else GOM_CUDA(ctx, cudaMemsetAsync(base + L.adam_m, 0, bytes, s));
+    if (adam_v) GOM_CUDA(ctx, cudaMemcpyAsync(base + L.adam_v, adam_v, bytes, cudaMemcpyHostToDevice, s));
+    else GOM_CUDA(ctx, cudaMemsetAsync(base + L.adam_v, 0, bytes, s));
+    // the bf16 copies of W1 and W2, rounded as the training step writes them
+    k_filter_bf16<<<(kNTheta + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float *>(base + L.theta),
+                                                        reinterpret_cast<uint16_t *>(base + L.w1),
+                                                        reinterpret_cast<uint16_t *>(base + L.w2));
+    GOM_CUDA(ctx, cudaGetLastError());
+    GOM_CUDA(ctx, cudaStreamSynchronize(s));
+    return GOM_OK;
+}
+
+int gom_filter_epoch(gom_ctx_t *ctx, float learning_rate, float pos_weight, int32_t step, double *loss)
+{
+    if (!ctx || !ctx->filter_base || !(learning_rate > 0.f) || !(pos_weight > 0.f) || step < 1) return GOM_E_ARG;
+    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    char *base = ctx->filter_base;
+    cudaStream_t s = ctx->stream;
+    GomFilterState st{};
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.flt.st, sizeof(st), cudaMemcpyDeviceToHost, s));
+    GOM_CUDA(ctx, cudaStreamSynchronize(s));
+    const int64_t N = std::min<int64_t>(static_cast<int64_t>(st.log_count), ctx->filter_cap);
+    if (N < 1) return GOM_E_STATE;
+    float *d_theta = reinterpret_cast<float *>(base + L.theta);
+    float *d_grad = reinterpret_cast<float *>(base + L.grad);
+    double *d_loss = reinterpret_cast<double *>(base + L.loss);
+    const int grid = static_cast<int>(std::min<int64_t>((N + 3) / 4, static_cast<int64_t>(ctx->sms) * 8));
+    GOM_CUDA(ctx, cudaMemsetAsync(d_grad, 0, sizeof(float) * kNTheta, s));
+    GOM_CUDA(ctx, cudaMemsetAsync(d_loss, 0, sizeof(double), s));
+    k_filter_grad<<<grid, 256, 0, s>>>(reinterpret_cast<const uint16_t *>(base + L.log_x),
+                                       reinterpret_cast<const uint8_t *>(base + L.log_y), N, d_theta, pos_weight,
+                                       d_grad, d_loss);
+    k_filter_step<<<(kNTheta + 255) / 256, 256, 0, s>>>(d_theta, reinterpret_cast<float *>(base + L.adam_m),
+                                                        reinterpret_cast<float *>(base + L.adam_v), d_grad,
+                                                        1.f / static_cast<float>(N), learning_rate, step,
+                                                        reinterpret_cast<uint16_t *>(base + L.w1),
+                                                        reinterpret_cast<uint16_t *>(base + L.w2));
+    GOM_CUDA(ctx, cudaGetLastError());
+    double l = 0.0;
+    GOM_CUDA(ctx, cudaMemcpyAsync(&l, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GOM_CUDA(ctx, cudaStreamSynchronize(s));
+    if (loss) *loss = l / static_cast<double>(N);
+    return GOM_OK;
+}
+
+int gom_filter_log(gom_ctx_t *ctx, int64_t max, uint16_t *x, uint8_t *y, int64_t *n)
+{
+    if (!ctx || !ctx->filter_base || max < 0 || !n) return GOM_E_ARG;
+    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    char *base = ctx->filter_base;
+    GomFilterState st{};
+    GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.flt.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *n = std::min<int64_t>(static_cast<int64_t>(st.log_count), ctx->filter_cap);
+    const int64_t c = std::min(*n, max);
+    if (c > 0 && x)
+        GOM_CUDA(ctx, cudaMemcpyAsync(x, base + L.log_x, sizeof(uint16_t) * kFilterIn * c, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    if (c > 0 && y) GOM_CUDA(ctx, cudaMemcpyAsync(y, base + L.log_y, c, cudaMemcpyDeviceToHost, ctx->stream));
+    GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return GOM_OK;
+}
+
+int gom_filter_logits(gom_ctx_t *ctx, int64_t n, float *logits)
+{
+    if (!ctx || !ctx->filter_base || n < 0 || (n > 0 && !logits) || n > ctx->filter_cap) return GOM_E_ARG;
+    if (n == 0) return GOM_OK;
+    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    char *base = ctx->filter_base;
+    cudaStream_t s = ctx->stream;
+    float *d_logit = reinterpret_cast<float *>(base + L.logit);
+    k_filter_eval<<<static_cast<int>(std::min<int64_t>((n + 7) / 8, 4096)), 256, 0, s>>>(
+        reinterpret_cast<const uint16_t *>(base + L.log_x), n, reinterpret_cast<const uint16_t *>(base + L.w1),
+        reinterpret_cast<const float *>(base + L.theta), reinterpret_cast<const uint16_t *>(base + L.w2), d_logit);
+    GOM_CUDA(ctx, cudaGetLastError());
+    GOM_CUDA(ctx, cudaMemcpyAsync(logits, d_logit, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    GOM_CUDA(ctx, cudaStreamSynchronize(s));
     return GOM_OK;
 }
 

@@ -97,6 +97,11 @@ SIGNATURES = [
     ("gom_filter_train", C.c_int, [_P, _I32, C.c_float, C.c_float, C.c_float, _U64, _P]),
     ("gom_filter_stats", C.c_int, [_P, _P]),
     ("gom_filter_skipped", C.c_int, [_P, _P]),
+    ("gom_filter_get_params", C.c_int, [_P, _P, _P, _P, _P]),
+    ("gom_filter_set_params", C.c_int, [_P, _P, _P, _P]),
+    ("gom_filter_epoch", C.c_int, [_P, C.c_float, C.c_float, _I32, _P]),
+    ("gom_filter_log", C.c_int, [_P, _I64, _P, _P, _P]),
+    ("gom_filter_logits", C.c_int, [_P, _I64, _P]),
     ("gom_ims_workspace_bytes", _SZ, [_P, _P, _I32, _I32]),
     ("gom_ims_create", C.c_int, [_P, _P, _I32, _I32, _I32, _U64, _P, _SZ, _P, _P]),
     ("gom_ims_run", C.c_int, [_P, _I32, _I64, _P]),
@@ -530,6 +535,46 @@ def gom_filter_stats(ctx: Ctx) -> dict:
     out = FilterStats()
     _check(load().gom_filter_stats(ctx.h, C.byref(out)), "gom_filter_stats", ctx)
     return out.as_dict()
+
+
+GOM_FILTER_PARAMS = 1153
+
+
+def gom_filter_get_params(ctx: Ctx) -> dict:
+    """theta, Adam moments and the last gradient (numpy float32 [1153] each)."""
+    out = {k: np.zeros(GOM_FILTER_PARAMS, dtype=np.float32) for k in ("theta", "adam_m", "adam_v", "grad")}
+    _check(load().gom_filter_get_params(ctx.h, *(out[k].ctypes.data for k in ("theta", "adam_m", "adam_v", "grad"))),
+           "gom_filter_get_params", ctx)
+    return out
+
+
+def gom_filter_set_params(ctx: Ctx, theta, adam_m=None, adam_v=None):
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) if a is not None else None for a in (theta, adam_m, adam_v)]
+    _check(load().gom_filter_set_params(ctx.h, *(a.ctypes.data if a is not None else None for a in arrs)),
+           "gom_filter_set_params", ctx)
+
+
+def gom_filter_epoch(ctx: Ctx, learning_rate: float, pos_weight: float, step: int) -> float:
+    loss = C.c_double()
+    _check(load().gom_filter_epoch(ctx.h, learning_rate, pos_weight, step, C.byref(loss)), "gom_filter_epoch", ctx)
+    return loss.value
+
+
+def gom_filter_log(ctx: Ctx, max_samples: int = 1 << 30):
+    """The training log: (features as bf16 bits uint16 [n][16], labels uint8 [n])."""
+    n = C.c_int64()
+    _check(load().gom_filter_log(ctx.h, 0, None, None, C.byref(n)), "gom_filter_log", ctx)
+    c = min(n.value, max_samples)
+    x = np.zeros((c, 16), dtype=np.uint16)
+    y = np.zeros(c, dtype=np.uint8)
+    _check(load().gom_filter_log(ctx.h, c, x.ctypes.data, y.ctypes.data, C.byref(n)), "gom_filter_log", ctx)
+    return x, y
+
+
+def gom_filter_logits(ctx: Ctx, n: int):
+    out = np.zeros(n, dtype=np.float32)
+    _check(load().gom_filter_logits(ctx.h, n, out.ctypes.data), "gom_filter_logits", ctx)
+    return out
 
 
 def gom_filter_skipped(ctx: Ctx, m: int):

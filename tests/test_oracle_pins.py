@@ -748,3 +748,18 @@ def test_fi_against_the_same_generation_without_it(oracle, nis):
             assert oracle.cut_value(g, a["pop"][i]) == a["f"][i]
         assert sb["fi_improving"] >= sb["fi_individuals"] - sb["fi_replaced"] >= 0
         assert sum(np.array_equal(a["pop"][i], a["xe"]) for i in range(24)) >= sb["fi_replaced"]
+
+
+def test_element_counters_sum_to_the_generation_counters(oracle):
+    """The per-element counters (accepted, donor-less, improving trials of
+    each element in the last generation) add up to the generation's own
+    counters, and an element's counts never exceed p."""
+    g = I.random_regular(150, 4, seed=12)
+    eptr, evars, k, colors = _setup(oracle, g)
+    run = oracle.Run(g, eptr, evars, colors, k, 20, 3)
+    run.keep_element_counts(True)
+    for _ in range(5):
+        st = run.generation()
+        acc, dl, imp = run.element_counts()
+        assert (acc.sum(), dl.sum(), imp.sum()) == (st["accepted"], st["donorless"], st["improving"])
+        assert (acc + dl <= 20).all() and (imp <= acc).all()
