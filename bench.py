@@ -117,10 +117,14 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """sha256 prefix of every device-code source of the library (kernels,
+    shared device headers, the parameter structures)."""
     h = hashlib.sha256()
-    for fn in ("gom_kernels.cu", "gom_internal.h"):
-        with open(os.path.join(ROOT, "paper_2203_08680_gb300", "csrc", fn), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2203_08680_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")) or fn == "gom_internal.h":
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -440,6 +444,10 @@ def torus100_ttt_extras(args, g, seed, stream):
     out = {"ims": ims_time_to_target(args, g, seed, stream)}
     out["linkage_tree"] = [linkage_tree_time_to_target(args, g, seed, stream, b) for b in (100, 128)]
     out["linkage_tree"].append(ims_time_to_target(args, g, seed, stream, bflt=128, base=128, c=2, chunk=16))
+    # Forced Improvement (Sec. 4), which the paper's parallel GOMEA leaves out: the neighbourhood FOS at p = 64
+    # and the paper's linkage tree at its bound of 100
+    out["forced_improvement"] = {"plain_p64": time_to_target(args, g, 64, seed, stream, "torus100", fi=True),
+                                 "linkage_tree_100": linkage_tree_time_to_target(args, g, seed, stream, 100, fi=True)}
     return out
 
 
@@ -701,20 +709,20 @@ def run_learned(args, wl, rank, world, local):
     return line
 
 
-def time_to_target(args, g, p, seed, stream, wl, fos=None):
+def time_to_target(args, g, p, seed, stream, wl, fos=None, fi=False):
     import torch
 
     from paper_2203_08680_gb300 import gom
     tw = g.total_weight()
     target = int(math.ceil(0.999 * tw))
-    P2 = gom.Population(g, p, seed, fos=fos, stream=stream)
+    P2 = gom.Population(g, p, seed, fos=fos, stream=stream, forced_improvement=fi or None)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     stats, nrun = P2.generation(args.ttt_gens, target)
     e1.record(stream)
     torch.cuda.synchronize()
-    ttt = {"target": target, "closed_form_optimum": tw if wl.startswith("torus") else None,
+    ttt = {"target": target, "forced_improvement": fi, "closed_form_optimum": tw if wl.startswith("torus") else None,
            "reached": bool(stats and stats[-1]["reached_target"]), "generations": nrun,
            "best": stats[-1]["best_fitness"] if stats else None, "ms": e0.elapsed_time(e1),
            "max_generations": args.ttt_gens}
@@ -722,7 +730,7 @@ def time_to_target(args, g, p, seed, stream, wl, fos=None):
     return ttt
 
 
-def linkage_tree_time_to_target(args, g, seed, stream, bound):
+def linkage_tree_time_to_target(args, g, seed, stream, bound, fi=False):
     """Time to target with the paper's linkage model: the bounded fixed
     linkage tree (UPGMA on the weights, Sec. 4.1) at `bound` variables, one
     population of --lt-pop individuals, up to --lt-gens generations.  The
@@ -734,7 +742,7 @@ def linkage_tree_time_to_target(args, g, seed, stream, bound):
     target = int(math.ceil(0.999 * tw))
     t0 = time.perf_counter()
     fos = gom.gom_build_fos(g, gom.GOM_FOS_BFLT, bound)
-    P = gom.Population(g, args.lt_pop, seed, fos=fos, stream=stream)
+    P = gom.Population(g, args.lt_pop, seed, fos=fos, stream=stream, forced_improvement=fi or None)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -742,7 +750,8 @@ def linkage_tree_time_to_target(args, g, seed, stream, bound):
     stats, nrun = P.generation(args.lt_gens, target)
     e1.record(stream)
     torch.cuda.synchronize()
-    out = {"fos": f"bounded linkage tree, bound {bound}", "population": args.lt_pop, "colours": P.k,
+    out = {"fos": f"bounded linkage tree, bound {bound}", "forced_improvement": fi, "population": args.lt_pop,
+           "colours": P.k,
            "target": target, "reached": bool(stats and stats[-1]["reached_target"]), "generations": nrun,
            "best": stats[-1]["best_fitness"] if stats else None, "ms": e0.elapsed_time(e1),
            "setup_ms": setup_s * 1e3, "max_generations": args.lt_gens}

@@ -276,9 +276,9 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     __syncwarp();
 
     // ---- phase 1: donors, lane = individual.  Pass A checks every pair's
-    // first candidate (straight-line: one table lookup each); pass B
-    // continues the search for the individuals whose first candidate equals
-    // them on F_j (run starts, then the word-parallel scan).  Each word's
+    // first two candidates (straight-line: two table lookups each); pass B
+    // searches from the start again for the individuals whose first two
+    // candidates equal them on F_j (run starts, then the word-parallel scan).  Each word's
     // flips of a chunk are packed like the patterns into sFM.
     for (int w2 = 0; w2 < Wv; ++w2) {
         const int i = 32 * w2 + lane;
@@ -293,9 +293,16 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
                 const uint32_t xf = (xo >> off) & fmask;
                 // starts exist for individuals < p only (others read candidate 0, and are dropped below)
                 const int st = vi ? sStart[(e2 * W + w2) * 32 + lane] : 0;
+                // the candidate after it in the scan's cyclic order (the parent itself skipped); with
+                // p = 2 there is none (it wraps to the start), left to pass B
+                int d2 = st + 1 == p ? 0 : st + 1;
+                if (d2 == i) d2 = d2 + 1 == p ? 0 : d2 + 1;
                 const uint32_t pd = packed_pattern(tabP, c, W, st, off, fmask);
+                const uint32_t pd2 = packed_pattern(tabP, c, W, d2, off, fmask);
                 if (pd != xf)
                     fmw |= (pd ^ xf) << off;
+                else if (pd2 != xf && d2 != st)
+                    fmw |= (pd2 ^ xf) << off;
                 else
                     fails |= 1u << el;
             }
