@@ -355,11 +355,19 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             const uint32_t Xa = myO[a];
             add_weighted<R, R>(T, Fa, (uint32_t)__ldg(P.wabs + f0 + a));
             const int xb = (int)__ldg(P.seg + f0 + q + a), xe = (int)__ldg(P.seg + f0 + q + a + 1);
-            for (int x = xb; x < xe; ++x) {
-                const int2 ed = __ldg(P.dep + d0 + x);
-                const uint32_t Xv = P.O[(int64_t)ed.x * W + w];
-                const uint32_t S = (uint32_t)(ed.y >> 31);
-                add_weighted<R, kWeightBits>(N, Fa & (Xa ^ Xv ^ S), (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
+            for (int x = xb; x < xe; x += 4) { // four edges' loads issued before their arithmetic
+                int2 ed[4];
+                uint32_t Xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ed[u] = x + u < xe ? __ldg(P.dep + d0 + x + u) : make_int2(0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) Xv[u] = x + u < xe ? P.O[(int64_t)ed[u].x * W + w] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t S = (uint32_t)(ed[u].y >> 31);
+                    if (x + u < xe)
+                        add_weighted<R, kWeightBits>(N, Fa & (Xa ^ Xv[u] ^ S), (uint32_t)(ed[u].y < 0 ? -ed[u].y : ed[u].y));
+                }
             }
         }
         for (int x = n_out; x < n_out + n_in; ++x) {

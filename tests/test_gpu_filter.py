@@ -255,14 +255,16 @@ def test_filter_gradient_and_adam_step_match_a_restatement():
     assert np.all(np.abs(got["grad"] - want) <= 1e-4 * mag + 1e-6)
     want_loss = np.mean(wt * (np.log1p(np.exp(-np.abs(out))) + np.maximum(out, 0) - t * out))
     assert abs(loss - want_loss) <= 1e-5 * abs(want_loss)
-    # Adam, step 1, on the kernel's own gradient (fp32)
+    # Adam, step 1, on the kernel's own gradient, in fp32: beta1 and beta2 are
+    # the fp32 values nearest 0.9 and 0.999, and 1 - beta is taken in fp32
     f32 = np.float32
+    b1, b2 = f32(0.9), f32(0.999)
     gm = got["grad"].astype(np.float32) * (f32(1) / f32(len(y)))
-    m1 = f32(0.1) * gm
-    v1 = f32(0.001) * gm * gm
-    th1 = theta0 - lr * (m1 / f32(1 - 0.9)) / (np.sqrt(v1 / f32(1 - 0.999)) + f32(1e-8))
-    assert np.allclose(got["adam_m"], m1, rtol=1e-6, atol=1e-12)
-    assert np.allclose(got["adam_v"], v1, rtol=1e-5, atol=1e-18)
+    m1 = (f32(1) - b1) * gm
+    v1 = (f32(1) - b2) * gm * gm
+    th1 = theta0 - lr * (m1 / (f32(1) - b1)) / (np.sqrt(v1 / (f32(1) - b2)) + f32(1e-8))
+    assert np.allclose(got["adam_m"], m1, rtol=2e-6, atol=1e-12)
+    assert np.allclose(got["adam_v"], v1, rtol=2e-6, atol=1e-18)
     assert np.allclose(got["theta"], th1, rtol=1e-6, atol=1e-6 * float(lr))
 
 

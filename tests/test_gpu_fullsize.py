@@ -50,6 +50,19 @@ def _oracle_fos(oracle, name, g):
     return _FOS[name]
 
 
+def _sample(p, seed):
+    """Individuals 0 and p - 1 and one random individual of every population
+    word of 32, so every word's lanes and bits are checked."""
+    rng = np.random.default_rng(seed)
+    words = (p + 31) // 32
+    return sorted({0, p - 1, *[min(p - 1, 32 * w + int(rng.integers(32))) for w in range(words)]})
+
+
+def _threads():
+    import os
+    return max(1, min(16, os.cpu_count() or 1))
+
+
 def _state(P):
     pop, fit, fe = P.population()
     xe, _ = P.elite()
@@ -68,8 +81,7 @@ def test_full_size_sampled_generation(oracle, name, p):
     assert P.k == k and np.array_equal(ex["color_of_elem"], co)
     assert np.array_equal(ex["elem_ptr"], ep) and np.array_equal(ex["elem_vars"], ev)
 
-    rng = np.random.default_rng(p + len(name))
-    sample = sorted({0, p - 1, *rng.choice(p, 2, replace=False).tolist()})
+    sample = _sample(p, p + len(name))
 
     pop0, f0, xe0, fe0 = _state(P)
     for i in sample:  # InitializePopulation, sampled
@@ -83,7 +95,7 @@ def test_full_size_sampled_generation(oracle, name, p):
 
     run = oracle.Run(g, ep, ev, co, k, p, seed, init=False)
     run.load(pop1, f1, xe1, fe1, 1)
-    run.generation(only=sample)
+    run.generation(only=sample, threads=_threads())
     ref = run.get()
     for i in sample:
         assert np.array_equal(pop2[i], ref["pop"][i]), (name, p, i)
@@ -96,6 +108,38 @@ def test_full_size_sampled_generation(oracle, name, p):
     assert fe2 == max(fe1, int(f2.max())) and fe1 == max(fe0, int(f1.max()))
     assert oracle.cut_value(g, xe2) == fe2
     assert st2[0]["best_fitness"] == f2.max() and st2[0]["elite_fitness"] == fe2
+
+
+@pytest.mark.parametrize("bitsliced", [False, True])
+@pytest.mark.parametrize("name,p,late", [("rreg1m_d12", 512, 100), ("torus1000", 256, 100)])
+def test_full_size_late_generation(oracle, name, p, late, bitsliced):
+    """A generation after `late` generations, when many donor searches run
+    past their first candidates: the oracle replays generation late + 1 from
+    the GPU's exported state for one individual of every population word
+    (and the first and last), bit for bit, on either mixing path."""
+    g = _graph(name)
+    P = gom.Population(g, p, 1)
+    try:
+        gom.gom_set_option(P.ctx, gom.GOM_OPT_BITSLICED, 1 if bitsliced else 0)
+    except gom.GomError:
+        pytest.skip("bit-sliced mixing unavailable")
+    ep, ev, k, co = _oracle_fos(oracle, name, g)
+    P.generation(late, want_stats=False)
+    popA, fA, xeA, feA = _state(P)
+    st, _ = P.generation(1)
+    popB, fB, xeB, feB = _state(P)
+    assert st[0]["generation"] == late
+    sample = _sample(p, 7 * p + late)
+    run = oracle.Run(g, ep, ev, co, k, p, 1, init=False)
+    run.load(popA, fA, xeA, feA, late)
+    run.generation(only=sample, threads=_threads())
+    ref = run.get()
+    for i in sample:
+        assert np.array_equal(popB[i], ref["pop"][i]), (name, p, i)
+        assert fB[i] == ref["f"][i], (name, p, i)
+    assert np.array_equal(P.fitness().cpu().numpy(), fB)
+    assert np.all(fB >= fA) and feB == max(feA, int(fB.max()))
+    assert st[0]["donorless"] > 0  # searches that find no donor: the population has partly converged
 
 
 def test_torus100_full_run(oracle):
