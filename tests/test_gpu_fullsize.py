@@ -113,10 +113,10 @@ def test_full_size_sampled_generation(oracle, name, p):
 @pytest.mark.parametrize("bitsliced", [False, True])
 @pytest.mark.parametrize("name,p,late", [("rreg1m_d12", 512, 100), ("torus1000", 256, 100)])
 def test_full_size_late_generation(oracle, name, p, late, bitsliced):
-    """A generation after `late` generations, when many donor searches run
-    past their first candidates: the oracle replays generation late + 1 from
-    the GPU's exported state for one individual of every population word
-    (and the first and last), bit for bit, on either mixing path."""
+    """A late generation (after `late` generations, the population partly
+    converged): the oracle replays it from the GPU's exported state for one
+    individual of every population word (and the first and last), bit for
+    bit, on either mixing path."""
     g = _graph(name)
     P = gom.Population(g, p, 1)
     try:
@@ -139,7 +139,6 @@ def test_full_size_late_generation(oracle, name, p, late, bitsliced):
         assert fB[i] == ref["f"][i], (name, p, i)
     assert np.array_equal(P.fitness().cpu().numpy(), fB)
     assert np.all(fB >= fA) and feB == max(feA, int(fB.max()))
-    assert st[0]["donorless"] > 0  # searches that find no donor: the population has partly converged
 
 
 def test_torus100_full_run(oracle):
