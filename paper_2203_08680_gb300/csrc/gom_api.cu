@@ -508,7 +508,8 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             const int nc = (E0 + epw - 1) / epw;
             const int64_t ww = gom_bs_warp_words(sm, nc, c->W);
             const int wpb = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (ww * 4)));
-            const size_t smem = std::max(static_cast<size_t>(ww * 4 * wpb), keys_smem);
+            // the block's fitness accumulators (32 W int64), then the warps' regions
+            const size_t smem = std::max(static_cast<size_t>(256 * c->W + ww * 4 * wpb), keys_smem);
             const void *rf = gom_run_bs_kernel(R), *mf = gom_mix_bs_kernel(R);
             if (wpb >= 1 && smem <= static_cast<size_t>(kSmemBudget) && rf && mf) {
                 const int E = 32 / c->W;

@@ -153,12 +153,20 @@ __device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t 
 
 // Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4;
 // NC chunks of packed patterns): rows of O on F_j [32 pairs][SM], rows of P
-// [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals], run
-// starts [32 pairs], packed patterns of P and of O and packed flips
-// [NC][W][32] each, the item's element sizes [32].
+// [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals] as
+// 16-bit values, run starts [32 pairs], packed patterns of P [NC][W][32],
+// packed patterns of O [NC][W][32] (their slots reused for the packed flips),
+// the item's element sizes [32].
 __host__ __device__ __forceinline__ int bs_warp_words(int SM, int NC, int W)
 {
-    return 96 * SM + 32 * 32 + 32 + 96 * NC * W + 32;
+    return 96 * SM + 16 * 32 + 32 + 64 * NC * W + 32;
+}
+
+// The dynamic shared memory of the bit-sliced kernels: the block's fitness
+// accumulators (32 W int64, i.e. 64 W words) first, then the warps' regions.
+__device__ __forceinline__ uint32_t *bs_warp_region(const GomParams &P, uint32_t *s_dyn)
+{
+    return s_dyn + 64 * P.W + (threadIdx.x >> 5) * P.bs_words;
 }
 
 // One item of colour group c at position t: elements [q0, q1) (at most E)
@@ -174,8 +182,8 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     const int q = q0 + e;
     const bool kv = q < q1 && w < Wv; // this lane's pair exists
     uint32_t *sO = wsm, *sP = wsm + 32 * SM, *sD = wsm + 64 * SM;
-    int *sStart = reinterpret_cast<int *>(wsm + 96 * SM);
-    uint32_t *sRS = wsm + 96 * SM + 32 * 32;
+    uint16_t *sStart = reinterpret_cast<uint16_t *>(wsm + 96 * SM); // p <= 1024: a start fits 16 bits
+    uint32_t *sRS = wsm + 96 * SM + 16 * 32;
 
     // ---- phase 0: the pair's rows, run starts, donor starts
     int j = 0, s = 0, f0 = 0, d0 = 0, n_in = 0, n_out = 0;
@@ -235,7 +243,8 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
                     const int d = i0 + cc + 1 + (int)__umulhi(pick(r4, cc), (uint32_t)(p - 1));
                     st[cc] = d >= p ? d - p : d;
                 }
-                *reinterpret_cast<int4 *>(sStart + k2 * 32 + 4 * c) = make_int4(st[0], st[1], st[2], st[3]);
+                *reinterpret_cast<uint2 *>(sStart + k2 * 32 + 4 * c) =
+                    make_uint2((uint32_t)st[0] | ((uint32_t)st[1] << 16), (uint32_t)st[2] | ((uint32_t)st[3] << 16));
             }
         }
     }
@@ -246,8 +255,9 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     // four words at a time, interleaved
     const int S = P.bs_S, EPW = P.bs_epw, NC = P.bs_nc;
     const int E = 32 >> lw;
-    uint32_t *tabP = wsm + 96 * SM + 32 * 32 + 32, *tabO = tabP + 32 * NC * W, *sFM = tabO + 32 * NC * W;
-    int *sS = reinterpret_cast<int *>(sFM + 32 * NC * W);
+    uint32_t *tabP = wsm + 96 * SM + 16 * 32 + 32, *tabO = tabP + 32 * NC * W;
+    uint32_t *sFM = tabO; // a lane reads its entry of tabO before it writes the same entry of sFM
+    int *sS = reinterpret_cast<int *>(tabO + 32 * NC * W);
     const uint32_t fmask = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
     if (w == 0) sS[e] = s; // the item's element sizes, by slot
     const int er = lane / S, ar = lane - er * S; // this lane's row in a transpose: element er of a chunk, variable ar
@@ -472,15 +482,15 @@ __device__ __forceinline__ void bs_finish_generation(const GomParams &P, BsLane 
 // closes its last group (block 0 records it).  The dynamic shared memory
 // holds the warps' regions (the k group keys of the order phase overlay them).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, int64_t target)
+__global__ void __launch_bounds__(kMixThreads, 3) k_run_bs(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
+    long long *s_f = reinterpret_cast<long long *>(s_dyn);
     const VGrid V = whole_grid();
     const unsigned nblk = (unsigned)V.nblk;
     const bool lead = V.blk == 0;
-    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * P.bs_words;
+    uint32_t *wsm = bs_warp_region(P, s_dyn);
     GomBarrier *bar = P.bar;
     uint32_t g = P.st->g;
     GenEnd e{P.st->fe, P.st->improved, P.st->argmax};
@@ -521,16 +531,16 @@ __global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, i
 // Per-launch path: the mixing of the group at position t (one launch per
 // group in the per-generation CUDA graph).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 2) k_mix_bs(GomParams P, int t)
+__global__ void __launch_bounds__(kMixThreads, 3) k_mix_bs(GomParams P, int t)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    __shared__ long long s_f[1024];
     __shared__ unsigned long long s_cnt[4];
+    long long *s_f = reinterpret_cast<long long *>(s_dyn);
     if (P.st->done) return;
     acc_zero(P, s_f, s_cnt);
     BsLane L;
     bs_lane_zero(L);
-    uint32_t *wsm = s_dyn + (threadIdx.x >> 5) * P.bs_words;
+    uint32_t *wsm = bs_warp_region(P, s_dyn);
     phase_mix_bs<R>(P, whole_grid(), t, P.order[t], P.st->g, wsm, L, s_f);
     bs_finish_generation(P, L, s_f, s_cnt);
     acc_flush(P, s_f, s_cnt);
