@@ -79,7 +79,7 @@ __device__ __forceinline__ void transpose32x4(uint32_t (&x)[4])
 // by side, the element's at bit offset `off`.
 __device__ __forceinline__ uint32_t packed_pattern(const uint32_t *tab, int c, int W, int d, int off, uint32_t fmask)
 {
-    return (tab[(c * W + (d >> 5)) * 32 + (d & 31)] >> off) & fmask;
+    return (tab[c * W * 32 + d] >> off) & fmask; // (d / 32) 32 + d mod 32 = d
 }
 
 // Word-parallel donor scan over the staged rows (32 candidates per step):
@@ -296,23 +296,24 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         for (int c = 0; c < NC; ++c) {
             const uint32_t xo = tabO[(c * W + w2) * 32 + lane]; // the parents' current patterns
             const int ne = min(EPW, min(E, q1 - q0) - c * EPW); // elements of this chunk in the item
+            const uint32_t *tc = tabP + c * W * 32;             // chunk c's patterns, by individual
+            const uint16_t *sc = sStart + (c * EPW * W + w2) * 32 + lane;
             uint32_t fmw = 0, fails = 0;
 #pragma unroll 4
             for (int el = 0; el < ne; ++el) {
-                const int off = el * S, e2 = c * EPW + el;
-                const uint32_t xf = (xo >> off) & fmask;
+                // the element's field of the packed words: its flips are (donor ^ parent) & field
+                const uint32_t field = fmask << (el * S);
                 // starts exist for individuals < p only (others read candidate 0, and are dropped below)
-                const int st = vi ? sStart[(e2 * W + w2) * 32 + lane] : 0;
+                const int st = vi ? sc[el * W * 32] : 0;
                 // the candidate after it in the scan's cyclic order (the parent itself skipped); with
                 // p = 2 there is none (it wraps to the start), left to pass B
                 int d2 = st + 1 == p ? 0 : st + 1;
                 if (d2 == i) d2 = d2 + 1 == p ? 0 : d2 + 1;
-                const uint32_t pd = packed_pattern(tabP, c, W, st, off, fmask);
-                const uint32_t pd2 = packed_pattern(tabP, c, W, d2, off, fmask);
-                if (pd != xf)
-                    fmw |= (pd ^ xf) << off;
-                else if (pd2 != xf && d2 != st)
-                    fmw |= (pd2 ^ xf) << off;
+                const uint32_t f1 = (tc[st] ^ xo) & field, f2 = (tc[d2] ^ xo) & field;
+                if (f1)
+                    fmw |= f1;
+                else if (f2 && d2 != st)
+                    fmw |= f2;
                 else
                     fails |= 1u << el;
             }
@@ -482,7 +483,7 @@ __device__ __forceinline__ void bs_finish_generation(const GomParams &P, BsLane 
 // closes its last group (block 0 records it).  The dynamic shared memory
 // holds the warps' regions (the k group keys of the order phase overlay them).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 3) k_run_bs(GomParams P, int G, int64_t target)
+__global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ unsigned long long s_cnt[4];
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_run_bs(GomParams P, int G, i
 // Per-launch path: the mixing of the group at position t (one launch per
 // group in the per-generation CUDA graph).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 3) k_mix_bs(GomParams P, int t)
+__global__ void __launch_bounds__(kMixThreads, 2) k_mix_bs(GomParams P, int t)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ unsigned long long s_cnt[4];
