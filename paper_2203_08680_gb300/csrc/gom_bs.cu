@@ -74,14 +74,6 @@ __device__ __forceinline__ void transpose32x4(uint32_t (&x)[4])
     }
 }
 
-// The pattern (bits on F_j) of individual d from a packed table: tab[(c W +
-// d / 32) 32 + d mod 32] holds the patterns of the elements of chunk c side
-// by side, the element's at bit offset `off`.
-__device__ __forceinline__ uint32_t packed_pattern(const uint32_t *tab, int c, int W, int d, int off, uint32_t fmask)
-{
-    return (tab[c * W * 32 + d] >> off) & fmask; // (d / 32) 32 + d mod 32 = d
-}
-
 // Word-parallel donor scan over the staged rows (32 candidates per step):
 // the first individual in cyclic order from `start`, skipping `self`, whose
 // generation-start bits on F_j differ from the parent's bits xf; -1 if none.
@@ -107,38 +99,50 @@ __device__ int scan_rows(const uint32_t *sP, int SM, int e, int W, int Wv, int p
     return -1;
 }
 
+// First position at or after x, in cyclic order over [0, p), whose bit is set
+// in the run starts rs[0..Wv); nz has bit w set iff rs[w] != 0 (so the next
+// non-empty word is one bit scan away).  -1 if no bit is set.
+__device__ __forceinline__ int next_run_start(const uint32_t *rs, uint32_t nz, int x)
+{
+    const int w = x >> 5;
+    const uint32_t m = rs[w] & (0xFFFFFFFFu << (x & 31));
+    if (m) return 32 * w + __ffs(m) - 1;
+    const uint32_t later = nz & ~((2u << w) - 1u); // words after w
+    const uint32_t any = later ? later : nz;        // else wrap round (word w's low bits included)
+    if (!any) return -1;
+    const int w2 = __ffs(any) - 1;
+    return 32 * w2 + __ffs(rs[w2]) - 1;
+}
+
 // The donor of individual `self` (Sec. 4.2): the first candidate in cyclic
 // order from `start`, skipping self, whose generation-start bits on F_j
-// differ from the parent's current bits xf, or -1.  Candidates' patterns come
-// from the packed table of P (chunk c, field offset off); rs are the run
-// starts of the element's patterns (bit d: pattern d differs from pattern
-// d - 1, cyclically), so candidates strictly inside a run equal to the parent
-// are passed in one step (a run start after such a run differs from xf);
-// after a few steps the word-parallel scan over the staged rows finishes the
-// search.  *pd receives the donor's pattern.  Divergent code.
-__device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t fmask, const uint32_t *sP,
-                                 const uint32_t *rs, int SM, int e, int W, int Wv, int p, int s, uint32_t xf,
-                                 int start, int self, uint32_t *pd)
+// differ from the parent's current bits xf, or -1.  The search resumes at
+// candidate `cur`, whose pattern is known to equal xf (start, or the one
+// after it).  Candidates' patterns come from the packed table tc of P (the
+// element's field at offset `off`); rs are the run starts of the element's
+// patterns (bit d: pattern d differs from pattern d - 1, cyclically), so the
+// candidates strictly inside a run equal to the parent are passed in one
+// step (a run start after such a run differs from xf); after a few steps the
+// word-parallel scan over the staged rows finishes the search.  *pd receives
+// the donor's pattern.  Divergent code.
+__device__ int find_donor_packed(const uint32_t *tc, int off, uint32_t fmask, const uint32_t *sP, const uint32_t *rs,
+                                 uint32_t nz, int SM, int e, int W, int Wv, int p, int s, uint32_t xf, int start,
+                                 int cur, int self, uint32_t *pd)
 {
-    uint32_t pat = packed_pattern(tabP, c, W, start, off, fmask);
-    if (pat != xf) {
-        *pd = pat;
-        return start;
-    }
-    int d = start; // pattern d == xf here
+    int d = cur; // pattern d == xf here
     for (int it = 0; it < 4; ++it) {
-        const int d2 = next_set_cyclic(rs, Wv, p, d);
-        if (d2 < 0) return -1;
+        const int d2 = next_run_start(rs, nz, d + 1 == p ? 0 : d + 1);
+        if (d2 < 0) return -1; // one run: every candidate equals the parent
         const int dist_d = d - start + (d < start ? p : 0);
         const int dist_2 = d2 - start + (d2 < start ? p : 0);
-        if (dist_2 <= dist_d) return -1;
+        if (dist_2 <= dist_d) return -1; // the jump passed the start
         if (d2 != self) {
-            *pd = packed_pattern(tabP, c, W, d2, off, fmask);
+            *pd = (tc[d2] >> off) & fmask;
             return d2;
         }
-        d = d2 + 1 == p ? 0 : d2 + 1;
+        d = d2 + 1 == p ? 0 : d2 + 1; // skip the parent's own column
         if (d == start) return -1;
-        pat = packed_pattern(tabP, c, W, d, off, fmask);
+        const uint32_t pat = (tc[d] >> off) & fmask;
         if (pat != xf) {
             *pd = pat;
             return d;
@@ -147,7 +151,7 @@ __device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t 
     const int d3 = d + 1 == p ? 0 : d + 1;
     if (d3 == start) return -1;
     const int r = scan_rows(sP, SM, e, W, Wv, p, s, xf, d3, self);
-    if (r >= 0) *pd = packed_pattern(tabP, c, W, r, off, fmask);
+    if (r >= 0) *pd = (tc[r] >> off) & fmask;
     return r;
 }
 
@@ -156,10 +160,11 @@ __device__ int find_donor_packed(const uint32_t *tabP, int c, int off, uint32_t 
 // [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals] as
 // 16-bit values, run starts [32 pairs], packed patterns of P [NC][W][32],
 // packed patterns of O [NC][W][32] (their slots reused for the packed flips),
-// the item's element sizes [32].
+// the item's element sizes [32] and the masks of their non-empty run-start
+// words [32].
 __host__ __device__ __forceinline__ int bs_warp_words(int SM, int NC, int W)
 {
-    return 96 * SM + 16 * 32 + 32 + 64 * NC * W + 32;
+    return 96 * SM + 16 * 32 + 32 + 64 * NC * W + 64;
 }
 
 // The dynamic shared memory of the bit-sliced kernels: the block's fitness
@@ -226,6 +231,10 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             rsw &= lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
         }
         sRS[lane] = rsw;
+        // element e's words with a run start: bits e W .. e W + W - 1 of the ballot
+        const uint32_t nzb = __ballot_sync(0xFFFFFFFFu, rsw != 0);
+        if (w == 0)
+            wsm[96 * SM + 16 * 32 + 32 + 64 * P.bs_nc * W + 32 + e] = W == 32 ? nzb : (nzb >> (e * W)) & ((1u << W) - 1u);
     }
     {   // donor starts: call (pair k2, c) covers individuals 32 w2 + 4c .. + 3
 #pragma unroll 1
@@ -258,6 +267,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     uint32_t *tabP = wsm + 96 * SM + 16 * 32 + 32, *tabO = tabP + 32 * NC * W;
     uint32_t *sFM = tabO; // a lane reads its entry of tabO before it writes the same entry of sFM
     int *sS = reinterpret_cast<int *>(tabO + 32 * NC * W);
+    const uint32_t *sNZ = tabO + 32 * NC * W + 32; // per element slot: its non-empty run-start words
     const uint32_t fmask = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
     if (w == 0) sS[e] = s; // the item's element sizes, by slot
     const int er = lane / S, ar = lane - er * S; // this lane's row in a transpose: element er of a chunk, variable ar
@@ -321,9 +331,12 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             for (uint32_t f = fails; f; f &= f - 1) { // pass B, divergent
                 const int el = __ffs(f) - 1, off = el * S, e2 = c * EPW + el;
                 const uint32_t xf = (xo >> off) & fmask;
+                const int st = sStart[(e2 * W + w2) * 32 + lane];
+                int d2 = st + 1 == p ? 0 : st + 1; // the second candidate, whose pattern equals xf too
+                if (d2 == i) d2 = d2 + 1 == p ? 0 : d2 + 1;
                 uint32_t pd = 0;
-                const int d = find_donor_packed(tabP, c, off, fmask, sP, sRS + e2 * W, SM, e2, W, Wv, p, sS[e2], xf,
-                                                sStart[(e2 * W + w2) * 32 + lane], i, &pd);
+                const int d = find_donor_packed(tabP + c * W * 32, off, fmask, sP, sRS + e2 * W, sNZ[e2], SM, e2, W, Wv, p,
+                                                sS[e2], xf, st, d2 == st ? st : d2, i, &pd);
                 if (d >= 0) fmw |= (pd ^ xf) << off;
             }
             sFM[(c * W + w2) * 32 + lane] = fmw;
