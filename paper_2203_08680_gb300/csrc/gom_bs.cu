@@ -296,9 +296,10 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     __syncwarp();
 
     // ---- phase 1: donors, lane = individual.  Pass A checks every pair's
-    // first two candidates (straight-line: two table lookups each); pass B
-    // searches from the start again for the individuals whose first two
-    // candidates equal them on F_j (run starts, then the word-parallel scan).  Each word's
+    // start candidate (one table lookup) and, when it equals the parent on
+    // F_j, takes the first run start after it (one more); pass B searches
+    // again from the start for the rare individuals whose run start is their
+    // own column (run starts, then the word-parallel scan).  Each word's
     // flips of a chunk are packed like the patterns into sFM.
     for (int w2 = 0; w2 < Wv; ++w2) {
         const int i = 32 * w2 + lane;
@@ -311,32 +312,33 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             uint32_t fmw = 0, fails = 0;
 #pragma unroll 4
             for (int el = 0; el < ne; ++el) {
+                const int e2 = c * EPW + el;
                 // the element's field of the packed words: its flips are (donor ^ parent) & field
                 const uint32_t field = fmask << (el * S);
                 // starts exist for individuals < p only (others read candidate 0, and are dropped below)
                 const int st = vi ? sc[el * W * 32] : 0;
-                // the candidate after it in the scan's cyclic order (the parent itself skipped); with
-                // p = 2 there is none (it wraps to the start), left to pass B
-                int d2 = st + 1 == p ? 0 : st + 1;
-                if (d2 == i) d2 = d2 + 1 == p ? 0 : d2 + 1;
-                const uint32_t f1 = (tc[st] ^ xo) & field, f2 = (tc[d2] ^ xo) & field;
-                if (f1)
+                const uint32_t f1 = (tc[st] ^ xo) & field;
+                if (f1) {
                     fmw |= f1;
-                else if (f2 && d2 != st)
-                    fmw |= f2;
-                else
-                    fails |= 1u << el;
+                } else {
+                    // every candidate from st up to the next run start has st's pattern, the
+                    // parent's; the run start itself differs from it, so it is the donor --
+                    // unless it is the parent's own column (pass B); no run start: no donor
+                    const int d2 = next_run_start(sRS + e2 * W, sNZ[e2], st + 1 == p ? 0 : st + 1);
+                    if (d2 == i)
+                        fails |= 1u << el;
+                    else if (d2 >= 0)
+                        fmw |= (tc[d2] ^ xo) & field;
+                }
             }
             if (!vi) fmw = fails = 0;
             for (uint32_t f = fails; f; f &= f - 1) { // pass B, divergent
                 const int el = __ffs(f) - 1, off = el * S, e2 = c * EPW + el;
                 const uint32_t xf = (xo >> off) & fmask;
                 const int st = sStart[(e2 * W + w2) * 32 + lane];
-                int d2 = st + 1 == p ? 0 : st + 1; // the second candidate, whose pattern equals xf too
-                if (d2 == i) d2 = d2 + 1 == p ? 0 : d2 + 1;
                 uint32_t pd = 0;
                 const int d = find_donor_packed(tabP + c * W * 32, off, fmask, sP, sRS + e2 * W, sNZ[e2], SM, e2, W, Wv, p,
-                                                sS[e2], xf, st, d2 == st ? st : d2, i, &pd);
+                                                sS[e2], xf, st, st, i, &pd);
                 if (d >= 0) fmw |= (pd ^ xf) << off;
             }
             sFM[(c * W + w2) * 32 + lane] = fmw;
