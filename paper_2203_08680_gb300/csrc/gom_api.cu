@@ -507,7 +507,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             const int epw = 32 / S, E0 = 32 / c->W;
             const int nc = (E0 + epw - 1) / epw;
             const int64_t ww = gom_bs_warp_words(sm, nc, c->W);
-            const int wpb = static_cast<int>(std::min<int64_t>(kMixThreads / 32, kSmemBudget / (ww * 4)));
+            const int wpb = static_cast<int>(std::min<int64_t>(kBsThreads / 32, kSmemBudget / (ww * 4)));
             // the block's fitness accumulators (32 W int64), then the warps' regions
             const size_t smem = std::max(static_cast<size_t>(256 * c->W + ww * 4 * wpb), keys_smem);
             const void *rf = gom_run_bs_kernel(R), *mf = gom_mix_bs_kernel(R);

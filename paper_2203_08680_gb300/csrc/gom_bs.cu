@@ -498,7 +498,7 @@ __device__ __forceinline__ void bs_finish_generation(const GomParams &P, BsLane 
 // closes its last group (block 0 records it).  The dynamic shared memory
 // holds the warps' regions (the k group keys of the order phase overlay them).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, int64_t target)
+__global__ void __launch_bounds__(kBsThreads, 5) k_run_bs(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ unsigned long long s_cnt[4];
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kMixThreads, 2) k_run_bs(GomParams P, int G, i
 // Per-launch path: the mixing of the group at position t (one launch per
 // group in the per-generation CUDA graph).
 template <int R>
-__global__ void __launch_bounds__(kMixThreads, 2) k_mix_bs(GomParams P, int t)
+__global__ void __launch_bounds__(kBsThreads, 5) k_mix_bs(GomParams P, int t)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
     __shared__ unsigned long long s_cnt[4];

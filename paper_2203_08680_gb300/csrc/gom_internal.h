@@ -166,6 +166,7 @@ struct GomFI {
 
 constexpr int kStatsCap = 1024;    // per-generation counters kept on the device
 constexpr int kMixThreads = 256;   // mixing kernel block size (8 warps)
+constexpr int kBsThreads = 128;    // bit-sliced kernels' block size (4 warps; 5 blocks per SM)
 constexpr int kStageAllMaxK = 128; // most colour groups of the stage-all mode (group order held per block)
 constexpr uint32_t kTagInit = 0x494E4954u;
 constexpr uint32_t kTagDonor = 0x444F4E52u;
