@@ -1,8 +1,8 @@
 // gom_bitplane.cuh -- bit-plane arithmetic shared by the bit-sliced mixing
 // path and Forced Improvement: one 32-bit register holds one bit of 32
 // individuals, so one logic instruction works on 32 trials.  Weighted sums
-// of bit-planes by ripple-carry adders, the signed delta T - 2N of a GOM
-// step, and the per-lane bit-sliced fitness accumulator with its flush into
+// of bit-planes by ripple-carry adders (the signed delta of a GOM step in
+// one chain per edge), and the per-lane bit-sliced fitness accumulator with its flush into
 // the block's fitness accumulators.  Anonymous namespace: each translation
 // unit that includes it compiles its own copy.
 #pragma once
@@ -38,6 +38,26 @@ __device__ __forceinline__ void add_weighted(uint32_t (&acc)[NA], uint32_t x, ui
             acc[t] = a ^ carry;
             carry = a & carry;
         }
+    }
+}
+
+// D += u * pos - u * neg over NP bit-planes, two's complement (pos and neg
+// disjoint; u < 2^UB).  A lane that subtracts adds the complement of u with a
+// carry of one in: its planes are ~u below UB, all ones above (the sign
+// extension), and a lane that adds has u below UB, zero above -- so plane t
+// is (bit t of u ? pos : neg) below UB and neg above, and one ripple-carry
+// chain serves both signs.  The caller keeps every partial sum inside
+// [-2^(NP-1), 2^(NP-1)); the carry out of the top plane is dropped.
+template <int NP, int UB>
+__device__ __forceinline__ void add_signed(uint32_t (&D)[NP], uint32_t pos, uint32_t neg, uint32_t u)
+{
+    uint32_t carry = neg;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+        const uint32_t in = t < UB ? (((u >> t) & 1u) ? pos : neg) : neg;
+        const uint32_t a = D[t];
+        D[t] = a ^ in ^ carry;
+        carry = (a & in) | (a & carry) | (in & carry);
     }
 }
 
@@ -80,36 +100,15 @@ __device__ __forceinline__ void bs_flush(const GomParams &P, BsLane &L, long lon
     L.since_flush = 0;
 }
 
-// delta = T - 2N over R + 2 bit-planes (two's complement), in place in T
-// (T has R + 2 planes, its top two zero on entry).  Returns, as planes, the
-// individuals whose delta is non-zero (*nz) and negative (*neg).
+// Adds the accepted deltas (non-negative and below 2^R: planes 0 .. R - 1 of
+// D, masked by acc) into the lane's fitness accumulator.
 template <int R>
-__device__ __forceinline__ void delta_planes(uint32_t (&T)[R + 2], const uint32_t (&N)[R], uint32_t *nz, uint32_t *neg)
-{
-    uint32_t carry = 0xFFFFFFFFu; // + 1 of the negation
-#pragma unroll
-    for (int t = 0; t < R + 2; ++t) {
-        const uint32_t a = T[t];
-        const uint32_t b = ~((t >= 1 && t - 1 < R) ? N[t - 1] : 0u);
-        T[t] = a ^ b ^ carry;
-        carry = (a & b) | (a & carry) | (b & carry);
-    }
-    uint32_t z = 0;
-#pragma unroll
-    for (int t = 0; t < R + 2; ++t) z |= T[t];
-    *nz = z;
-    *neg = T[R + 1];
-}
-
-// Adds the accepted deltas (non-negative: bits 0 .. R of D, masked by acc)
-// into the lane's fitness accumulator.
-template <int R>
-__device__ __forceinline__ void fit_add(BsLane &L, const uint32_t (&D)[R + 2], uint32_t acc)
+__device__ __forceinline__ void fit_add(BsLane &L, const uint32_t (&D)[R + 1], uint32_t acc)
 {
     uint32_t carry = 0;
 #pragma unroll
     for (int t = 0; t < kFitPlanes; ++t) {
-        const uint32_t in = t <= R ? (D[t] & acc) : 0u;
+        const uint32_t in = t < R ? (D[t] & acc) : 0u;
         const uint32_t a = L.fit[t];
         L.fit[t] = a ^ in ^ carry;
         carry = (a & in) | (a & carry) | (in & carry);

@@ -368,18 +368,19 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     if (L.since_flush >= (1 << (kFitPlanes - R))) bs_flush(P, L, s_f);
     if (kv) {
         const uint32_t *myD = sD + lane * SM, *myO = sO + lane * SM;
-        uint32_t T[R + 2], N[R];
+        // the delta of every trial, R + 1 planes two's complement: an edge that
+        // a trial toggles adds |w| if it was uncut (with its sign folded into
+        // the cut bit), -|w| if it was cut (Eq. 1); no partial sum leaves
+        // (-2^R, 2^R) since the element's sum of |w| is below 2^R
+        uint32_t D[R + 1];
 #pragma unroll
-        for (int t = 0; t < R + 2; ++t) T[t] = 0;
-#pragma unroll
-        for (int t = 0; t < R; ++t) N[t] = 0;
+        for (int t = 0; t <= R; ++t) D[t] = 0;
         uint32_t hd = 0;
         for (int a = 0; a < s; ++a) {
             const uint32_t Fa = myD[a];
             hd |= Fa;
             if (!Fa) continue; // no trial flips variable a: none of its edges changes
             const uint32_t Xa = myO[a];
-            add_weighted<R, R>(T, Fa, (uint32_t)__ldg(P.wabs + f0 + a));
             const int xb = (int)__ldg(P.seg + f0 + q + a), xe = (int)__ldg(P.seg + f0 + q + a + 1);
             for (int x = xb; x < xe; x += 4) { // four edges' loads issued before their arithmetic
                 int2 ed[4];
@@ -390,9 +391,10 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
                 for (int u = 0; u < 4; ++u) Xv[u] = x + u < xe ? P.O[(int64_t)ed[u].x * W + w] : 0u;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const uint32_t S = (uint32_t)(ed[u].y >> 31);
+                    // an outgoing edge toggles wherever a flips
+                    const uint32_t cut = Xa ^ Xv[u] ^ (uint32_t)(ed[u].y >> 31);
                     if (x + u < xe)
-                        add_weighted<R, kWeightBits>(N, Fa & (Xa ^ Xv[u] ^ S), (uint32_t)(ed[u].y < 0 ? -ed[u].y : ed[u].y));
+                        add_signed<R + 1, kWeightBits>(D, Fa & ~cut, Fa & cut, (uint32_t)(ed[u].y < 0 ? -ed[u].y : ed[u].y));
                 }
             }
         }
@@ -401,26 +403,13 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
             const int a = ed.x & 0xFF, b = ed.x >> 8;
             const uint32_t tg = myD[a] ^ myD[b];
             if (!tg) continue; // the edge toggles for no individual
-            const uint32_t c = myO[a] ^ myO[b] ^ (uint32_t)(ed.y >> 31);
-            const uint32_t u = (uint32_t)(ed.y < 0 ? -ed.y : ed.y);
-            add_weighted<R, kWeightBits>(T, tg, u);
-            add_weighted<R, kWeightBits>(N, tg & c, u);
-        }
-        // delta = T - 2N in R + 2 bits (two's complement), in place in T
-        {
-            uint32_t carry = 0xFFFFFFFFu; // + 1 of the negation
-#pragma unroll
-            for (int t = 0; t < R + 2; ++t) {
-                const uint32_t a = T[t];
-                const uint32_t b = ~((t >= 1 && t - 1 < R) ? N[t - 1] : 0u);
-                T[t] = a ^ b ^ carry;
-                carry = (a & b) | (a & carry) | (b & carry);
-            }
+            const uint32_t cut = myO[a] ^ myO[b] ^ (uint32_t)(ed.y >> 31);
+            add_signed<R + 1, kWeightBits>(D, tg & ~cut, tg & cut, (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
         }
         uint32_t nz = 0;
 #pragma unroll
-        for (int t = 0; t < R + 2; ++t) nz |= T[t];
-        const uint32_t neg = T[R + 1];
+        for (int t = 0; t <= R; ++t) nz |= D[t];
+        const uint32_t neg = D[R];
         const uint32_t pos = nz & ~neg;
         const int lim = p - 32 * w;
         const uint32_t vm = lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
@@ -438,15 +427,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
                     P.O[v * W + w] = myO[a] ^ m;
                 }
             }
-            // the accepted deltas (>= 0: their sign plane is clear) into the fitness accumulator
-            uint32_t carry = 0;
-#pragma unroll
-            for (int t = 0; t < kFitPlanes; ++t) {
-                const uint32_t in = t <= R ? (T[t] & acc) : 0u;
-                const uint32_t a = L.fit[t];
-                L.fit[t] = a ^ in ^ carry;
-                carry = (a & in) | (a & carry) | (in & carry);
-            }
+            fit_add<R>(L, D, acc); // the accepted deltas (>= 0, below 2^R)
         }
     }
     ++L.since_flush;

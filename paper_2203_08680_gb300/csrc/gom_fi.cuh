@@ -108,11 +108,9 @@ __device__ __forceinline__ void fi_item(const GomParams &P, int t, int q0, int q
     if (!act) return;
     const int4 h0 = __ldg(P.hdr + 2 * q), h1 = __ldg(P.hdr + 2 * q + 1);
     const int f0 = h0.y, d0 = h0.z, s = h0.w & 0xFF, n_in = h0.w >> 8, n_out = h1.x;
-    uint32_t T[R + 2], N[R];
+    uint32_t D[R + 1]; // the trials' deltas, two's complement (|partial sums| < 2^R)
 #pragma unroll
-    for (int x = 0; x < R + 2; ++x) T[x] = 0;
-#pragma unroll
-    for (int x = 0; x < R; ++x) N[x] = 0;
+    for (int x = 0; x <= R; ++x) D[x] = 0;
     uint32_t hd = 0;
     for (int a = 0; a < s; ++a) {
         const int64_t v = __ldg(P.fv + f0 + a);
@@ -120,12 +118,12 @@ __device__ __forceinline__ void fi_item(const GomParams &P, int t, int q0, int q
         const uint32_t Fa = (Xa ^ (0u - (uint32_t)P.xe[v])) & act;
         hd |= Fa;
         if (!Fa) continue;
-        add_weighted<R, R>(T, Fa, (uint32_t)__ldg(P.wabs + f0 + a));
         const int xb = (int)__ldg(P.seg + f0 + q + a), xe = (int)__ldg(P.seg + f0 + q + a + 1);
         for (int x = xb; x < xe; ++x) {
             const int2 ed = __ldg(P.dep + d0 + x);
             const uint32_t Xv = P.O[(int64_t)ed.x * W + w];
-            add_weighted<R, kWeightBits>(N, Fa & (Xa ^ Xv ^ (uint32_t)(ed.y >> 31)), (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
+            const uint32_t cut = Xa ^ Xv ^ (uint32_t)(ed.y >> 31);
+            add_signed<R + 1, kWeightBits>(D, Fa & ~cut, Fa & cut, (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
         }
     }
     for (int x = n_out; x < n_out + n_in; ++x) {
@@ -135,12 +133,13 @@ __device__ __forceinline__ void fi_item(const GomParams &P, int t, int q0, int q
         const uint32_t Fa = (Xa ^ (0u - (uint32_t)P.xe[va])) & act, Fb = (Xb ^ (0u - (uint32_t)P.xe[vb])) & act;
         const uint32_t tg = Fa ^ Fb;
         if (!tg) continue;
-        const uint32_t u = (uint32_t)(ed.y < 0 ? -ed.y : ed.y);
-        add_weighted<R, kWeightBits>(T, tg, u);
-        add_weighted<R, kWeightBits>(N, tg & (Xa ^ Xb ^ (uint32_t)(ed.y >> 31)), u);
+        const uint32_t cut = Xa ^ Xb ^ (uint32_t)(ed.y >> 31);
+        add_signed<R + 1, kWeightBits>(D, tg & ~cut, tg & cut, (uint32_t)(ed.y < 0 ? -ed.y : ed.y));
     }
-    uint32_t nz, neg;
-    delta_planes<R>(T, N, &nz, &neg);
+    uint32_t nz = 0;
+#pragma unroll
+    for (int x = 0; x <= R; ++x) nz |= D[x];
+    const uint32_t neg = D[R];
     const uint32_t pos = nz & ~neg;
     const uint32_t acc = hd & act & (pos | (~nz & ~P.fi.eq[w]));
     cnt[0] += __popc(act);
@@ -154,7 +153,7 @@ __device__ __forceinline__ void fi_item(const GomParams &P, int t, int q0, int q
             const uint32_t m = (Xa ^ (0u - (uint32_t)P.xe[v])) & acc;
             if (m) P.O[v * W + w] = Xa ^ m;
         }
-        fit_add<R>(L, T, acc);
+        fit_add<R>(L, D, acc);
     }
 }
 
