@@ -317,19 +317,24 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
                 const uint32_t field = fmask << (el * S);
                 // starts exist for individuals < p only (others read candidate 0, and are dropped below)
                 const int st = vi ? sc[el * W * 32] : 0;
-                const uint32_t f1 = (tc[st] ^ xo) & field;
-                if (f1) {
-                    fmw |= f1;
-                } else {
-                    // every candidate from st up to the next run start has st's pattern, the
-                    // parent's; the run start itself differs from it, so it is the donor --
-                    // unless it is the parent's own column (pass B); no run start: no donor
-                    const int d2 = next_run_start(sRS + e2 * W, sNZ[e2], st + 1 == p ? 0 : st + 1);
-                    if (d2 == i)
-                        fails |= 1u << el;
-                    else if (d2 >= 0)
-                        fmw |= (tc[d2] ^ xo) & field;
-                }
+                // every candidate from st up to the next run start d2 has st's pattern; when
+                // that is the parent's, d2 differs from it and is the donor -- unless it is
+                // the parent's own column (pass B); no run start: no donor.  d2 is found
+                // whatever st's pattern (branch-free, all loads issued together)
+                const int x = st + 1 == p ? 0 : st + 1, wx = x >> 5;
+                const uint32_t *rs = sRS + e2 * W;
+                const uint32_t nzm = sNZ[e2];
+                const uint32_t later = nzm & ~((2u << wx) - 1u); // run-start words after wx
+                const uint32_t any = later ? later : nzm;          // else wrap round
+                const int wy = any ? __ffs(any) - 1 : 0;
+                const uint32_t t1 = tc[st], r1 = rs[wx], r2 = rs[wy];
+                const uint32_t m = r1 & (0xFFFFFFFFu << (x & 31));
+                const int d2 = m ? 32 * wx + __ffs(m) - 1 : any ? 32 * wy + __ffs(r2) - 1 : -1;
+                const uint32_t t2 = tc[d2 < 0 ? 0 : d2];
+                const uint32_t f1 = (t1 ^ xo) & field;
+                const uint32_t f2 = d2 >= 0 && d2 != i ? (t2 ^ xo) & field : 0u;
+                fmw |= f1 ? f1 : f2;
+                fails |= !f1 && d2 == i ? 1u << el : 0u;
             }
             if (!vi) fmw = fails = 0;
             for (uint32_t f = fails; f; f &= f - 1) { // pass B, divergent
