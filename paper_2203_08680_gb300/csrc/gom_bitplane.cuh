@@ -1,9 +1,9 @@
 // gom_bitplane.cuh -- bit-plane arithmetic shared by the bit-sliced mixing
 // path and Forced Improvement: one 32-bit register holds one bit of 32
 // individuals, so one logic instruction works on 32 trials.  Weighted sums
-// of bit-planes by ripple-carry adders (the signed delta of a GOM step in
-// one chain per edge), and the per-lane bit-sliced fitness accumulator with its flush into
-// the block's fitness accumulators.  Anonymous namespace: each translation
+// of bit-planes by ripple-carry adders (the signed delta of a GOM step in one
+// chain per edge), and the per-lane bit-sliced fitness accumulator with its
+// flush into the block's fitness accumulators.  Anonymous namespace: each translation
 // unit that includes it compiles its own copy.
 #pragma once
 

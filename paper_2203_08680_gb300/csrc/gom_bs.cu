@@ -74,6 +74,12 @@ __device__ __forceinline__ void transpose32x4(uint32_t (&x)[4])
     }
 }
 
+// Brings the 128-byte line holding *ptr into L2 (a hint: no data returned).
+__device__ __forceinline__ void prefetch_l2(const void *ptr)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 // Word-parallel donor scan over the staged rows (32 candidates per step):
 // the first individual in cyclic order from `start`, skipping `self`, whose
 // generation-start bits on F_j differ from the parent's bits xf; -1 if none.
@@ -200,6 +206,17 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         s = a.w & 0xFF;
         n_in = a.w >> 8;
         n_out = b.x;
+        // the element's edge list and segment offsets are read in phase 2:
+        // ask for their lines in L2 now (the W lanes of the element take every
+        // W-th line; the arrays start on 256-byte boundaries, so every line
+        // named here holds bytes of the array)
+        const uintptr_t d_at = reinterpret_cast<uintptr_t>(P.dep + d0), d_end = d_at + 8u * (uint32_t)(n_out + n_in);
+        for (uintptr_t at = (d_at & ~uintptr_t(127)) + 128u * (uint32_t)w; at < d_end; at += 128u * (uint32_t)W)
+            prefetch_l2(reinterpret_cast<const void *>(at));
+        if (w == 0) {
+            prefetch_l2(P.seg + f0 + q);
+            prefetch_l2(P.seg + f0 + q + s);
+        }
     }
     for (int a4 = 0; a4 < SM; a4 += 4) {
         uint32_t xo[4], xp[4];
