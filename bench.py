@@ -70,8 +70,9 @@ BATCH_WORKLOADS = {
 # autotuner candidates: (warps per block, register budget in resident blocks, grid cap, item cost)
 LEARNED_WORKLOADS = {
     "learned1000": "learned trial filter on the 2D torus 1000x1000 (n=1,000,000), int32 weights U[1,100], pop 256: "
-                   "MLP (16 features, 64 hidden, bf16 weights, fp32 accumulation) trained on the accept/reject "
-                   "log of 50 plain generations, then run to the fitness plain GOM reaches at generation 200",
+                   "MLP (16 features, 64 hidden, bf16 weights, fp32 accumulation) trained on the log of 50 plain "
+                   "generations (label: the element had an improving trial), then run to the fitness plain GOM "
+                   "reaches at generation 200",
 }
 BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300)]
 SEED = 1
@@ -677,9 +678,10 @@ def run_learned(args, wl, rank, world, local):
     ws = torch.empty(gom.gom_filter_workspace_bytes(B.ctx, cap) + 256, dtype=torch.uint8, device=dev)
     ws = ws[(-ws.data_ptr()) % 256:]
     gom.gom_filter_attach(B.ctx, ws, cap)
+    gom.gom_set_option(B.ctx, gom.GOM_OPT_FILTER_LABEL, args.learn_label)
     gom.gom_filter_set_mode(B.ctx, 1)
     (stB1, n1), t1 = timed(lambda: B.generation(warm, target))
-    tr, t2 = timed(lambda: gom.gom_filter_train(B.ctx, epochs=200, learning_rate=0.02, pos_weight=1.0,
+    tr, t2 = timed(lambda: gom.gom_filter_train(B.ctx, epochs=args.learn_epochs, learning_rate=0.02, pos_weight=1.0,
                                                 target_recall=args.learn_recall))
     gom.gom_filter_configure(B.ctx, tr["threshold"], args.learn_recall, args.learn_min_recall)
     gom.gom_filter_set_mode(B.ctx, 2)
@@ -880,8 +882,11 @@ def main():
                     help="default workload: skip the torus100, batch256 and learned1000 keys")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(LEARNED_WORKLOADS))
-    ap.add_argument("--learn-recall", type=float, default=0.9, help="learned filter: recall target")
-    ap.add_argument("--learn-min-recall", type=float, default=0.5, help="learned filter: self-disable recall")
+    ap.add_argument("--learn-recall", type=float, default=0.7, help="learned filter: recall target")
+    ap.add_argument("--learn-min-recall", type=float, default=0.35, help="learned filter: self-disable recall")
+    ap.add_argument("--learn-label", type=int, default=1, choices=[0, 1],
+                    help="learned filter: useful = 0 an accepted trial, 1 an improving trial")
+    ap.add_argument("--learn-epochs", type=int, default=25, help="learned filter: training epochs (full batch)")
     ap.add_argument("--pop", type=int, default=0)
     ap.add_argument("--ttt-gens", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

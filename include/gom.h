@@ -110,6 +110,11 @@ extern "C" {
                             for this many generations, the current one included (0, the default:
                             only individuals without an accepted step) */
 
+#define GOM_OPT_FILTER_LABEL 7 /* learned trial filter: what makes an element's trials of a
+                                  generation useful -- its training label and the unit of its
+                                  recall estimate: 0 (default) an accepted trial, 1 an improving
+                                  trial (a strictly better fitness) */
+
 /* Supported maxima of the library. */
 #define GOM_MAX_POPULATION 1024 /* individuals */
 #define GOM_MAX_ELEMENT 128     /* variables in one FOS element (the paper's largest

@@ -119,6 +119,26 @@ int build_graph(gom_ctx *ctx, bool timed, cudaGraph_t *out_graph, cudaGraphExec_
         last = node;
         e = add_kernel(g, &node, last, (const void *)k_order, ctx->grid_order, 256, ctx->order_smem, args1);
     }
+    // the learned filter's select phase: decisions, and for the bit-sliced
+    // path while it skips, the compacted list of the elements to run
+    int compact = prm.learn == 2 && prm.flt.compact ? 1 : 0;
+    int sel_warps = 0;
+    const int sel_grid = std::max(1, ctx->sms * 8); // 64 warps per SM: the size of the count array
+    if (e == cudaSuccess && prm.learn) {
+        void *argsS[] = {&prm, &compact};
+        last = node;
+        e = add_kernel(g, &node, last, (const void *)k_filter_select, sel_grid, 256, 0, argsS);
+        sel_warps = sel_grid * 8;
+        if (e == cudaSuccess && compact) {
+            void *argsC[] = {&prm, &sel_warps};
+            last = node;
+            e = add_kernel(g, &node, last, (const void *)k_filter_scan, 1, 1024, 0, argsC);
+            if (e == cudaSuccess) {
+                last = node;
+                e = add_kernel(g, &node, last, (const void *)k_filter_compact, sel_grid, 256, 0, args1);
+            }
+        }
+    }
     std::vector<int> ts(ctx->k);
     for (int t = 0; t < ctx->k && e == cudaSuccess; ++t) {
         last = node;
@@ -193,6 +213,10 @@ int accumulate_timing(gom_ctx *ctx)
 // copy (the timed variant only if it exists).  Waits for the stream.
 int rebuild_graphs(gom_ctx *ctx)
 {
+    // the learned filter's counting unit and list mode follow the mixing path in use
+    ctx->prm.flt.compact = use_bs(ctx) ? 1 : 0;
+    ctx->prm.flt.items_per_elem =
+        use_bs(ctx) || !ctx->prm.split ? 1 : (ctx->prm.Wv + ctx->wpi - 1) / std::max(ctx->wpi, 1);
     GOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const bool had_timed = ctx->texec != nullptr;
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
@@ -510,17 +534,23 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
             const int wpb = static_cast<int>(std::min<int64_t>(kBsThreads / 32, kSmemBudget / (ww * 4)));
             // the block's fitness accumulators (32 W int64), then the warps' regions
             const size_t smem = std::max(static_cast<size_t>(256 * c->W + ww * 4 * wpb), keys_smem);
-            const void *rf = gom_run_bs_kernel(R), *mf = gom_mix_bs_kernel(R);
-            if (wpb >= 1 && smem <= static_cast<size_t>(kSmemBudget) && rf && mf) {
+            // the kernels without the learned filter's code, and with it (same grids)
+            const void *rf = gom_run_bs_kernel(R, false), *mf = gom_mix_bs_kernel(R, false);
+            const void *rfl = gom_run_bs_kernel(R, true), *mfl = gom_mix_bs_kernel(R, true);
+            if (wpb >= 1 && smem <= static_cast<size_t>(kSmemBudget) && rf && mf && rfl && mfl) {
                 const int E = 32 / c->W;
                 const int64_t items = (max_group + E - 1) / E;
                 const int64_t need = std::max<int64_t>(1, (items + wpb - 1) / wpb);
-                GOM_CUDA(c, raise_smem_limit(rf, smem));
-                GOM_CUDA(c, raise_smem_limit(mf, smem));
-                int occ_r = 0, occ_m = 0;
+                for (const void *fn : {rf, mf, rfl, mfl}) GOM_CUDA(c, raise_smem_limit(fn, smem));
+                int occ_r = 0, occ_m = 0, occ_rl = 0, occ_ml = 0;
                 GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_r, rf, 32 * wpb, smem));
                 GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_m, mf, 32 * wpb, smem));
+                GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rl, rfl, 32 * wpb, smem));
+                GOM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ml, mfl, 32 * wpb, smem));
+                occ_r = std::min(occ_r, occ_rl);
+                occ_m = std::min(occ_m, occ_ml);
                 if (occ_r > 0 && occ_m > 0) {
+                    c->bs_r = R;
                     c->bs_ok = true;
                     c->run_bs_fn = rf;
                     c->mix_bs_fn = mf;
@@ -843,6 +873,11 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
         ctx->prm.fi.nis = static_cast<int32_t>(value);
         return rebuild_graphs(ctx);
     }
+    if (option == GOM_OPT_FILTER_LABEL) {
+        if (value < 0 || value > 1) return GOM_E_ARG;
+        ctx->prm.flt.label = static_cast<int32_t>(value);
+        return rebuild_graphs(ctx);
+    }
     return GOM_E_ARG;
 }
 
@@ -871,6 +906,10 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value)
     }
     if (option == GOM_OPT_FI_NIS) {
         *value = ctx->prm.fi.nis;
+        return GOM_OK;
+    }
+    if (option == GOM_OPT_FILTER_LABEL) {
+        *value = ctx->prm.flt.label;
         return GOM_OK;
     }
     return GOM_E_ARG;

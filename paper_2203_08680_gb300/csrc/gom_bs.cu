@@ -43,6 +43,7 @@
 #include "gom_bitplane.cuh"
 #include "gom_device.cuh"
 #include "gom_fi.cuh"
+#include "gom_filter_dev.cuh"
 #include "gom_internal.h"
 #include "gom_kernels.cuh"
 
@@ -180,25 +181,76 @@ __device__ __forceinline__ uint32_t *bs_warp_region(const GomParams &P, uint32_t
     return s_dyn + 64 * P.W + (threadIdx.x >> 5) * P.bs_words;
 }
 
-// One item of colour group c at position t: elements [q0, q1) (at most E)
-// with every word, all trials of Alg. 2.
-template <int R>
-__device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint32_t g, uint32_t *wsm, BsLane &L,
-                                        long long *s_f)
+// Learned filter bookkeeping after a bit-sliced item (warp-wide): each
+// element's accepted, donor-less and improving trials (summed over its W
+// lanes) into this generation's history, the block's item counters s_fc (run,
+// useful, audited, audited and useful; one item per element on this path),
+// and for the elements the sampling hash picks a training sample -- the
+// features as the select phase saw them, label: the element was useful (an
+// accepted trial, or with P.flt.label an improving one).
+__device__ __noinline__ void bs_record(const GomParams &P, int q, bool ke, bool audited, uint32_t g, unsigned acc,
+                                       unsigned dl, unsigned imp, unsigned long long *s_fc)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = P.W, lw = __ffs(W) - 1, E = 32 >> lw;
+    for (int off = 1; off < W; off <<= 1) {
+        acc += __shfl_xor_sync(kFull, acc, off);
+        dl += __shfl_xor_sync(kFull, dl, off);
+        imp += __shfl_xor_sync(kFull, imp, off);
+    }
+    const bool useful = P.flt.label ? imp != 0 : acc != 0;
+    if (ke && (lane & (W - 1)) == 0) {
+        uint32_t *cur = P.flt.hist + (size_t)(g & 1) * 3 * (size_t)P.m;
+        cur[q] = acc;
+        cur[P.m + q] = dl;
+        cur[2 * (size_t)P.m + q] = imp;
+        atomicAdd(&s_fc[0], 1ull);
+        if (useful) atomicAdd(&s_fc[1], 1ull);
+        if (audited) atomicAdd(&s_fc[2], 1ull);
+        if (audited && useful) atomicAdd(&s_fc[3], 1ull);
+    }
+    for (int e2 = 0; e2 < E; ++e2) {
+        const int src = e2 << lw;
+        const int q2 = __shfl_sync(kFull, q, src);
+        const bool ok = __shfl_sync(kFull, ke ? 1 : 0, src) != 0;
+        const bool u2 = __shfl_sync(kFull, useful ? 1 : 0, src) != 0;
+        if (ok && filter_sample(q2, g)) {
+            float x[kFilterIn];
+            filter_features(P, q2, g, x);
+            filter_log_sample(P, x, u2);
+        }
+    }
+    __syncwarp();
+}
+
+// One item of colour group c at position t: entries [k0, k1) (at most E) of
+// the group's elements -- positions k0 .. k1 - 1, or with the learned filter
+// skipping, the positions qlist[k0 .. k1) of the compacted list -- with every
+// word, all trials of Alg. 2.
+template <int R, bool LEARN>
+__device__ __forceinline__ void bs_item(const GomParams &P, const int32_t *qlist, int k0, int k1, uint32_t g,
+                                        uint32_t *wsm, BsLane &L, long long *s_f, unsigned long long *s_fc)
 {
     const int lane = threadIdx.x & 31;
     const int W = P.W, Wv = P.Wv, p = P.p, SM = P.bs_sm;
     const int lw = __ffs(W) - 1;
     const int e = lane >> lw, w = lane & (W - 1);
-    const int q = q0 + e;
-    const bool kv = q < q1 && w < Wv; // this lane's pair exists
+    const bool ke = k0 + e < k1; // this lane's element exists
+    int q = k0 + e;
+    bool audited = false;
+    if (LEARN && qlist && ke) {
+        const int32_t en = qlist[k0 + e];
+        q = en & 0x7FFFFFFF;
+        audited = en < 0;
+    }
+    const bool kv = ke && w < Wv; // this lane's pair exists
     uint32_t *sO = wsm, *sP = wsm + 32 * SM, *sD = wsm + 64 * SM;
     uint16_t *sStart = reinterpret_cast<uint16_t *>(wsm + 96 * SM); // p <= 1024: a start fits 16 bits
     uint32_t *sRS = wsm + 96 * SM + 16 * 32;
 
     // ---- phase 0: the pair's rows, run starts, donor starts
     int j = 0, s = 0, f0 = 0, d0 = 0, n_in = 0, n_out = 0;
-    if (q < q1) {
+    if (ke) {
         const int4 a = __ldg(P.hdr + 2 * q), b = __ldg(P.hdr + 2 * q + 1);
         j = a.x;
         f0 = a.y;
@@ -323,7 +375,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         const bool vi = i < p;
         for (int c = 0; c < NC; ++c) {
             const uint32_t xo = tabO[(c * W + w2) * 32 + lane]; // the parents' current patterns
-            const int ne = min(EPW, min(E, q1 - q0) - c * EPW); // elements of this chunk in the item
+            const int ne = min(EPW, min(E, k1 - k0) - c * EPW); // elements of this chunk in the item
             const uint32_t *tc = tabP + c * W * 32;             // chunk c's patterns, by individual
             const uint16_t *sc = sStart + (c * EPW * W + w2) * 32 + lane;
             uint32_t fmw = 0, fails = 0;
@@ -386,6 +438,7 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     __syncwarp();
 
     // ---- phase 2: bit-plane partial evaluation, acceptance, write, lane = pair
+    unsigned i_acc = 0, i_dl = 0, i_imp = 0; // this pair's accepted, donor-less and improving trials
     // each item adds less than 2^R to an individual's sum: flush before it could pass 2^kFitPlanes
     if (L.since_flush >= (1 << (kFitPlanes - R))) bs_flush(P, L, s_f);
     if (kv) {
@@ -437,9 +490,12 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
         const uint32_t vm = lim >= 32 ? 0xFFFFFFFFu : ((1u << lim) - 1u);
         const uint32_t eqv = P.eqw[(g & 1) * W + w];
         const uint32_t acc = hd & vm & (pos | (~nz & ~eqv));
-        L.n_acc += __popc(acc);
-        L.n_imp += __popc(acc & pos);
-        L.n_dl += __popc(vm & ~hd);
+        i_acc = __popc(acc);
+        i_imp = __popc(acc & pos);
+        i_dl = __popc(vm & ~hd);
+        L.n_acc += i_acc;
+        L.n_imp += i_imp;
+        L.n_dl += i_dl;
         if (P.fi.on && acc) atomicOr(&P.fi.accw[w], acc); // Forced Improvement: who had an accepted step
         if (acc) {
             for (int a = 0; a < s; ++a) {
@@ -454,26 +510,30 @@ __device__ __forceinline__ void bs_item(const GomParams &P, int q0, int q1, uint
     }
     ++L.since_flush;
     __syncwarp();
+    if (LEARN && P.learn) bs_record(P, q, ke, audited, g, i_acc, i_dl, i_imp, s_fc);
 }
 
 // One colour group (position t, colour c) on the bit-sliced path: items of
-// E = 32 / W consecutive elements of the group; warp x takes item x, then
-// items nwarps + the claims it draws from work[t] (P.dyn), one ahead, or
-// x + nwarps, x + 2 nwarps, ... (static stride).
-template <int R>
+// E = 32 / W consecutive elements of the group -- of the compacted list of the
+// elements to run while the learned filter skips elements; warp x takes item
+// x, then items nwarps + the claims it draws from work[t] (P.dyn), one ahead,
+// or x + nwarps, x + 2 nwarps, ... (static stride).
+template <int R, bool LEARN>
 __device__ void phase_mix_bs(const GomParams &P, const VGrid &V, int t, int c, uint32_t g, uint32_t *wsm, BsLane &L,
-                             long long *s_f)
+                             long long *s_f, unsigned long long *s_fc)
 {
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)(V.thread() >> 5), nwarps = (int)(V.threads() >> 5);
     const int E = 32 / P.W;
-    const int qa = P.cptr[c], qz = P.cptr[c + 1];
-    const int items = (qz - qa + E - 1) / E;
+    const bool cl = LEARN && P.learn == 2 && P.flt.compact;
+    const int32_t *qlist = cl ? P.flt.act : nullptr;
+    const int ka = cl ? P.flt.act_ptr[c] : P.cptr[c], kz = cl ? P.flt.act_ptr[c + 1] : P.cptr[c + 1];
+    const int items = (kz - ka + E - 1) / E;
     unsigned claim = 0;
     if (P.dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     for (int it = gwarp, next = gwarp + nwarps; it < items;) {
-        const int q0 = qa + it * E;
-        bs_item<R>(P, q0, min(q0 + E, qz), g, wsm, L, s_f);
+        const int k0 = ka + it * E;
+        bs_item<R, LEARN>(P, qlist, k0, min(k0 + E, kz), g, wsm, L, s_f, s_fc);
         if (P.dyn) {
             it = nwarps + (int)__shfl_sync(0xFFFFFFFFu, claim, 0);
             if (it < items && lane == 0) claim = atomicAdd(&P.work[t], 1u);
@@ -500,11 +560,11 @@ __device__ __forceinline__ void bs_finish_generation(const GomParams &P, BsLane 
 // computes a generation's end from the fitness array after the barrier that
 // closes its last group (block 0 records it).  The dynamic shared memory
 // holds the warps' regions (the k group keys of the order phase overlay them).
-template <int R>
+template <int R, bool LEARN>
 __global__ void __launch_bounds__(kBsThreads, 5) k_run_bs(GomParams P, int G, int64_t target)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    __shared__ unsigned long long s_cnt[4];
+    __shared__ unsigned long long s_cnt[4], s_fc[4];
     long long *s_f = reinterpret_cast<long long *>(s_dyn);
     const VGrid V = whole_grid();
     const unsigned nblk = (unsigned)V.nblk;
@@ -527,18 +587,22 @@ __global__ void __launch_bounds__(kBsThreads, 5) k_run_bs(GomParams P, int G, in
         if (tr) P.trace[0] = global_ns();
         phase_gen_start(P, V, e.improved, e.argmax, g, true);
         phase_order(P, V, reinterpret_cast<unsigned long long *>(s_dyn), g);
+        fc_zero(s_fc);
         acc_zero(P, s_f, s_cnt);
         if (tr) P.trace[1] = P.trace[2] = global_ns();
         if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        if (LEARN && P.learn && !phase_filter_select(P, V, g, &bar->count, nblk, bnext, P.learn == 2 && P.flt.compact))
+            return;
         if (tr) P.trace[3] = global_ns();
         for (int t = 0; t < P.k; ++t) {
             if (t > 0 && !grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
             if (tr) P.trace[4 + 2 * t] = global_ns();
-            phase_mix_bs<R>(P, V, t, P.order[t], g, wsm, L, s_f);
+            phase_mix_bs<R, LEARN>(P, V, t, P.order[t], g, wsm, L, s_f, s_fc);
             if (tr) P.trace[5 + 2 * t] = global_ns();
         }
         bs_finish_generation(P, L, s_f, s_cnt);
         acc_flush(P, s_f, s_cnt);
+        if (LEARN) fc_flush(P, s_fc);
         if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
         if (P.fi.on && !fi_generation<R>(P, V, &bar->count, nblk, bnext, e, P.order, s_f, s_cnt)) return;
         if (tr) P.trace[4 + 2 * P.k] = global_ns();
@@ -549,20 +613,22 @@ __global__ void __launch_bounds__(kBsThreads, 5) k_run_bs(GomParams P, int G, in
 
 // Per-launch path: the mixing of the group at position t (one launch per
 // group in the per-generation CUDA graph).
-template <int R>
+template <int R, bool LEARN>
 __global__ void __launch_bounds__(kBsThreads, 5) k_mix_bs(GomParams P, int t)
 {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    __shared__ unsigned long long s_cnt[4];
+    __shared__ unsigned long long s_cnt[4], s_fc[4];
     long long *s_f = reinterpret_cast<long long *>(s_dyn);
     if (P.st->done) return;
+    fc_zero(s_fc);
     acc_zero(P, s_f, s_cnt);
     BsLane L;
     bs_lane_zero(L);
     uint32_t *wsm = bs_warp_region(P, s_dyn);
-    phase_mix_bs<R>(P, whole_grid(), t, P.order[t], P.st->g, wsm, L, s_f);
+    phase_mix_bs<R, LEARN>(P, whole_grid(), t, P.order[t], P.st->g, wsm, L, s_f, s_fc);
     bs_finish_generation(P, L, s_f, s_cnt);
     acc_flush(P, s_f, s_cnt);
+    if (LEARN) fc_flush(P, s_fc);
 }
 
 // Forced Improvement on the per-launch path (one CUDA graph per
@@ -642,12 +708,14 @@ const void *gom_fi_kernel(int which, int r)
 
 int gom_bs_warp_words(int sm, int nc, int w) { return bs_warp_words(sm, nc, w); }
 
-const void *gom_run_bs_kernel(int r)
+const void *gom_run_bs_kernel(int r, bool learn)
 {
-    return r <= 12 ? (const void *)k_run_bs<12> : r <= 16 ? (const void *)k_run_bs<16> : nullptr;
+    if (learn) return r <= 12 ? (const void *)k_run_bs<12, true> : r <= 16 ? (const void *)k_run_bs<16, true> : nullptr;
+    return r <= 12 ? (const void *)k_run_bs<12, false> : r <= 16 ? (const void *)k_run_bs<16, false> : nullptr;
 }
 
-const void *gom_mix_bs_kernel(int r)
+const void *gom_mix_bs_kernel(int r, bool learn)
 {
-    return r <= 12 ? (const void *)k_mix_bs<12> : r <= 16 ? (const void *)k_mix_bs<16> : nullptr;
+    if (learn) return r <= 12 ? (const void *)k_mix_bs<12, true> : r <= 16 ? (const void *)k_mix_bs<16, true> : nullptr;
+    return r <= 12 ? (const void *)k_mix_bs<12, false> : r <= 16 ? (const void *)k_mix_bs<16, false> : nullptr;
 }

@@ -25,8 +25,9 @@ struct gom_ctx {
     bool persistent = false;      // current path: k_run (true) or the per-generation graph
     // the bit-sliced mixing path (gom_bs.cu), where the FOS and weights allow it
     bool bs_ok = false;           // available for this context
-    bool bs_on = false;           // selected (GOM_OPT_BITSLICED); used while the learned filter is off
-    const void *run_bs_fn = nullptr, *mix_bs_fn = nullptr;
+    bool bs_on = false;           // selected (GOM_OPT_BITSLICED)
+    const void *run_bs_fn = nullptr, *mix_bs_fn = nullptr; // the instances for the learned filter's mode
+    int bs_r = 0;                 // their accumulator width R
     size_t bs_smem = 0;           // dynamic shared memory of both (warp regions, group keys)
     int bs_threads = 0;           // their block size
     int bs_grid_run = 0, bs_grid_mix = 0;
@@ -62,9 +63,9 @@ struct gom_ctx {
 };
 
 
-// The bit-sliced path runs the context's generations (selected, and the
-// learned filter's kernel instances not in use).
-inline bool use_bs(const gom_ctx *ctx) { return ctx->bs_on && ctx->prm.learn == 0; }
+// The bit-sliced path runs the context's generations (selected and
+// available; the learned filter works on either path).
+inline bool use_bs(const gom_ctx *ctx) { return ctx->bs_on; }
 
 inline int cuda_fail(gom_ctx *ctx, cudaError_t e)
 {

@@ -189,7 +189,8 @@ __device__ bool grid_barrier(unsigned long long *count, int *err, unsigned nblk,
 }
 
 // Generation start (Alg. 3): P <- O (skipped with copy = false, when every
-// item's generation-start data is staged from O before anything is written),
+// item's generation-start data is staged from O before anything is written;
+// with the learned filter on, the change marks of the generation before),
 // the new elitist copied out of O[argmax] when it changed, the elitist flags
 // eqw[g mod 2] (P[i] == x_e over all variables), the other buffer set for
 // generation g+1, and the item claim counters zeroed.
@@ -219,9 +220,20 @@ __device__ void phase_gen_start(const GomParams &P, const VGrid &V, int improved
         if (tid < FC_N) P.flt.st->cnt[tid] = 0;
     }
     uint32_t eq = kFull;
+    // the learned filter's change marks: variable v changed in some individual
+    // during generation g - 1 (O now against P, its start; none before the
+    // first generation).  The W words of v sit in W consecutive lanes of one
+    // warp, and a warp's active lanes in the last round are whole such groups.
+    const bool marks = P.learn && copy;
     for (int64_t idx = tid; idx < total; idx += nth) {
         const int64_t v = idx >> lw;
         const uint32_t word = P.O[idx];
+        if (marks) {
+            uint32_t ch = g > 0 ? word ^ P.P[idx] : 0u;
+            const unsigned am = __activemask();
+            for (int off = 1; off < W; off <<= 1) ch |= __shfl_xor_sync(am, ch, off);
+            if (w == 0) P.flt.dirty[v] = ch != 0;
+        }
         if (copy) P.P[idx] = word;
         uint32_t xb;
         if (improved) {
@@ -298,7 +310,8 @@ struct GenEnd {
 // into last/total, then, with at least 16 audits, the recall estimate --
 // useful items run / (useful items run + skipped items x the useful fraction
 // of the audited ones).  The threshold steps down (skip less) while the
-// estimate is under target_recall and up while it is well over it; two
+// estimate is under target_recall and up while it is well over it, and up
+// too while the filter skips too little to be audited 16 times; two
 // generations in a row under min_recall turn the filter off, and the run goes
 // on as plain GOM.
 __device__ void filter_generation_end(const GomParams &P, uint32_t g)
@@ -322,6 +335,8 @@ __device__ void filter_generation_end(const GomParams &P, uint32_t g)
             st->enabled = 0;
             st->disabled_at = (int32_t)g;
         }
+    } else if (P.learn == 2 && st->enabled) {
+        st->threshold += 0.125f; // too few audits to estimate the recall: skip a little more
     }
 }
 

@@ -25,11 +25,16 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets inside the filter workspace.
 struct FilterLayout {
-    size_t st, hist, skipped, w1, w2, theta, adam_m, adam_v, grad, loss, log_x, log_y, logit, total;
+    size_t st, hist, skipped, w1, w2, theta, adam_m, adam_v, grad, loss, log_x, log_y, logit;
+    size_t dirty, quiet, dec, act, act_ptr, wcnt, total;
 };
 
-FilterLayout filter_layout(int64_t m, int64_t cap)
+// The select phase's warps: at most 64 resident warps per SM in any launch.
+int64_t select_warps_cap(const gom_ctx *ctx) { return 64 * static_cast<int64_t>(ctx->sms); }
+
+FilterLayout filter_layout(const gom_ctx *ctx, int64_t cap)
 {
+    const int64_t m = ctx->m;
     FilterLayout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -50,6 +55,12 @@ FilterLayout filter_layout(int64_t m, int64_t cap)
     L.log_x = take(sizeof(uint16_t) * kFilterIn * static_cast<size_t>(cap));
     L.log_y = take(static_cast<size_t>(cap));
     L.logit = take(sizeof(float) * static_cast<size_t>(cap));
+    L.dirty = take(static_cast<size_t>(ctx->n));
+    L.quiet = take(static_cast<size_t>(m));
+    L.dec = take(static_cast<size_t>(m));
+    L.act = take(sizeof(int32_t) * static_cast<size_t>(m));
+    L.act_ptr = take(sizeof(int32_t) * static_cast<size_t>(ctx->k + 1));
+    L.wcnt = take(sizeof(uint32_t) * static_cast<size_t>(select_warps_cap(ctx)));
     L.total = off;
     return L;
 }
@@ -152,28 +163,25 @@ __global__ void k_filter_bf16(const float *theta, uint16_t *w1, uint16_t *w2)
         w2[i - kNW1 - kFilterHidden] = __bfloat16_as_ushort(__float2bfloat16_rn(theta[i]));
 }
 
-// Logit of every logged sample, with the bf16 weights the mixing kernels use
-// and the same summation order (two units per lane, fixed-order warp sum).
+// Logit of every logged sample, with the bf16 weights the select phase uses
+// and its summation order (one thread per sample: unit h's sum over k from
+// its bias, then the output's sum over h from zero, then the output bias).
 __global__ void k_filter_eval(const uint16_t *X, int64_t N, const uint16_t *w1, const float *theta,
                               const uint16_t *w2, float *logit)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float *b1 = theta + kNW1, *b2 = theta + kNW1 + 2 * kFilterHidden;
-    for (int64_t n = warp; n < N; n += nwarps) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
         float x[kFilterIn];
 #pragma unroll
         for (int k = 0; k < kFilterIn; ++k) x[k] = bf16_bits(X[n * kFilterIn + k]);
-        float part = 0.f;
-        for (int h = lane; h < kFilterHidden; h += 32) {
+        float out = 0.f;
+        for (int h = 0; h < kFilterHidden; ++h) {
             float z = b1[h];
 #pragma unroll
             for (int k = 0; k < kFilterIn; ++k) z = fmaf(bf16_bits(w1[h * kFilterIn + k]), x[k], z);
-            part = fmaf(bf16_bits(w2[h]), fmaxf(z, 0.f), part);
+            out = fmaf(bf16_bits(w2[h]), fmaxf(z, 0.f), out);
         }
-        for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
-        if (lane == 0) logit[n] = part + b2[0];
+        logit[n] = out + b2[0];
     }
 }
 
@@ -202,13 +210,13 @@ extern "C" {
 size_t gom_filter_workspace_bytes(gom_ctx_t *ctx, int64_t log_capacity)
 {
     if (!ctx || log_capacity < 0) return 0;
-    return filter_layout(ctx->m, log_capacity).total;
+    return filter_layout(ctx, log_capacity).total;
 }
 
 int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_t log_capacity)
 {
     if (!ctx || log_capacity < 0) return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, log_capacity);
+    const FilterLayout L = filter_layout(ctx, log_capacity);
     if (!d_workspace || ws_bytes < L.total || reinterpret_cast<uintptr_t>(d_workspace) % kAlign)
         return GOM_E_WORKSPACE;
     char *base = static_cast<char *>(d_workspace);
@@ -224,6 +232,12 @@ int gom_filter_attach(gom_ctx_t *ctx, void *d_workspace, size_t ws_bytes, int64_
     F.log_x = reinterpret_cast<uint16_t *>(base + L.log_x);
     F.log_y = reinterpret_cast<uint8_t *>(base + L.log_y);
     F.log_cap = log_capacity;
+    F.dirty = reinterpret_cast<uint8_t *>(base + L.dirty);
+    F.quiet = reinterpret_cast<uint8_t *>(base + L.quiet);
+    F.dec = reinterpret_cast<uint8_t *>(base + L.dec);
+    F.act = reinterpret_cast<int32_t *>(base + L.act);
+    F.act_ptr = reinterpret_cast<int32_t *>(base + L.act_ptr);
+    F.wcnt = reinterpret_cast<uint32_t *>(base + L.wcnt);
     ctx->filter_base = base;
     ctx->filter_cap = log_capacity;
     GomFilterState st{};
@@ -243,7 +257,8 @@ int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode)
 {
     if (!ctx || mode < 0 || mode > 2) return GOM_E_ARG;
     if (mode > 0 && !ctx->filter_base) return GOM_E_STATE;
-    if (mode == 2 && ctx->prm.stage_all && ctx->persistent) return GOM_E_STATE;
+    // the change marks compare O with P, which the stage-all mode does not keep
+    if (mode > 0 && ctx->prm.stage_all && ctx->persistent) return GOM_E_STATE;
     // the kernel instances with (or without) the filter's bookkeeping, on the same grids
     const bool learn = mode > 0;
     const void *mix = gom_mix_kernel(ctx->wpi, ctx->variant, learn);
@@ -264,6 +279,10 @@ int gom_filter_set_mode(gom_ctx_t *ctx, int32_t mode)
     }
     ctx->mix_fn = mix;
     ctx->run_fn = run;
+    if (ctx->bs_ok) { // the bit-sliced instances with (or without) the filter's select phase and bookkeeping
+        ctx->run_bs_fn = gom_run_bs_kernel(ctx->bs_r, learn);
+        ctx->mix_bs_fn = gom_mix_bs_kernel(ctx->bs_r, learn);
+    }
     ctx->prm.learn = mode;
     return rebuild_graphs(ctx);
 }
@@ -290,7 +309,7 @@ int gom_filter_train(gom_ctx_t *ctx, int32_t epochs, float learning_rate, float 
     if (!ctx || !ctx->filter_base || epochs < 1 || !(learning_rate > 0.f) || !(pos_weight > 0.f) ||
         !(target_recall > 0.f && target_recall <= 1.f))
         return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     cudaStream_t s = ctx->stream;
     GomFilterState st{};
@@ -394,7 +413,7 @@ int gom_filter_stats(gom_ctx_t *ctx, gom_filter_stats_t *out)
 int gom_filter_get_params(gom_ctx_t *ctx, float *theta, float *adam_m, float *adam_v, float *grad)
 {
     if (!ctx || !ctx->filter_base) return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     const size_t bytes = sizeof(float) * kNTheta;
     if (theta) GOM_CUDA(ctx, cudaMemcpyAsync(theta, base + L.theta, bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -408,7 +427,7 @@ int gom_filter_get_params(gom_ctx_t *ctx, float *theta, float *adam_m, float *ad
 int gom_filter_set_params(gom_ctx_t *ctx, const float *theta, const float *adam_m, const float *adam_v)
 {
     if (!ctx || !ctx->filter_base || !theta) return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     cudaStream_t s = ctx->stream;
     const size_t bytes = sizeof(float) * kNTheta;
@@ -429,7 +448,7 @@ int gom_filter_set_params(gom_ctx_t *ctx, const float *theta, const float *adam_
 int gom_filter_epoch(gom_ctx_t *ctx, float learning_rate, float pos_weight, int32_t step, double *loss)
 {
     if (!ctx || !ctx->filter_base || !(learning_rate > 0.f) || !(pos_weight > 0.f) || step < 1) return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     cudaStream_t s = ctx->stream;
     GomFilterState st{};
@@ -462,7 +481,7 @@ int gom_filter_epoch(gom_ctx_t *ctx, float learning_rate, float pos_weight, int3
 int gom_filter_log(gom_ctx_t *ctx, int64_t max, uint16_t *x, uint8_t *y, int64_t *n)
 {
     if (!ctx || !ctx->filter_base || max < 0 || !n) return GOM_E_ARG;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     GomFilterState st{};
     GOM_CUDA(ctx, cudaMemcpyAsync(&st, ctx->prm.flt.st, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
@@ -481,7 +500,7 @@ int gom_filter_logits(gom_ctx_t *ctx, int64_t n, float *logits)
 {
     if (!ctx || !ctx->filter_base || n < 0 || (n > 0 && !logits) || n > ctx->filter_cap) return GOM_E_ARG;
     if (n == 0) return GOM_OK;
-    const FilterLayout L = filter_layout(ctx->m, ctx->filter_cap);
+    const FilterLayout L = filter_layout(ctx, ctx->filter_cap);
     char *base = ctx->filter_base;
     cudaStream_t s = ctx->stream;
     float *d_logit = reinterpret_cast<float *>(base + L.logit);

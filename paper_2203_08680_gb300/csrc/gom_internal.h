@@ -142,8 +142,19 @@ struct GomFilter {
     const uint16_t *w2;   // [64] bf16 bits
     const float *b2;      // [1]
     uint16_t *log_x;      // [cap][16] bf16 features
-    uint8_t *log_y;       // [cap] label: the item accepted at least one trial
+    uint8_t *log_y;       // [cap] label: the item was useful (see label)
     int64_t log_cap;
+    uint8_t *dirty;       // [n] 1: the variable changed in some individual during the previous generation
+    uint8_t *quiet;       // [m] generations in a row (saturating at 255) an element had no accepted trial
+                          //   and no change in its variables or outside neighbours
+    uint8_t *dec;         // [m] the select phase's decision per position (DEC_RUN / DEC_SKIP / DEC_AUDIT)
+    int32_t *act;         // [m] positions to run, in order (bit 31: audited); bit-sliced path
+    int32_t *act_ptr;     // [k + 1] colour c's part of act: [act_ptr[c], act_ptr[c + 1])
+    uint32_t *wcnt;       // [select warps] elements to run per select warp, then their first slots
+    int32_t items_per_elem; // mixing items of one element (the unit of the filter's item counters)
+    int32_t compact;      // 1: the bit-sliced mixing runs the compacted list while the filter skips
+    int32_t label;        // what makes an element useful (its training label): 0 an accepted trial, 1 an
+                          //   improving trial
 };
 
 struct GomDevStats { // mirrors gom_gen_stats_t

@@ -22,6 +22,7 @@
 
 #include "gom_device.cuh"
 #include "gom_fi.cuh"
+#include "gom_filter_dev.cuh"
 #include "gom_internal.h"
 #include "gom_kernels.cuh"
 
@@ -366,101 +367,21 @@ __device__ __forceinline__ void stage_draws(const GomParams &P, uint32_t *sl, ui
 }
 
 // ----------------------------------------------------------------------------
-// Learned trial filter.  Features of the element at position q for
-// generation g (the same in every lane): its size and edge counts, its
-// accepted / donor-less / improving trials of the previous generation (as
-// fractions of p), whether it accepted nothing or had no donor at all, the
-// generation, the population's accept / improve / donor-less rates of the
-// previous generation, and a constant.
-__device__ __forceinline__ float bf16_bits_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
-
-__device__ __forceinline__ void filter_features(const GomParams &P, int q, uint32_t g, float (&x)[kFilterIn])
-{
-    const int4 a = P.hdr[2 * q], b = P.hdr[2 * q + 1];
-    const int s = a.w & 0xFF, n_in = a.w >> 8, n_out = b.x;
-    const float inv_p = 1.f / (float)P.p;
-    const uint32_t *prev = P.flt.hist + (size_t)((g + 1) & 1) * 3 * (size_t)P.m;
-    const uint32_t acc = prev[q], dl = prev[P.m + q], imp = prev[2 * (size_t)P.m + q];
-    x[0] = (float)s / 16.f;
-    x[1] = (float)n_out / 64.f;
-    x[2] = (float)n_in / 32.f;
-    x[3] = (float)acc * inv_p;
-    x[4] = (float)dl * inv_p;
-    x[5] = (float)imp * inv_p;
-    x[6] = acc == 0 ? 1.f : 0.f;
-    x[7] = dl >= (uint32_t)P.p ? 1.f : 0.f;
-    x[8] = log2f(1.f + (float)g) / 16.f;
-    x[9] = x[10] = x[11] = 0.f;
-    if (g > 0) {
-        const GomDevStats &S = P.stats[(g - 1) % kStatsCap];
-        const float tr = (float)S.trials;
-        x[9] = (float)S.accepted / tr;
-        x[10] = (float)S.improving / tr;
-        x[11] = (float)S.donorless / tr;
-    }
-    x[12] = 1.f;
-    x[13] = x[14] = x[15] = 0.f;
-}
-
-// The MLP's output (logit): 64 ReLU units over the 16 features (rounded to
-// bf16, as logged), bf16 weights, fp32 accumulation, two units per lane and a
-// fixed-order warp sum -- the order of the training code's evaluation.
-__device__ __forceinline__ float filter_logit(const GomParams &P, const float (&x0)[kFilterIn])
-{
-    const int lane = threadIdx.x & 31;
-    float x[kFilterIn]; // the features as the training log holds them (bf16)
-#pragma unroll
-    for (int k = 0; k < kFilterIn; ++k) x[k] = __bfloat162float(__float2bfloat16_rn(x0[k]));
-    float part = 0.f;
-    for (int h = lane; h < kFilterHidden; h += 32) {
-        float z = P.flt.b1[h];
-#pragma unroll
-        for (int k = 0; k < kFilterIn; ++k) z = fmaf(bf16_bits_to_f32(P.flt.w1[h * kFilterIn + k]), x[k], z);
-        part = fmaf(bf16_bits_to_f32(P.flt.w2[h]), fmaxf(z, 0.f), part);
-    }
-    for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-    return part + P.flt.b2[0];
-}
-
-// One in 16 elements of a generation whose trials the filter would skip is run
-// anyway (an audit), to estimate how many useful elements it skips.
-__device__ __forceinline__ bool filter_audit(int q, uint32_t g)
-{
-    uint32_t h = (uint32_t)q * 0x9E3779B1u ^ (g * 0x85EBCA77u);
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    return (h & 15u) == 0;
-}
-
-// One in 32 elements of a generation gives a training sample.
-__device__ __forceinline__ bool filter_sample(int q, uint32_t g)
-{
-    uint32_t h = (uint32_t)q * 0xCC9E2D51u ^ (g * 0x1B873593u);
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    return (h & 31u) == 0;
-}
+// Learned trial filter: features, logit, hashes and the select phase are in
+// gom_filter_dev.cuh; the decision of each element is taken there, after the
+// generation start, and read here when an item is staged.
 
 // Slice validity states: no item, staged, skipped by the filter, staged for an audit.
 enum : int { IT_NONE = 0, IT_STAGED = 1, IT_SKIPPED = 2, IT_AUDIT = 3 };
 
-// The filter's decision on a decoded item (warp-wide): IT_STAGED, IT_SKIPPED
-// (the element is marked skipped and counted) or IT_AUDIT; written to the
+// The filter's decision on a decoded item (warp-wide), as the select phase
+// took it for its element: IT_STAGED, IT_SKIPPED or IT_AUDIT; written to the
 // slice header.
-__device__ __forceinline__ int filter_decide(const GomParams &P, uint32_t *sl, uint32_t g)
+__device__ __forceinline__ int filter_decide(const GomParams &P, uint32_t *sl)
 {
-    int state = IT_STAGED;
-    if (P.flt.st->enabled) {
-        const int q = reinterpret_cast<const int *>(sl)[H_Q];
-        float x[kFilterIn];
-        filter_features(P, q, g, x);
-        if (filter_logit(P, x) < P.flt.st->threshold) {
-            state = filter_audit(q, g) ? IT_AUDIT : IT_SKIPPED;
-            if ((threadIdx.x & 31) == 0 && state == IT_SKIPPED) P.flt.skipped[q] = 1;
-        }
-    }
+    const int q = reinterpret_cast<const int *>(sl)[H_Q];
+    const uint8_t d = P.flt.dec[q];
+    const int state = d == DEC_SKIP ? IT_SKIPPED : d == DEC_AUDIT ? IT_AUDIT : IT_STAGED;
     __syncwarp();
     if ((threadIdx.x & 31) == 0) sl[H_VALID] = (uint32_t)state;
     __syncwarp();
@@ -481,7 +402,7 @@ __device__ __forceinline__ int stage_item(const GomParams &P, int c, int it, uin
     __syncwarp();
     int state = IT_STAGED;
     if (LEARN && P.learn == 2) {
-        state = filter_decide(P, sl, g);
+        state = filter_decide(P, sl);
         if (state == IT_SKIPPED) return state;
     }
     stage_lists<WPI>(P, sl);
@@ -539,7 +460,7 @@ __device__ void stage_all_items(const GomParams &P, int gwarp, uint32_t *slices,
 // Learned filter bookkeeping after an item ran: the element's accepted,
 // donor-less and improving trials into this generation's history, and for
 // sampled elements a training sample (the features as at the decision,
-// label: the item accepted a trial).  Returns the item's counter increments
+// label: the item was useful, see GomFilter::label).  Returns the item's counter increments
 // (bits: run, useful, audited, audited and useful) for the caller to sum.
 __device__ __forceinline__ unsigned item_record(const GomParams &P, const int *h, uint32_t g, unsigned acc, unsigned dl,
                                             unsigned imp)
@@ -556,23 +477,14 @@ __device__ __forceinline__ unsigned item_record(const GomParams &P, const int *h
         if (dl) atomicAdd(&cur[P.m + q], dl);
         if (imp) atomicAdd(&cur[2 * (size_t)P.m + q], imp);
     }
+    const bool useful = P.flt.label ? imp != 0 : acc != 0;
     if (first && filter_sample(q, g)) {
         float x[kFilterIn];
         filter_features(P, q, g, x);
-        unsigned long long idx = 0;
-        if (lane == 0) idx = atomicAdd(&P.flt.st->log_count, 1ull);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (P.flt.log_cap > 0) { // a ring: the log keeps the latest log_cap samples
-            idx %= (unsigned long long)P.flt.log_cap;
-            float v = 0.f;
-#pragma unroll
-            for (int k = 0; k < kFilterIn; ++k) v = lane == k ? x[k] : v;
-            if (lane < kFilterIn) P.flt.log_x[idx * kFilterIn + lane] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-            if (lane == 0) P.flt.log_y[idx] = acc ? 1 : 0;
-        }
+        filter_log_sample(P, x, useful);
     }
-    // the item's counter increments: run, run with an acceptance, audited, audited with an acceptance
-    return 1u | (acc ? 2u : 0u) | (audited ? 4u : 0u) | (audited && acc ? 8u : 0u);
+    // the item's counter increments: run, useful, audited, audited and useful
+    return 1u | (useful ? 2u : 0u) | (audited ? 4u : 0u) | (audited && useful ? 8u : 0u);
 }
 
 // All trials of a staged item (Alg. 2 for each individual of its words):
@@ -809,7 +721,7 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
     // one call site of run_item and of stage_item (the loop body is the hot code)
     const bool dyn = P.dyn && !single;
     unsigned claim = 0;
-    unsigned fc[FC_N] = {}, skipped_trials = 0; // learned filter: this warp's counters of the group
+    unsigned fc[FC_N] = {}; // learned filter: this warp's counters of the group
     if (dyn && lane == 0) claim = atomicAdd(&P.work[t], 1u);
     for (int next = gwarp + nwarps;; next += nwarps) {
         if (state != IT_SKIPPED) {
@@ -820,11 +732,7 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
                 fc[FC_AUDITED] += (f >> 2) & 1u;
                 fc[FC_AUDITED_USEFUL] += (f >> 3) & 1u;
             }
-        } else if (LEARN) {
-            const int sub = reinterpret_cast<const int *>(sl)[H_SUB], w = 32 * WPI;
-            ++fc[FC_SKIPPED];
-            skipped_trials += P.split ? min(P.p, w * (sub + 1)) - w * sub : P.p;
-        }
+        } // a skipped element was counted by the select phase
         // stage-all mode: the staged item is the warp's only one, its slice stays as it is
         if (single) break;
         // stop on the first item past the group (items are numbered densely)
@@ -836,7 +744,6 @@ __device__ __forceinline__ void phase_mix(const GomParams &P, const VGrid &V, in
     if (LEARN && P.learn && lane == 0) {
         for (int x = 0; x < FC_N; ++x)
             if (fc[x]) atomicAdd(&P.flt.st->cnt[x], (unsigned long long)fc[x]);
-        if (skipped_trials) atomicAdd((unsigned long long *)&P.st->cnt[3], (unsigned long long)skipped_trials);
     }
 }
 
@@ -959,6 +866,28 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix(GomParams P, int t)
     acc_flush(P, s_f, s_cnt);
 }
 
+// The learned filter's select phase on the per-generation graph path: the
+// decisions (with `compact`, each warp's count of elements to run), the scan
+// of the counts (one block) and the compacted list, each a node of its own,
+// launched on the same grid for the first and the last.
+__global__ void __launch_bounds__(256) k_filter_select(GomParams P, int compact)
+{
+    if (P.st->done) return;
+    filter_select_decide(P, whole_grid(), P.st->g, compact != 0);
+}
+
+__global__ void __launch_bounds__(1024) k_filter_scan(GomParams P, int nwarps)
+{
+    if (P.st->done) return;
+    filter_select_scan(P, nwarps);
+}
+
+__global__ void __launch_bounds__(256) k_filter_compact(GomParams P)
+{
+    if (P.st->done) return;
+    filter_select_compact(P, whole_grid());
+}
+
 __global__ void __launch_bounds__(1024) k_gen_end(GomParams P)
 {
     if (P.st->done) return;
@@ -1025,6 +954,8 @@ __device__ void run_generations(const GomParams &P, const VGrid V, GomBarrier *b
         if (all) stage_all_items<WPI, MaskT>(P, gwarp, slices, g, q == 0);
         if (tr) P.trace[2] = global_ns();
         if (!grid_barrier(&bar->count, &P.st->err, nblk, bnext, kBarrierNs)) return;
+        // the learned filter's decisions, before the first item is staged
+        if (LEARN && P.learn && !phase_filter_select(P, V, g, &bar->count, nblk, bnext, false)) return;
         if (tr) P.trace[3] = global_ns();
         unsigned n_dl = 0, n_acc = 0, n_imp = 0;
         for (int t = 0; t < P.k; ++t) {

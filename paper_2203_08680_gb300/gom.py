@@ -27,6 +27,7 @@ GOM_OPT_DYNAMIC = 3
 GOM_OPT_BITSLICED = 4
 GOM_OPT_FORCED_IMPROVEMENT = 5
 GOM_OPT_FI_NIS = 6
+GOM_OPT_FILTER_LABEL = 7
 INT64_MAX = 2 ** 63 - 1
 
 ERRORS = {-1: "GOM_E_ARG", -2: "GOM_E_GRAPH", -3: "GOM_E_NOT_COLORED", -4: "GOM_E_WORKSPACE",

@@ -34,13 +34,28 @@ def _same_stats(a, o):
         assert a[gk] == o[ok], (gk, a, o)
 
 
+def _mixing_path(P, bitsliced):
+    """Selects the per-lane or the bit-sliced mixing path (skips the test
+    where the bit-sliced one is unavailable)."""
+    try:
+        gom.gom_set_option(P.ctx, gom.GOM_OPT_BITSLICED, 1 if bitsliced else 0)
+    except gom.GomError:
+        pytest.skip("bit-sliced mixing unavailable")
+
+
+@pytest.mark.parametrize("bitsliced", [False, True])
 @pytest.mark.parametrize("persistent", [True, False])
-def test_filter_log_mode_is_plain_and_filtered_mode_replays(oracle, persistent):
+def test_filter_log_mode_is_plain_and_filtered_mode_replays(oracle, persistent, bitsliced):
+    """Mode 1 is plain GOM; in mode 2 the select phase skips elements (on the
+    bit-sliced path the mixing runs only the compacted list of the others) and
+    the oracle, replaying each generation without the marked elements, agrees
+    bit for bit."""
     g = I.torus2d(300, seed=31)
     p, seed = 64, 5
     P = gom.Population(g, p, seed, persistent=persistent)
     if persistent:  # the persistent path here stages one item at a time
         assert gom.gom_get_option(P.ctx, gom.GOM_OPT_PERSISTENT) == 1
+    _mixing_path(P, bitsliced)
     _attach(P)
     gom.gom_filter_set_mode(P.ctx, 1)
     run, _ = _oracle_run(oracle, g, p, seed)
@@ -68,13 +83,15 @@ def test_filter_log_mode_is_plain_and_filtered_mode_replays(oracle, persistent):
     assert fs["enabled"] == 1 and fs["total"]["skipped"] > 0 and skipped_any
 
 
-def test_filter_turns_itself_off_when_recall_drops(oracle):
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_filter_turns_itself_off_when_recall_drops(oracle, bitsliced):
     """A threshold above every logit skips every element; the audits find
     useful ones among them, the estimated recall falls below the minimum and
     the filter turns itself off: the next generations are plain GOM."""
     g = I.torus2d(300, seed=32)
     p, seed = 64, 6
     P = gom.Population(g, p, seed, persistent=False)
+    _mixing_path(P, bitsliced)
     _attach(P)
     gom.gom_filter_set_mode(P.ctx, 1)
     P.generation(3)
@@ -92,11 +109,12 @@ def test_filter_turns_itself_off_when_recall_drops(oracle):
 
 
 def test_filter_refused_in_stage_all_mode():
+    """The stage-all mode does not keep P, which the change marks read."""
     P = gom.Population(I.torus2d(10), 16, 1, persistent=True)
     _attach(P, 1024)
-    gom.gom_filter_set_mode(P.ctx, 1)
-    with pytest.raises(gom.GomError):
-        gom.gom_filter_set_mode(P.ctx, 2)
+    for mode in (1, 2):
+        with pytest.raises(gom.GomError):
+            gom.gom_filter_set_mode(P.ctx, mode)
 
 
 # ---------------------------------------------------------------------------
@@ -141,17 +159,34 @@ def _element_structure(g, ep, ev):
     return size, nout, nin
 
 
-def test_filter_log_features_and_labels_match_an_oracle_replay(oracle):
+def _element_neighbours(g, ep, ev):
+    """Per element: its variables, and the far end of each of its outside edges."""
+    m = len(ep) - 1
+    out = []
+    for j in range(m):
+        F = ev[ep[j]:ep[j + 1]]
+        inside = set(int(v) for v in F)
+        nb = [int(g.col[x]) for u in F for x in range(g.row_ptr[u], g.row_ptr[u + 1]) if int(g.col[x]) not in inside]
+        out.append((np.asarray(F, dtype=np.int64), np.asarray(nb, dtype=np.int64)))
+    return out
+
+
+@pytest.mark.parametrize("bitsliced", [False, True])
+def test_filter_log_features_and_labels_match_an_oracle_replay(oracle, bitsliced):
     """Every logged sample -- the 16 features of an element at the start of a
     generation and its label (the element accepted a trial in that
     generation) -- equals the restatement of the feature definitions from
     the oracle's run: element structure, the element's accepted, donor-less
     and improving trials of the previous generation, log2(1 + g), the
-    population's rates of the previous generation.  p = 32, so one item is
-    one element and the label covers all its trials."""
+    population's rates of the previous generation, the fractions of its
+    variables and outside edges whose variable changed in some individual
+    during the previous generation, and its quiet count (generations in a row
+    with no accepted trial and no such change, up to 16).  p = 32, so one
+    per-lane item is one element and the label covers all its trials."""
     g = I.torus2d(60, seed=41)
     p, seed, G = 32, 7, 8
     P = gom.Population(g, p, seed, persistent=False)
+    _mixing_path(P, bitsliced)
     _attach(P, 1 << 14)
     gom.gom_filter_set_mode(P.ctx, 1)
     P.generation(G)
@@ -162,12 +197,20 @@ def test_filter_log_features_and_labels_match_an_oracle_replay(oracle):
     run.keep_element_counts(True)
     by_pos = np.concatenate([np.flatnonzero(co == c) for c in range(k)])  # colour-order position -> element
     size, nout, nin = _element_structure(g, ep, ev)
+    nbrs = _element_neighbours(g, ep, ev)
     f32 = np.float32
     inv_p = f32(1) / f32(p)
     prev = (np.zeros(len(by_pos), np.int64),) * 3
     prev_st = None
+    quiet = np.zeros(len(by_pos), np.int64)
+    pop_prev = None  # the population at the start of the previous generation
     rows = []
     for gen in range(G):
+        pop_now = run.get()["pop"]
+        changed = (pop_now != pop_prev).any(axis=0) if pop_prev is not None else np.zeros(g.n, bool)
+        dF = np.array([int(changed[F].sum()) for F, _ in nbrs])
+        dN = np.array([int(changed[nb].sum()) for _, nb in nbrs])
+        quiet = np.where((prev[0] == 0) & (dF == 0) & (dN == 0), np.minimum(quiet + 1, 255), 0)
         st = run.generation()
         acc, dl, imp = run.element_counts()
         for q, j in enumerate(by_pos):
@@ -184,12 +227,16 @@ def test_filter_log_features_and_labels_match_an_oracle_replay(oracle):
                 x[9], x[10], x[11] = (f32(prev_st["accepted"]) / tr, f32(prev_st["improving"]) / tr,
                                       f32(prev_st["donorless"]) / tr)
             x[12] = 1
+            x[13] = f32(dF[j]) / f32(size[j])
+            x[14] = f32(dN[j]) / f32(nout[j]) if nout[j] > 0 else f32(0)
+            x[15] = f32(min(quiet[j], 16)) / f32(16)
             rows.append(tuple(_bf16_bits(x)) + (int(acc[j] > 0),))
-        prev, prev_st = (acc, dl, imp), st
+        prev, prev_st, pop_prev = (acc, dl, imp), st, pop_now
     got = sorted(tuple(int(v) for v in r) + (int(l),) for r, l in zip(x_gpu, y_gpu))
     assert len(got) == len(rows) > 100
     assert got == sorted(rows)
     assert 0 < sum(r[-1] for r in rows) < len(rows)  # both labels occur
+    assert any(r[13] or r[14] for r in rows) and any(r[15] for r in rows)  # the new features vary
 
 
 def _forward64(theta, xb):
