@@ -305,7 +305,8 @@ int gom_get_option(gom_ctx_t *ctx, int32_t option, int64_t *value);
  * by block 0: [0] generation start, [1] end of the start/order phase, [2]
  * end of the staging of every group's items (stage-all mode, used when every
  * colour group fits one wave of warps; otherwise no staging happens there),
- * [3] after the barrier that opens the generation, then for each
+ * [3] after the barrier that opens the generation (and, with the learned
+ * filter on, after its select phase), then for each
  * colour-group position t: [4+2t] when the group starts (after its barrier
  * for t > 0), [5+2t] when block 0 finished its share of the group; [4+2k]
  * after the barrier that closes the generation.  ns[capacity] host array; *count receives 5 + 2k (GOM_E_ARG if

@@ -12,24 +12,32 @@
 //   phase 0  (lane = pair) the parent's current rows on F_j and the
 //            generation-start rows of P on F_j into shared memory, the run
 //            starts of P's patterns on F_j, and the Philox donor starts of
-//            all 1024 trials (one Philox call per 4 individuals)
-//   phase 1  (lane = individual, one pair after the other) the donor search
-//            of Sec. 4.2 with the run starts and the word-parallel scan; one
-//            ballot per variable turns the accepted candidates' flips into
-//            flip planes F_a (bit b: individual b flips variable a)
+//            all 1024 trials (one Philox call per 4 individuals); then, by
+//            32 x 32 bit transposes, the patterns of P and of the parents on
+//            the item's elements packed side by side per individual
+//   phase 1  (lane = individual, one word after the other) the donor search
+//            of Sec. 4.2: one lookup of the start candidate's packed pattern
+//            and of the next run start after it, the run-start walk and the
+//            word-parallel scan for the rare rest; the packed flips (donor ^
+//            parent) go back through transposes into flip planes F_a (bit b:
+//            individual b flips variable a)
 //   phase 2  (lane = pair) the partial evaluation (Sec. 2.2, Alg. 4) as
-//            bit-plane arithmetic: with t_e the toggle plane of edge e (F_a
-//            for an edge leaving F_j, F_a ^ F_b inside), c_e its cut plane
-//            before the trial and S_e all ones for a negative weight,
-//              T = sum_e |w_e| t_e,   N = sum_e |w_e| (t_e & (c_e ^ S_e)),
-//              delta = T - 2 N        (each edge counted once),
-//            summed with ripple-carry bit-plane adders (T's outside-edge part
-//            is sum_a A_a F_a, A_a = sum of |w| over a's outside edges);
-//            then the accept plane (Alg. 2: delta > 0, or delta = 0 and not
-//            the elitist), counters by popcount, the accepted flips XORed
-//            into the rows, and the accepted deltas into a bit-sliced
-//            per-lane fitness accumulator, flushed into the block's
-//            accumulators once per generation (or before it could overflow).
+//            bit-plane arithmetic: an edge e that a trial toggles (t_e = F_a
+//            for an edge leaving F_j, F_a ^ F_b inside) changes the cut by
+//            +|w_e| if it was uncut and -|w_e| if it was cut (its cut plane
+//            c_e taken with the weight's sign folded in), so
+//              delta = sum_e |w_e| (t_e & ~c_e) - |w_e| (t_e & c_e),
+//            one signed ripple-carry chain per edge on R + 1 two's-complement
+//            planes (each edge counted once); then the accept plane (Alg. 2:
+//            delta > 0, or delta = 0 and not the elitist), counters by
+//            popcount, the accepted flips XORed into the rows, and the
+//            accepted deltas into a bit-sliced per-lane fitness accumulator,
+//            flushed into the block's accumulators once per generation (or
+//            before it could overflow).
+// With the learned trial filter on, a select phase after the generation start
+// (gom_filter_dev.cuh) decides which elements run and lists them in order, the
+// groups run only the listed elements, and each item records its elements'
+// history and training samples.
 // Elements of one colour group share no variable and no edge (LMIG
 // colouring), so the rows a pair reads and writes belong to it alone during
 // the group.
