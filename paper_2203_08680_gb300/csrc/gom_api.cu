@@ -526,7 +526,7 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
     {
         const int R = tabs.max_abs_w < (int64_t(1) << 12) ? 12 : 16;
         if (coop && variant == kVarNarrow && max_w <= 255 && tabs.max_abs_w < (int64_t(1) << 16)) {
-            const int sm = static_cast<int>((std::max<int64_t>(tabs.max_s, 1) + 3) & ~int64_t(3));
+            const int sm = static_cast<int>(std::max<int64_t>(tabs.max_s, 1) | 1); // odd row stride: no bank conflicts
             const int S = static_cast<int>(std::max<int64_t>(tabs.max_s, 1));
             const int epw = 32 / S, E0 = 32 / c->W;
             const int nc = (E0 + epw - 1) / epw;

@@ -170,8 +170,9 @@ __device__ int find_donor_packed(const uint32_t *tc, int off, uint32_t fmask, co
     return r;
 }
 
-// Shared-memory words of one warp's region (SM = P.bs_sm, a multiple of 4;
-// NC chunks of packed patterns): rows of O on F_j [32 pairs][SM], rows of P
+// Shared-memory words of one warp's region (SM = P.bs_sm, odd, so that the
+// 32 lanes reading word a of their own rows hit 32 different banks; NC
+// chunks of packed patterns): rows of O on F_j [32 pairs][SM], rows of P
 // [32][SM], flip planes [32][SM], donor starts [32 pairs][32 individuals] as
 // 16-bit values, run starts [32 pairs], packed patterns of P [NC][W][32],
 // packed patterns of O [NC][W][32] (their slots reused for the packed flips),
@@ -289,8 +290,12 @@ __device__ __forceinline__ void bs_item(const GomParams &P, const int32_t *qlist
                 xp[c] = P.P[v * W + w];
             }
         }
-        *reinterpret_cast<uint4 *>(sO + lane * SM + a4) = make_uint4(xo[0], xo[1], xo[2], xo[3]);
-        *reinterpret_cast<uint4 *>(sP + lane * SM + a4) = make_uint4(xp[0], xp[1], xp[2], xp[3]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (a4 + c < SM) {
+                sO[lane * SM + a4 + c] = xo[c];
+                sP[lane * SM + a4 + c] = xp[c];
+            }
     }
     __syncwarp();
     {   // run starts of the element's patterns in word w: bit b set iff the

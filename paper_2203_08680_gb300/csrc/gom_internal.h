@@ -210,7 +210,7 @@ struct GomParams {
     int32_t learn;      // learned filter: 0 off, 1 history and training log, 2 also skip elements
     GomFI fi;
     int32_t bs_sm;      // bit-sliced path: words per staged row block of one pair (>= the largest
-                        //   element, a multiple of 4)
+                        //   element, odd: a lane-strided row access is free of bank conflicts)
     int32_t bs_S;       //   field width of one element in a packed pattern (the largest element)
     int32_t bs_epw;     //   elements per packed pattern word (32 / bs_S)
     int32_t bs_nc;      //   packed words per individual for one item (ceil(E / bs_epw), E = 32 / W)
