@@ -564,8 +564,12 @@ int gom_init_population(const gom_graph_t *g, const gom_fos_t *fos, int32_t pop,
                     c->prm.bs_epw = epw;
                     c->prm.bs_nc = nc;
                     c->prm.bs_words = static_cast<int32_t>(ww);
-                    // the default where every resident warp gets an item of the largest group
-                    c->bs_on = items >= static_cast<int64_t>(c->sms) * occ_r * wpb;
+                    // the default where the largest group gives at least a quarter of the
+                    // resident warps an item, and a variable row has at most 16 words: with
+                    // fewer items the per-lane path's finer items win, and with 32 words
+                    // (one element per item) its scalar trials do (measured on the torus,
+                    // 3D torus and random regular workloads, p = 64 to 1024)
+                    c->bs_on = c->W <= 16 && 4 * items >= static_cast<int64_t>(c->sms) * occ_r * wpb;
                 }
             }
         }
