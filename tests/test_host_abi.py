@@ -51,6 +51,26 @@ GRAPHS = {
     "empty": lambda: I.empty_graph(20),
 }
 
+# larger FOS (4,096 to 20,000 elements), colouring only: the oracle's plain
+# UPGMA of the linkage-tree test would take too long on them
+LARGE = {
+    "torus100": lambda: I.torus2d(100),
+    "torus3d20": lambda: I.torus3d(20, seed=4),
+    "rreg20k_d6": lambda: I.random_regular(20000, 6, seed=11),
+    "rreg5k_d12": lambda: I.random_regular(5000, 12, seed=13),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LARGE))
+def test_large_coloring_equals_oracle(oracle, name):
+    """The library's Welsh-Powell colouring equals the oracle's on larger graphs."""
+    g = LARGE[name]()
+    fos = gom.gom_build_fos(g)
+    k = gom.gom_color_fos(g, fos)
+    ep, ev = oracle.build_fos(g)
+    ko, co = oracle.color(g, ep, ev)
+    assert k == ko and np.array_equal(gom.gom_fos_export(fos)["color_of_elem"], co)
+
 
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("kind", [gom.GOM_FOS_NEIGHBOURHOOD, gom.GOM_FOS_SINGLETON])
