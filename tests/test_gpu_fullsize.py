@@ -111,7 +111,8 @@ def test_full_size_sampled_generation(oracle, name, p):
 
 
 @pytest.mark.parametrize("bitsliced", [False, True])
-@pytest.mark.parametrize("name,p,late", [("rreg1m_d12", 512, 100), ("torus1000", 256, 100)])
+@pytest.mark.parametrize("name,p,late", [("rreg1m_d12", 512, 100), ("torus1000", 256, 100), ("torus3d50", 512, 150),
+                                         ("rreg1m_d6", 128, 100)])
 def test_full_size_late_generation(oracle, name, p, late, bitsliced):
     """A late generation (after `late` generations, the population partly
     converged): the oracle replays it from the GPU's exported state for one
