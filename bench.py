@@ -74,7 +74,8 @@ LEARNED_WORKLOADS = {
                    "generations (label: the element had an improving trial), then run to the fitness plain GOM "
                    "reaches at generation 200",
 }
-BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300)]
+BATCH_CONFIGS = [(4, 3, 0, 300), (4, 3, 0, 100), (4, 3, 0, 1000), (2, 3, 0, 300), (4, 2, 0, 300), (8, 3, 0, 300),
+                 (8, 2, 0, 300)]
 SEED = 1
 # the largest single-GPU plain configuration: the 1000x1000 torus (the learned filter's graph), plain GOM
 DEFAULT_WORKLOAD = "torus1000"

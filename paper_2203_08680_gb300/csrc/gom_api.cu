@@ -859,6 +859,7 @@ int gom_set_option(gom_ctx_t *ctx, int32_t option, int64_t value)
     if (option == GOM_OPT_BITSLICED) {
         if (value != 0 && value != 1) return GOM_E_ARG;
         if (value && !ctx->bs_ok) return GOM_E_STATE;
+        ctx->bs_set = static_cast<int>(value); // batched launches follow it too
         if (ctx->bs_on == (value != 0)) return GOM_OK;
         ctx->bs_on = value != 0;
         return rebuild_graphs(ctx); // the graphs hold the mixing kernel

@@ -160,6 +160,8 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
                 slice_layout(c->max_s, c->max_edges, c->W, wpi, c->variant, split != 0, (wv + wpi - 1) / wpi);
             max_warp_words = std::max<int64_t>(max_warp_words, SL.base_words);
         }
+        if (c->bs_ok && conf.min_blocks == 2) // a bit-sliced warp region
+            max_warp_words = std::max<int64_t>(max_warp_words, c->prm.bs_words);
     }
     const int32_t f_words = 2 * 32 * maxW;
     const int64_t slices = std::max<int64_t>(int64_t(8) * maxk,
@@ -236,6 +238,18 @@ int gom_batch_create(gom_ctx_t *const *ctxs, int32_t num, const gom_batch_config
         I.nblk = nb[b];
         I.wpi = wpi;
         I.variant = cs[b]->variant;
+        // the bit-sliced phase, as the caller set it for the context, else where
+        // it pays on a single context (at most 16 words per row, items for at
+        // least a quarter of the warps), counted on this instance's warps
+        const int64_t bs_items = (c->max_group + (32 / c->W) - 1) / (32 / c->W);
+        // (only in the kernel with the larger register budget, 2 blocks of 256 threads)
+        const bool use_bs = c->bs_ok && conf.min_blocks == 2 &&
+                            (c->bs_set >= 0 ? c->bs_set == 1
+                                            : c->W <= 16 && 4 * bs_items >= int64_t(nb[b]) * conf.warps_per_block);
+        if (use_bs) {
+            I.variant = kVarBits;
+            I.bs_r = c->bs_r;
+        }
         I.target = INT64_MAX;
         blk += nb[b];
     }

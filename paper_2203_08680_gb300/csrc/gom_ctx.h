@@ -26,6 +26,8 @@ struct gom_ctx {
     // the bit-sliced mixing path (gom_bs.cu), where the FOS and weights allow it
     bool bs_ok = false;           // available for this context
     bool bs_on = false;           // selected (GOM_OPT_BITSLICED)
+    int bs_set = -1;              // GOM_OPT_BITSLICED as the caller set it (-1: never set; batched launches
+                                  //   then choose by the instance's share of warps)
     const void *run_bs_fn = nullptr, *mix_bs_fn = nullptr; // the instances for the learned filter's mode
     int bs_r = 0;                 // their accumulator width R
     size_t bs_smem = 0;           // dynamic shared memory of both (warp regions, group keys)

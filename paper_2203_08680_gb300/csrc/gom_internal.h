@@ -69,7 +69,8 @@ int build_elem_tables(const gom_graph_t *g, const gom_fos &fos, ElemTables *out)
 // masks and deltas), wide = <= 64 variables (64-bit masks and deltas), huge =
 // 65 to GOM_MAX_ELEMENT variables (128-bit masks, 64-bit deltas; at most two
 // population words per item, no learned filter).
-enum : int32_t { kVarNarrow = 0, kVarWide = 1, kVarHuge = 2 };
+enum : int32_t { kVarNarrow = 0, kVarWide = 1, kVarHuge = 2, kVarBits = 3 }; // kVarBits: batched instances on
+                                                                          // the bit-sliced phase
 inline int32_t kernel_variant(int64_t max_s, int64_t max_abs_w)
 {
     if (max_s <= 32 && max_abs_w < (int64_t(1) << 30)) return kVarNarrow;
@@ -103,10 +104,10 @@ struct GomBarrier { // grid barrier of the persistent kernel: monotonic arrival 
 struct GomBatchInst {
     int32_t blk0, nblk; // its blocks [blk0, blk0 + nblk) of the launch
     int32_t wpi;        // words per item of its mixing (1, 2, 4)
-    int32_t variant;    // kernel variant (kVarNarrow, kVarWide, kVarHuge)
+    int32_t variant;    // kernel variant (kVarNarrow, kVarWide, kVarHuge; kVarBits: the bit-sliced phase)
     int64_t target;     // target fitness of the current call
     int32_t gens;       // generations of the current call for this instance
-    int32_t pad;
+    int32_t bs_r;       // kVarBits: the width R of its plane accumulators (12 or 16)
     int32_t gens_run;   // generations run by the last call
     int32_t err;        // the instance's device error word after the last call
 };

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "gom_bs.cuh"
 #include "gom_device.cuh"
 #include "gom_fi.cuh"
 #include "gom_filter_dev.cuh"
@@ -1006,6 +1007,17 @@ __device__ __noinline__ void batch_variant(const GomParams &P, const VGrid V, Go
     run_generations<WPI, MaskT, AccT, false>(P, V, bar, G, target, S);
 }
 
+// The bit-sliced variant of the batched path: the instance's generations on
+// the bit-sliced phase (gom_bs.cuh), warp w of the block in the w-th region
+// of P.bs_words words after the fitness accumulators.
+template <int R>
+__device__ __noinline__ void batch_variant_bs(const GomParams &P, const VGrid V, GomBarrier *bar, int G,
+                                              int64_t target, const RunShared &S)
+{
+    bs_generations<R, false>(P, V, bar, G, target, reinterpret_cast<unsigned long long *>(S.dyn),
+                             S.dyn + (threadIdx.x >> 5) * P.bs_words, S.f, S.cnt, nullptr);
+}
+
 // Batched path: many independent instances in one cooperative launch.  Each
 // instance owns a range of blocks and runs its own generations on them, with
 // its own barrier counter and its own stop decision, exactly as its
@@ -1045,7 +1057,14 @@ __global__ void __launch_bounds__(kMixThreads, MINB)
     const RunShared S{s_dyn + f_words, reinterpret_cast<long long *>(s_dyn), s_cnt, nullptr, nullptr};
     GomBarrier *bar = bars + b;
     G = min(G, I.gens);
-    if (I.variant == kVarNarrow) {
+    if (MINB == 2 && I.variant == kVarBits) { // the bit-sliced phase needs the larger register budget
+        if constexpr (MINB == 2) {
+            if (I.bs_r <= 12)
+                batch_variant_bs<12>(sP, V, bar, G, I.target, S);
+            else
+                batch_variant_bs<16>(sP, V, bar, G, I.target, S);
+        }
+    } else if (I.variant == kVarNarrow || I.variant == kVarBits) {
         if (I.wpi == 4)
             batch_variant<4, uint32_t, int32_t>(sP, V, bar, G, I.target, S);
         else if (I.wpi == 2)

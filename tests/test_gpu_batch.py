@@ -88,6 +88,30 @@ def test_batch_equals_oracle_per_instance(oracle, config):
     assert spans[-1][0] + spans[-1][1] == spans[-1][2]
 
 
+@pytest.mark.parametrize("config", [(4, 2), (8, 2), (1, 2)])
+@pytest.mark.parametrize("share", ["all", "half"])
+def test_batch_bitsliced_instances_equal_oracle(oracle, config, share):
+    """Instances on the bit-sliced phase inside the batched launch (the
+    kernel with the larger register budget): every instance where it is
+    available ("all"), or every other one ("half", the rest per lane), each
+    bit for bit equal to its own oracle run."""
+    items = _instances(_MIX, extra_wide=True)
+    pops = _populations(items)
+    on = 0
+    for b, P in enumerate(pops):
+        want = 1 if share == "all" or b % 2 == 0 else 0
+        try:
+            gom.gom_set_option(P.ctx, gom.GOM_OPT_BITSLICED, want)
+            on += want
+        except gom.GomError:
+            pass  # not available for this instance (the 40-variable star)
+    assert on >= 3
+    batch = _batch(pops, config)
+    runs = gom.gom_batch_generation(batch, 6)
+    assert list(runs) == [6] * len(items)
+    _check_against_oracle(oracle, items, pops, batch, 6)
+
+
 def test_batch_per_instance_targets(oracle):
     """Instance b stops after the first generation reaching targets[b];
     the others go on."""
