@@ -88,9 +88,13 @@ extern "C" {
                                works on 32 trials); the donor search stays per individual.
                                Available for elements of at most 32 variables, |w| <= 255 and
                                element weight sums (of |w| over their edges) below 2^16; the
-                               default where available and the colour groups are large enough to
-                               fill the GPU (GOM_E_STATE when set to 1 where unavailable).  Same
-                               results either way.  Not used while the learned filter is on */
+                               default where available, a variable row has at most 16 words
+                               (p <= 512) and the largest colour group gives at least a quarter
+                               of the resident warps an item (GOM_E_STATE when set to 1 where
+                               unavailable).  Same results either way; the learned filter works
+                               on both.  A batched launch follows the value the caller set for
+                               the context, else the same rule on the warps the instance gets
+                               (bit-sliced instances only with min_blocks 2) */
 
 #define GOM_OPT_FORCED_IMPROVEMENT 5 /* 1: Forced Improvement (Sec. 4, Alg. 1) after each generation's
                                         mixing, in this library's parallel reading (the paper's
