@@ -241,14 +241,18 @@ Inverted invert(int32_t n, const gom_fos &fos)
 }
 
 // Calls visit(j2) for every LMIG neighbour j2 of element j: the elements
-// holding a variable of F_j or of adj(F_j).  With a mark array each neighbour
-// is visited once; without one (mark == nullptr) a neighbour may be visited
-// several times, which is enough for first-fit colouring.
+// holding a variable of F_j or of adj(F_j).  vmark (one entry per variable)
+// makes each such variable's element list scanned once per j.  With a mark
+// array each neighbour is visited once; without one (mark == nullptr) a
+// neighbour may be visited several times, which is enough for first-fit
+// colouring.
 template <class V>
 void for_each_lmig_neighbour(const gom_graph_t *g, const gom_fos &fos, const Inverted &inv,
-                             int64_t j, int32_t *mark, V visit)
+                             int64_t j, int32_t *mark, int32_t *vmark, V visit)
 {
     auto touch_var = [&](int32_t v) {
+        if (vmark[v] == j) return;
+        vmark[v] = static_cast<int32_t>(j);
         for (int64_t r = inv.ptr[v]; r < inv.ptr[v + 1]; ++r) {
             const int32_t j2 = inv.elems[r];
             if (j2 == j) continue;
@@ -276,10 +280,10 @@ int color_fos(const gom_graph_t *g, gom_fos *fos)
     // LMIG degree of every element
     std::vector<int64_t> deg(m, 0);
     parallel_ranges(m, [&](int64_t b, int64_t e) {
-        std::vector<int32_t> mark(m, -1);
+        std::vector<int32_t> mark(m, -1), vmark(fos->n, -1);
         for (int64_t j = b; j < e; ++j) {
             int64_t d = 0;
-            for_each_lmig_neighbour(g, *fos, inv, j, mark.data(), [&](int32_t) { ++d; });
+            for_each_lmig_neighbour(g, *fos, inv, j, mark.data(), vmark.data(), [&](int32_t) { ++d; });
             deg[j] = d;
         }
     });
@@ -290,23 +294,44 @@ int color_fos(const gom_graph_t *g, gom_fos *fos)
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
 
-    // first fit in that order
+    // first fit in that order.  The colours taken by j's LMIG neighbours are
+    // the colours of the coloured elements that hold a variable of C_j = F_j
+    // united with adj(F_j); cset[v] keeps, as a bitset, the colours of the
+    // coloured elements holding v, so j's forbidden colours are the union of
+    // cset over C_j (each variable once), and colouring j with c adds c to
+    // cset[v] for v in F_j.  Same colours as visiting the neighbours one by one.
     std::vector<int32_t> color(m, -1);
-    std::vector<int64_t> used; // used[c] == j: colour c taken by a neighbour of j
     int32_t k = 0;
+    int64_t words = 1; // 64-bit words per variable's bitset, doubled when the colours outgrow it
+    std::vector<uint64_t> cset(static_cast<size_t>(fos->n) * words, 0), forbid;
+    std::vector<int32_t> vmark(fos->n, -1);
     for (int64_t t = 0; t < m; ++t) {
         const int32_t j = order[t];
-        for_each_lmig_neighbour(g, *fos, inv, j, nullptr, [&](int32_t j2) {
-            const int32_t c = color[j2];
-            if (c >= 0) used[c] = j;
-        });
+        forbid.assign(words, 0);
+        auto take = [&](int32_t v) {
+            if (vmark[v] == j) return;
+            vmark[v] = j;
+            const uint64_t *cs = cset.data() + static_cast<size_t>(v) * words;
+            for (int64_t x = 0; x < words; ++x) forbid[x] |= cs[x];
+        };
+        for (int64_t q = fos->eptr[j]; q < fos->eptr[j + 1]; ++q) {
+            const int32_t u = fos->evars[q];
+            take(u);
+            for (int64_t e = g->row_ptr[u]; e < g->row_ptr[u + 1]; ++e) take(g->col[e]);
+        }
         int32_t c = 0;
-        while (c < k && used[c] == j) ++c;
-        if (c == k) {
-            ++k;
-            used.push_back(-1);
+        while (c < k && ((forbid[c >> 6] >> (c & 63)) & 1u)) ++c;
+        if (c == k) ++k;
+        if (k > 64 * words) { // re-stride the bitsets to twice the words
+            std::vector<uint64_t> wider(static_cast<size_t>(fos->n) * 2 * words, 0);
+            for (int64_t v = 0; v < fos->n; ++v)
+                for (int64_t x = 0; x < words; ++x) wider[static_cast<size_t>(v) * 2 * words + x] = cset[v * words + x];
+            cset.swap(wider);
+            words *= 2;
         }
         color[j] = c;
+        for (int64_t q = fos->eptr[j]; q < fos->eptr[j + 1]; ++q)
+            cset[static_cast<size_t>(fos->evars[q]) * words + (c >> 6)] |= uint64_t(1) << (c & 63);
     }
 
     fos->k = k;
